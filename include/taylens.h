@@ -1,0 +1,141 @@
+/*
+ * taylens.h -- C ABI of the GB300 (sm_103a) full-sky Taylor-lensing library.
+ *
+ * Method: Naess & Louis 2013, "Lensing simulations by Taylor expansion -- not so
+ * inefficient after all" (arXiv:1307.0719). The library computes, on one GPU,
+ *   - the unlensed T and Q/U maps and all their mixed theta/phi derivative maps
+ *     d_theta^j d_phi^k s, j + k <= n, on the HEALPix RING grid (Sec. II.B, Eq. 4),
+ *   - the deflection alpha = grad(phi) (Sec. I, Eqs. 1-2; Sec. II.A),
+ *   - the lensed maps by the pixel-relative Taylor expansion around the centre of
+ *     the pixel containing the displaced point x + alpha (Sec. I, the expansion
+ *     after Fig. 1; Sec. II.B, Eq. 4), with the polarisation rotation R of Eq. 2.
+ *
+ * Conventions shared by every call
+ *  - Harmonic coefficients ("alm"): complex128, interleaved (re, im), triangular
+ *    layout idx(l, m) = m (2 lmax + 1 - m) / 2 + l for 0 <= m <= l <= lmax
+ *    (real fields, m >= 0 only). The imaginary part of m = 0 entries is ignored.
+ *    Q +- iU = -sum (E_lm +- i B_lm) +-2Y_lm (HEALPix convention).
+ *  - Maps: HEALPix RING order, Npix = 12 nside^2. Element type is double for
+ *    TL_FP64 plans and float for TL_MIXED_* plans.
+ *  - Every pointer argument named "device" must point to device memory owned by
+ *    the caller, 16-byte aligned; the library never frees it. Calls are enqueued
+ *    on the given stream (a cudaStream_t passed as void*, NULL = legacy default
+ *    stream) and return before the GPU work finishes.
+ *  - Errors: every call returns a tl_status. Argument errors are detected on the
+ *    host before any GPU work is enqueued. TL_ERR_CUDA reports a failed CUDA
+ *    runtime call (launch or allocation); the plan stays valid after argument
+ *    errors but should be destroyed after TL_ERR_CUDA.
+ *  - A plan may be used by one host thread at a time; different plans are
+ *    independent.
+ */
+#ifndef TAYLENS_H
+#define TAYLENS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tl_plan tl_plan; /* opaque; owns its device tables and workspace */
+
+typedef enum {
+  TL_OK = 0,
+  TL_ERR_ARG = 1,         /* invalid argument (NULL, misaligned, out of range) */
+  TL_ERR_NOMEM = 2,       /* device or host allocation failed                  */
+  TL_ERR_CUDA = 3,        /* a CUDA runtime call failed                         */
+  TL_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up                 */
+  TL_ERR_UNSUPPORTED = 5  /* valid request this build does not implement       */
+} tl_status;
+
+/* `spins` bitmask */
+enum { TL_SPIN_T = 1, TL_SPIN_QU = 2 };
+
+/* `precision`: arithmetic of the Legendre stage, ring FFTs and Taylor sums.
+ * TL_FP64        everything in double.
+ * TL_MIXED_FP32  float recurrence and contraction with double seeds and
+ *                exponent rescaling; double pixel geometry; float maps. */
+enum { TL_FP64 = 0, TL_MIXED_FP32 = 1, TL_MIXED_TF32 = 2, TL_MIXED_TF32x3 = 3, TL_MIXED_BF16x3 = 4 };
+
+/* `flags` */
+enum { TL_ROTATE = 1 /* apply the polarisation rotation R of Eq. 2 (default on) */ };
+
+/*
+ * Create a plan for one (nside, lmax, order) geometry.
+ *   nside     power of two, 1 .. 8192
+ *   lmax      1 .. 4 nside (band limit of every field, including phi)
+ *   order     Taylor order n, 0 .. 6 (total degree j + k <= n; 0 = nearest-pixel lookup)
+ *   spins     TL_SPIN_T, TL_SPIN_QU or both
+ *   precision TL_FP64 or TL_MIXED_FP32 (others return TL_ERR_UNSUPPORTED)
+ *   flags     TL_ROTATE or 0
+ *   out       receives the plan; unchanged on error
+ * Allocates the plan's device tables and workspace on the current device.
+ * Errors: TL_ERR_ARG, TL_ERR_UNSUPPORTED, TL_ERR_NOMEM, TL_ERR_CUDA.
+ */
+tl_status tl_plan_create(int nside, int lmax, int order, int spins, int precision, int flags,
+                         tl_plan **out);
+
+/* Free a plan (synchronises the device first). NULL is accepted. */
+tl_status tl_plan_destroy(tl_plan *plan);
+
+/* Device bytes held by the plan (tables + workspace). 0 for NULL. */
+size_t tl_plan_workspace_bytes(const tl_plan *plan);
+
+/* Number of derivative maps per field, (order+1)(order+2)/2. */
+int tl_plan_maps_per_field(const tl_plan *plan);
+
+/*
+ * Derivative maps of one field (Sec. II.B, Eq. 4: the maps d_theta^j d_phi^k s
+ * evaluated at every pixel centre), in natural units.
+ *   alm   device; spin 0: nalm complex (T); spin 2: 2*nalm complex, E then B
+ *   spin  0 or 2 (the plan must include that field)
+ *   maps  device, [K][Npix] with K = maps_per_field (spin 0) or 2*maps_per_field
+ *         (spin 2: all Q maps, then all U maps). Map index of (j, k) inside a
+ *         field is (j+k)(j+k+1)/2 + j.
+ */
+tl_status tl_synth_derivs(tl_plan *plan, const double *alm, int spin, void *maps, void *stream);
+
+/*
+ * Deflection field alpha = grad(phi) at every pixel centre (Sec. I, Eqs. 1-2):
+ * a_theta = d_theta phi, a_phi = d_phi phi / sin(theta), components on the
+ * orthonormal (e_theta, e_phi) basis.
+ *   alm_phi  device, nalm complex;  a_theta, a_phi  device, [Npix] each.
+ */
+tl_status tl_deflection(tl_plan *plan, const double *alm_phi, void *a_theta, void *a_phi,
+                        void *stream);
+
+/*
+ * Lensed maps (Eqs. 1-2 approximated by Eq. 4 around the pixel containing
+ * x + alpha, then the rotation R when the plan has TL_ROTATE).
+ *   alm_T, alm_E, alm_B   device, nalm complex each; alm_B may be NULL (B = 0);
+ *                         alm_E/alm_B ignored and Q_out/U_out untouched for
+ *                         T-only plans; alm_T may be NULL only for QU-only plans
+ *   alm_phi               device, nalm complex (may be NULL: no lensing)
+ *   T_out, Q_out, U_out   device, [Npix] each in RING order
+ */
+tl_status tl_lens(tl_plan *plan, const double *alm_T, const double *alm_E, const double *alm_B,
+                  const double *alm_phi, void *T_out, void *Q_out, void *U_out, void *stream);
+
+/*
+ * tl_lens with HOST buffers: copies the alm from host memory to the plan's
+ * device staging area, runs tl_lens, copies the maps back and synchronises the
+ * stream before returning. Host buffers should be pinned for full speed.
+ * Same layouts as tl_lens; outputs are double (TL_FP64) or float (mixed).
+ */
+tl_status tl_lens_host(tl_plan *plan, const double *alm_T, const double *alm_E,
+                       const double *alm_B, const double *alm_phi, void *T_out, void *Q_out,
+                       void *U_out, void *stream);
+
+/* Human-readable text for a status code (static storage). */
+const char *tl_status_string(tl_status status);
+
+/* Milliseconds of the stages of the most recent tl_lens on this plan, measured
+ * with CUDA events when the plan was created with TL_TIMING in the environment
+ * variable TAYLENS_TIMING=1; stage order: prep, deflection, legendre_T,
+ * legendre_QU, ringfft, gather. Returns the number of stages written (<= n). */
+int tl_last_stage_ms(const tl_plan *plan, float *ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TAYLENS_H */

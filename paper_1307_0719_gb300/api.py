@@ -1,0 +1,151 @@
+"""Python face of the C ABI (include/taylens.h). Argument marshalling only: every
+step of the lensing path runs in libtaylens.so on the GPU."""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import check
+
+FP64 = _lib.TL_FP64
+MIXED_FP32 = _lib.TL_MIXED_FP32
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _alm(t, name):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype == torch.complex128:
+        t = torch.view_as_real(t)
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous complex128 (or float64 [..., 2])")
+    return t
+
+
+class Plan:
+    """A (nside, lmax, order) geometry with its device tables and workspace."""
+
+    def __init__(self, nside: int, lmax: int, order: int, pol: bool = True,
+                 precision: int = FP64, rotate: bool = True):
+        L = _lib.lib()
+        self.nside, self.lmax, self.order, self.pol, self.precision = nside, lmax, order, pol, precision
+        self.npix = 12 * nside * nside
+        self.nalm = (lmax + 1) * (lmax + 2) // 2
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        spins = _lib.TL_SPIN_T | (_lib.TL_SPIN_QU if pol else 0)
+        flags = _lib.TL_ROTATE if rotate else 0
+        h = ctypes.c_void_p()
+        check(L.tl_plan_create(nside, lmax, order, spins, precision, flags, ctypes.byref(h)),
+              "tl_plan_create")
+        self._h = h
+        self.nmaps = L.tl_plan_maps_per_field(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().tl_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def workspace_bytes(self) -> int:
+        return _lib.lib().tl_plan_workspace_bytes(self._h)
+
+    def synth_derivs(self, alm, spin: int = 0, out=None, stream=None):
+        """[K, Npix] maps d_theta^j d_phi^k of the field (spin 0: T; spin 2: alm = [E, B]
+        stacked, output Q maps then U maps)."""
+        a = _alm(alm, "alm")
+        K = self.nmaps * (2 if spin == 2 else 1)
+        if out is None:
+            out = torch.empty((K, self.npix), dtype=self.dtype, device=a.device)
+        check(_lib.lib().tl_synth_derivs(self._h, _ptr(a), spin, _ptr(out), _stream(stream)),
+              "tl_synth_derivs")
+        return out
+
+    def deflection(self, alm_phi, stream=None):
+        a = _alm(alm_phi, "alm_phi")
+        out = torch.empty((2, self.npix), dtype=self.dtype, device=a.device)
+        check(_lib.lib().tl_deflection(self._h, _ptr(a), _ptr(out[0]), _ptr(out[1]), _stream(stream)),
+              "tl_deflection")
+        return out
+
+    def lens(self, alm_T, alm_E=None, alm_B=None, alm_phi=None, out=None, stream=None):
+        """Lensed (T, Q, U) maps (Q, U None for T-only plans)."""
+        aT, aE, aB, aP = (_alm(alm_T, "alm_T"), _alm(alm_E, "alm_E"), _alm(alm_B, "alm_B"),
+                          _alm(alm_phi, "alm_phi"))
+        nf = 3 if self.pol else 1
+        if out is None:
+            out = torch.empty((nf, self.npix), dtype=self.dtype, device=aT.device)
+        Q = out[1] if self.pol else None
+        U = out[2] if self.pol else None
+        check(_lib.lib().tl_lens(self._h, _ptr(aT), _ptr(aE), _ptr(aB), _ptr(aP), _ptr(out[0]),
+                                 _ptr(Q), _ptr(U), _stream(stream)), "tl_lens")
+        return out
+
+    def lens_host(self, alm_T, alm_E=None, alm_B=None, alm_phi=None, out=None, stream=None):
+        """tl_lens_host: alm in (pinned) host memory, maps returned in host memory."""
+        def h(t):
+            if t is None:
+                return None
+            if t.dtype == torch.complex128:
+                t = torch.view_as_real(t)
+            assert not t.is_cuda and t.is_contiguous()
+            return t
+        nf = 3 if self.pol else 1
+        if out is None:
+            out = torch.empty((nf, self.npix), dtype=self.dtype, pin_memory=True)
+        Q = out[1] if self.pol else None
+        U = out[2] if self.pol else None
+        check(_lib.lib().tl_lens_host(self._h, _ptr(h(alm_T)), _ptr(h(alm_E)), _ptr(h(alm_B)),
+                                      _ptr(h(alm_phi)), _ptr(out[0]), _ptr(Q), _ptr(U),
+                                      _stream(stream)), "tl_lens_host")
+        return out
+
+    def last_stage_ms(self):
+        buf = (ctypes.c_float * 8)()
+        n = _lib.lib().tl_last_stage_ms(self._h, buf, 8)
+        return list(buf[:n])
+
+
+def lens(nside, lmax, order, alm_T, alm_E=None, alm_B=None, alm_phi=None, precision=FP64,
+         rotate=True):
+    p = Plan(nside, lmax, order, pol=alm_E is not None, precision=precision, rotate=rotate)
+    try:
+        return p.lens(alm_T, alm_E, alm_B, alm_phi)
+    finally:
+        torch.cuda.synchronize()
+        p.close()
+
+
+def synth_derivs(nside, lmax, order, alm, spin=0, precision=FP64):
+    p = Plan(nside, lmax, order, pol=(spin == 2), precision=precision)
+    try:
+        return p.synth_derivs(alm, spin)
+    finally:
+        torch.cuda.synchronize()
+        p.close()
+
+
+def deflection(nside, lmax, alm_phi, precision=FP64):
+    p = Plan(nside, lmax, 1, pol=False, precision=precision)
+    try:
+        return p.deflection(alm_phi)
+    finally:
+        torch.cuda.synchronize()
+        p.close()

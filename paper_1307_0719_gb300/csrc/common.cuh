@@ -1,0 +1,107 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/taylens.h"
+
+#define TL_MAX_ORDER 6
+#define TL_MAX_NDER 6  // highest theta-derivative order a Legendre kernel carries
+
+namespace tl {
+
+// ---------------------------------------------------------------------------
+// HEALPix RING geometry (Gorski et al. 2005), one entry per ring r = 0 .. 4N-2
+// (ring number r+1 counted from the north pole).
+struct RingTable {
+  double *z;       // cos(theta)
+  double *sint;    // sin(theta)
+  double *theta;   // colatitude
+  double *phi0;    // longitude of the ring's first pixel
+  double *log2_sh; // log2 sin(theta/2)
+  double *log2_ch; // log2 cos(theta/2)
+  double *dls;     // [ring][k], k = 1..TL_MAX_NDER+1: d^k/dtheta^k ln sin(theta/2)
+  double *dlc;     // [ring][k]: d^k/dtheta^k ln cos(theta/2)
+  int *nphi;       // pixels in the ring (4 i in the caps, 4 N in the belt)
+  int *inorth;     // ring number counted from the nearer pole
+  long long *first;// index of the ring's first pixel
+};
+
+// Bluestein chirp spectra for the non-power-of-two sub-transform lengths.
+struct BluesteinTable {
+  void *spec;          // concatenated spectra (T2 of the plan's precision)
+  long long *offset;   // [nside]: offset of length i's spectrum, -1 if i is a power of two
+  int *mlen;           // [nside]: its FFT length M (power of two >= 2i-1)
+};
+
+struct StageTimer;
+
+}  // namespace tl
+
+struct tl_plan {
+  int nside, lmax, mmax, order, spins, precision, flags;
+  int nrings;
+  long long npix;
+  int nmaps;      // maps per field
+  int device;
+  int elem;       // bytes per map element (8 or 4)
+  tl::RingTable ring;
+  tl::BluesteinTable blue;
+  double *lnorm0;       // [lmax+1] log2 of sqrt((2m+1)/4pi) sqrt(C(2m,m)) (device)
+  void *twiddle;        // [TW/2] e^{-2 pi i k / TW} in T2 (device)
+  int tw_len;
+  int blue_maxm;        // largest Bluestein FFT length (0 if none)
+  // workspace
+  void *rec_T, *rec_P, *rec_QU; // coefficient records
+  void *d7_T, *d7_Q, *d7_U, *d7_P; // per-ring Fourier coefficients [j][ring][m] (T2)
+  void *d3;            // derivative maps [3*nmaps][npix] (T), Taylor-ready
+  void *alpha;         // [2][npix] (T)
+  void *stage_alm;     // host-path staging: 4 * nalm complex128
+  void *stage_out;     // host-path staging: 3 * npix (T)
+  size_t bytes;
+  // optional stage timing
+  int timing;
+  cudaEvent_t ev[8];
+  float stage_ms[7];
+  int nstage;
+};
+
+namespace tl {
+
+inline long long nalm(int lmax) { return (long long)(lmax + 1) * (lmax + 2) / 2; }
+inline int maps_per_field(int order) { return (order + 1) * (order + 2) / 2; }
+
+// kernel launchers (defined in the .cu files)
+cudaError_t launch_prep_spin0(const tl_plan *p, const double *alm, void *rec, cudaStream_t s);
+cudaError_t launch_prep_spin2(const tl_plan *p, const double *alm_E, const double *alm_B, void *rec,
+                              cudaStream_t s);
+cudaError_t launch_legendre_spin0(const tl_plan *p, int nder, const void *rec, void *d7,
+                                  cudaStream_t s);
+cudaError_t launch_legendre_spin2(const tl_plan *p, int nder, const void *rec, void *d7q, void *d7u,
+                                  cudaStream_t s);
+
+// One output map of the ring FFT stage.
+struct MapJob {
+  int plane;       // which D7 plane set: 0 = T, 1 = Q, 2 = U, 3 = phi
+  int j, k;        // derivative orders
+  int div_sint;    // divide by sin(theta) of the ring
+  double scale;    // multiplies d_theta^j d_phi^k (after undoing the 1/L^j, L^k normalisation)
+  void *out;       // [npix] map
+};
+cudaError_t launch_ringfft(const tl_plan *p, const MapJob *jobs, int njobs, int nder_planes,
+                           cudaStream_t s);
+cudaError_t launch_bluestein_setup(tl_plan *p, cudaStream_t s);
+cudaError_t launch_gather(const tl_plan *p, const void *alpha, const void *d3, void *T, void *Q,
+                          void *U, cudaStream_t s);
+
+// normalisation of theta derivatives inside the Legendre stage: lambda^(j) / L^j
+inline double deriv_norm(const tl_plan *p) { return (double)(p->lmax + 1); }
+
+}  // namespace tl
+
+#define TL_CUDA_TRY(call)                         \
+  do {                                            \
+    cudaError_t _e = (call);                      \
+    if (_e != cudaSuccess) return _e;             \
+  } while (0)

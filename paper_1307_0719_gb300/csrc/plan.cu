@@ -1,0 +1,455 @@
+// Plan creation, workspace and the C ABI (taylens.h).
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "legendre.cuh"
+
+namespace tl {
+size_t ringfft_smem_bytes(const tl_plan *p);
+cudaError_t launch_bluestein_setup_impl(tl_plan *p, const double2 *tw64, cudaStream_t s);
+}  // namespace tl
+
+using namespace tl;
+
+static const double kPi = 3.14159265358979323846;
+
+static tl_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TL_OK;
+  if (e == cudaErrorMemoryAllocation) return TL_ERR_NOMEM;
+  return TL_ERR_CUDA;
+}
+
+#define TRY_CUDA(call)                          \
+  do {                                          \
+    cudaError_t _e = (call);                    \
+    if (_e != cudaSuccess) return from_cuda(_e); \
+  } while (0)
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+extern "C" const char *tl_status_string(tl_status s) {
+  switch (s) {
+    case TL_OK: return "ok";
+    case TL_ERR_ARG: return "invalid argument";
+    case TL_ERR_NOMEM: return "out of memory";
+    case TL_ERR_CUDA: return "CUDA runtime error";
+    case TL_ERR_TIMEOUT: return "device wait timed out";
+    case TL_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+// ---------------------------------------------------------------------------
+// host tables
+
+// Polynomial in one variable, coefficients in increasing degree.
+typedef std::vector<double> Poly;
+static Poly poly_deriv(const Poly &p) {
+  Poly d(p.size() > 1 ? p.size() - 1 : 1, 0.0);
+  for (size_t i = 1; i < p.size(); ++i) d[i - 1] = p[i] * (double)i;
+  return d;
+}
+static Poly poly_mul(const Poly &a, const Poly &b) {
+  Poly r(a.size() + b.size() - 1, 0.0);
+  for (size_t i = 0; i < a.size(); ++i)
+    for (size_t j = 0; j < b.size(); ++j) r[i + j] += a[i] * b[j];
+  return r;
+}
+static double poly_eval(const Poly &p, double x) {
+  double r = 0.0;
+  for (size_t i = p.size(); i-- > 0;) r = r * x + p[i];
+  return r;
+}
+
+struct HostRings {
+  std::vector<double> z, sint, theta, phi0, lsh, lch, dls, dlc;
+  std::vector<int> nphi, inorth;
+  std::vector<long long> first;
+};
+
+// HEALPix RING rings (Gorski et al. 2005) plus what the Legendre seeds need:
+// log2 sin(th/2), log2 cos(th/2) and d^k/dth^k of ln sin(th/2), ln cos(th/2).
+// With w = cot(th/2): d/dth ln sin(th/2) = w/2 and dw/dth = -(1+w^2)/2; with
+// v = tan(th/2): d/dth ln cos(th/2) = -v/2 and dv/dth = (1+v^2)/2.
+static void build_rings(int N, HostRings &h) {
+  const int nr = 4 * N - 1;
+  const long long npix = 12LL * N * N, ncap = 2LL * N * (N - 1);
+  const int K = TL_MAX_NDER + 1;
+  std::vector<Poly> ps(K + 1), pc(K + 1);
+  ps[1] = Poly{0.0, 0.5};
+  pc[1] = Poly{0.0, -0.5};
+  for (int k = 1; k < K; ++k) {
+    ps[k + 1] = poly_mul(poly_deriv(ps[k]), Poly{-0.5, 0.0, -0.5});
+    pc[k + 1] = poly_mul(poly_deriv(pc[k]), Poly{0.5, 0.0, 0.5});
+  }
+  h.z.resize(nr); h.sint.resize(nr); h.theta.resize(nr); h.phi0.resize(nr);
+  h.lsh.resize(nr); h.lch.resize(nr); h.dls.resize((size_t)nr * K); h.dlc.resize((size_t)nr * K);
+  h.nphi.resize(nr); h.inorth.resize(nr); h.first.resize(nr);
+  for (int r = 0; r < nr; ++r) {
+    const int i = r + 1;
+    const int in = i < 4 * N - i ? i : 4 * N - i;
+    double omz_m, omz_p;  // 1 - z and 1 + z, each without cancellation
+    double z;
+    if (in < N) {
+      const double omz = (double)in * in / (3.0 * N * N);
+      if (i < 2 * N) { z = 1.0 - omz; omz_m = omz; omz_p = 2.0 - omz; }
+      else { z = -(1.0 - omz); omz_m = 2.0 - omz; omz_p = omz; }
+      h.nphi[r] = 4 * in;
+      h.phi0[r] = kPi / (4.0 * in);
+    } else {
+      z = 4.0 / 3.0 - 2.0 * i / (3.0 * N);
+      omz_m = 1.0 - z;
+      omz_p = 1.0 + z;
+      h.nphi[r] = 4 * N;
+      h.phi0[r] = ((i - N) % 2 == 0) ? kPi / (4.0 * N) : 0.0;
+    }
+    h.inorth[r] = in;
+    h.z[r] = z;
+    h.sint[r] = sqrt(omz_m * omz_p);
+    h.theta[r] = (z >= 0.0) ? 2.0 * asin(sqrt(0.5 * omz_m)) : kPi - 2.0 * asin(sqrt(0.5 * omz_p));
+    h.lsh[r] = 0.5 * log2(0.5 * omz_m);
+    h.lch[r] = 0.5 * log2(0.5 * omz_p);
+    const double w = sqrt(omz_p / omz_m), v = sqrt(omz_m / omz_p);
+    for (int k = 1; k <= K; ++k) {
+      h.dls[(size_t)r * K + (k - 1)] = poly_eval(ps[k], w);
+      h.dlc[(size_t)r * K + (k - 1)] = poly_eval(pc[k], v);
+    }
+    if (i < N) h.first[r] = 2LL * i * (i - 1);
+    else if (i <= 3 * N) h.first[r] = ncap + (long long)(i - N) * 4 * N;
+    else { const long long is = 4LL * N - i; h.first[r] = npix - 2 * is * (is + 1); }
+  }
+}
+
+template <typename V>
+static cudaError_t upload(V **dptr, const std::vector<V> &h, size_t *bytes) {
+  size_t b = sizeof(V) * (h.empty() ? 1 : h.size());
+  cudaError_t e = cudaMalloc((void **)dptr, b);
+  if (e != cudaSuccess) return e;
+  *bytes += b;
+  if (!h.empty()) return cudaMemcpy(*dptr, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice);
+  return cudaSuccess;
+}
+
+static cudaError_t dalloc(void **p, size_t b, size_t *bytes) {
+  cudaError_t e = cudaMalloc(p, b ? b : 16);
+  if (e == cudaSuccess) *bytes += b;
+  return e;
+}
+
+static void free_plan(tl_plan *p) {
+  if (!p) return;
+  void *ptrs[] = {p->ring.z, p->ring.sint, p->ring.theta, p->ring.phi0, p->ring.log2_sh, p->ring.log2_ch,
+                  p->ring.dls, p->ring.dlc, p->ring.nphi, p->ring.inorth, p->ring.first, p->blue.spec,
+                  p->blue.offset, p->blue.mlen, p->lnorm0, p->twiddle, p->rec_T, p->rec_P, p->rec_QU,
+                  p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->stage_alm, p->stage_out};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  if (p->timing)
+    for (int i = 0; i < 8; ++i)
+      if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  free(p);
+}
+
+static tl_status create_impl(int nside, int lmax, int order, int spins, int precision, int flags, tl_plan *p) {
+  p->nside = nside; p->lmax = lmax; p->mmax = lmax; p->order = order; p->spins = spins;
+  p->precision = precision; p->flags = flags;
+  p->nrings = 4 * nside - 1;
+  p->npix = 12LL * nside * nside;
+  p->nmaps = maps_per_field(order);
+  p->elem = (precision == TL_FP64) ? 8 : 4;
+  TRY_CUDA(cudaGetDevice(&p->device));
+  size_t *B = &p->bytes;
+
+  HostRings h;
+  build_rings(nside, h);
+  TRY_CUDA(upload(&p->ring.z, h.z, B)); TRY_CUDA(upload(&p->ring.sint, h.sint, B));
+  TRY_CUDA(upload(&p->ring.theta, h.theta, B)); TRY_CUDA(upload(&p->ring.phi0, h.phi0, B));
+  TRY_CUDA(upload(&p->ring.log2_sh, h.lsh, B)); TRY_CUDA(upload(&p->ring.log2_ch, h.lch, B));
+  TRY_CUDA(upload(&p->ring.dls, h.dls, B)); TRY_CUDA(upload(&p->ring.dlc, h.dlc, B));
+  TRY_CUDA(upload(&p->ring.nphi, h.nphi, B)); TRY_CUDA(upload(&p->ring.inorth, h.inorth, B));
+  TRY_CUDA(upload(&p->ring.first, h.first, B));
+
+  // log2 of sqrt((2m+1)/(4 pi)) sqrt(C(2m, m)) = log2 sqrt((2m+1)/4pi) + m + 1/2 sum_k log2((2k-1)/(2k))
+  std::vector<double> ln0(lmax + 1);
+  double acc = 0.0;
+  for (int m = 0; m <= lmax; ++m) {
+    if (m > 0) acc += log1p(-1.0 / (2.0 * m)) / log(2.0);
+    ln0[m] = 0.5 * log2((2.0 * m + 1.0) / (4.0 * kPi)) + m + 0.5 * acc;
+  }
+  TRY_CUDA(upload(&p->lnorm0, ln0, B));
+
+  // Bluestein lengths: cap rings use sub-transforms of length i = 1 .. nside-1
+  std::vector<long long> off(nside + 1, -1);
+  std::vector<int> ml(nside + 1, 0);
+  long long tot = 0;
+  int maxm = 0;
+  for (int i = 1; i < nside; ++i) {
+    if ((i & (i - 1)) == 0) continue;
+    int M = 1;
+    while (M < 2 * i - 1) M <<= 1;
+    off[i] = tot;
+    ml[i] = M;
+    tot += M;
+    if (M > maxm) maxm = M;
+  }
+  p->blue_maxm = maxm;
+  TRY_CUDA(upload(&p->blue.offset, off, B));
+  TRY_CUDA(upload(&p->blue.mlen, ml, B));
+  const size_t e2 = 2 * (size_t)p->elem;
+  TRY_CUDA(dalloc(&p->blue.spec, e2 * (size_t)(tot > 0 ? tot : 1), B));
+
+  // twiddles e^{-2 pi i k / TW}, k < TW/2, for every power-of-two length used
+  int TW = 2;
+  while (TW < maxm || TW < nside) TW <<= 1;
+  p->tw_len = TW;
+  std::vector<double> tw64(TW);  // interleaved (re, im)
+  for (int k = 0; k < TW / 2; ++k) {
+    double a = 2.0 * kPi * (double)k / (double)TW;
+    tw64[2 * k] = cos(a);
+    tw64[2 * k + 1] = -sin(a);
+  }
+  double *dtw64 = nullptr;
+  {
+    size_t dummy = 0;
+    TRY_CUDA(upload(&dtw64, tw64, &dummy));
+  }
+  if (precision == TL_FP64) {
+    TRY_CUDA(dalloc(&p->twiddle, sizeof(double) * TW, B));
+    TRY_CUDA(cudaMemcpy(p->twiddle, dtw64, sizeof(double) * TW, cudaMemcpyDeviceToDevice));
+  } else {
+    std::vector<float> tw32(TW);
+    for (int k = 0; k < TW; ++k) tw32[k] = (float)tw64[k];
+    TRY_CUDA(upload((float **)&p->twiddle, tw32, B));
+  }
+  cudaError_t e = launch_bluestein_setup_impl(p, (const double2 *)dtw64, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(dtw64);
+  TRY_CUDA(e);
+
+  // workspace
+  const long long na = nalm(lmax);
+  const size_t t2 = e2, rec0 = 4 * (size_t)p->elem, rec2 = 8 * (size_t)p->elem;
+  const size_t plane = (size_t)p->nrings * (p->mmax + 1) * t2;
+  const bool pol = (spins & TL_SPIN_QU) != 0;
+  TRY_CUDA(dalloc(&p->rec_T, rec0 * na, B));
+  TRY_CUDA(dalloc(&p->rec_P, rec0 * na, B));
+  TRY_CUDA(dalloc(&p->d7_T, plane * (order + 1), B));
+  TRY_CUDA(dalloc(&p->d7_P, plane * 2, B));
+  if (pol) {
+    TRY_CUDA(dalloc(&p->rec_QU, rec2 * na, B));
+    TRY_CUDA(dalloc(&p->d7_Q, plane * (order + 1), B));
+    TRY_CUDA(dalloc(&p->d7_U, plane * (order + 1), B));
+  }
+  const int nfield = pol ? 3 : 1;
+  TRY_CUDA(dalloc(&p->d3, (size_t)p->elem * nfield * p->nmaps * p->npix, B));
+  TRY_CUDA(dalloc(&p->alpha, (size_t)p->elem * 2 * p->npix, B));
+
+  const char *env = getenv("TAYLENS_TIMING");
+  p->timing = (env && env[0] == '1') ? 1 : 0;
+  if (p->timing)
+    for (int i = 0; i < 8; ++i) TRY_CUDA(cudaEventCreate(&p->ev[i]));
+  return TL_OK;
+}
+
+extern "C" tl_status tl_plan_create(int nside, int lmax, int order, int spins, int precision, int flags,
+                                    tl_plan **out) {
+  if (!out) return TL_ERR_ARG;
+  if (nside < 1 || nside > 8192 || (nside & (nside - 1)) != 0) return TL_ERR_ARG;
+  if (lmax < 1 || lmax > 4 * nside) return TL_ERR_ARG;
+  if (order < 0 || order > TL_MAX_ORDER) return TL_ERR_ARG;
+  if (spins != TL_SPIN_T && spins != (TL_SPIN_T | TL_SPIN_QU)) {
+    return (spins == TL_SPIN_QU) ? TL_ERR_UNSUPPORTED : TL_ERR_ARG;
+  }
+  if (precision < TL_FP64 || precision > TL_MIXED_BF16x3) return TL_ERR_ARG;
+  if (precision != TL_FP64 && precision != TL_MIXED_FP32) return TL_ERR_UNSUPPORTED;
+  if (flags & ~TL_ROTATE) return TL_ERR_ARG;
+  // the ring FFT keeps a whole ring in shared memory
+  {
+    tl_plan probe;
+    memset(&probe, 0, sizeof(probe));
+    probe.nside = nside;
+    probe.precision = precision;
+    int maxm = 0;
+    for (int i = 1; i < nside; ++i) {
+      if ((i & (i - 1)) == 0) continue;
+      int M = 1;
+      while (M < 2 * i - 1) M <<= 1;
+      if (M > maxm) maxm = M;
+    }
+    probe.blue_maxm = maxm;
+    if (ringfft_smem_bytes(&probe) > 227 * 1024) return TL_ERR_UNSUPPORTED;
+  }
+  tl_plan *p = (tl_plan *)calloc(1, sizeof(tl_plan));
+  if (!p) return TL_ERR_NOMEM;
+  tl_status st = create_impl(nside, lmax, order, spins, precision, flags, p);
+  if (st != TL_OK) {
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return st;
+  }
+  *out = p;
+  return TL_OK;
+}
+
+extern "C" tl_status tl_plan_destroy(tl_plan *p) {
+  if (!p) return TL_OK;
+  cudaDeviceSynchronize();
+  free_plan(p);
+  return TL_OK;
+}
+
+extern "C" size_t tl_plan_workspace_bytes(const tl_plan *p) { return p ? p->bytes : 0; }
+
+extern "C" int tl_plan_maps_per_field(const tl_plan *p) { return p ? p->nmaps : 0; }
+
+// ---------------------------------------------------------------------------
+// stages
+
+static void mark(tl_plan *p, int i, cudaStream_t s) {
+  if (p->timing && i < 8) cudaEventRecord(p->ev[i], s);
+}
+
+static tl_status deflection_impl(tl_plan *p, const double *alm_phi, void *ath, void *aph, cudaStream_t s) {
+  TRY_CUDA(launch_prep_spin0(p, alm_phi, p->rec_P, s));
+  TRY_CUDA(launch_legendre_spin0(p, 1, p->rec_P, p->d7_P, s));
+  const double L = deriv_norm(p);
+  MapJob jobs[2] = {{3, 1, 0, 0, L, ath}, {3, 0, 1, 1, L, aph}};
+  TRY_CUDA(launch_ringfft(p, jobs, 2, 2, s));
+  return TL_OK;
+}
+
+extern "C" tl_status tl_deflection(tl_plan *p, const double *alm_phi, void *ath, void *aph, void *stream) {
+  if (!p || !alm_phi || !ath || !aph) return TL_ERR_ARG;
+  if (!aligned16(alm_phi) || !aligned16(ath) || !aligned16(aph)) return TL_ERR_ARG;
+  return deflection_impl(p, alm_phi, ath, aph, (cudaStream_t)stream);
+}
+
+static double fact(int n) {
+  double r = 1.0;
+  for (int i = 2; i <= n; ++i) r *= i;
+  return r;
+}
+
+extern "C" tl_status tl_synth_derivs(tl_plan *p, const double *alm, int spin, void *maps, void *stream) {
+  if (!p || !alm || !maps) return TL_ERR_ARG;
+  if (!aligned16(alm) || !aligned16(maps)) return TL_ERR_ARG;
+  if (spin != 0 && spin != 2) return TL_ERR_ARG;
+  if (spin == 2 && !(p->spins & TL_SPIN_QU)) return TL_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double L = deriv_norm(p);
+  const long long na = nalm(p->lmax);
+  std::vector<MapJob> jobs;
+  char *base = (char *)maps;
+  const size_t mapb = (size_t)p->elem * p->npix;
+  if (spin == 0) {
+    TRY_CUDA(launch_prep_spin0(p, alm, p->rec_T, s));
+    TRY_CUDA(launch_legendre_spin0(p, p->order, p->rec_T, p->d7_T, s));
+    for (int n = 0; n <= p->order; ++n)
+      for (int j = 0; j <= n; ++j) {
+        int k = n - j;
+        jobs.push_back(MapJob{0, j, k, 0, pow(L, n), base + mapb * (n * (n + 1) / 2 + j)});
+      }
+  } else {
+    TRY_CUDA(launch_prep_spin2(p, alm, alm + 2 * na, p->rec_QU, s));
+    TRY_CUDA(launch_legendre_spin2(p, p->order, p->rec_QU, p->d7_Q, p->d7_U, s));
+    for (int f = 0; f < 2; ++f)
+      for (int n = 0; n <= p->order; ++n)
+        for (int j = 0; j <= n; ++j) {
+          int k = n - j;
+          jobs.push_back(MapJob{1 + f, j, k, 0, pow(L, n),
+                                base + mapb * (f * p->nmaps + n * (n + 1) / 2 + j)});
+        }
+  }
+  TRY_CUDA(launch_ringfft(p, jobs.data(), (int)jobs.size(), p->order + 1, s));
+  return TL_OK;
+}
+
+extern "C" tl_status tl_lens(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,
+                             const double *alm_phi, void *T_out, void *Q_out, void *U_out, void *stream) {
+  if (!p || !alm_T || !T_out) return TL_ERR_ARG;
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  if (pol && (!alm_E || !Q_out || !U_out)) return TL_ERR_ARG;
+  const void *ptrs[] = {alm_T, alm_E, alm_B, alm_phi, T_out, Q_out, U_out};
+  for (const void *q : ptrs)
+    if (q && !aligned16(q)) return TL_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t mapb = (size_t)p->elem * p->npix;
+  p->nstage = 0;
+  mark(p, 0, s);
+  // 1. deflection
+  if (alm_phi) {
+    tl_status st = deflection_impl(p, alm_phi, p->alpha, (char *)p->alpha + mapb, s);
+    if (st != TL_OK) return st;
+  } else {
+    TRY_CUDA(cudaMemsetAsync(p->alpha, 0, 2 * mapb, s));
+  }
+  mark(p, 1, s);
+  // 2. Legendre stage of the unlensed fields
+  TRY_CUDA(launch_prep_spin0(p, alm_T, p->rec_T, s));
+  TRY_CUDA(launch_legendre_spin0(p, p->order, p->rec_T, p->d7_T, s));
+  mark(p, 2, s);
+  if (pol) {
+    TRY_CUDA(launch_prep_spin2(p, alm_E, alm_B, p->rec_QU, s));
+    TRY_CUDA(launch_legendre_spin2(p, p->order, p->rec_QU, p->d7_Q, p->d7_U, s));
+  }
+  mark(p, 3, s);
+  // 3. ring FFTs into Taylor-ready maps: d_th^j d_ph^k s / (j! k! L^(j+k))
+  std::vector<MapJob> jobs;
+  const int nf = pol ? 3 : 1;
+  for (int f = 0; f < nf; ++f)
+    for (int n = 0; n <= p->order; ++n)
+      for (int j = 0; j <= n; ++j) {
+        int k = n - j;
+        jobs.push_back(MapJob{f, j, k, 0, 1.0 / (fact(j) * fact(k)),
+                              (char *)p->d3 + mapb * (f * p->nmaps + n * (n + 1) / 2 + j)});
+      }
+  TRY_CUDA(launch_ringfft(p, jobs.data(), (int)jobs.size(), p->order + 1, s));
+  mark(p, 4, s);
+  // 4. gather + Taylor + rotate
+  TRY_CUDA(launch_gather(p, p->alpha, p->d3, T_out, pol ? Q_out : nullptr, pol ? U_out : nullptr, s));
+  mark(p, 5, s);
+  p->nstage = p->timing ? 5 : 0;
+  return TL_OK;
+}
+
+extern "C" tl_status tl_lens_host(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,
+                                  const double *alm_phi, void *T_out, void *Q_out, void *U_out, void *stream) {
+  if (!p || !alm_T || !T_out) return TL_ERR_ARG;
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  if (pol && (!alm_E || !Q_out || !U_out)) return TL_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long na = nalm(p->lmax);
+  const size_t ab = (size_t)na * 16, mapb = (size_t)p->elem * p->npix;
+  if (!p->stage_alm) TRY_CUDA(dalloc(&p->stage_alm, 4 * ab, &p->bytes));
+  if (!p->stage_out) TRY_CUDA(dalloc(&p->stage_out, 3 * mapb, &p->bytes));
+  char *a = (char *)p->stage_alm;
+  double *dT = (double *)a, *dE = (double *)(a + ab), *dB = (double *)(a + 2 * ab), *dP = (double *)(a + 3 * ab);
+  TRY_CUDA(cudaMemcpyAsync(dT, alm_T, ab, cudaMemcpyHostToDevice, s));
+  if (pol) TRY_CUDA(cudaMemcpyAsync(dE, alm_E, ab, cudaMemcpyHostToDevice, s));
+  if (pol && alm_B) TRY_CUDA(cudaMemcpyAsync(dB, alm_B, ab, cudaMemcpyHostToDevice, s));
+  if (alm_phi) TRY_CUDA(cudaMemcpyAsync(dP, alm_phi, ab, cudaMemcpyHostToDevice, s));
+  char *o = (char *)p->stage_out;
+  tl_status st = tl_lens(p, dT, pol ? dE : nullptr, (pol && alm_B) ? dB : nullptr, alm_phi ? dP : nullptr, o,
+                         pol ? o + mapb : nullptr, pol ? o + 2 * mapb : nullptr, stream);
+  if (st != TL_OK) return st;
+  TRY_CUDA(cudaMemcpyAsync(T_out, o, mapb, cudaMemcpyDeviceToHost, s));
+  if (pol) {
+    TRY_CUDA(cudaMemcpyAsync(Q_out, o + mapb, mapb, cudaMemcpyDeviceToHost, s));
+    TRY_CUDA(cudaMemcpyAsync(U_out, o + 2 * mapb, mapb, cudaMemcpyDeviceToHost, s));
+  }
+  TRY_CUDA(cudaStreamSynchronize(s));
+  return TL_OK;
+}
+
+extern "C" int tl_last_stage_ms(const tl_plan *p, float *ms, int n) {
+  if (!p || !ms || !p->timing || p->nstage == 0) return 0;
+  tl_plan *q = (tl_plan *)p;
+  if (cudaEventSynchronize(q->ev[p->nstage]) != cudaSuccess) return 0;
+  int k = 0;
+  for (int i = 0; i < p->nstage && k < n; ++i, ++k) cudaEventElapsedTime(&ms[k], q->ev[i], q->ev[i + 1]);
+  return k;
+}
