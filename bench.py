@@ -1,0 +1,363 @@
+"""Benchmark: lensed T/Q/U map sets per second at Nside 2048, lmax 4096, order 4.
+
+One step = one full lensing pass through the C ABI (deflection synthesis, Legendre
+stage of T and Q/U with all derivative orders, ring FFTs into the derivative maps,
+gather + Taylor sum + rotation) for one synthetic sky whose coefficients are
+already resident in HBM. The headline is the mixed-precision form
+(TL_MIXED_FP32); the plain FP64 GPU form is timed on the same GPU beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank lenses its own independent
+realisations (weak scaling, no data-path collective); the time is the max over
+ranks. --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import skygen  # noqa: E402
+
+WORKLOAD = "nside2048_lmax4096_n4_TQU"
+METRIC = "lensed TQU maps/sec @Nside2048 lmax4096 order4 (mixed vs FP64 GPU, err vs oracle)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
+FP32_LANES = 152 * 128
+
+
+def legendre_flops_per_launch(nside: int, lmax: int, order: int, spin: int, phi: bool = True) -> float:
+    """Algorithmic flops of one Legendre-stage launch, per (ring pair, l, m) triple:
+    the derivative recurrence costs sum_{j<=n} (2j + 3) flops per ring (one multiply,
+    j Leibniz multiply-adds and the closing multiply-add of each order), the
+    contraction 2 flops per real coefficient and order: spin 0 has re/im (and the
+    potential's re/im for j <= 1 when it shares the launch), spin 2 has the four
+    reals of S1 and S2 plus one add for cos(theta) + m s/(l(l+1)). Spin 0 runs
+    its recurrence once per ring pair (north/south parity), spin 2 on both rings."""
+    n = order
+    rec = sum(2 * j + 3 for j in range(n + 1))
+    if spin == 0:
+        per = rec + 4 * (n + 1) + (8 if phi else 0)
+    else:
+        per = 2 * (rec + 1 + 8 * (n + 1))
+    pairs = 2 * nside  # north rings incl. the equator
+    lm = (lmax + 1) * (lmax + 2) // 2
+    return float(per) * pairs * lm
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard(n_units: int, rank: int, world: int):
+    """Independent realisations owned by a rank (contiguous split)."""
+    base, extra = divmod(n_units, world)
+    start = rank * base + min(rank, extra)
+    return list(range(start, start + base + (1 if rank < extra else 0)))
+
+
+def oracle_sample(w, sky, npix_sample: int, seed: int = 0, nthreads=None):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: the pixel-relative
+    Taylor lensing of `npix_sample` output pixels (each needs the deflection at its
+    own ring and the derivative coefficients at its expansion pixel's ring, i.e.
+    two of the map's 2 x (4 Nside - 1) ring syntheses). Returns (seconds, pix, values)."""
+    import oracle.healpix as hp
+    import oracle.lens as OL
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(hp.npix(w.nside), npix_sample, replace=False))
+    t0 = time.perf_counter()
+    out = OL.lens_at_pixels(w.nside, w.lmax, w.order, pix, sky["T"], sky.get("E"), sky.get("B"),
+                            sky["phi"], nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return dt, pix, out
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = skygen.WORKLOADS[args.workload]
+    sky = skygen.workload_sky(args.workload)
+    cores = os.cpu_count() or 1
+    nrings_total = 2 * (4 * w.nside - 1)
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, pix, _ = oracle_sample(w, sky, args.sample_pixels, seed=i, nthreads=cores)
+        if i >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    # full-map time extrapolated by the number of ring syntheses
+    est_map_s = t * nrings_total / (2 * args.sample_pixels)
+    value = 1.0 / est_map_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "maps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nside": w.nside, "lmax": w.lmax, "order": w.order,
+                   "fields": "TQU", "form": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "maps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.sample_pixels} output pixels per step "
+                                   f"({2 * args.sample_pixels} of {nrings_total} ring syntheses); "
+                                   "full-map time extrapolated by ring count"},
+        "e2e": {"value": value, "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    os.environ["TAYLENS_TIMING"] = "1"
+    from paper_1307_0719_gb300 import api
+
+    w = skygen.WORKLOADS[args.workload]
+    # each rank lenses its own realisation (seeds offset by rank): weak scaling
+    sky = skygen.make_sky(w.nside, w.lmax, w.pol, w.seed_t + 1000 * rank, w.seed_e + 1000 * rank,
+                          w.seed_phi + 1000 * rank, w.damp_t, w.damp_e)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in sky.items()}
+    plan = api.Plan(w.nside, w.lmax, w.order, pol=w.pol, precision=api.MIXED_FP32)
+    out = torch.empty((3, plan.npix), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.lens(d["T"], d["E"], d["B"], d["phi"], out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stage_sum = None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            st = np.array(plan.last_stage_ms())  # events on the launch stream
+            stage_sum = st if stage_sum is None else stage_sum + st
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    stages = stage_sum / args.steps
+    names = ["prep_T", "legendre_T", "deflection_fft", "prep_QU", "legendre_QU", "ringfft", "gather"]
+    stage_ms = {n: float(v) for n, v in zip(names, stages)}
+
+    # roofline of the dominant kernel
+    flops_qu = legendre_flops_per_launch(w.nside, w.lmax, w.order, 2)
+    flops_t = legendre_flops_per_launch(w.nside, w.lmax, w.order, 0)
+    dom = max(("legendre_QU", "legendre_T", "ringfft", "gather"), key=lambda k: stage_ms[k])
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            peaks = json.load(f)
+    clocks = clk.summary()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    if dom in ("legendre_QU", "legendre_T"):
+        fl = flops_qu if dom == "legendre_QU" else flops_t
+        achieved = fl / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": f"legendre_spin{'2' if dom == 'legendre_QU' else '0'}_kernel<float,{w.order}>",
+                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": None}
+
+    # end to end through tl_lens_host (pinned host buffers, copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hin = {k: torch.from_numpy(v).pin_memory() for k, v in sky.items()}
+        hout = torch.empty((3, plan.npix), dtype=torch.float32).pin_memory()
+        plan.lens_host(hin["T"], hin["E"], hin["B"], hin["phi"], out=hout)
+        k2 = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            plan.lens_host(hin["T"], hin["E"], hin["B"], hin["phi"], out=hout)
+        e2e_s = (time.perf_counter() - t0) / k2
+        nb = plan.nalm * 16
+        e2e = {"value": world / e2e_s, "unit": "maps/s", "h2d_bytes_per_step": 4 * nb,
+               "d2h_bytes_per_step": 3 * plan.npix * 4}
+        del hin, hout
+
+    lensed = out.cpu().numpy()
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
+
+    # plain FP64 GPU form on the same GPU
+    fp64 = None
+    if not args.no_fp64:
+        p64 = api.Plan(w.nside, w.lmax, w.order, pol=w.pol, precision=api.FP64)
+        o64 = torch.empty((3, p64.npix), dtype=torch.float64, device=dev)
+        p64.lens(d["T"], d["E"], d["B"], d["phi"], out=o64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = max(1, args.fp64_steps)
+        e0.record(stream)
+        for _ in range(k64):
+            p64.lens(d["T"], d["E"], d["B"], d["phi"], out=o64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        st64 = dict(zip(names, [float(x) for x in p64.last_stage_ms()]))
+        lensed64 = o64.cpu().numpy()
+        p64.close()
+        fp64 = {"maps_per_s": world * 1e3 / ms64, "ms_per_step": ms64, "steps": k64, "stage_ms": st64,
+                "mixed_over_fp64": value / (world * 1e3 / ms64)}
+    else:
+        lensed64 = None
+
+    # rank 0: CPU baseline (oracle) on a bounded sample + error of both forms there
+    cpu = None
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        dt, pix, ref = oracle_sample(w, sky, args.sample_pixels, nthreads=cores)
+        nrings_total = 2 * (4 * w.nside - 1)
+        est = dt * nrings_total / (2 * args.sample_pixels)
+        cpu = {"value": 1.0 / est, "unit": "maps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.sample_pixels} output pixels ({2 * args.sample_pixels} of "
+                         f"{nrings_total} ring syntheses) in {dt:.1f} s; full-map time "
+                         "extrapolated by ring count"}
+
+        def errs(maps):
+            o = {}
+            for i, f in enumerate("TQU"):
+                r = ref[f]
+                dlt = maps[i][pix] - r
+                o[f] = {"rel_rms": float(np.sqrt(np.mean(dlt ** 2) / np.mean(r ** 2))),
+                        "max_rel": float(np.max(np.abs(dlt)) / np.sqrt(np.mean(r ** 2)))}
+            return o
+        err = {"mixed_fp32": errs(lensed), "npix": int(len(pix))}
+        if lensed64 is not None:
+            err["fp64"] = errs(lensed64)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Gaussian alm, analytic spectra)",
+            "config": {"workload": args.workload, "nside": w.nside, "lmax": w.lmax, "order": w.order,
+                       "fields": "TQU", "form": "mixed FP32 (FP64 seeds/rescaling, FP64 geometry)",
+                       "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (alm 537 MB, "
+                       "derivative maps 9 GB per step)"},
+            "stage_ms": stage_ms, "roofline": roof, "clocks": clocks,
+            "gpu_launches": 8 * args.steps, "e2e": e2e, "fp64": fp64, "err_vs_oracle": err,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(skygen.WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--sample-pixels", type=int, default=16)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -130,9 +130,12 @@ tl_status tl_lens_host(tl_plan *plan, const double *alm_T, const double *alm_E,
 const char *tl_status_string(tl_status status);
 
 /* Milliseconds of the stages of the most recent tl_lens on this plan, measured
- * with CUDA events when the plan was created with TL_TIMING in the environment
- * variable TAYLENS_TIMING=1; stage order: prep, deflection, legendre_T,
- * legendre_QU, ringfft, gather. Returns the number of stages written (<= n). */
+ * with CUDA events on the call's stream when the environment variable
+ * TAYLENS_TIMING=1 was set at plan creation (otherwise returns 0). Stage order:
+ * prep_T (T and phi coefficients), legendre_T (spin-0 stage, with phi's j <= 1
+ * planes), deflection_fft, prep_QU, legendre_QU, ringfft (all T/Q/U maps),
+ * gather. Synchronises on the last event.
+ * Returns the number of stages written (<= n). */
 int tl_last_stage_ms(const tl_plan *plan, float *ms, int n);
 
 #ifdef __cplusplus

@@ -53,6 +53,7 @@ struct tl_plan {
   int tw_len;
   int blue_maxm;        // largest Bluestein FFT length (0 if none)
   // workspace
+  void *tab0, *tab2;    // plan-time step tables {k_l, A_{l+1}} for spin 0 and spin 2
   void *rec_T, *rec_P, *rec_QU; // coefficient records
   void *d7_T, *d7_Q, *d7_U, *d7_P; // per-ring Fourier coefficients [j][ring][m] (T2)
   void *d3;            // derivative maps [3*nmaps][npix] (T), Taylor-ready
@@ -73,13 +74,12 @@ inline long long nalm(int lmax) { return (long long)(lmax + 1) * (lmax + 2) / 2;
 inline int maps_per_field(int order) { return (order + 1) * (order + 2) / 2; }
 
 // kernel launchers (defined in the .cu files)
-cudaError_t launch_prep_spin0(const tl_plan *p, const double *alm, void *rec, cudaStream_t s);
-cudaError_t launch_prep_spin2(const tl_plan *p, const double *alm_E, const double *alm_B, void *rec,
-                              cudaStream_t s);
-cudaError_t launch_legendre_spin0(const tl_plan *p, int nder, const void *rec, void *d7,
-                                  cudaStream_t s);
-cudaError_t launch_legendre_spin2(const tl_plan *p, int nder, const void *rec, void *d7q, void *d7u,
-                                  cudaStream_t s);
+cudaError_t launch_steptab(const tl_plan *p, int s, void *tab, cudaStream_t st);
+// prepares rec_T from alm (if not NULL) and rec_P from alm_phi (if not NULL)
+cudaError_t launch_prep_spin0(const tl_plan *p, const double *alm, const double *alm_phi, cudaStream_t s);
+cudaError_t launch_prep_spin2(const tl_plan *p, const double *alm_E, const double *alm_B, cudaStream_t s);
+cudaError_t launch_legendre_spin0(const tl_plan *p, int nder, bool phi, void *d7, void *d7p, cudaStream_t s);
+cudaError_t launch_legendre_spin2(const tl_plan *p, int nder, cudaStream_t s);
 
 // One output map of the ring FFT stage.
 struct MapJob {

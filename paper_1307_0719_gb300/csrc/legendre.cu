@@ -1,5 +1,13 @@
-// Legendre stage kernels and coefficient preparation. See legendre.cuh for the
-// mathematics (Naess & Louis 2013, Sec. II.B, Eq. 4 derivative maps).
+// Legendre stage kernels, their plan-time step tables and the per-call
+// coefficient preparation. See legendre.cuh for the mathematics (Naess & Louis
+// 2013, Sec. II.B: the derivative maps of Eq. 4).
+//
+// Normalised recurrence. With lam_l = k_l mu_l and k_{l+1} = beta_{l+1} k_{l-1}
+// (k_{l0} = k_{l0+1} = 1) the three-term recurrence becomes
+//     mu_{l+1} = A_{l+1} X mu_l - mu_{l-1},   A_{l+1} = alpha_{l+1} k_l / k_{l+1},
+// so each step of each derivative order ends in one fused multiply-add; k_l is
+// folded into the coefficients (sum_l a_l lam_l = sum_l (a_l k_l) mu_l). The
+// table {k_l, A_{l+1}} depends only on (l, m, s) and is built once per plan.
 #include <math.h>
 
 #include "legendre.cuh"
@@ -7,76 +15,114 @@
 namespace tl {
 
 // ---------------------------------------------------------------------------
-// coefficient preparation
+// step tables and coefficient preparation
 
 __device__ __forceinline__ double rec_alpha(int L, int m, int s) {
   double L2 = (double)L * L;
   return sqrt((4.0 * L2 - 1.0) * L2 / ((L2 - (double)m * m) * (L2 - (double)s * s)));
 }
 
+// One thread per m: tab[idx(l, m)] = {k_l, A_{l+1}} for l0 <= l <= lmax (A = 0 at lmax).
 template <typename T>
-__global__ void prep_spin0_kernel(int lmax, const double *__restrict__ alm, Rec0<T> *__restrict__ rec) {
-  int m = blockIdx.y;
-  int l = m + blockIdx.x * blockDim.x + threadIdx.x;
-  if (l > lmax) return;
-  long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
-  Rec0<T> r;
-  r.re = (T)alm[2 * idx];
-  r.im = (m == 0) ? (T)0 : (T)alm[2 * idx + 1];
-  if (l < lmax) {
-    double an = rec_alpha(l + 1, m, 0);
-    r.alpha = (T)an;
-    r.beta = (l > m) ? (T)(an / rec_alpha(l, m, 0)) : (T)0;
-  } else {
-    r.alpha = (T)0;
-    r.beta = (T)0;
+__global__ void steptab_kernel(int lmax, int s, typename RealTraits<T>::T2 *__restrict__ tab) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > lmax) return;
+  const int as = s < 0 ? -s : s;
+  const int l0 = m > as ? m : as;
+  typename RealTraits<T>::T2 *tm = tab + (long long)m * (2 * lmax + 1 - m) / 2;
+  for (int l = m; l < l0 && l <= lmax; ++l) {
+    tm[l].x = (T)0;
+    tm[l].y = (T)0;
   }
+  double k_prev = 1.0, k_cur = 1.0, a_cur = 0.0;  // k_{l-1}, k_l, alpha_l
+  for (int l = l0; l <= lmax; ++l) {
+    double A = 0.0, k_next = 0.0;
+    if (l < lmax) {
+      const double a_next = rec_alpha(l + 1, m, s);
+      k_next = (l == l0) ? 1.0 : (a_next / a_cur) * k_prev;  // beta_{l+1} k_{l-1}
+      A = a_next * k_cur / k_next;
+      a_cur = a_next;
+    }
+    tm[l].x = (T)k_cur;
+    tm[l].y = (T)A;
+    k_prev = k_cur;
+    k_cur = k_next;
+  }
+}
+
+template <typename T>
+__global__ void prep_spin0_kernel(int lmax, const double *__restrict__ alm,
+                                  const typename RealTraits<T>::T2 *__restrict__ tab, Rec0<T> *__restrict__ rec) {
+  const int m = blockIdx.y;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > lmax) return;
+  const long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
+  const typename RealTraits<T>::T2 kA = tab[idx];
+  Rec0<T> r;
+  r.re = (T)(alm[2 * idx] * (double)kA.x);
+  r.im = (m == 0) ? (T)0 : (T)(alm[2 * idx + 1] * (double)kA.x);
+  r.A = kA.y;
+  r.pad = (T)0;
+  rec[idx] = r;
+}
+
+// coefficients of a second spin-0 field that shares the basis (the lensing potential)
+template <typename T>
+__global__ void prep_phi_kernel(int lmax, const double *__restrict__ alm,
+                                const typename RealTraits<T>::T2 *__restrict__ tab,
+                                typename RealTraits<T>::T2 *__restrict__ rec) {
+  const int m = blockIdx.y;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+  if (l > lmax) return;
+  const long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
+  const double k = (double)tab[idx].x;
+  typename RealTraits<T>::T2 r;
+  r.x = (T)(alm[2 * idx] * k);
+  r.y = (m == 0) ? (T)0 : (T)(alm[2 * idx + 1] * k);
   rec[idx] = r;
 }
 
 template <typename T>
 __global__ void prep_spin2_kernel(int lmax, const double *__restrict__ almE, const double *__restrict__ almB,
-                                  Rec2<T> *__restrict__ rec) {
-  int m = blockIdx.y;
-  int l = m + blockIdx.x * blockDim.x + threadIdx.x;
+                                  const typename RealTraits<T>::T2 *__restrict__ tab, Rec2<T> *__restrict__ rec) {
+  const int m = blockIdx.y;
+  const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
   if (l > lmax) return;
-  long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
+  const long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
   const int s = 2;
-  int l0 = m > s ? m : s;
+  const int l0 = m > s ? m : s;
   Rec2<T> r;
   if (l < l0) {
-    r.c1r = r.c1i = r.c2r = r.c2i = r.alpha = r.beta = r.cterm = r.pad = (T)0;
+    r.c1r = r.c1i = r.c2r = r.c2i = r.A = r.cterm = r.pad0 = r.pad1 = (T)0;
     rec[idx] = r;
     return;
   }
-  double er = almE ? almE[2 * idx] : 0.0;
-  double ei = (almE && m > 0) ? almE[2 * idx + 1] : 0.0;
-  double br = almB ? almB[2 * idx] : 0.0;
-  double bi = (almB && m > 0) ? almB[2 * idx + 1] : 0.0;
-  double sg = ((l + m) & 1) ? -1.0 : 1.0;
-  r.c1r = (T)(er - bi);
-  r.c1i = (T)(ei + br);
+  const typename RealTraits<T>::T2 kA = tab[idx];
+  const double k = (double)kA.x;
+  const double er = almE ? almE[2 * idx] : 0.0;
+  const double ei = (almE && m > 0) ? almE[2 * idx + 1] : 0.0;
+  const double br = almB ? almB[2 * idx] : 0.0;
+  const double bi = (almB && m > 0) ? almB[2 * idx + 1] : 0.0;
+  const double sg = ((l + m) & 1) ? -k : k;
+  r.c1r = (T)((er - bi) * k);
+  r.c1i = (T)((ei + br) * k);
   r.c2r = (T)(sg * (er + bi));
   r.c2i = (T)(sg * (ei - br));
-  if (l < lmax) {
-    double an = rec_alpha(l + 1, m, s);
-    r.alpha = (T)an;
-    r.beta = (l > l0) ? (T)(an / rec_alpha(l, m, s)) : (T)0;
-  } else {
-    r.alpha = (T)0;
-    r.beta = (T)0;
-  }
+  r.A = kA.y;
   r.cterm = (T)((double)m * s / ((double)l * (l + 1.0)));
-  r.pad = (T)0;
+  r.pad0 = r.pad1 = (T)0;
   rec[idx] = r;
 }
 
 // ---------------------------------------------------------------------------
 // seeds
 
-// Binomial coefficient, small arguments, compile-time friendly.
-__host__ __device__ constexpr int binom(int n, int k) {
-  return (k < 0 || k > n) ? 0 : (k == 0 || k == n) ? 1 : binom(n - 1, k - 1) + binom(n - 1, k);
+// Binomial coefficient for small arguments; a plain loop, so that with the
+// unrolled (constant) arguments of the kernels below it folds to a constant.
+__host__ __device__ __forceinline__ constexpr int binom(int n, int k) {
+  int r = 1;
+  for (int t = 1; t <= k; ++t) r = r * (n - k + t) / t;
+  return r;
 }
 
 // Seed mantissas (normalised derivatives) of s_lambda_{l0,m} at ring r.
@@ -89,8 +135,9 @@ __device__ __forceinline__ void seed_values(const RingTable &rt, int r, double E
   int s0 = (int)ceil((E - RT::H) / (double)RT::SB);
   if (s0 > 0) s0 = 0;
   sc = s0;
-  double mant = sign * exp2(E - (double)RT::SB * s0);
-  // d^j/dth^j f = f * B_j, B_{j+1} = sum_i C(j,i) g_{i+1} B_{j-i}
+  const double mant = sign * exp2(E - (double)RT::SB * s0);
+  // d^j/dth^j f = f * B_j with B_{j+1} = sum_i C(j,i) g_{i+1} B_{j-i},
+  // g_k = d^k/dth^k ln f = a d^k ln sin(th/2) + b d^k ln cos(th/2)
   double g[NDER + 1];
   const double *dls = rt.dls + (size_t)r * (TL_MAX_NDER + 1);
   const double *dlc = rt.dlc + (size_t)r * (TL_MAX_NDER + 1);
@@ -113,114 +160,149 @@ __device__ __forceinline__ void seed_values(const RingTable &rt, int r, double E
   }
 }
 
-// Leibniz step: nxt^(j) = alpha (X cur^(j) + sum_{i>=1} e[j][i] cur^(j-i)) - beta prev^(j)
+// Leibniz coefficients e[j][i] = C(j, i) cos^(i)(theta) / L^i, i = 1..j, once per thread.
+template <typename T, int NDER> struct Leib {
+  T e[NDER + 1][NDER + 1];
+};
 template <typename T, int NDER>
-__device__ __forceinline__ void rec_step(T (&cur)[NDER + 1], T (&prev)[NDER + 1], const T (&dcos)[NDER + 1],
-                                         T X, T alpha, T beta) {
-  T nxt[NDER + 1];
+__device__ __forceinline__ void leibniz_coefs(double x, double st, double invL, Leib<T, NDER> &L) {
+  double p = 1.0, dc[NDER + 1];
 #pragma unroll
-  for (int j = 0; j <= NDER; ++j) {
-    T acc = X * cur[j];
-#pragma unroll
-    for (int i = 1; i <= j; ++i) acc = fma((T)binom(j, i) * dcos[i], cur[j - i], acc);
-    nxt[j] = fma(alpha, acc, -beta * prev[j]);
+  for (int i = 0; i <= NDER; ++i) {
+    const double v = (i % 4 == 0) ? x : (i % 4 == 1) ? -st : (i % 4 == 2) ? -x : st;
+    dc[i] = v * p;
+    p *= invL;
   }
 #pragma unroll
-  for (int j = 0; j <= NDER; ++j) {
-    prev[j] = cur[j];
-    cur[j] = nxt[j];
+  for (int j = 0; j <= NDER; ++j)
+#pragma unroll
+    for (int i = 0; i <= NDER; ++i) L.e[j][i] = (i >= 1 && i <= j) ? (T)(binom(j, i) * dc[i]) : (T)0;
+}
+
+// In-place step: old (mu_{l-1}) becomes mu_{l+1} from cur (mu_l):
+//   old^(j) = A (X cur^(j) + sum_{i>=1} e[j][i] cur^(j-i)) - old^(j)
+template <typename T, int NDER>
+__device__ __forceinline__ void step_into(T (&old)[NDER + 1], const T (&cur)[NDER + 1], const Leib<T, NDER> &L,
+                                          T X, T A) {
+#pragma unroll
+  for (int j = NDER; j >= 0; --j) {
+    T acc = X * cur[j];
+#pragma unroll
+    for (int i = 1; i <= j; ++i) acc = fma(L.e[j][i], cur[j - i], acc);
+    old[j] = fma(A, acc, -old[j]);
   }
 }
 
+// Exponent rescaling while the values are below the representable range.
 template <typename T, int NDER>
-__device__ __forceinline__ void maybe_rescale(T (&cur)[NDER + 1], T (&prev)[NDER + 1], int &sc) {
+__device__ __forceinline__ void rescale(T (&a)[NDER + 1], T (&b)[NDER + 1], const T lead, int &sc) {
   typedef RealTraits<T> RT;
-  const T thr = (T)exp2(RT::H);
-  if (sc < 0 && fabs(cur[0]) > thr) {
-    const T f = (T)exp2(-(double)RT::SB);
+  if (sc < 0 && fabs(lead) > RT::THR) {
 #pragma unroll
     for (int j = 0; j <= NDER; ++j) {
-      cur[j] *= f;
-      prev[j] *= f;
+      a[j] *= RT::STEP;
+      b[j] *= RT::STEP;
     }
     ++sc;
   }
 }
 
-// normalised derivatives of cos(theta): dcos[i] = cos(th + i pi/2) / L^i
-template <typename T, int NDER>
-__device__ __forceinline__ void cos_derivs(double x, double st, double invL, T (&dcos)[NDER + 1]) {
-  double p = 1.0;
-#pragma unroll
-  for (int i = 0; i <= NDER; ++i) {
-    double v = (i % 4 == 0) ? x : (i % 4 == 1) ? -st : (i % 4 == 2) ? -x : st;
-    dcos[i] = (T)(v * p);
-    p *= invL;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // spin 0: one thread per north ring (incl. the equator) and one m per block
-// row; the south ring follows from lam^(j)(pi - th) = (-1)^(l+m+j) lam^(j)(th).
+// row; the south ring follows from lam^(j)(pi - th) = (-1)^(l+m+j) lam^(j)(th),
+// so even and odd l - m are accumulated apart. With PHI, the lensing potential's
+// coefficients are contracted against the same basis for j <= 1 (deflection).
 
-template <typename T, int NDER>
+template <typename T, int NDER, bool PHI>
 __global__ void __launch_bounds__(128) legendre_spin0_kernel(RingTable rt, const double *__restrict__ lnorm0,
                                                              int nside, int lmax, int mmax, int nrings,
                                                              const Rec0<T> *__restrict__ rec,
-                                                             typename RealTraits<T>::T2 *__restrict__ d7) {
+                                                             const typename RealTraits<T>::T2 *__restrict__ recp,
+                                                             typename RealTraits<T>::T2 *__restrict__ d7,
+                                                             typename RealTraits<T>::T2 *__restrict__ d7p) {
   typedef typename RealTraits<T>::T2 T2;
+  constexpr int NP = PHI ? 2 : 0;  // phi derivative orders carried (0 and 1)
   const int m = blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;  // north ring index 0 .. 2N-1
   if (r >= 2 * nside) return;
   const double invL = 1.0 / (double)(lmax + 1);
   const double x = rt.z[r], st = rt.sint[r];
-  T dcos[NDER + 1];
-  cos_derivs<T, NDER>(x, st, invL, dcos);
+  Leib<T, NDER> LC;
+  leibniz_coefs<T, NDER>(x, st, invL, LC);
 
-  T cur[NDER + 1], prev[NDER + 1];
+  T a[NDER + 1], b[NDER + 1];  // alternately mu_{l-1} and mu_l
   int sc;
   {
-    double E = lnorm0[m] + (double)m * (rt.log2_sh[r] + rt.log2_ch[r]);
-    seed_values<T, NDER>(rt, r, E, (double)m, (double)m, (m & 1) ? -1.0 : 1.0, invL, cur, sc);
+    const double E = lnorm0[m] + (double)m * (rt.log2_sh[r] + rt.log2_ch[r]);
+    seed_values<T, NDER>(rt, r, E, (double)m, (double)m, (m & 1) ? -1.0 : 1.0, invL, b, sc);
   }
 #pragma unroll
-  for (int j = 0; j <= NDER; ++j) prev[j] = (T)0;
+  for (int j = 0; j <= NDER; ++j) a[j] = (T)0;
 
-  // accumulators: even / odd l-m, real / imaginary
-  T ae_r[NDER + 1], ae_i[NDER + 1], ao_r[NDER + 1], ao_i[NDER + 1];
+  T er[NDER + 1], ei[NDER + 1], orr[NDER + 1], oi[NDER + 1];
 #pragma unroll
-  for (int j = 0; j <= NDER; ++j) ae_r[j] = ae_i[j] = ao_r[j] = ao_i[j] = (T)0;
+  for (int j = 0; j <= NDER; ++j) er[j] = ei[j] = orr[j] = oi[j] = (T)0;
+  T per[2], pei[2], por[2], poi[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) per[j] = pei[j] = por[j] = poi[j] = (T)0;
 
-  const Rec0<T> *rm = rec + (long long)m * (2 * lmax + 1 - m) / 2;
+  const long long base = (long long)m * (2 * lmax + 1 - m) / 2;
+  const Rec0<T> *rm = rec + base;
+  const T2 *pm = PHI ? recp + base : nullptr;
   const T X = (T)x;
-  for (int l = m; l <= lmax; l += 2) {
-    // even l - m
+  Rec0<T> cn = rm[m];
+  T2 pn;
+  if (PHI) pn = pm[m];
+  for (int l = m;; l += 2) {
+    // ---- even l - m: value in b
     {
-      Rec0<T> c = rm[l];
+      const Rec0<T> c = cn;
+      T2 pc;
+      if (PHI) pc = pn;
+      if (l + 1 <= lmax) {
+        cn = rm[l + 1];
+        if (PHI) pn = pm[l + 1];
+      }
       if (sc == 0) {
 #pragma unroll
         for (int j = 0; j <= NDER; ++j) {
-          ae_r[j] = fma(c.re, cur[j], ae_r[j]);
-          ae_i[j] = fma(c.im, cur[j], ae_i[j]);
+          er[j] = fma(c.re, b[j], er[j]);
+          ei[j] = fma(c.im, b[j], ei[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          per[j] = fma(pc.x, b[j], per[j]);
+          pei[j] = fma(pc.y, b[j], pei[j]);
         }
       }
       if (l == lmax) break;
-      rec_step<T, NDER>(cur, prev, dcos, X, c.alpha, c.beta);
-      maybe_rescale<T, NDER>(cur, prev, sc);
+      step_into<T, NDER>(a, b, LC, X, c.A);
+      rescale<T, NDER>(a, b, a[0], sc);
     }
-    // odd l - m
+    // ---- odd l - m: value in a
     {
-      Rec0<T> c = rm[l + 1];
+      const Rec0<T> c = cn;
+      T2 pc;
+      if (PHI) pc = pn;
+      if (l + 2 <= lmax) {
+        cn = rm[l + 2];
+        if (PHI) pn = pm[l + 2];
+      }
       if (sc == 0) {
 #pragma unroll
         for (int j = 0; j <= NDER; ++j) {
-          ao_r[j] = fma(c.re, cur[j], ao_r[j]);
-          ao_i[j] = fma(c.im, cur[j], ao_i[j]);
+          orr[j] = fma(c.re, a[j], orr[j]);
+          oi[j] = fma(c.im, a[j], oi[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          por[j] = fma(pc.x, a[j], por[j]);
+          poi[j] = fma(pc.y, a[j], poi[j]);
         }
       }
       if (l + 1 == lmax) break;
-      rec_step<T, NDER>(cur, prev, dcos, X, c.alpha, c.beta);
-      maybe_rescale<T, NDER>(cur, prev, sc);
+      step_into<T, NDER>(b, a, LC, X, c.A);
+      rescale<T, NDER>(a, b, b[0], sc);
     }
   }
   if (m > mmax) return;
@@ -229,13 +311,24 @@ __global__ void __launch_bounds__(128) legendre_spin0_kernel(RingTable rt, const
 #pragma unroll
   for (int j = 0; j <= NDER; ++j) {
     T2 vn, vs;
-    vn.x = ae_r[j] + ao_r[j];
-    vn.y = ae_i[j] + ao_i[j];
-    T sgn = (j & 1) ? (T)-1 : (T)1;
-    vs.x = sgn * (ae_r[j] - ao_r[j]);
-    vs.y = sgn * (ae_i[j] - ao_i[j]);
+    vn.x = er[j] + orr[j];
+    vn.y = ei[j] + oi[j];
+    const T sgn = (j & 1) ? (T)-1 : (T)1;
+    vs.x = sgn * (er[j] - orr[j]);
+    vs.y = sgn * (ei[j] - oi[j]);
     d7[((size_t)j * nrings + r) * ld + m] = vn;
     if (rs != r) d7[((size_t)j * nrings + rs) * ld + m] = vs;
+  }
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    T2 vn, vs;
+    vn.x = per[j] + por[j];
+    vn.y = pei[j] + poi[j];
+    const T sgn = (j & 1) ? (T)-1 : (T)1;
+    vs.x = sgn * (per[j] - por[j]);
+    vs.y = sgn * (pei[j] - poi[j]);
+    d7p[((size_t)j * nrings + r) * ld + m] = vn;
+    if (rs != r) d7p[((size_t)j * nrings + rs) * ld + m] = vs;
   }
 }
 
@@ -246,6 +339,18 @@ __global__ void __launch_bounds__(128) legendre_spin0_kernel(RingTable rt, const
 //   S1^(j) = sum_l (E + iB) 2lam^(j),  S2^(j) = sum_l (-1)^(l+m) (E - iB) 2lam^(j);
 // with -2lam^(j)(th) = (-1)^(l+m+j) 2lam^(j)(pi - th), the pair combines into
 //   F^Q(th) = -(S1(th) + (-1)^j S2(pi-th))/2,  F^U(th) = i (S1(th) - (-1)^j S2(pi-th))/2.
+
+template <typename T, int NDER>
+__device__ __forceinline__ void acc2(const Rec2<T> &c, const T (&v)[NDER + 1], T (&s1r)[NDER + 1],
+                                     T (&s1i)[NDER + 1], T (&s2r)[NDER + 1], T (&s2i)[NDER + 1]) {
+#pragma unroll
+  for (int j = 0; j <= NDER; ++j) {
+    s1r[j] = fma(c.c1r, v[j], s1r[j]);
+    s1i[j] = fma(c.c1i, v[j], s1i[j]);
+    s2r[j] = fma(c.c2r, v[j], s2r[j]);
+    s2i[j] = fma(c.c2i, v[j], s2i[j]);
+  }
+}
 
 template <typename T, int NDER, int RP>
 __global__ void __launch_bounds__(2 * RP) legendre_spin2_kernel(RingTable rt, const double *__restrict__ lnorm0,
@@ -269,49 +374,53 @@ __global__ void __launch_bounds__(2 * RP) legendre_spin2_kernel(RingTable rt, co
 
   if (active) {
     const double x = rt.z[r], st = rt.sint[r];
-    T dcos[NDER + 1];
-    cos_derivs<T, NDER>(x, st, invL, dcos);
-    T cur[NDER + 1], prev[NDER + 1];
-    int sc;
-    int l0;
+    Leib<T, NDER> LC;
+    leibniz_coefs<T, NDER>(x, st, invL, LC);
+    T a[NDER + 1], b[NDER + 1];
+    int sc, l0;
     {
       const double lsh = rt.log2_sh[r], lch = rt.log2_ch[r];
-      double E, a, b;
+      double E, ea, eb;
       if (m >= 2) {
         l0 = m;
-        double md = (double)m;
+        const double md = (double)m;
         E = lnorm0[m] + 0.5 * log2(md * (md - 1.0) / ((md + 1.0) * (md + 2.0))) + (md + 2.0) * lsh +
             (md - 2.0) * lch;
-        a = md + 2.0;
-        b = md - 2.0;
+        ea = md + 2.0;
+        eb = md - 2.0;
       } else {
         l0 = 2;
-        // sqrt(5/(4 pi)) sqrt(C(4, 2+m))
-        double c4 = (m == 0) ? 6.0 : 4.0;
+        const double c4 = (m == 0) ? 6.0 : 4.0;  // C(4, 2+m)
         E = log2(sqrt(5.0 / (4.0 * 3.14159265358979323846)) * sqrt(c4)) + (2.0 + m) * lsh + (2.0 - m) * lch;
-        a = 2.0 + m;
-        b = 2.0 - m;
+        ea = 2.0 + m;
+        eb = 2.0 - m;
       }
-      seed_values<T, NDER>(rt, r, E, a, b, (m & 1) ? -1.0 : 1.0, invL, cur, sc);
+      seed_values<T, NDER>(rt, r, E, ea, eb, (m & 1) ? -1.0 : 1.0, invL, b, sc);
     }
 #pragma unroll
-    for (int j = 0; j <= NDER; ++j) prev[j] = (T)0;
+    for (int j = 0; j <= NDER; ++j) a[j] = (T)0;
     const Rec2<T> *rm = rec + (long long)m * (2 * lmax + 1 - m) / 2;
     const T X = (T)x;
-    for (int l = l0; l <= lmax; ++l) {
-      const Rec2<T> c = rm[l];
-      if (sc == 0) {
-#pragma unroll
-        for (int j = 0; j <= NDER; ++j) {
-          s1r[j] = fma(c.c1r, cur[j], s1r[j]);
-          s1i[j] = fma(c.c1i, cur[j], s1i[j]);
-          s2r[j] = fma(c.c2r, cur[j], s2r[j]);
-          s2i[j] = fma(c.c2i, cur[j], s2i[j]);
+    if (l0 <= lmax) {
+      Rec2<T> cn = rm[l0];
+      for (int l = l0;; l += 2) {
+        {
+          const Rec2<T> c = cn;
+          if (l + 1 <= lmax) cn = rm[l + 1];
+          if (sc == 0) acc2<T, NDER>(c, b, s1r, s1i, s2r, s2i);
+          if (l == lmax) break;
+          step_into<T, NDER>(a, b, LC, X + c.cterm, c.A);
+          rescale<T, NDER>(a, b, a[0], sc);
+        }
+        {
+          const Rec2<T> c = cn;
+          if (l + 2 <= lmax) cn = rm[l + 2];
+          if (sc == 0) acc2<T, NDER>(c, a, s1r, s1i, s2r, s2i);
+          if (l + 1 == lmax) break;
+          step_into<T, NDER>(b, a, LC, X + c.cterm, c.A);
+          rescale<T, NDER>(a, b, b[0], sc);
         }
       }
-      if (l == lmax) break;
-      rec_step<T, NDER>(cur, prev, dcos, X + c.cterm, c.alpha, c.beta);
-      maybe_rescale<T, NDER>(cur, prev, sc);
     }
   }
 #pragma unroll
@@ -328,16 +437,16 @@ __global__ void __launch_bounds__(2 * RP) legendre_spin2_kernel(RingTable rt, co
   const size_t ld = (size_t)(mmax + 1);
 #pragma unroll
   for (int j = 0; j <= NDER; ++j) {
-    T2 p = xch[partner][j];
-    T sg = (j & 1) ? (T)-1 : (T)1;
-    T ar = s1r[j] + sg * p.x, ai = s1i[j] + sg * p.y;  // S1 + (-1)^j S2'
-    T br = s1r[j] - sg * p.x, bi = s1i[j] - sg * p.y;  // S1 - (-1)^j S2'
+    const T2 p = xch[partner][j];
+    const T sg = (j & 1) ? (T)-1 : (T)1;
+    const T ar = s1r[j] + sg * p.x, ai = s1i[j] + sg * p.y;  // S1 + (-1)^j S2'
+    const T br = s1r[j] - sg * p.x, bi = s1i[j] - sg * p.y;  // S1 - (-1)^j S2'
     T2 q, u;
     q.x = (T)-0.5 * ar;
     q.y = (T)-0.5 * ai;
-    u.x = (T)-0.5 * bi;  // i (br + i bi)/2
+    u.x = (T)-0.5 * bi;  // i (br + i bi) / 2
     u.y = (T)0.5 * br;
-    size_t o = ((size_t)j * nrings + r) * ld + m;
+    const size_t o = ((size_t)j * nrings + r) * ld + m;
     d7q[o] = q;
     d7u[o] = u;
   }
@@ -347,84 +456,97 @@ __global__ void __launch_bounds__(2 * RP) legendre_spin2_kernel(RingTable rt, co
 // launchers
 
 template <typename T>
-static cudaError_t prep0(const tl_plan *p, const double *alm, void *rec, cudaStream_t s) {
+static cudaError_t steptab_t(int lmax, int s, void *tab, cudaStream_t st) {
+  steptab_kernel<T><<<(lmax + 1 + 127) / 128, 128, 0, st>>>(lmax, s, (typename RealTraits<T>::T2 *)tab);
+  return cudaGetLastError();
+}
+cudaError_t launch_steptab(const tl_plan *p, int s, void *tab, cudaStream_t st) {
+  return p->precision == TL_FP64 ? steptab_t<double>(p->lmax, s, tab, st) : steptab_t<float>(p->lmax, s, tab, st);
+}
+
+template <typename T>
+static cudaError_t prep0(const tl_plan *p, const double *alm, const double *alm_phi, cudaStream_t s) {
+  typedef typename RealTraits<T>::T2 T2;
   dim3 grid((p->lmax + 1 + 127) / 128, p->lmax + 1);
-  prep_spin0_kernel<T><<<grid, 128, 0, s>>>(p->lmax, alm, (Rec0<T> *)rec);
+  if (alm) prep_spin0_kernel<T><<<grid, 128, 0, s>>>(p->lmax, alm, (const T2 *)p->tab0, (Rec0<T> *)p->rec_T);
+  if (alm_phi) prep_phi_kernel<T><<<grid, 128, 0, s>>>(p->lmax, alm_phi, (const T2 *)p->tab0, (T2 *)p->rec_P);
   return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t prep2(const tl_plan *p, const double *almE, const double *almB, void *rec, cudaStream_t s) {
+static cudaError_t prep2(const tl_plan *p, const double *almE, const double *almB, cudaStream_t s) {
+  typedef typename RealTraits<T>::T2 T2;
   dim3 grid((p->lmax + 1 + 127) / 128, p->lmax + 1);
-  prep_spin2_kernel<T><<<grid, 128, 0, s>>>(p->lmax, almE, almB, (Rec2<T> *)rec);
+  prep_spin2_kernel<T><<<grid, 128, 0, s>>>(p->lmax, almE, almB, (const T2 *)p->tab2, (Rec2<T> *)p->rec_QU);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_spin0(const tl_plan *p, const double *alm, void *rec, cudaStream_t s) {
-  return p->precision == TL_FP64 ? prep0<double>(p, alm, rec, s) : prep0<float>(p, alm, rec, s);
+cudaError_t launch_prep_spin0(const tl_plan *p, const double *alm, const double *alm_phi, cudaStream_t s) {
+  return p->precision == TL_FP64 ? prep0<double>(p, alm, alm_phi, s) : prep0<float>(p, alm, alm_phi, s);
 }
-cudaError_t launch_prep_spin2(const tl_plan *p, const double *almE, const double *almB, void *rec,
-                              cudaStream_t s) {
-  return p->precision == TL_FP64 ? prep2<double>(p, almE, almB, rec, s) : prep2<float>(p, almE, almB, rec, s);
+cudaError_t launch_prep_spin2(const tl_plan *p, const double *almE, const double *almB, cudaStream_t s) {
+  return p->precision == TL_FP64 ? prep2<double>(p, almE, almB, s) : prep2<float>(p, almE, almB, s);
 }
 
-template <typename T, int NDER>
-static cudaError_t leg0(const tl_plan *p, const void *rec, void *d7, cudaStream_t s) {
+template <typename T, int NDER, bool PHI>
+static cudaError_t leg0(const tl_plan *p, void *d7, void *d7p, cudaStream_t s) {
+  typedef typename RealTraits<T>::T2 T2;
   const int threads = 64;
   dim3 grid((2 * p->nside + threads - 1) / threads, p->mmax + 1);
-  legendre_spin0_kernel<T, NDER><<<grid, threads, 0, s>>>(
-      p->ring, p->lnorm0, p->nside, p->lmax, p->mmax, p->nrings, (const Rec0<T> *)rec,
-      (typename RealTraits<T>::T2 *)d7);
+  legendre_spin0_kernel<T, NDER, PHI><<<grid, threads, 0, s>>>(
+      p->ring, p->lnorm0, p->nside, p->lmax, p->mmax, p->nrings, (const Rec0<T> *)p->rec_T,
+      (const T2 *)p->rec_P, (T2 *)d7, (T2 *)d7p);
   return cudaGetLastError();
 }
 
 template <typename T, int NDER>
-static cudaError_t leg2(const tl_plan *p, const void *rec, void *dq, void *du, cudaStream_t s) {
+static cudaError_t leg2(const tl_plan *p, cudaStream_t s) {
   constexpr int RP = 32;
   dim3 grid((2 * p->nside + RP - 1) / RP, p->mmax + 1);
   legendre_spin2_kernel<T, NDER, RP><<<grid, 2 * RP, 0, s>>>(
-      p->ring, p->lnorm0, p->nside, p->lmax, p->mmax, p->nrings, (const Rec2<T> *)rec,
-      (typename RealTraits<T>::T2 *)dq, (typename RealTraits<T>::T2 *)du);
+      p->ring, p->lnorm0, p->nside, p->lmax, p->mmax, p->nrings, (const Rec2<T> *)p->rec_QU,
+      (typename RealTraits<T>::T2 *)p->d7_Q, (typename RealTraits<T>::T2 *)p->d7_U);
   return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t leg0_dispatch(const tl_plan *p, int nder, const void *rec, void *d7, cudaStream_t s) {
+template <typename T, bool PHI>
+static cudaError_t leg0_dispatch(const tl_plan *p, int nder, void *d7, void *d7p, cudaStream_t s) {
   switch (nder) {
-    case 0: return leg0<T, 0>(p, rec, d7, s);
-    case 1: return leg0<T, 1>(p, rec, d7, s);
-    case 2: return leg0<T, 2>(p, rec, d7, s);
-    case 3: return leg0<T, 3>(p, rec, d7, s);
-    case 4: return leg0<T, 4>(p, rec, d7, s);
-    case 5: return leg0<T, 5>(p, rec, d7, s);
-    case 6: return leg0<T, 6>(p, rec, d7, s);
+    case 0: return PHI ? cudaErrorInvalidValue : leg0<T, 0, false>(p, d7, d7p, s);
+    case 1: return leg0<T, 1, PHI>(p, d7, d7p, s);
+    case 2: return leg0<T, 2, PHI>(p, d7, d7p, s);
+    case 3: return leg0<T, 3, PHI>(p, d7, d7p, s);
+    case 4: return leg0<T, 4, PHI>(p, d7, d7p, s);
+    case 5: return leg0<T, 5, PHI>(p, d7, d7p, s);
+    case 6: return leg0<T, 6, PHI>(p, d7, d7p, s);
   }
   return cudaErrorInvalidValue;
 }
 
 template <typename T>
-static cudaError_t leg2_dispatch(const tl_plan *p, int nder, const void *rec, void *dq, void *du, cudaStream_t s) {
+static cudaError_t leg2_dispatch(const tl_plan *p, int nder, cudaStream_t s) {
   switch (nder) {
-    case 0: return leg2<T, 0>(p, rec, dq, du, s);
-    case 1: return leg2<T, 1>(p, rec, dq, du, s);
-    case 2: return leg2<T, 2>(p, rec, dq, du, s);
-    case 3: return leg2<T, 3>(p, rec, dq, du, s);
-    case 4: return leg2<T, 4>(p, rec, dq, du, s);
-    case 5: return leg2<T, 5>(p, rec, dq, du, s);
-    case 6: return leg2<T, 6>(p, rec, dq, du, s);
+    case 0: return leg2<T, 0>(p, s);
+    case 1: return leg2<T, 1>(p, s);
+    case 2: return leg2<T, 2>(p, s);
+    case 3: return leg2<T, 3>(p, s);
+    case 4: return leg2<T, 4>(p, s);
+    case 5: return leg2<T, 5>(p, s);
+    case 6: return leg2<T, 6>(p, s);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_legendre_spin0(const tl_plan *p, int nder, const void *rec, void *d7, cudaStream_t s) {
-  return p->precision == TL_FP64 ? leg0_dispatch<double>(p, nder, rec, d7, s)
-                                 : leg0_dispatch<float>(p, nder, rec, d7, s);
+// Spin-0 stage on the prepared T records (into d7) and, when phi is set, the
+// potential's j <= 1 planes (into d7p) from the same recurrence.
+cudaError_t launch_legendre_spin0(const tl_plan *p, int nder, bool phi, void *d7, void *d7p, cudaStream_t s) {
+  if (p->precision == TL_FP64)
+    return phi ? leg0_dispatch<double, true>(p, nder, d7, d7p, s) : leg0_dispatch<double, false>(p, nder, d7, d7p, s);
+  return phi ? leg0_dispatch<float, true>(p, nder, d7, d7p, s) : leg0_dispatch<float, false>(p, nder, d7, d7p, s);
 }
 
-cudaError_t launch_legendre_spin2(const tl_plan *p, int nder, const void *rec, void *dq, void *du,
-                                  cudaStream_t s) {
-  return p->precision == TL_FP64 ? leg2_dispatch<double>(p, nder, rec, dq, du, s)
-                                 : leg2_dispatch<float>(p, nder, rec, dq, du, s);
+cudaError_t launch_legendre_spin2(const tl_plan *p, int nder, cudaStream_t s) {
+  return p->precision == TL_FP64 ? leg2_dispatch<double>(p, nder, s) : leg2_dispatch<float>(p, nder, s);
 }
 
 }  // namespace tl

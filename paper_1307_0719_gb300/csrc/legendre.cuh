@@ -6,7 +6,7 @@
 // derivative maps of Eq. 4; the paper obtains them by repeated SHTs).
 //
 // Recurrence (Wigner d-functions, spin s, fixed m):
-//   lam_{l+1} = alpha_{l+1} [ (cos th + m s/(l(l+1))) lam_l ] - beta_{l+1} lam_{l-1},
+//   lam_{l+1} = alpha_{l+1} (cos th + m s/(l(l+1))) lam_l - beta_{l+1} lam_{l-1},
 //   alpha_L = sqrt((4L^2-1) L^2 / ((L^2-m^2)(L^2-s^2))),  beta_{l+1} = alpha_{l+1}/alpha_l.
 // Its theta-dependence is only through cos(theta), so differentiating it j times
 // with Leibniz's rule gives the derivative recurrence
@@ -32,23 +32,27 @@ template <> struct RealTraits<float> {
   typedef float4 T4;
   static constexpr double H = 32.0;    // rescale when |mantissa| > 2^H
   static constexpr int SB = 64;        // one scale step = 2^SB
+  static constexpr float THR = 0x1p32f;     // 2^H
+  static constexpr float STEP = 0x1p-64f;   // 2^-SB
 };
 template <> struct RealTraits<double> {
   typedef double2 T2;
   typedef double4 T4;
   static constexpr double H = 200.0;
   static constexpr int SB = 400;
+  static constexpr double THR = 0x1p200;
+  static constexpr double STEP = 0x1p-400;
 };
 
-// Coefficient record of the spin-0 stage at index idx(l, m):
-// the coefficient and the recurrence factors of the step l -> l+1.
+// Coefficient record of the spin-0 stage at index idx(l, m): the coefficient
+// times k_l and the factor A_{l+1} of the normalised step l -> l+1.
 template <typename T> struct __align__(4 * sizeof(T)) Rec0 {
-  T re, im, alpha, beta;
+  T re, im, A, pad;
 };
-// Spin-2 stage: c1 = E + iB, c2 = (-1)^(l+m) (E - iB); step factors; m s/(l(l+1)).
+// Spin-2 stage: k_l (E + iB), k_l (-1)^(l+m) (E - iB), A_{l+1} and m s/(l(l+1)).
 template <typename T> struct __align__(4 * sizeof(T)) Rec2 {
   T c1r, c1i, c2r, c2i;
-  T alpha, beta, cterm, pad;
+  T A, cterm, pad0, pad1;
 };
 
 }  // namespace tl

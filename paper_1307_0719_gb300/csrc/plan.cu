@@ -144,7 +144,8 @@ static void free_plan(tl_plan *p) {
   if (!p) return;
   void *ptrs[] = {p->ring.z, p->ring.sint, p->ring.theta, p->ring.phi0, p->ring.log2_sh, p->ring.log2_ch,
                   p->ring.dls, p->ring.dlc, p->ring.nphi, p->ring.inorth, p->ring.first, p->blue.spec,
-                  p->blue.offset, p->blue.mlen, p->lnorm0, p->twiddle, p->rec_T, p->rec_P, p->rec_QU,
+                  p->blue.offset, p->blue.mlen, p->lnorm0, p->twiddle, p->tab0, p->tab2, p->rec_T, p->rec_P,
+                  p->rec_QU,
                   p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->stage_alm, p->stage_out};
   for (void *q : ptrs)
     if (q) cudaFree(q);
@@ -235,11 +236,15 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   const size_t t2 = e2, rec0 = 4 * (size_t)p->elem, rec2 = 8 * (size_t)p->elem;
   const size_t plane = (size_t)p->nrings * (p->mmax + 1) * t2;
   const bool pol = (spins & TL_SPIN_QU) != 0;
+  TRY_CUDA(dalloc(&p->tab0, t2 * na, B));
+  TRY_CUDA(launch_steptab(p, 0, p->tab0, 0));
   TRY_CUDA(dalloc(&p->rec_T, rec0 * na, B));
-  TRY_CUDA(dalloc(&p->rec_P, rec0 * na, B));
+  TRY_CUDA(dalloc(&p->rec_P, t2 * na, B));
   TRY_CUDA(dalloc(&p->d7_T, plane * (order + 1), B));
   TRY_CUDA(dalloc(&p->d7_P, plane * 2, B));
   if (pol) {
+    TRY_CUDA(dalloc(&p->tab2, t2 * na, B));
+    TRY_CUDA(launch_steptab(p, 2, p->tab2, 0));
     TRY_CUDA(dalloc(&p->rec_QU, rec2 * na, B));
     TRY_CUDA(dalloc(&p->d7_Q, plane * (order + 1), B));
     TRY_CUDA(dalloc(&p->d7_U, plane * (order + 1), B));
@@ -247,6 +252,7 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   const int nfield = pol ? 3 : 1;
   TRY_CUDA(dalloc(&p->d3, (size_t)p->elem * nfield * p->nmaps * p->npix, B));
   TRY_CUDA(dalloc(&p->alpha, (size_t)p->elem * 2 * p->npix, B));
+  TRY_CUDA(cudaDeviceSynchronize());
 
   const char *env = getenv("TAYLENS_TIMING");
   p->timing = (env && env[0] == '1') ? 1 : 0;
@@ -313,13 +319,19 @@ static void mark(tl_plan *p, int i, cudaStream_t s) {
   if (p->timing && i < 8) cudaEventRecord(p->ev[i], s);
 }
 
-static tl_status deflection_impl(tl_plan *p, const double *alm_phi, void *ath, void *aph, cudaStream_t s) {
-  TRY_CUDA(launch_prep_spin0(p, alm_phi, p->rec_P, s));
-  TRY_CUDA(launch_legendre_spin0(p, 1, p->rec_P, p->d7_P, s));
+// alpha from the phi planes (j = 0, 1) already in d7_P
+static tl_status deflection_fft(tl_plan *p, void *ath, void *aph, cudaStream_t s) {
   const double L = deriv_norm(p);
   MapJob jobs[2] = {{3, 1, 0, 0, L, ath}, {3, 0, 1, 1, L, aph}};
   TRY_CUDA(launch_ringfft(p, jobs, 2, 2, s));
   return TL_OK;
+}
+
+// stand-alone deflection: phi through the spin-0 stage alone (uses rec_T)
+static tl_status deflection_impl(tl_plan *p, const double *alm_phi, void *ath, void *aph, cudaStream_t s) {
+  TRY_CUDA(launch_prep_spin0(p, alm_phi, nullptr, s));
+  TRY_CUDA(launch_legendre_spin0(p, 1, false, p->d7_P, nullptr, s));
+  return deflection_fft(p, ath, aph, s);
 }
 
 extern "C" tl_status tl_deflection(tl_plan *p, const double *alm_phi, void *ath, void *aph, void *stream) {
@@ -346,19 +358,20 @@ extern "C" tl_status tl_synth_derivs(tl_plan *p, const double *alm, int spin, vo
   char *base = (char *)maps;
   const size_t mapb = (size_t)p->elem * p->npix;
   if (spin == 0) {
-    TRY_CUDA(launch_prep_spin0(p, alm, p->rec_T, s));
-    TRY_CUDA(launch_legendre_spin0(p, p->order, p->rec_T, p->d7_T, s));
+    TRY_CUDA(launch_prep_spin0(p, alm, nullptr, s));
+    TRY_CUDA(launch_legendre_spin0(p, p->order, false, p->d7_T, nullptr, s));
     for (int n = 0; n <= p->order; ++n)
       for (int j = 0; j <= n; ++j) {
         int k = n - j;
         jobs.push_back(MapJob{0, j, k, 0, pow(L, n), base + mapb * (n * (n + 1) / 2 + j)});
       }
   } else {
-    TRY_CUDA(launch_prep_spin2(p, alm, alm + 2 * na, p->rec_QU, s));
-    TRY_CUDA(launch_legendre_spin2(p, p->order, p->rec_QU, p->d7_Q, p->d7_U, s));
-    for (int f = 0; f < 2; ++f)
-      for (int n = 0; n <= p->order; ++n)
-        for (int j = 0; j <= n; ++j) {
+    TRY_CUDA(launch_prep_spin2(p, alm, alm + 2 * na, s));
+    TRY_CUDA(launch_legendre_spin2(p, p->order, s));
+    // Q and U of the same (j, k) share one packed transform (similar magnitudes)
+    for (int n = 0; n <= p->order; ++n)
+      for (int j = 0; j <= n; ++j)
+        for (int f = 0; f < 2; ++f) {
           int k = n - j;
           jobs.push_back(MapJob{1 + f, j, k, 0, pow(L, n),
                                 base + mapb * (f * p->nmaps + n * (n + 1) / 2 + j)});
@@ -379,40 +392,50 @@ extern "C" tl_status tl_lens(tl_plan *p, const double *alm_T, const double *alm_
   cudaStream_t s = (cudaStream_t)stream;
   const size_t mapb = (size_t)p->elem * p->npix;
   p->nstage = 0;
+  void *ath = p->alpha, *aph = (char *)p->alpha + mapb;
   mark(p, 0, s);
-  // 1. deflection
-  if (alm_phi) {
-    tl_status st = deflection_impl(p, alm_phi, p->alpha, (char *)p->alpha + mapb, s);
+  // 1. spin-0 Legendre stage: T with all derivative orders; the lensing potential
+  //    shares its basis for j <= 1 (needs order >= 1, else it runs on its own)
+  const bool fuse = alm_phi && p->order >= 1;
+  if (alm_phi && !fuse) {
+    tl_status st = deflection_impl(p, alm_phi, ath, aph, s);
     if (st != TL_OK) return st;
-  } else {
+  }
+  TRY_CUDA(launch_prep_spin0(p, alm_T, fuse ? alm_phi : nullptr, s));
+  mark(p, 1, s);
+  TRY_CUDA(launch_legendre_spin0(p, p->order, fuse, p->d7_T, p->d7_P, s));
+  mark(p, 2, s);
+  // 2. deflection alpha = grad phi at the pixel centres
+  if (fuse) {
+    tl_status st = deflection_fft(p, ath, aph, s);
+    if (st != TL_OK) return st;
+  } else if (!alm_phi) {
     TRY_CUDA(cudaMemsetAsync(p->alpha, 0, 2 * mapb, s));
   }
-  mark(p, 1, s);
-  // 2. Legendre stage of the unlensed fields
-  TRY_CUDA(launch_prep_spin0(p, alm_T, p->rec_T, s));
-  TRY_CUDA(launch_legendre_spin0(p, p->order, p->rec_T, p->d7_T, s));
-  mark(p, 2, s);
-  if (pol) {
-    TRY_CUDA(launch_prep_spin2(p, alm_E, alm_B, p->rec_QU, s));
-    TRY_CUDA(launch_legendre_spin2(p, p->order, p->rec_QU, p->d7_Q, p->d7_U, s));
-  }
   mark(p, 3, s);
-  // 3. ring FFTs into Taylor-ready maps: d_th^j d_ph^k s / (j! k! L^(j+k))
+  // 3. spin-2 Legendre stage
+  if (pol) TRY_CUDA(launch_prep_spin2(p, alm_E, alm_B, s));
+  mark(p, 4, s);
+  if (pol) TRY_CUDA(launch_legendre_spin2(p, p->order, s));
+  mark(p, 5, s);
+  // 4. ring FFTs into Taylor-ready maps: d_th^j d_ph^k s / (j! k! L^(j+k))
   std::vector<MapJob> jobs;
   const int nf = pol ? 3 : 1;
-  for (int f = 0; f < nf; ++f)
+  // T maps pair among themselves in (j, k) order; Q and U of the same (j, k) pair
+  for (int f = 0; f < nf; f += (f == 0 ? 1 : 2))
     for (int n = 0; n <= p->order; ++n)
-      for (int j = 0; j <= n; ++j) {
-        int k = n - j;
-        jobs.push_back(MapJob{f, j, k, 0, 1.0 / (fact(j) * fact(k)),
-                              (char *)p->d3 + mapb * (f * p->nmaps + n * (n + 1) / 2 + j)});
-      }
+      for (int j = 0; j <= n; ++j)
+        for (int g = f; g < (f == 0 ? 1 : 3); ++g) {
+          int k = n - j;
+          jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)),
+                                (char *)p->d3 + mapb * (g * p->nmaps + n * (n + 1) / 2 + j)});
+        }
   TRY_CUDA(launch_ringfft(p, jobs.data(), (int)jobs.size(), p->order + 1, s));
-  mark(p, 4, s);
-  // 4. gather + Taylor + rotate
+  mark(p, 6, s);
+  // 5. gather + Taylor + rotate
   TRY_CUDA(launch_gather(p, p->alpha, p->d3, T_out, pol ? Q_out : nullptr, pol ? U_out : nullptr, s));
-  mark(p, 5, s);
-  p->nstage = p->timing ? 5 : 0;
+  mark(p, 7, s);
+  p->nstage = p->timing ? 7 : 0;
   return TL_OK;
 }
 

@@ -196,8 +196,12 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   const JobDev JB = hasb ? jobs.job[jb] : jobs.job[ja];
   const T2 *FA = (const T2 *)ps.base[JA.plane] + (size_t)JA.j * plane_len + (size_t)r * (mmax + 1);
   const T2 *FB = (const T2 *)ps.base[JB.plane] + (size_t)JB.j * plane_len + (size_t)r * (mmax + 1);
-  const T wa = (T)(JA.scale * (JA.div_sint ? 1.0 / rt.sint[r] : 1.0));
-  const T wb = hasb ? (T)(JB.scale * (JB.div_sint ? 1.0 / rt.sint[r] : 1.0)) : (T)0;
+  // both packed maps are transformed in the normalised units of the Legendre stage
+  // (similar magnitudes, so the shared transform's rounding does not leak from a
+  // large map into a small one); each job's scale is applied on output
+  const T wa = (T)(JA.div_sint ? 1.0 / rt.sint[r] : 1.0);
+  const T wb = hasb ? (T)(JB.div_sint ? 1.0 / rt.sint[r] : 1.0) : (T)0;
+  const T sa = (T)JA.scale, sb = (T)JB.scale;
 
   // ---- fold m modulo N into the Hermitian spectrum Z_t, stored at Y[(t%4)*ni + t/4]
   // chunks: C threads share one residue class when N < nth
@@ -280,15 +284,15 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
     ib1.y = b1.x;
     T2 X0 = cadd(a0, b0), X2 = csub(a0, b0);
     T2 X1 = cadd(a1, ib1), X3 = csub(a1, ib1);
-    outA[p1] = X0.x;
-    outA[p1 + ni] = X1.x;
-    outA[p1 + 2 * ni] = X2.x;
-    outA[p1 + 3 * ni] = X3.x;
+    outA[p1] = sa * X0.x;
+    outA[p1 + ni] = sa * X1.x;
+    outA[p1 + 2 * ni] = sa * X2.x;
+    outA[p1 + 3 * ni] = sa * X3.x;
     if (hasb) {
-      outB[p1] = X0.y;
-      outB[p1 + ni] = X1.y;
-      outB[p1 + 2 * ni] = X2.y;
-      outB[p1 + 3 * ni] = X3.y;
+      outB[p1] = sb * X0.y;
+      outB[p1 + ni] = sb * X1.y;
+      outB[p1 + 2 * ni] = sb * X2.y;
+      outB[p1 + 3 * ni] = sb * X3.y;
     }
   }
 }
