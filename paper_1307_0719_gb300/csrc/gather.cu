@@ -8,12 +8,26 @@
 //     so the sum is a bivariate polynomial in (L dth, L dph), L = lmax + 1
 //  5. Q' + iU' = e^{-2 i beta} (Q + iU), beta the angle at x' of e_theta(x)
 //     carried to x' by parallel transport along the geodesic               (Eq. 2, R)
-// Pixel geometry and the rotation angle are computed in double precision.
+//
+// Geometry. The double-precision form evaluates x' as a unit vector and takes
+// atan2 of its components. The mixed form (float maps) works in increments: in a
+// frame turned to the pixel's longitude, the displaced point is
+//     X = s cos d + z a_th sinc d,  Y = a_ph sinc d,  Z - z = -z (1 - cos d) - s a_th sinc d,
+// and  phi' - phi_p = atan2(Y, X),
+//      th' - th_p   = atan2(a_th sinc d + z w, cos d + s w),  w = Y^2 / (rho + X),  rho = |(X, Y)|,
+// which carry no cancellation, so float arithmetic gives them to ~1e-7 relative.
+// The pixel lookup then runs in double on z_p + dz and phi_p + dphi (additions,
+// floor and one square root), and the offsets to the expansion centre subtract
+// centre differences taken from the double ring table. Rings with sin(theta) < 0.1
+// (where rho + X can cancel for a point carried over the pole) and deflections
+// above 0.02 rad use the double form.
 #include <math.h>
 
 #include "legendre.cuh"
 
 namespace tl {
+
+static constexpr double kPiD = 3.14159265358979323846;
 
 struct PixLoc {
   int ring;  // 0-based ring index
@@ -48,13 +62,13 @@ __device__ __forceinline__ PixLoc pix2loc(long long p, int nside, long long npix
 
 __device__ __forceinline__ long long floordiv2(long long a) { return (a >= 0) ? a / 2 : -((1 - a) / 2); }
 
-// HEALPix ang2pix (RING) from z = cos(theta), s = sin(theta) >= 0 and phi in
-// [0, 2pi): belt cells are bounded by the lines N(t + 1/2) -+ (3/4) N z in Z
-// (t = 2 phi / pi); cap cells by tp * tmp and (1 - tp) * tmp in Z with
-// tmp = N sqrt(3 (1 - |z|)), tp = frac(t) (Gorski et al. 2005).
-__device__ __forceinline__ PixLoc ang2loc(double z, double s, double phi, int nside) {
+// HEALPix ang2pix (RING) from z = cos(theta), omz = 1 - |z| and phi in [0, 2pi):
+// belt cells are bounded by the lines N(t + 1/2) -+ (3/4) N z in Z (t = 2 phi / pi);
+// cap cells by tp * tmp and (1 - tp) * tmp in Z with tmp = N sqrt(3 (1 - |z|)),
+// tp = frac(t) (Gorski et al. 2005).
+__device__ __forceinline__ PixLoc ang2loc(double z, double omz, double phi, int nside) {
   const double N = (double)nside;
-  double t = phi * (2.0 / 3.14159265358979323846);
+  double t = phi * (2.0 / kPiD);
   if (t >= 4.0) t -= 4.0;
   if (t < 0.0) t += 4.0;
   const double za = fabs(z);
@@ -75,8 +89,7 @@ __device__ __forceinline__ PixLoc ang2loc(double z, double s, double phi, int ns
     L.idx = (int)ip;
   } else {
     const double tp = t - floor(t);
-    const double omz = s * s / (1.0 + za);
-    const double tmp = N * sqrt(3.0 * omz);
+    const double tmp = N * sqrt(3.0 * (omz > 0.0 ? omz : 0.0));
     long long jp = (long long)floor(tp * tmp);
     long long jm = (long long)floor((1.0 - tp) * tmp);
     long long ir = jp + jm + 1;
@@ -88,6 +101,120 @@ __device__ __forceinline__ PixLoc ang2loc(double z, double s, double phi, int ns
     L.idx = (int)ip;
   }
   return L;
+}
+
+__device__ __forceinline__ double ring_phi(const RingTable &rt, int ring, int idx) {
+  return rt.phi0[ring] + 2.0 * kPiD * (double)idx / (double)rt.nphi[ring];
+}
+
+struct Geo {
+  long long q;
+  double dth, dph;  // offsets to the expansion centre
+  double c2b, s2b;  // cos 2 beta, sin 2 beta
+};
+
+// Double-precision geometry (any pixel, any deflection).
+__device__ __forceinline__ void geo64(const RingTable &rt, int nside, double z, double s, double phi, double ath,
+                                      double aph, bool rot, Geo &g) {
+  const double d = hypot(ath, aph);
+  double sp, cp;
+  sincos(phi, &sp, &cp);
+  double sd, cd;
+  sincos(d, &sd, &cd);
+  const double sinc = sd / d;
+  // n = (s cp, s sp, z), e_th = (z cp, z sp, -s), e_ph = (-sp, cp, 0)
+  const double ux = ath * z * cp - aph * sp, uy = ath * z * sp + aph * cp, uz = -ath * s;
+  const double nx = cd * s * cp + sinc * ux;
+  const double ny = cd * s * sp + sinc * uy;
+  const double nz = cd * z + sinc * uz;
+  const double s2 = hypot(nx, ny);
+  double phi2 = atan2(ny, nx);
+  if (phi2 < 0.0) phi2 += 2.0 * kPiD;
+  const double th2 = atan2(s2, nz);
+  const PixLoc lq = ang2loc(nz, s2 * s2 / (1.0 + fabs(nz)), phi2, nside);
+  g.q = rt.first[lq.ring] + lq.idx;
+  g.dth = th2 - rt.theta[lq.ring];
+  double dph = phi2 - ring_phi(rt, lq.ring, lq.idx);
+  if (dph >= kPiD) dph -= 2.0 * kPiD;
+  if (dph < -kPiD) dph += 2.0 * kPiD;
+  g.dph = dph;
+  g.c2b = 1.0;
+  g.s2b = 0.0;
+  if (rot) {
+    // e_theta(x) transported to x' (rotation about n x u by d):
+    // t = (1 - cos^2(delta) omc) e_th - sin(delta) cos(delta) omc e_ph - sin(d) cos(delta) n
+    const double cdl = ath / d, sdl = aph / d;
+    const double sh = sin(0.5 * d);
+    const double omc = 2.0 * sh * sh;
+    const double ct = 1.0 - cdl * cdl * omc, cph = -sdl * cdl * omc, cn = -sd * cdl;
+    const double tx = ct * z * cp + cph * (-sp) + cn * s * cp;
+    const double ty = ct * z * sp + cph * cp + cn * s * sp;
+    const double tz = ct * (-s) + cn * z;
+    double cp2 = 1.0, sp2 = 0.0;
+    if (s2 > 0.0) {
+      cp2 = nx / s2;
+      sp2 = ny / s2;
+    }
+    const double cb = tx * nz * cp2 + ty * nz * sp2 - tz * s2;  // t . e_theta'
+    const double sb = -tx * sp2 + ty * cp2;                      // t . e_phi'
+    const double nrm = cb * cb + sb * sb;
+    g.c2b = (cb * cb - sb * sb) / nrm;
+    g.s2b = 2.0 * cb * sb / nrm;
+  }
+}
+
+// Increment-form geometry in float (see the header comment); pixel lookup in double.
+__device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, double z, double s, double phi,
+                                      float ath, float aph, bool rot, Geo &g) {
+  const float d2 = ath * ath + aph * aph;
+  const float d = sqrtf(d2);
+  float sh, ch;
+  sincosf(0.5f * d, &sh, &ch);
+  const float hsinc = (d > 0.0f) ? sh / (0.5f * d) : 1.0f;  // sinc(d/2)
+  const float sinc = hsinc * ch;                             // sin(d)/d
+  const float omc = 2.0f * sh * sh;                          // 1 - cos d
+  const float zf = (float)z, sf = (float)s;
+  const float X = sf * (1.0f - omc) + zf * ath * sinc;
+  const float Y = aph * sinc;
+  const float dz = -zf * omc - sf * ath * sinc;
+  const float rho = sqrtf(X * X + Y * Y);
+  const float w = Y * Y / (rho + X);
+  const float dthp = atan2f(ath * sinc + zf * w, (1.0f - omc) + sf * w);  // th' - th_p
+  const float dphp = atan2f(Y, X);                                        // phi' - phi_p
+  // pixel lookup in double on the accurate increments
+  const double z2 = z + (double)dz;
+  const double omz_p = s * s / (1.0 + fabs(z));
+  const double omz2 = omz_p - (z >= 0.0 ? (double)dz : -(double)dz);
+  double phi2 = phi + (double)dphp;
+  if (phi2 >= 2.0 * kPiD) phi2 -= 2.0 * kPiD;
+  if (phi2 < 0.0) phi2 += 2.0 * kPiD;
+  const PixLoc lq = ang2loc(z2, omz2, phi2, nside);
+  g.q = rt.first[lq.ring] + lq.idx;
+  g.dth = (double)(dthp - (float)(rt.theta[lq.ring] - rt.theta[ring]));
+  double dc = ring_phi(rt, lq.ring, lq.idx) - phi;  // centre offset, wrapped
+  if (dc >= kPiD) dc -= 2.0 * kPiD;
+  if (dc < -kPiD) dc += 2.0 * kPiD;
+  float dph = dphp - (float)dc;
+  if (dph >= (float)kPiD) dph -= 2.0f * (float)kPiD;
+  if (dph < -(float)kPiD) dph += 2.0f * (float)kPiD;
+  g.dph = (double)dph;
+  g.c2b = 1.0;
+  g.s2b = 0.0;
+  if (rot) {
+    // t = (1 - a_th^2 h) e_th - a_ph a_th h e_ph - a_th sinc n, h = (1 - cos d)/d^2,
+    // in the frame turned to phi_p: e_th = (z, 0, -s), e_ph = (0, 1, 0), n = (s, 0, z)
+    const float h = 0.5f * hsinc * hsinc;
+    const float ct = 1.0f - ath * ath * h;
+    const float tx = ct * zf - ath * sinc * sf;
+    const float ty = -aph * ath * h;
+    const float tz = -ct * sf - ath * sinc * zf;
+    const float Z = zf + dz;
+    const float cb = Z * (tx * X + ty * Y) / rho - tz * rho;  // t . e_theta'
+    const float sb = (-tx * Y + ty * X) / rho;                // t . e_phi'
+    const float nrm = cb * cb + sb * sb;
+    g.c2b = (double)((cb * cb - sb * sb) / nrm);
+    g.s2b = (double)(2.0f * cb * sb / nrm);
+  }
 }
 
 template <typename T, int ORDER>
@@ -114,70 +241,34 @@ __global__ void __launch_bounds__(256) gather_kernel(RingTable rt, int nside, lo
                                                      const T *__restrict__ d3, T *__restrict__ Tout,
                                                      T *__restrict__ Qout, T *__restrict__ Uout, int rotate) {
   constexpr int NM = (ORDER + 1) * (ORDER + 2) / 2;
+  constexpr bool FAST = sizeof(T) == 4;
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npix) return;
   const PixLoc loc = pix2loc(p, nside, npix);
   const double z = rt.z[loc.ring], s = rt.sint[loc.ring];
-  const double phi = rt.phi0[loc.ring] + 2.0 * 3.14159265358979323846 * (double)loc.idx / (double)rt.nphi[loc.ring];
-  const double ath = (double)a_th[p], aph = (double)a_ph[p];
-  const double d = hypot(ath, aph);
+  const double phi = ring_phi(rt, loc.ring, loc.idx);
+  const T ath = a_th[p], aph = a_ph[p];
+  const bool rot = POL && rotate;
 
-  long long q = p;
-  double dth = 0.0, dph = 0.0, c2b = 1.0, s2b = 0.0;
-  if (d > 0.0) {
-    double sp, cp;
-    sincos(phi, &sp, &cp);
-    double sd, cd;
-    sincos(d, &sd, &cd);
-    const double sinc = sd / d;
-    // n = (s cp, s sp, z), e_th = (z cp, z sp, -s), e_ph = (-sp, cp, 0)
-    const double ux = ath * z * cp - aph * sp, uy = ath * z * sp + aph * cp, uz = -ath * s;
-    const double nx = cd * s * cp + sinc * ux;
-    const double ny = cd * s * sp + sinc * uy;
-    const double nz = cd * z + sinc * uz;
-    const double s2 = hypot(nx, ny);
-    double phi2 = atan2(ny, nx);
-    if (phi2 < 0.0) phi2 += 2.0 * 3.14159265358979323846;
-    const double th2 = atan2(s2, nz);
-    const PixLoc lq = ang2loc(nz, s2, phi2, nside);
-    q = rt.first[lq.ring] + lq.idx;
-    const double thq = rt.theta[lq.ring];
-    const double phq = rt.phi0[lq.ring] + 2.0 * 3.14159265358979323846 * (double)lq.idx / (double)rt.nphi[lq.ring];
-    dth = th2 - thq;
-    dph = phi2 - phq;
-    if (dph >= 3.14159265358979323846) dph -= 2.0 * 3.14159265358979323846;
-    if (dph < -3.14159265358979323846) dph += 2.0 * 3.14159265358979323846;
-    if (POL && rotate) {
-      // e_theta(x) transported to x' (rotation about n x u by d):
-      // t = (1 - cos^2(delta) omc) e_th - sin(delta) cos(delta) omc e_ph - sin(d) cos(delta) n
-      const double cdl = ath / d, sdl = aph / d;
-      const double sh = sin(0.5 * d);
-      const double omc = 2.0 * sh * sh;
-      const double ct = 1.0 - cdl * cdl * omc, cph = -sdl * cdl * omc, cn = -sd * cdl;
-      const double tx = ct * z * cp + cph * (-sp) + cn * s * cp;
-      const double ty = ct * z * sp + cph * cp + cn * s * sp;
-      const double tz = ct * (-s) + cn * z;
-      // basis at x'
-      double cp2 = 1.0, sp2 = 0.0;
-      if (s2 > 0.0) {
-        cp2 = nx / s2;
-        sp2 = ny / s2;
-      }
-      const double et2x = nz * cp2, et2y = nz * sp2, et2z = -s2;
-      const double cb = tx * et2x + ty * et2y + tz * et2z;  // t . e_theta'
-      const double sb = -tx * sp2 + ty * cp2;                // t . e_phi'
-      const double nrm = cb * cb + sb * sb;
-      c2b = (cb * cb - sb * sb) / nrm;
-      s2b = 2.0 * cb * sb / nrm;
-    }
+  Geo g;
+  g.q = p;
+  g.dth = g.dph = 0.0;
+  g.c2b = 1.0;
+  g.s2b = 0.0;
+  if (ath != (T)0 || aph != (T)0) {
+    if (FAST && s >= 0.1 && (float)(ath * ath + aph * aph) < 4e-4f)
+      geo32(rt, nside, loc.ring, z, s, phi, (float)ath, (float)aph, rot, g);
+    else
+      geo64(rt, nside, z, s, phi, (double)ath, (double)aph, rot, g);
   }
-  const T x = (T)(Lnorm * dth), y = (T)(Lnorm * dph);
-  Tout[p] = taylor_eval<T, ORDER>(d3, npix, q, x, y);
+  const T x = (T)(Lnorm * g.dth), y = (T)(Lnorm * g.dph);
+  Tout[p] = taylor_eval<T, ORDER>(d3, npix, g.q, x, y);
   if (POL) {
-    const T qv = taylor_eval<T, ORDER>(d3 + (long long)NM * npix, npix, q, x, y);
-    const T uv = taylor_eval<T, ORDER>(d3 + 2LL * NM * npix, npix, q, x, y);
-    Qout[p] = (T)(c2b * (double)qv + s2b * (double)uv);
-    Uout[p] = (T)(-s2b * (double)qv + c2b * (double)uv);
+    const T qv = taylor_eval<T, ORDER>(d3 + (long long)NM * npix, npix, g.q, x, y);
+    const T uv = taylor_eval<T, ORDER>(d3 + 2LL * NM * npix, npix, g.q, x, y);
+    const T c2 = (T)g.c2b, s2 = (T)g.s2b;
+    Qout[p] = c2 * qv + s2 * uv;
+    Uout[p] = -s2 * qv + c2 * uv;
   }
 }
 
@@ -190,7 +281,6 @@ static cudaError_t gather_t(const tl_plan *p, const void *alpha, const void *d3,
   const T *aph = ath + p->npix;
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
   const int rot = (p->flags & TL_ROTATE) ? 1 : 0;
-  // T-only plans keep the T maps at field 0; QU-only plans store Q, U at fields 1, 2
   if (pol)
     gather_kernel<T, ORDER, true><<<(unsigned)blocks, threads, 0, s>>>(
         p->ring, p->nside, p->npix, (double)(p->lmax + 1), ath, aph, (const T *)d3, (T *)Tq, (T *)Q, (T *)U, rot);
