@@ -95,6 +95,22 @@ cudaError_t launch_bluestein_setup(tl_plan *p, cudaStream_t s);
 cudaError_t launch_gather(const tl_plan *p, const void *alpha, const void *d3, void *T, void *Q,
                           void *U, cudaStream_t s);
 
+// host table builders (tables.cu); arrays sized by the caller:
+// rings: 4 nside - 1 entries (dls, dlc: (4 nside - 1) * (TL_MAX_NDER + 1)),
+// lnorm0: lmax + 1, Bluestein off/ml: nside + 1, twiddles: TW doubles
+struct RingHostView {
+  double *z, *sint, *theta, *phi0, *lsh, *lch, *dls, *dlc;
+  int *nphi, *inorth;
+  long long *first;
+};
+void host_ring_tables(int nside, const RingHostView &h);
+void host_lnorm0(int lmax, double *out);
+long long host_bluestein_layout(int nside, long long *off, int *ml, int *maxm);
+int host_twiddle_len(int nside, int maxm);
+void host_twiddles(int TW, double *tw);
+size_t ringfft_smem_bytes(const tl_plan *p);
+cudaError_t launch_bluestein_setup_impl(tl_plan *p, const double2 *tw64, cudaStream_t s);
+
 // normalisation of theta derivatives inside the Legendre stage: lambda^(j) / L^j
 inline double deriv_norm(const tl_plan *p) { return (double)(p->lmax + 1); }
 
@@ -105,3 +121,4 @@ inline double deriv_norm(const tl_plan *p) { return (double)(p->lmax + 1); }
     cudaError_t _e = (call);                      \
     if (_e != cudaSuccess) return _e;             \
   } while (0)
+

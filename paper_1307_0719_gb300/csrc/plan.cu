@@ -8,14 +8,7 @@
 
 #include "legendre.cuh"
 
-namespace tl {
-size_t ringfft_smem_bytes(const tl_plan *p);
-cudaError_t launch_bluestein_setup_impl(tl_plan *p, const double2 *tw64, cudaStream_t s);
-}  // namespace tl
-
 using namespace tl;
-
-static const double kPi = 3.14159265358979323846;
 
 static tl_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return TL_OK;
@@ -44,26 +37,7 @@ extern "C" const char *tl_status_string(tl_status s) {
 }
 
 // ---------------------------------------------------------------------------
-// host tables
-
-// Polynomial in one variable, coefficients in increasing degree.
-typedef std::vector<double> Poly;
-static Poly poly_deriv(const Poly &p) {
-  Poly d(p.size() > 1 ? p.size() - 1 : 1, 0.0);
-  for (size_t i = 1; i < p.size(); ++i) d[i - 1] = p[i] * (double)i;
-  return d;
-}
-static Poly poly_mul(const Poly &a, const Poly &b) {
-  Poly r(a.size() + b.size() - 1, 0.0);
-  for (size_t i = 0; i < a.size(); ++i)
-    for (size_t j = 0; j < b.size(); ++j) r[i + j] += a[i] * b[j];
-  return r;
-}
-static double poly_eval(const Poly &p, double x) {
-  double r = 0.0;
-  for (size_t i = p.size(); i-- > 0;) r = r * x + p[i];
-  return r;
-}
+// host tables (tables.cu) gathered into vectors
 
 struct HostRings {
   std::vector<double> z, sint, theta, phi0, lsh, lch, dls, dlc;
@@ -71,57 +45,14 @@ struct HostRings {
   std::vector<long long> first;
 };
 
-// HEALPix RING rings (Gorski et al. 2005) plus what the Legendre seeds need:
-// log2 sin(th/2), log2 cos(th/2) and d^k/dth^k of ln sin(th/2), ln cos(th/2).
-// With w = cot(th/2): d/dth ln sin(th/2) = w/2 and dw/dth = -(1+w^2)/2; with
-// v = tan(th/2): d/dth ln cos(th/2) = -v/2 and dv/dth = (1+v^2)/2.
 static void build_rings(int N, HostRings &h) {
-  const int nr = 4 * N - 1;
-  const long long npix = 12LL * N * N, ncap = 2LL * N * (N - 1);
-  const int K = TL_MAX_NDER + 1;
-  std::vector<Poly> ps(K + 1), pc(K + 1);
-  ps[1] = Poly{0.0, 0.5};
-  pc[1] = Poly{0.0, -0.5};
-  for (int k = 1; k < K; ++k) {
-    ps[k + 1] = poly_mul(poly_deriv(ps[k]), Poly{-0.5, 0.0, -0.5});
-    pc[k + 1] = poly_mul(poly_deriv(pc[k]), Poly{0.5, 0.0, 0.5});
-  }
+  const size_t nr = 4 * (size_t)N - 1, K = TL_MAX_NDER + 1;
   h.z.resize(nr); h.sint.resize(nr); h.theta.resize(nr); h.phi0.resize(nr);
-  h.lsh.resize(nr); h.lch.resize(nr); h.dls.resize((size_t)nr * K); h.dlc.resize((size_t)nr * K);
+  h.lsh.resize(nr); h.lch.resize(nr); h.dls.resize(nr * K); h.dlc.resize(nr * K);
   h.nphi.resize(nr); h.inorth.resize(nr); h.first.resize(nr);
-  for (int r = 0; r < nr; ++r) {
-    const int i = r + 1;
-    const int in = i < 4 * N - i ? i : 4 * N - i;
-    double omz_m, omz_p;  // 1 - z and 1 + z, each without cancellation
-    double z;
-    if (in < N) {
-      const double omz = (double)in * in / (3.0 * N * N);
-      if (i < 2 * N) { z = 1.0 - omz; omz_m = omz; omz_p = 2.0 - omz; }
-      else { z = -(1.0 - omz); omz_m = 2.0 - omz; omz_p = omz; }
-      h.nphi[r] = 4 * in;
-      h.phi0[r] = kPi / (4.0 * in);
-    } else {
-      z = 4.0 / 3.0 - 2.0 * i / (3.0 * N);
-      omz_m = 1.0 - z;
-      omz_p = 1.0 + z;
-      h.nphi[r] = 4 * N;
-      h.phi0[r] = ((i - N) % 2 == 0) ? kPi / (4.0 * N) : 0.0;
-    }
-    h.inorth[r] = in;
-    h.z[r] = z;
-    h.sint[r] = sqrt(omz_m * omz_p);
-    h.theta[r] = (z >= 0.0) ? 2.0 * asin(sqrt(0.5 * omz_m)) : kPi - 2.0 * asin(sqrt(0.5 * omz_p));
-    h.lsh[r] = 0.5 * log2(0.5 * omz_m);
-    h.lch[r] = 0.5 * log2(0.5 * omz_p);
-    const double w = sqrt(omz_p / omz_m), v = sqrt(omz_m / omz_p);
-    for (int k = 1; k <= K; ++k) {
-      h.dls[(size_t)r * K + (k - 1)] = poly_eval(ps[k], w);
-      h.dlc[(size_t)r * K + (k - 1)] = poly_eval(pc[k], v);
-    }
-    if (i < N) h.first[r] = 2LL * i * (i - 1);
-    else if (i <= 3 * N) h.first[r] = ncap + (long long)(i - N) * 4 * N;
-    else { const long long is = 4LL * N - i; h.first[r] = npix - 2 * is * (is + 1); }
-  }
+  RingHostView v{h.z.data(), h.sint.data(), h.theta.data(), h.phi0.data(), h.lsh.data(), h.lch.data(),
+                 h.dls.data(), h.dlc.data(), h.nphi.data(), h.inorth.data(), h.first.data()};
+  host_ring_tables(N, v);
 }
 
 template <typename V>
@@ -174,29 +105,14 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   TRY_CUDA(upload(&p->ring.nphi, h.nphi, B)); TRY_CUDA(upload(&p->ring.inorth, h.inorth, B));
   TRY_CUDA(upload(&p->ring.first, h.first, B));
 
-  // log2 of sqrt((2m+1)/(4 pi)) sqrt(C(2m, m)) = log2 sqrt((2m+1)/4pi) + m + 1/2 sum_k log2((2k-1)/(2k))
   std::vector<double> ln0(lmax + 1);
-  double acc = 0.0;
-  for (int m = 0; m <= lmax; ++m) {
-    if (m > 0) acc += log1p(-1.0 / (2.0 * m)) / log(2.0);
-    ln0[m] = 0.5 * log2((2.0 * m + 1.0) / (4.0 * kPi)) + m + 0.5 * acc;
-  }
+  host_lnorm0(lmax, ln0.data());
   TRY_CUDA(upload(&p->lnorm0, ln0, B));
 
-  // Bluestein lengths: cap rings use sub-transforms of length i = 1 .. nside-1
-  std::vector<long long> off(nside + 1, -1);
-  std::vector<int> ml(nside + 1, 0);
-  long long tot = 0;
+  std::vector<long long> off(nside + 1);
+  std::vector<int> ml(nside + 1);
   int maxm = 0;
-  for (int i = 1; i < nside; ++i) {
-    if ((i & (i - 1)) == 0) continue;
-    int M = 1;
-    while (M < 2 * i - 1) M <<= 1;
-    off[i] = tot;
-    ml[i] = M;
-    tot += M;
-    if (M > maxm) maxm = M;
-  }
+  const long long tot = host_bluestein_layout(nside, off.data(), ml.data(), &maxm);
   p->blue_maxm = maxm;
   TRY_CUDA(upload(&p->blue.offset, off, B));
   TRY_CUDA(upload(&p->blue.mlen, ml, B));
@@ -204,15 +120,10 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   TRY_CUDA(dalloc(&p->blue.spec, e2 * (size_t)(tot > 0 ? tot : 1), B));
 
   // twiddles e^{-2 pi i k / TW}, k < TW/2, for every power-of-two length used
-  int TW = 2;
-  while (TW < maxm || TW < nside) TW <<= 1;
+  const int TW = host_twiddle_len(nside, maxm);
   p->tw_len = TW;
   std::vector<double> tw64(TW);  // interleaved (re, im)
-  for (int k = 0; k < TW / 2; ++k) {
-    double a = 2.0 * kPi * (double)k / (double)TW;
-    tw64[2 * k] = cos(a);
-    tw64[2 * k + 1] = -sin(a);
-  }
+  host_twiddles(TW, tw64.data());
   double *dtw64 = nullptr;
   {
     size_t dummy = 0;
@@ -286,7 +197,7 @@ extern "C" tl_status tl_plan_create(int nside, int lmax, int order, int spins, i
       while (M < 2 * i - 1) M <<= 1;
       if (M > maxm) maxm = M;
     }
-    probe.blue_maxm = maxm;
+    probe.blue_maxm = maxm;  // as host_bluestein_layout, without its tables
     if (ringfft_smem_bytes(&probe) > 227 * 1024) return TL_ERR_UNSUPPORTED;
   }
   tl_plan *p = (tl_plan *)calloc(1, sizeof(tl_plan));
