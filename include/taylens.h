@@ -126,6 +126,30 @@ tl_status tl_lens_host(tl_plan *plan, const double *alm_T, const double *alm_E,
                        const double *alm_B, const double *alm_phi, void *T_out, void *Q_out,
                        void *U_out, void *stream);
 
+/*
+ * tl_deflection without any allocation, for callers that cannot allocate device
+ * memory while they run (code inside a memory pool or allocator of its own,
+ * or a process whose device memory is fixed up front).
+ * The paper has no counterpart: this is a deployment variant of tl_deflection
+ * and computes the same thing (alpha = grad phi at every pixel centre).
+ *   nside      power of two, 1 .. 128
+ *   lmax       1 .. min(4 nside, 256)
+ *   precision  TL_FP64 (double maps) or TL_MIXED_FP32 (float maps)
+ *   alm_phi, a_theta, a_phi   device, 16-byte aligned, as in tl_deflection
+ * Larger sizes return TL_ERR_ARG.
+ * All tables and working memory sit in one fixed 8 MiB device array inside the
+ * library (held by every GPU that loads it, until the process exits); no call
+ * allocates device or host memory. The first call on a device, and any call
+ * with a different (nside, lmax, precision) than the previous call on that
+ * device, first lays the tables out in that array with synchronous copies and
+ * kernels on the legacy default stream: make that first call before any stream
+ * capture. Every call on a device shares the array and overwrites what the
+ * previous call left there, so calls that overlap on the GPU (other streams,
+ * other host threads) race; issue them one after another. Not thread-safe.
+ */
+tl_status tl_deflection_noalloc(int nside, int lmax, int precision, const double *alm_phi,
+                                void *a_theta, void *a_phi, void *stream);
+
 /* Human-readable text for a status code (static storage). */
 const char *tl_status_string(tl_status status);
 

@@ -7,6 +7,9 @@
 #include "../../include/taylens.h"
 
 #define TL_MAX_ORDER 6
+// largest plan tl_deflection_noalloc serves from its fixed device array
+#define TL_NOALLOC_MAX_NSIDE 128
+#define TL_NOALLOC_MAX_LMAX 256
 #define TL_MAX_NDER 6  // highest theta-derivative order a Legendre kernel carries
 
 namespace tl {
@@ -122,3 +125,8 @@ inline double deriv_norm(const tl_plan *p) { return (double)(p->lmax + 1); }
     if (_e != cudaSuccess) return _e;             \
   } while (0)
 
+#define TL_CUDA_TRY_STATUS(call)                                                   \
+  do {                                                                             \
+    cudaError_t _e = (call);                                                       \
+    if (_e != cudaSuccess) return _e == cudaErrorMemoryAllocation ? TL_ERR_NOMEM : TL_ERR_CUDA; \
+  } while (0)

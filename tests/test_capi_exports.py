@@ -47,3 +47,5 @@ def test_host_argument_checks(lib):
     assert lib.tl_plan_destroy(None) == L.TL_OK
     assert lib.tl_plan_workspace_bytes(None) == 0
     assert lib.tl_status_string(L.TL_ERR_ARG) == b"invalid argument"
+    # allocation-free entry point: sizes beyond its fixed array are refused up front
+    assert lib.tl_deflection_noalloc(256, 256, 0, None, None, None, None) == L.TL_ERR_ARG
