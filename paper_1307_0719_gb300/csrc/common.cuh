@@ -55,6 +55,7 @@ struct tl_plan {
   void *twiddle;        // [TW/2] e^{-2 pi i k / TW} in T2 (device)
   int tw_len;
   int blue_maxm;        // largest Bluestein FFT length (0 if none)
+  int fft_batch;        // Bluestein sub-transforms run together in the ring FFT (1 or 4; 0 = choose)
   // workspace
   void *tab0, *tab2;    // plan-time step tables {k_l, A_{l+1}} for spin 0 and spin 2
   void *rec_T, *rec_P, *rec_QU; // coefficient records

@@ -165,6 +165,8 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   TRY_CUDA(dalloc(&p->alpha, (size_t)p->elem * 2 * p->npix, B));
   TRY_CUDA(cudaDeviceSynchronize());
 
+  const char *fb = getenv("TAYLENS_FFT_BATCH");
+  p->fft_batch = fb ? atoi(fb) : 0;
   const char *env = getenv("TAYLENS_TIMING");
   p->timing = (env && env[0] == '1') ? 1 : 0;
   if (p->timing)

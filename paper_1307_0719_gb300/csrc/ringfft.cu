@@ -49,7 +49,7 @@ template <> __device__ __forceinline__ void sincos_pi<double>(double x, double *
 
 // In-place radix-2 DIT FFT on `batch` contiguous arrays of length n (power of two)
 // in shared memory. dir = -1: sum x e^{-2 pi i k t/n}; dir = +1: e^{+...}.
-// tw[k] = e^{-2 pi i k / TW}, k < TW/2.
+// tw[k] = e^{-2 pi i k / TW}, k < TW/2. Index arithmetic by shifts and masks.
 template <typename T2>
 __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict__ tw, int TW) {
   const int nth = blockDim.x, tid = threadIdx.x;
@@ -57,26 +57,29 @@ __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict_
   const int lg = 31 - __clz(n);
   const int total = n * batch;
   for (int e = tid; e < total; e += nth) {
-    int b = e / n, k = e - b * n;
-    int r = __brev(k) >> (32 - lg);
+    const int k = e & (n - 1);
+    const int r = __brev(k) >> (32 - lg);
     if (k < r) {
-      T2 t = a[b * n + k];
-      a[b * n + k] = a[b * n + r];
-      a[b * n + r] = t;
+      const int base = e - k;
+      T2 t = a[base + k];
+      a[base + k] = a[base + r];
+      a[base + r] = t;
     }
   }
   __syncthreads();
-  const int nbf = (n >> 1) * batch;
-  for (int len = 2; len <= n; len <<= 1) {
-    const int half = len >> 1;
-    const int step = TW / len;
+  const int hn = n >> 1;
+  const int nbf = hn * batch;
+  const int lgtw = 31 - __clz(TW);
+  for (int sh = 0; sh < lg; ++sh) {  // len = 2^(sh+1), half = 2^sh
+    const int half = 1 << sh;
+    const int tws = lgtw - sh - 1;  // twiddle stride TW / len = 2^tws
     for (int e = tid; e < nbf; e += nth) {
-      int b = e / (n >> 1), q = e - b * (n >> 1);
-      int grp = q / half, pos = q - grp * half;
-      int i0 = b * n + grp * len + pos, i1 = i0 + half;
-      T2 w = tw[pos * step];
+      const int b = e >> (lg - 1), q = e & (hn - 1);
+      const int grp = q >> sh, pos = q & (half - 1);
+      const int i0 = (b << lg) + (grp << (sh + 1)) + pos, i1 = i0 + half;
+      T2 w = tw[pos << tws];
       if (dir > 0) w.y = -w.y;
-      T2 u = a[i0], v = cmul(a[i1], w);
+      const T2 u = a[i0], v = cmul(a[i1], w);
       a[i0] = cadd(u, v);
       a[i1] = csub(u, v);
     }
@@ -84,42 +87,37 @@ __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict_
   }
 }
 
-// Bluestein: y_p = sum_{t<n} y_t e^{+2 pi i t p / n} in place, n arbitrary,
-// using work[M] and the tabulated spectrum bh = DFT_M(conj chirp) / M.
+// Bluestein on `batch` contiguous sequences y[b n + t] of length n (n arbitrary),
+// in place: y_p <- sum_{t<n} y_t e^{+2 pi i t p / n}. With tp = (t^2 + p^2 - (p-t)^2)/2
+// the DFT is a chirp, a circular convolution of length M >= 2n - 1 (done by two
+// power-of-two FFTs against the tabulated spectrum bh = DFT_M(conj chirp) / M)
+// and a chirp. work holds batch * M entries.
 template <typename T, typename T2>
-__device__ void bluestein_inplace(T2 *y, int n, int M, T2 *work, const T2 *__restrict__ bh,
-                                  const T2 *__restrict__ tw, int TW) {
+__device__ void bluestein_batch(T2 *y, int n, int M, int batch, T2 *work, const T2 *__restrict__ bh,
+                                const T2 *__restrict__ chirp, const T2 *__restrict__ tw, int TW) {
   const int nth = blockDim.x, tid = threadIdx.x;
-  const long long twon = 2LL * n;
   for (int t = tid; t < M; t += nth) {
-    T2 v;
     if (t < n) {
-      long long q = ((long long)t * t) % twon;  // chirp e^{i pi t^2 / n}
-      T s, c;
-      sincos_pi<T>((T)q / (T)n, &s, &c);
-      T2 w;
-      w.x = c;
-      w.y = s;
-      v = cmul(y[t], w);
+      const T2 w = chirp[t];  // e^{i pi t^2 / n}
+      for (int b = 0; b < batch; ++b) work[b * M + t] = cmul(y[b * n + t], w);
     } else {
-      v.x = (T)0;
-      v.y = (T)0;
+      T2 z;
+      z.x = (T)0;
+      z.y = (T)0;
+      for (int b = 0; b < batch; ++b) work[b * M + t] = z;
     }
-    work[t] = v;
   }
   __syncthreads();
-  fft_pow2<T2>(work, M, 1, -1, tw, TW);
-  for (int k = tid; k < M; k += nth) work[k] = cmul(work[k], bh[k]);
+  fft_pow2<T2>(work, M, batch, -1, tw, TW);
+  for (int k = tid; k < M; k += nth) {
+    const T2 h = bh[k];
+    for (int b = 0; b < batch; ++b) work[b * M + k] = cmul(work[b * M + k], h);
+  }
   __syncthreads();
-  fft_pow2<T2>(work, M, 1, +1, tw, TW);
+  fft_pow2<T2>(work, M, batch, +1, tw, TW);
   for (int p = tid; p < n; p += nth) {
-    long long q = ((long long)p * p) % twon;
-    T s, c;
-    sincos_pi<T>((T)q / (T)n, &s, &c);
-    T2 w;
-    w.x = c;
-    w.y = s;
-    y[p] = cmul(work[p], w);
+    const T2 w = chirp[p];
+    for (int b = 0; b < batch; ++b) y[b * n + p] = cmul(work[b * M + p], w);
   }
   __syncthreads();
 }
@@ -138,35 +136,35 @@ struct PlaneSet {
   const void *base[4];  // T, Q, U, phi planes: [j][ring][m]
 };
 
-// G_m contribution of one job at coefficient m (times e^{i m phi0} and weight).
+// sum over the aliasing class m = t0 + qN (q >= 0, m <= mmax) of
+//   (-1)^q [shifted rings] * w_m (i m / L)^k F_m,   w_0 = 1, w_m = 2
+// i.e. the class's contribution without its common phase e^{i t0 phi0}.
 template <typename T, typename T2>
-__device__ __forceinline__ T2 g_term(const T2 *__restrict__ F, int m, int k, T invL, T phase_den, T w0) {
-  T2 f = F[m];
-  // (i m / L)^k
-  T mk = (T)1;
-  T mm = (T)m * invL;
-  for (int q = 0; q < k; ++q) mk *= mm;
+__device__ __forceinline__ T2 fold_class(const T2 *__restrict__ F, int t0, int N, int mstep, int mmax, int k,
+                                         T invL, bool shifted, int qstep_odd) {
+  T2 acc;
+  acc.x = (T)0;
+  acc.y = (T)0;
+  int q = 0;
+  for (int m = t0; m <= mmax; m += mstep, q += 1) {
+    const T2 f = F[m];
+    T mk = (T)1;
+    const T mm = (T)m * invL;
+    for (int r = 0; r < k; ++r) mk *= mm;
+    if (m > 0) mk *= (T)2;
+    if (shifted && ((q * qstep_odd) & 1)) mk = -mk;
+    acc.x = fma(f.x, mk, acc.x);
+    acc.y = fma(f.y, mk, acc.y);
+  }
+  // (i)^k
   T2 g;
   switch (k & 3) {
-    case 0: g.x = f.x * mk; g.y = f.y * mk; break;
-    case 1: g.x = -f.y * mk; g.y = f.x * mk; break;
-    case 2: g.x = -f.x * mk; g.y = -f.y * mk; break;
-    default: g.x = f.y * mk; g.y = -f.x * mk; break;
+    case 0: g = acc; break;
+    case 1: g.x = -acc.y; g.y = acc.x; break;
+    case 2: g.x = -acc.x; g.y = -acc.y; break;
+    default: g.x = acc.y; g.y = -acc.x; break;
   }
-  // e^{i m phi0} = e^{i pi m / phase_den} on shifted rings (phase_den = 0: phi0 = 0)
-  T w = (m == 0) ? w0 : (T)2 * w0;
-  if (phase_den != (T)0) {
-    int den = (int)phase_den;
-    int q = m % (2 * den);
-    T s, c;
-    sincos_pi<T>((T)q / phase_den, &s, &c);
-    T2 e;
-    e.x = c;
-    e.y = s;
-    g = cmul(g, e);
-  }
-  g.x *= w;
-  g.y *= w;
+  (void)N;
   return g;
 }
 
@@ -174,7 +172,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, int mmax, int nrings, PlaneSet ps,
                                                       int plane_len, JobList jobs, BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
-                                                      int wlen, double invL_d) {
+                                                      int bbatch, double invL_d) {
   typedef typename RealTraits<T>::T2 T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = blockIdx.x;
@@ -183,14 +181,15 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   const bool hasb = jb < jobs.n;
   const int N = rt.nphi[r];
   const int ni = N >> 2;
+  const int half = N >> 1;
   const long long first = rt.first[r];
   const T invL = (T)invL_d;
   const int nth = blockDim.x, tid = threadIdx.x;
   T2 *Y = (T2 *)smem_raw;  // [4][ni], decimated order
-  T2 *W = Y + N;           // [wlen] work
-  // shifted rings: phi0 = pi / (4 inorth) for caps, pi/(4N) for shifted belt rings
-  // half-pixel-shifted rings have phi0 = pi / (4 ni): e^{i m phi0} = e^{i pi m / (4 ni)}
-  const T phase_den = (rt.phi0[r] == 0.0) ? (T)0 : (T)(4 * ni);
+  T2 *W = Y + N;           // work area
+  // half-pixel-shifted rings have phi0 = pi / (4 ni) = pi / N: e^{i m phi0} = e^{i t phi0} (-1)^q
+  // for m = t + q N
+  const bool shifted = rt.phi0[r] != 0.0;
 
   const JobDev JA = jobs.job[ja];
   const JobDev JB = hasb ? jobs.job[jb] : jobs.job[ja];
@@ -203,51 +202,80 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   const T wb = hasb ? (T)(JB.div_sint ? 1.0 / rt.sint[r] : 1.0) : (T)0;
   const T sa = (T)JA.scale, sb = (T)JB.scale;
 
-  // ---- fold m modulo N into the Hermitian spectrum Z_t, stored at Y[(t%4)*ni + t/4]
-  // chunks: C threads share one residue class when N < nth
-  const int C = (N >= nth) ? 1 : nth / N;
-  if (C == 1) {
-    for (int t = tid; t < N; t += nth) {
-      const int tm = (N - t) % N;
-      T2 Ba = {0, 0}, Bam = {0, 0}, Bb = {0, 0}, Bbm = {0, 0};
-      for (int m = t; m <= mmax; m += N) {
-        Ba = cadd(Ba, g_term<T, T2>(FA, m, JA.k, invL, phase_den, wa));
-        if (hasb) Bb = cadd(Bb, g_term<T, T2>(FB, m, JB.k, invL, phase_den, wb));
+  // ---- fold m modulo N into the Hermitian spectrum; thread handles classes t and N - t
+  // (t = 0 .. N/2): C_t = (B_t + conj(B_{-t}))/2, C_{-t} = conj(C_t), Z = C^a + i C^b.
+  // Z_t is stored at Y[(t % 4) ni + t / 4] (decimated order).
+  const int ncls = half + 1;
+  const int C = (ncls >= nth) ? 1 : nth / ncls;  // threads sharing one class pair
+  {
+    const int c = tid / ncls, t = tid - (tid / ncls) * ncls;
+    for (int tt = (C == 1 ? tid : t); tt < ncls && c < C; tt += (C == 1 ? nth : ncls)) {
+      const int tm = (N - tt) % N;
+      const int m0 = tt + c * N, m1 = tm + c * N, step = C * N;
+      T2 Ba = fold_class<T, T2>(FA, m0, N, step, mmax, JA.k, invL, shifted, C);
+      T2 Bam = fold_class<T, T2>(FA, m1, N, step, mmax, JA.k, invL, shifted, C);
+      T2 Bb = {0, 0}, Bbm = {0, 0};
+      if (hasb) {
+        Bb = fold_class<T, T2>(FB, m0, N, step, mmax, JB.k, invL, shifted, C);
+        Bbm = fold_class<T, T2>(FB, m1, N, step, mmax, JB.k, invL, shifted, C);
       }
-      for (int m = tm; m <= mmax; m += N) {
-        Bam = cadd(Bam, g_term<T, T2>(FA, m, JA.k, invL, phase_den, wa));
-        if (hasb) Bbm = cadd(Bbm, g_term<T, T2>(FB, m, JB.k, invL, phase_den, wb));
+      // chunk c starts at q = c: its first sign is (-1)^c on shifted rings
+      if (shifted && (c & 1)) {
+        Ba.x = -Ba.x; Ba.y = -Ba.y; Bam.x = -Bam.x; Bam.y = -Bam.y;
+        Bb.x = -Bb.x; Bb.y = -Bb.y; Bbm.x = -Bbm.x; Bbm.y = -Bbm.y;
       }
-      // Z = (Ba + conj(Bam))/2 + i (Bb + conj(Bbm))/2
-      T2 z;
-      z.x = (T)0.5 * (Ba.x + Bam.x) - (T)0.5 * (Bb.y - Bbm.y);
-      z.y = (T)0.5 * (Ba.y - Bam.y) + (T)0.5 * (Bb.x + Bbm.x);
-      Y[(t & 3) * ni + (t >> 2)] = z;
+      if (shifted) {
+        // class phases e^{i t phi0} and e^{i (N-t) phi0} = -conj(e^{i t phi0}) (t > 0)
+        T s, co;
+        sincos_pi<T>((T)tt / (T)N, &s, &co);
+        T2 e, em;
+        e.x = co;
+        e.y = s;
+        if (tt == 0) em = e;
+        else {
+          em.x = -co;
+          em.y = s;
+        }
+        Ba = cmul(Ba, e);
+        Bb = cmul(Bb, e);
+        Bam = cmul(Bam, em);
+        Bbm = cmul(Bbm, em);
+      }
+      T2 ca, cb;  // C^a_t, C^b_t (weights of the maps included)
+      ca.x = (T)0.5 * wa * (Ba.x + Bam.x);
+      ca.y = (T)0.5 * wa * (Ba.y - Bam.y);
+      cb.x = (T)0.5 * wb * (Bb.x + Bbm.x);
+      cb.y = (T)0.5 * wb * (Bb.y - Bbm.y);
+      if (C == 1) {
+        T2 z, zm;
+        z.x = ca.x - cb.y;
+        z.y = ca.y + cb.x;
+        zm.x = ca.x + cb.y;  // conj(C^a) + i conj(C^b)
+        zm.y = -ca.y + cb.x;
+        Y[(tt & 3) * ni + (tt >> 2)] = z;
+        if (tt != 0 && tt != half) Y[(tm & 3) * ni + (tm >> 2)] = zm;
+      } else {
+        W[2 * (c * ncls + tt)] = ca;
+        W[2 * (c * ncls + tt) + 1] = cb;
+      }
     }
-  } else {
-    // partial sums in W[c * N + t], then a fixed-order reduction (deterministic)
-    const int c = tid / N, t = tid - c * N;
-    if (c < C) {
-      const int tm = (N - t) % N;
-      T2 Ba = {0, 0}, Bam = {0, 0}, Bb = {0, 0}, Bbm = {0, 0};
-      for (int m = t + c * N; m <= mmax; m += C * N) {
-        Ba = cadd(Ba, g_term<T, T2>(FA, m, JA.k, invL, phase_den, wa));
-        if (hasb) Bb = cadd(Bb, g_term<T, T2>(FB, m, JB.k, invL, phase_den, wb));
-      }
-      for (int m = tm + c * N; m <= mmax; m += C * N) {
-        Bam = cadd(Bam, g_term<T, T2>(FA, m, JA.k, invL, phase_den, wa));
-        if (hasb) Bbm = cadd(Bbm, g_term<T, T2>(FB, m, JB.k, invL, phase_den, wb));
-      }
-      T2 z;
-      z.x = (T)0.5 * (Ba.x + Bam.x) - (T)0.5 * (Bb.y - Bbm.y);
-      z.y = (T)0.5 * (Ba.y - Bam.y) + (T)0.5 * (Bb.x + Bbm.x);
-      W[c * N + t] = z;
-    }
+  }
+  if (C > 1) {
     __syncthreads();
-    for (int t2 = tid; t2 < N; t2 += nth) {
-      T2 acc = {0, 0};
-      for (int cc = 0; cc < C; ++cc) acc = cadd(acc, W[cc * N + t2]);
-      Y[(t2 & 3) * ni + (t2 >> 2)] = acc;
+    for (int tt = tid; tt < ncls; tt += nth) {
+      T2 ca = {0, 0}, cb = {0, 0};
+      for (int c = 0; c < C; ++c) {
+        ca = cadd(ca, W[2 * (c * ncls + tt)]);
+        cb = cadd(cb, W[2 * (c * ncls + tt) + 1]);
+      }
+      const int tm = (N - tt) % N;
+      T2 z, zm;
+      z.x = ca.x - cb.y;
+      z.y = ca.y + cb.x;
+      zm.x = ca.x + cb.y;
+      zm.y = -ca.y + cb.x;
+      Y[(tt & 3) * ni + (tt >> 2)] = z;
+      if (tt != 0 && tt != half) Y[(tm & 3) * ni + (tm >> 2)] = zm;
     }
   }
   __syncthreads();
@@ -259,31 +287,36 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
     const long long off = bt.offset[ni];
     const int M = bt.mlen[ni];
     const T2 *bh = (const T2 *)bt.spec + off;
-    for (int t2 = 0; t2 < 4; ++t2) bluestein_inplace<T, T2>(Y + t2 * ni, ni, M, W, bh, tw, TW);
+    const T2 *ch = bh + M;  // the length's chirp follows its spectrum
+    if (bbatch >= 4) {
+      bluestein_batch<T, T2>(Y, ni, M, 4, W, bh, ch, tw, TW);
+    } else {
+      for (int t2 = 0; t2 < 4; ++t2) bluestein_batch<T, T2>(Y + t2 * ni, ni, M, 1, W, bh, ch, tw, TW);
+    }
   }
 
   // ---- radix-4 pass: X_{p1 + ni p2} = sum_t2 i^{t2 p2} e^{2 pi i t2 p1 / N} Y_t2(p1)
   T *outA = (T *)JA.out + first;
   T *outB = hasb ? (T *)JB.out + first : nullptr;
   for (int p1 = tid; p1 < ni; p1 += nth) {
+    T s, c;
+    sincos_pi<T>((T)(2 * p1) / (T)N, &s, &c);
+    T2 w1;
+    w1.x = c;
+    w1.y = s;
+    const T2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
     T2 y[4];
     y[0] = Y[p1];
-#pragma unroll
-    for (int t2 = 1; t2 < 4; ++t2) {
-      T s, c;
-      sincos_pi<T>((T)(2 * t2 * p1) / (T)N, &s, &c);
-      T2 w;
-      w.x = c;
-      w.y = s;
-      y[t2] = cmul(Y[t2 * ni + p1], w);
-    }
-    T2 a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
-    T2 b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
+    y[1] = cmul(Y[ni + p1], w1);
+    y[2] = cmul(Y[2 * ni + p1], w2);
+    y[3] = cmul(Y[3 * ni + p1], w3);
+    const T2 a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
+    const T2 b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
     T2 ib1;  // i * b1
     ib1.x = -b1.y;
     ib1.y = b1.x;
-    T2 X0 = cadd(a0, b0), X2 = csub(a0, b0);
-    T2 X1 = cadd(a1, ib1), X3 = csub(a1, ib1);
+    const T2 X0 = cadd(a0, b0), X2 = csub(a0, b0);
+    const T2 X1 = cadd(a1, ib1), X3 = csub(a1, ib1);
     outA[p1] = sa * X0.x;
     outA[p1 + ni] = sa * X1.x;
     outA[p1 + 2 * ni] = sa * X2.x;
@@ -333,17 +366,37 @@ __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const l
     v.y = (T)(w[k].y / M);
     spec[off + k] = v;
   }
+  // then the chirp e^{i pi t^2 / n}, t < n
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const long long q = ((long long)t * t) % twon;
+    double s, c;
+    sincospi((double)q / (double)n, &s, &c);
+    T2 v;
+    v.x = (T)c;
+    v.y = (T)s;
+    spec[off + M + t] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
 
-// shared memory of the ring FFT: the ring (<= 4 nside) plus a work area that
-// holds the largest Bluestein transform or the folding partial sums (512)
-size_t ringfft_smem_bytes(const tl_plan *p) {
-  size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
-  int wl = p->blue_maxm > 512 ? p->blue_maxm : 512;
-  return e2 * (size_t)(4 * p->nside + wl);
+// Shared memory of the ring FFT: the ring (<= 4 nside entries) plus a work area
+// for the folding partial sums (2 x 512) and Bluestein: four sub-transforms at
+// once when that fits in 227 KB, else one at a time.
+static size_t ringfft_smem_for(const tl_plan *p, int batch) {
+  const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
+  size_t wl = (size_t)batch * (size_t)p->blue_maxm;
+  if (wl < 1024) wl = 1024;
+  return e2 * ((size_t)4 * p->nside + wl);
 }
+static int ringfft_batch(const tl_plan *p) {
+  if (p->fft_batch == 1) return 1;
+  const bool fits4 = ringfft_smem_for(p, 4) <= 227 * 1024;
+  if (p->fft_batch == 4) return fits4 ? 4 : 1;
+  // default: batch only while two blocks still fit on an SM
+  return ringfft_smem_for(p, 4) <= 113 * 1024 ? 4 : 1;
+}
+size_t ringfft_smem_bytes(const tl_plan *p) { return ringfft_smem_for(p, ringfft_batch(p)); }
 
 template <typename T>
 static cudaError_t ringfft_t(const tl_plan *p, const MapJob *jobs, int njobs, cudaStream_t s) {
@@ -364,12 +417,12 @@ static cudaError_t ringfft_t(const tl_plan *p, const MapJob *jobs, int njobs, cu
   ps.base[2] = p->d7_U;
   ps.base[3] = p->d7_P;
   const int plane_len = p->nrings * (p->mmax + 1);
-  size_t smem = ringfft_smem_bytes(p);
-  int wlen = (int)(smem / sizeof(typename RealTraits<T>::T2)) - 4 * p->nside;
+  const int batch = ringfft_batch(p);
+  const size_t smem = ringfft_smem_for(p, batch);
   TL_CUDA_TRY(cudaFuncSetAttribute(ringfft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(p->nrings, (njobs + 1) / 2);
   ringfft_kernel<T><<<grid, 512, smem, s>>>(p->ring, p->nside, p->mmax, p->nrings, ps, plane_len, jl, p->blue,
-                                            (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, wlen,
+                                            (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch,
                                             1.0 / (double)(p->lmax + 1));
   return cudaGetLastError();
 }

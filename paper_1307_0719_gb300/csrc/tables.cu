@@ -99,7 +99,8 @@ void host_lnorm0(int lmax, double *out) {
 }
 
 // Bluestein lengths: cap rings use sub-transforms of length i = 1 .. nside-1; each
-// non-power-of-two i gets a spectrum of M = pow2 >= 2i - 1 entries.
+// non-power-of-two i gets a spectrum of M = pow2 >= 2i - 1 entries followed by its
+// chirp of i entries.
 long long host_bluestein_layout(int nside, long long *off, int *ml, int *maxm) {
   long long tot = 0;
   int mx = 0;
@@ -113,7 +114,7 @@ long long host_bluestein_layout(int nside, long long *off, int *ml, int *maxm) {
     while (M < 2 * i - 1) M <<= 1;
     off[i] = tot;
     ml[i] = M;
-    tot += M;
+    tot += M + i;
     if (M > mx) mx = M;
   }
   *maxm = mx;
