@@ -37,7 +37,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_LANES = 152 * 128
 
 
-def legendre_flops_per_launch(nside: int, lmax: int, order: int, spin: int, phi: bool = True) -> float:
+def legendre_flops_per_launch(nside: int, lmax: int, order: int, spin: int, phi: bool = True,
+                              part: str = "all", nreal: int = 1) -> float:
     """Algorithmic flops of one Legendre-stage launch, per (ring pair, l, m) triple:
     the derivative recurrence costs sum_{j<=n} (2j + 3) flops per ring (one multiply,
     j Leibniz multiply-adds and the closing multiply-add of each order), the
@@ -48,9 +49,10 @@ def legendre_flops_per_launch(nside: int, lmax: int, order: int, spin: int, phi:
     n = order
     rec = sum(2 * j + 3 for j in range(n + 1))
     if spin == 0:
-        per = rec + 4 * (n + 1) + (8 if phi else 0)
+        r_part, c_part = rec, 4 * (n + 1) + (8 if phi else 0)
     else:
-        per = 2 * (rec + 1 + 8 * (n + 1))
+        r_part, c_part = 2 * (rec + 1), 2 * 8 * (n + 1)
+    per = {"all": r_part + nreal * c_part, "recurrence": r_part, "contraction": nreal * c_part}[part]
     pairs = 2 * nside  # north rings incl. the equator
     lm = (lmax + 1) * (lmax + 2) // 2
     return float(per) * pairs * lm
@@ -188,16 +190,23 @@ def run_ours(args):
     from paper_1307_0719_gb300 import api
 
     w = skygen.WORKLOADS[args.workload]
-    # each rank lenses its own realisation (seeds offset by rank): weak scaling
-    sky = skygen.make_sky(w.nside, w.lmax, w.pol, w.seed_t + 1000 * rank, w.seed_e + 1000 * rank,
-                          w.seed_phi + 1000 * rank, w.damp_t, w.damp_e)
-    d = {k: torch.from_numpy(v).to(dev) for k, v in sky.items()}
-    plan = api.Plan(w.nside, w.lmax, w.order, pol=w.pol, precision=api.MIXED_FP32)
-    out = torch.empty((3, plan.npix), dtype=torch.float32, device=dev)
+    forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3}
+    prec = forms[args.form]
+    nb = args.batch if args.batch else (2 if args.form != "fp32" else 1)
+    # each rank lenses its own realisations (seeds offset by rank and index): weak scaling
+    skies = [skygen.make_sky(w.nside, w.lmax, w.pol, w.seed_t + 1000 * rank + 100 * i,
+                             w.seed_e + 1000 * rank + 100 * i, w.seed_phi + 1000 * rank + 100 * i,
+                             w.damp_t, w.damp_e) for i in range(nb)]
+    sky = skies[0]
+    dl = [{k: torch.from_numpy(v).to(dev) for k, v in sk.items()} for sk in skies]
+    d = dl[0]
+    plan = api.Plan(w.nside, w.lmax, w.order, pol=w.pol, precision=prec)
+    outs = [torch.empty((3, plan.npix), dtype=torch.float32, device=dev) for _ in range(nb)]
+    out = outs[0]
     stream = torch.cuda.current_stream()
 
     def step():
-        plan.lens(d["T"], d["E"], d["B"], d["phi"], out=out)
+        plan.lens_batch(dl, outs=outs)
 
     for _ in range(args.warmup):
         step()
@@ -224,14 +233,19 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = world * nb * args.steps / (ms / 1e3)
     stages = stage_sum / args.steps
     names = ["prep_T", "legendre_T", "deflection_fft", "prep_QU", "legendre_QU", "ringfft", "gather"]
     stage_ms = {n: float(v) for n, v in zip(names, stages)}
 
-    # roofline of the dominant kernel
-    flops_qu = legendre_flops_per_launch(w.nside, w.lmax, w.order, 2)
-    flops_t = legendre_flops_per_launch(w.nside, w.lmax, w.order, 0)
+    # roofline of the dominant kernel (stage times are per Legendre launch, which on
+    # tensor-core plans covers two realisations; see the per-step stage sums)
+    tc = args.form != "fp32"
+    part = "recurrence" if tc else "all"
+    nr_launch = min(nb, 2) if tc else 1
+    flops_qu = legendre_flops_per_launch(w.nside, w.lmax, w.order, 2, part=part)
+    flops_t = legendre_flops_per_launch(w.nside, w.lmax, w.order, 0, part=part)
+    tflops_qu = legendre_flops_per_launch(w.nside, w.lmax, w.order, 2, part="contraction", nreal=nr_launch)
     dom = max(("legendre_QU", "legendre_T", "ringfft", "gather"), key=lambda k: stage_ms[k])
     peaks = {}
     if os.path.exists(PEAKS_FILE):
@@ -243,10 +257,14 @@ def run_ours(args):
     if dom in ("legendre_QU", "legendre_T"):
         fl = flops_qu if dom == "legendre_QU" else flops_t
         achieved = fl / (stage_ms[dom] / 1e3) / 1e12
-        roof = {"kernel": f"legendre_spin{'2' if dom == 'legendre_QU' else '0'}_kernel<float,{w.order}>",
-                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+        kname = f"legendre_spin{'2' if dom == 'legendre_QU' else '0'}_{'tc' if tc else 'kernel'}<{w.order}>"
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz"}
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
+                "counts": "recurrence only; the contraction runs on the tensor cores" if tc else
+                          "recurrence + contraction"}
+        if tc and dom == "legendre_QU":
+            roof["tensor_tflops_contraction"] = tflops_qu / (stage_ms[dom] / 1e3) / 1e12
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
                 "unit": "GB/s", "frac": None, "traffic": None}
@@ -254,7 +272,7 @@ def run_ours(args):
     # end to end through tl_lens_host (pinned host buffers, copies inside the timed region)
     e2e = None
     if not args.no_e2e:
-        hin = {k: torch.from_numpy(v).pin_memory() for k, v in sky.items()}
+        hin = {k: torch.from_numpy(v).pin_memory() for k, v in sky.items()}  # one realisation per call
         hout = torch.empty((3, plan.npix), dtype=torch.float32).pin_memory()
         plan.lens_host(hin["T"], hin["E"], hin["B"], hin["phi"], out=hout)
         k2 = max(1, min(args.steps, 3))
@@ -263,9 +281,9 @@ def run_ours(args):
         for _ in range(k2):
             plan.lens_host(hin["T"], hin["E"], hin["B"], hin["phi"], out=hout)
         e2e_s = (time.perf_counter() - t0) / k2
-        nb = plan.nalm * 16
-        e2e = {"value": world / e2e_s, "unit": "maps/s", "h2d_bytes_per_step": 4 * nb,
-               "d2h_bytes_per_step": 3 * plan.npix * 4}
+        nbytes = plan.nalm * 16
+        e2e = {"value": world / e2e_s, "unit": "maps/s", "h2d_bytes_per_step": 4 * nbytes,
+               "d2h_bytes_per_step": 3 * plan.npix * 4, "realisations_per_call": 1}
         del hin, hout
 
     lensed = out.cpu().numpy()
@@ -325,14 +343,17 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[args.form],
             "data": "synthetic (seeded Gaussian alm, analytic spectra)",
             "config": {"workload": args.workload, "nside": w.nside, "lmax": w.lmax, "order": w.order,
-                       "fields": "TQU", "form": "mixed FP32 (FP64 seeds/rescaling, FP64 geometry)",
+                       "fields": "TQU", "form": {"fp32": "mixed FP32 (SIMT contraction)",
+                                                 "tf32": "mixed, TF32 tensor-core contraction",
+                                                 "tf32x3": "mixed, 3xTF32 tensor-core contraction"}[args.form]
+                       + "; FP64 seeds and rescaling; double pixel lookup", "realisations_per_step": nb,
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (alm 537 MB, "
                        "derivative maps 9 GB per step)"},
             "stage_ms": stage_ms, "roofline": roof, "clocks": clocks,
-            "gpu_launches": 8 * args.steps, "e2e": e2e, "fp64": fp64, "err_vs_oracle": err,
+            "gpu_launches": args.steps * ((8 * nb) if not tc else (5 + 5 * nb)), "e2e": e2e, "fp64": fp64, "err_vs_oracle": err,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -348,6 +369,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(skygen.WORKLOADS))
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--form", default="tf32x3", choices=["fp32", "tf32", "tf32x3"])
+    ap.add_argument("--batch", type=int, default=0, help="realisations per step (default 2 on tensor cores)")
     ap.add_argument("--sample-pixels", type=int, default=16)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -52,9 +52,17 @@ typedef enum {
 enum { TL_SPIN_T = 1, TL_SPIN_QU = 2 };
 
 /* `precision`: arithmetic of the Legendre stage, ring FFTs and Taylor sums.
- * TL_FP64        everything in double.
- * TL_MIXED_FP32  float recurrence and contraction with double seeds and
- *                exponent rescaling; double pixel geometry; float maps. */
+ * TL_FP64          everything in double.
+ * TL_MIXED_FP32    float recurrence and contraction with double seeds and
+ *                  exponent rescaling; float maps; double pixel lookup.
+ * TL_MIXED_TF32    as TL_MIXED_FP32, but tl_lens / tl_lens_batch contract the
+ *                  recurrence against the coefficients on the tensor cores in
+ *                  TF32 (10-bit mantissas, FP32 accumulation), two realisations
+ *                  per Legendre launch.
+ * TL_MIXED_TF32x3  the same with each operand split into TF32 hi + lo parts and
+ *                  three products accumulated (errors close to FP32).
+ * TL_MIXED_BF16x3  declared, not built (TL_ERR_UNSUPPORTED).
+ * tl_synth_derivs and tl_deflection use the float (SIMT) stage in all mixed forms. */
 enum { TL_FP64 = 0, TL_MIXED_FP32 = 1, TL_MIXED_TF32 = 2, TL_MIXED_TF32x3 = 3, TL_MIXED_BF16x3 = 4 };
 
 /* `flags` */
@@ -66,7 +74,7 @@ enum { TL_ROTATE = 1 /* apply the polarisation rotation R of Eq. 2 (default on) 
  *   lmax      1 .. 4 nside (band limit of every field, including phi)
  *   order     Taylor order n, 0 .. 6 (total degree j + k <= n; 0 = nearest-pixel lookup)
  *   spins     TL_SPIN_T, TL_SPIN_QU or both
- *   precision TL_FP64 or TL_MIXED_FP32 (others return TL_ERR_UNSUPPORTED)
+ *   precision TL_FP64, TL_MIXED_FP32, TL_MIXED_TF32 or TL_MIXED_TF32x3
  *   flags     TL_ROTATE or 0
  *   out       receives the plan; unchanged on error
  * Allocates the plan's device tables and workspace on the current device.
@@ -115,6 +123,19 @@ tl_status tl_deflection(tl_plan *plan, const double *alm_phi, void *a_theta, voi
  */
 tl_status tl_lens(tl_plan *plan, const double *alm_T, const double *alm_E, const double *alm_B,
                   const double *alm_phi, void *T_out, void *Q_out, void *U_out, void *stream);
+
+/*
+ * Lens nreal realisations of this plan's geometry in one call. Arrays of nreal
+ * device pointers (host arrays); entries as in tl_lens; alm_B may be NULL (all
+ * B = 0); alm_phi may be NULL (none lensed), otherwise every entry must be set.
+ * On tensor-core plans (TL_MIXED_TF32, TL_MIXED_TF32x3) realisations go through
+ * the Legendre stage two at a time, sharing the recurrence (the coefficient sets
+ * of both fill the columns of one tensor-core product); ring FFTs and the gather
+ * then run per realisation. On other plans this equals nreal calls of tl_lens.
+ */
+tl_status tl_lens_batch(tl_plan *plan, int nreal, const double *const *alm_T, const double *const *alm_E,
+                        const double *const *alm_B, const double *const *alm_phi, void *const *T_out,
+                        void *const *Q_out, void *const *U_out, void *stream);
 
 /*
  * tl_lens with HOST buffers: copies the alm from host memory to the plan's

@@ -24,6 +24,7 @@ SIGNATURES = {
     "tl_deflection": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "tl_lens": (ctypes.c_int, [_P] * 9),
     "tl_lens_host": (ctypes.c_int, [_P] * 9),
+    "tl_lens_batch": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 8),
     "tl_deflection_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "tl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tl_last_stage_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),

@@ -11,6 +11,8 @@ from ._lib import check
 
 FP64 = _lib.TL_FP64
 MIXED_FP32 = _lib.TL_MIXED_FP32
+MIXED_TF32 = _lib.TL_MIXED_TF32
+MIXED_TF32x3 = _lib.TL_MIXED_TF32x3
 
 
 def _ptr(t):
@@ -97,6 +99,27 @@ class Plan:
         check(_lib.lib().tl_lens(self._h, _ptr(aT), _ptr(aE), _ptr(aB), _ptr(aP), _ptr(out[0]),
                                  _ptr(Q), _ptr(U), _stream(stream)), "tl_lens")
         return out
+
+    def lens_batch(self, skies, outs=None, stream=None):
+        """Lens several realisations with one call (tl_lens_batch). `skies` is a list of
+        dicts with keys T, E, B, phi (CUDA complex128); returns a list of [3 or 1, Npix]."""
+        n = len(skies)
+        nf = 3 if self.pol else 1
+        dev = skies[0]["T"].device
+        if outs is None:
+            outs = [torch.empty((nf, self.npix), dtype=self.dtype, device=dev) for _ in range(n)]
+        arr = lambda xs: (ctypes.c_void_p * n)(*[None if x is None else x.data_ptr() for x in xs])
+        keep = [{k: _alm(sk.get(k), k) for k in ("T", "E", "B", "phi")} for sk in skies]
+        aT = arr([k["T"] for k in keep])
+        aE = arr([k["E"] for k in keep]) if self.pol else None
+        aB = arr([k["B"] for k in keep]) if self.pol else None
+        aP = arr([k["phi"] for k in keep])
+        To = arr([o[0] for o in outs])
+        Qo = arr([o[1] for o in outs]) if self.pol else None
+        Uo = arr([o[2] for o in outs]) if self.pol else None
+        check(_lib.lib().tl_lens_batch(self._h, n, aT, aE, aB, aP, To, Qo, Uo, _stream(stream)),
+              "tl_lens_batch")
+        return outs
 
     def lens_host(self, alm_T, alm_E=None, alm_B=None, alm_phi=None, out=None, stream=None):
         """tl_lens_host: alm in (pinned) host memory, maps returned in host memory."""

@@ -60,6 +60,13 @@ struct tl_plan {
   void *tab0, *tab2;    // plan-time step tables {k_l, A_{l+1}} for spin 0 and spin 2
   void *rec_T, *rec_P, *rec_QU; // coefficient records
   void *d7_T, *d7_Q, *d7_U, *d7_P; // per-ring Fourier coefficients [j][ring][m] (T2)
+  // tensor-core Legendre stage (TL_MIXED_TF32, TL_MIXED_TF32x3): blocks of 8 l per m
+  int batch;             // realisations sharing one Legendre launch (1, or 2 on tensor cores)
+  int tc_nder;           // derivative orders carried there (max(order, 1))
+  long long *tc_blk0, *tc_blk2;   // [lmax+1] first block of each m (spin 0 / spin 2)
+  float *tc_step0, *tc_step2;     // [blocks][16]: A_{l+1} x 8, m s/(l(l+1)) x 8
+  void *tc_b0, *tc_bp, *tc_b2;    // [blocks][32 lanes] float4 coefficient fragments
+  long long d7_rstride, d7p_rstride;  // T2 elements between realisations' D7 planes
   void *d3;            // derivative maps [3*nmaps][npix] (T), Taylor-ready
   void *alpha;         // [2][npix] (T)
   void *stage_alm;     // host-path staging: 4 * nalm complex128
@@ -95,6 +102,17 @@ struct MapJob {
 };
 cudaError_t launch_ringfft(const tl_plan *p, const MapJob *jobs, int njobs, int nder_planes,
                            cudaStream_t s);
+// as launch_ringfft with explicit plane bases (T, Q, U, phi) for one realisation
+cudaError_t launch_ringfft_planes(const tl_plan *p, const void *const *planes, const MapJob *jobs, int njobs,
+                                  cudaStream_t s);
+cudaError_t launch_tcstep(const tl_plan *p, int s, const long long *blkofs, const void *tab, float *out,
+                          cudaStream_t st);
+cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *const *a, const double *const *b,
+                          const long long *blkofs, const void *tab, void *out, cudaStream_t st);
+cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void *dq, void *du, long long rstride,
+                                     cudaStream_t s);
+cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, bool phi, void *d7, void *d7p,
+                                     long long rstride, long long rstride_p, cudaStream_t s);
 cudaError_t launch_bluestein_setup(tl_plan *p, cudaStream_t s);
 cudaError_t launch_gather(const tl_plan *p, const void *alpha, const void *d3, void *T, void *Q,
                           void *U, cudaStream_t s);

@@ -77,7 +77,8 @@ static void free_plan(tl_plan *p) {
                   p->ring.dls, p->ring.dlc, p->ring.nphi, p->ring.inorth, p->ring.first, p->blue.spec,
                   p->blue.offset, p->blue.mlen, p->lnorm0, p->twiddle, p->tab0, p->tab2, p->rec_T, p->rec_P,
                   p->rec_QU,
-                  p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->stage_alm, p->stage_out};
+                  p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->stage_alm, p->stage_out,
+                  p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (p->timing)
@@ -147,18 +148,47 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   const size_t t2 = e2, rec0 = 4 * (size_t)p->elem, rec2 = 8 * (size_t)p->elem;
   const size_t plane = (size_t)p->nrings * (p->mmax + 1) * t2;
   const bool pol = (spins & TL_SPIN_QU) != 0;
+  const bool tc = (precision == TL_MIXED_TF32 || precision == TL_MIXED_TF32x3);
+  p->batch = tc ? 2 : 1;
+  p->tc_nder = order > 1 ? order : 1;
+  const int nplanes = tc ? p->tc_nder + 1 : order + 1;  // D7 planes per field and realisation
+  p->d7_rstride = (long long)nplanes * p->nrings * (p->mmax + 1);
+  p->d7p_rstride = 2LL * p->nrings * (p->mmax + 1);
   TRY_CUDA(dalloc(&p->tab0, t2 * na, B));
   TRY_CUDA(launch_steptab(p, 0, p->tab0, 0));
   TRY_CUDA(dalloc(&p->rec_T, rec0 * na, B));
   TRY_CUDA(dalloc(&p->rec_P, t2 * na, B));
-  TRY_CUDA(dalloc(&p->d7_T, plane * (order + 1), B));
-  TRY_CUDA(dalloc(&p->d7_P, plane * 2, B));
+  TRY_CUDA(dalloc(&p->d7_T, plane * nplanes * p->batch, B));
+  TRY_CUDA(dalloc(&p->d7_P, plane * 2 * p->batch, B));
   if (pol) {
     TRY_CUDA(dalloc(&p->tab2, t2 * na, B));
     TRY_CUDA(launch_steptab(p, 2, p->tab2, 0));
     TRY_CUDA(dalloc(&p->rec_QU, rec2 * na, B));
-    TRY_CUDA(dalloc(&p->d7_Q, plane * (order + 1), B));
-    TRY_CUDA(dalloc(&p->d7_U, plane * (order + 1), B));
+    TRY_CUDA(dalloc(&p->d7_Q, plane * nplanes * p->batch, B));
+    TRY_CUDA(dalloc(&p->d7_U, plane * nplanes * p->batch, B));
+  }
+  if (tc) {
+    // blocks of 8 l per m, from l0 = m (spin 0) or max(m, 2) (spin 2)
+    std::vector<long long> b0(lmax + 1), b2(lmax + 1);
+    long long n0 = 0, n2 = 0;
+    for (int m = 0; m <= lmax; ++m) {
+      b0[m] = n0;
+      n0 += (lmax - m + 8) / 8;
+      b2[m] = n2;
+      const int l0 = m > 2 ? m : 2;
+      n2 += (lmax >= l0) ? (lmax - l0 + 8) / 8 : 0;
+    }
+    TRY_CUDA(upload(&p->tc_blk0, b0, B));
+    TRY_CUDA(dalloc((void **)&p->tc_step0, 64 * (size_t)n0, B));
+    TRY_CUDA(launch_tcstep(p, 0, p->tc_blk0, p->tab0, p->tc_step0, 0));
+    TRY_CUDA(dalloc(&p->tc_b0, 512 * (size_t)n0, B));
+    TRY_CUDA(dalloc(&p->tc_bp, 512 * (size_t)n0, B));
+    if (pol) {
+      TRY_CUDA(upload(&p->tc_blk2, b2, B));
+      TRY_CUDA(dalloc((void **)&p->tc_step2, 64 * (size_t)(n2 > 0 ? n2 : 1), B));
+      TRY_CUDA(launch_tcstep(p, 2, p->tc_blk2, p->tab2, p->tc_step2, 0));
+      TRY_CUDA(dalloc(&p->tc_b2, 512 * (size_t)(n2 > 0 ? n2 : 1), B));
+    }
   }
   const int nfield = pol ? 3 : 1;
   TRY_CUDA(dalloc(&p->d3, (size_t)p->elem * nfield * p->nmaps * p->npix, B));
@@ -184,7 +214,7 @@ extern "C" tl_status tl_plan_create(int nside, int lmax, int order, int spins, i
     return (spins == TL_SPIN_QU) ? TL_ERR_UNSUPPORTED : TL_ERR_ARG;
   }
   if (precision < TL_FP64 || precision > TL_MIXED_BF16x3) return TL_ERR_ARG;
-  if (precision != TL_FP64 && precision != TL_MIXED_FP32) return TL_ERR_UNSUPPORTED;
+  if (precision == TL_MIXED_BF16x3) return TL_ERR_UNSUPPORTED;
   if (flags & ~TL_ROTATE) return TL_ERR_ARG;
   // the ring FFT keeps a whole ring in shared memory
   {
@@ -294,19 +324,73 @@ extern "C" tl_status tl_synth_derivs(tl_plan *p, const double *alm, int spin, vo
   return TL_OK;
 }
 
-extern "C" tl_status tl_lens(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,
-                             const double *alm_phi, void *T_out, void *Q_out, void *U_out, void *stream) {
-  if (!p || !alm_T || !T_out) return TL_ERR_ARG;
+// ring FFTs into Taylor-ready maps d_th^j d_ph^k s / (j! k! L^(j+k)) for one realisation
+static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s) {
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
-  if (pol && (!alm_E || !Q_out || !U_out)) return TL_ERR_ARG;
-  const void *ptrs[] = {alm_T, alm_E, alm_B, alm_phi, T_out, Q_out, U_out};
-  for (const void *q : ptrs)
-    if (q && !aligned16(q)) return TL_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
   const size_t mapb = (size_t)p->elem * p->npix;
-  p->nstage = 0;
+  std::vector<MapJob> jobs;
+  const int nf = pol ? 3 : 1;
+  // T maps pair among themselves in (j, k) order; Q and U of the same (j, k) pair
+  for (int f = 0; f < nf; f += (f == 0 ? 1 : 2))
+    for (int n = 0; n <= p->order; ++n)
+      for (int j = 0; j <= n; ++j)
+        for (int g = f; g < (f == 0 ? 1 : 3); ++g) {
+          int k = n - j;
+          jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)),
+                                (char *)p->d3 + mapb * (g * p->nmaps + n * (n + 1) / 2 + j)});
+        }
+  TRY_CUDA(launch_ringfft_planes(p, planes, jobs.data(), (int)jobs.size(), s));
+  return TL_OK;
+}
+
+// Lens nreal <= p->batch realisations that share one Legendre launch.
+static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, const double *const *aE,
+                            const double *const *aB, const double *const *aP, void *const *To, void *const *Qo,
+                            void *const *Uo, cudaStream_t s) {
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  const size_t mapb = (size_t)p->elem * p->npix;
+  const size_t t2 = 2 * (size_t)p->elem;
   void *ath = p->alpha, *aph = (char *)p->alpha + mapb;
+  const bool phi = aP[0] != nullptr;
+  p->nstage = 0;
   mark(p, 0, s);
+  if (p->batch > 1) {
+    // ---- tensor-core Legendre stage for all realisations of the chunk
+    const bool fuse = phi;  // tc_nder >= 1 always
+    TRY_CUDA(launch_tcprep(p, 0, nreal, aT, nullptr, p->tc_blk0, p->tab0, p->tc_b0, s));
+    if (fuse) TRY_CUDA(launch_tcprep(p, 0, nreal, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
+    mark(p, 1, s);
+    TRY_CUDA(launch_legendre_spin0_tc(p, p->tc_nder, nreal, fuse, p->d7_T, p->d7_P, p->d7_rstride,
+                                      p->d7p_rstride, s));
+    mark(p, 2, s);
+    mark(p, 3, s);
+    if (pol) TRY_CUDA(launch_tcprep(p, 2, nreal, aE, aB, p->tc_blk2, p->tab2, p->tc_b2, s));
+    mark(p, 4, s);
+    if (pol) TRY_CUDA(launch_legendre_spin2_tc(p, p->tc_nder, nreal, p->d7_Q, p->d7_U, p->d7_rstride, s));
+    mark(p, 5, s);
+    for (int r = 0; r < nreal; ++r) {
+      const size_t off = (size_t)r * p->d7_rstride * t2, offp = (size_t)r * p->d7p_rstride * t2;
+      const void *planes[4] = {(char *)p->d7_T + off, pol ? (char *)p->d7_Q + off : nullptr,
+                               pol ? (char *)p->d7_U + off : nullptr, (char *)p->d7_P + offp};
+      if (phi) {
+        const double L = deriv_norm(p);
+        MapJob jobs[2] = {{3, 1, 0, 0, L, ath}, {3, 0, 1, 1, L, aph}};
+        TRY_CUDA(launch_ringfft_planes(p, planes, jobs, 2, s));
+      } else {
+        TRY_CUDA(cudaMemsetAsync(p->alpha, 0, 2 * mapb, s));
+      }
+      tl_status st = lens_fft(p, planes, s);
+      if (st != TL_OK) return st;
+      TRY_CUDA(launch_gather(p, p->alpha, p->d3, To[r], pol ? Qo[r] : nullptr, pol ? Uo[r] : nullptr, s));
+    }
+    mark(p, 6, s);
+    mark(p, 7, s);
+    p->nstage = p->timing ? 7 : 0;
+    return TL_OK;
+  }
+  // ---- one realisation on the SIMT Legendre stage
+  const double *alm_T = aT[0], *alm_E = aE ? aE[0] : nullptr, *alm_B = aB ? aB[0] : nullptr;
+  const double *alm_phi = aP[0];
   // 1. spin-0 Legendre stage: T with all derivative orders; the lensing potential
   //    shares its basis for j <= 1 (needs order >= 1, else it runs on its own)
   const bool fuse = alm_phi && p->order >= 1;
@@ -331,25 +415,55 @@ extern "C" tl_status tl_lens(tl_plan *p, const double *alm_T, const double *alm_
   mark(p, 4, s);
   if (pol) TRY_CUDA(launch_legendre_spin2(p, p->order, s));
   mark(p, 5, s);
-  // 4. ring FFTs into Taylor-ready maps: d_th^j d_ph^k s / (j! k! L^(j+k))
-  std::vector<MapJob> jobs;
-  const int nf = pol ? 3 : 1;
-  // T maps pair among themselves in (j, k) order; Q and U of the same (j, k) pair
-  for (int f = 0; f < nf; f += (f == 0 ? 1 : 2))
-    for (int n = 0; n <= p->order; ++n)
-      for (int j = 0; j <= n; ++j)
-        for (int g = f; g < (f == 0 ? 1 : 3); ++g) {
-          int k = n - j;
-          jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)),
-                                (char *)p->d3 + mapb * (g * p->nmaps + n * (n + 1) / 2 + j)});
-        }
-  TRY_CUDA(launch_ringfft(p, jobs.data(), (int)jobs.size(), p->order + 1, s));
+  // 4. ring FFTs
+  const void *planes[4] = {p->d7_T, p->d7_Q, p->d7_U, p->d7_P};
+  tl_status st = lens_fft(p, planes, s);
+  if (st != TL_OK) return st;
   mark(p, 6, s);
   // 5. gather + Taylor + rotate
-  TRY_CUDA(launch_gather(p, p->alpha, p->d3, T_out, pol ? Q_out : nullptr, pol ? U_out : nullptr, s));
+  TRY_CUDA(launch_gather(p, p->alpha, p->d3, To[0], pol ? Qo[0] : nullptr, pol ? Uo[0] : nullptr, s));
   mark(p, 7, s);
   p->nstage = p->timing ? 7 : 0;
   return TL_OK;
+}
+
+extern "C" tl_status tl_lens_batch(tl_plan *p, int nreal, const double *const *alm_T, const double *const *alm_E,
+                                   const double *const *alm_B, const double *const *alm_phi, void *const *T_out,
+                                   void *const *Q_out, void *const *U_out, void *stream) {
+  if (!p || nreal < 0 || (nreal > 0 && (!alm_T || !T_out))) return TL_ERR_ARG;
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  if (pol && nreal > 0 && (!alm_E || !Q_out || !U_out)) return TL_ERR_ARG;
+  for (int r = 0; r < nreal; ++r) {
+    if (!alm_T[r] || !T_out[r]) return TL_ERR_ARG;
+    if (pol && (!alm_E[r] || !Q_out[r] || !U_out[r])) return TL_ERR_ARG;
+    const bool hp = alm_phi && alm_phi[r];
+    const bool hp0 = alm_phi && alm_phi[0];
+    if (hp != hp0) return TL_ERR_ARG;  // all realisations lensed, or none
+    const void *ptrs[] = {alm_T[r], pol ? alm_E[r] : nullptr, (pol && alm_B) ? alm_B[r] : nullptr,
+                          alm_phi ? alm_phi[r] : nullptr, T_out[r], pol ? Q_out[r] : nullptr,
+                          pol ? U_out[r] : nullptr};
+    for (const void *q : ptrs)
+      if (q && !aligned16(q)) return TL_ERR_ARG;
+  }
+  static const double *const kNull[2] = {nullptr, nullptr};
+  for (int r0 = 0; r0 < nreal; r0 += p->batch) {
+    const int n = (nreal - r0) < p->batch ? (nreal - r0) : p->batch;
+    tl_status st = lens_chunk(p, n, alm_T + r0, pol ? alm_E + r0 : nullptr, (pol && alm_B) ? alm_B + r0 : nullptr,
+                              alm_phi ? alm_phi + r0 : kNull, T_out + r0, pol ? Q_out + r0 : nullptr,
+                              pol ? U_out + r0 : nullptr, (cudaStream_t)stream);
+    if (st != TL_OK) return st;
+  }
+  return TL_OK;
+}
+
+extern "C" tl_status tl_lens(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,
+                             const double *alm_phi, void *T_out, void *Q_out, void *U_out, void *stream) {
+  if (!p || !alm_T || !T_out) return TL_ERR_ARG;
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  if (pol && (!alm_E || !Q_out || !U_out)) return TL_ERR_ARG;
+  const double *aT[1] = {alm_T}, *aE[1] = {alm_E}, *aB[1] = {alm_B}, *aP[1] = {alm_phi};
+  void *To[1] = {T_out}, *Qo[1] = {Q_out}, *Uo[1] = {U_out};
+  return tl_lens_batch(p, 1, aT, aE, aB, aP, To, Qo, Uo, stream);
 }
 
 extern "C" tl_status tl_lens_host(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,

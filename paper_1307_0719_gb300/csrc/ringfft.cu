@@ -399,7 +399,8 @@ static int ringfft_batch(const tl_plan *p) {
 size_t ringfft_smem_bytes(const tl_plan *p) { return ringfft_smem_for(p, ringfft_batch(p)); }
 
 template <typename T>
-static cudaError_t ringfft_t(const tl_plan *p, const MapJob *jobs, int njobs, cudaStream_t s) {
+static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const MapJob *jobs, int njobs,
+                             cudaStream_t s) {
   JobList jl;
   if (njobs > TL_MAX_JOBS) return cudaErrorInvalidValue;
   jl.n = njobs;
@@ -412,10 +413,7 @@ static cudaError_t ringfft_t(const tl_plan *p, const MapJob *jobs, int njobs, cu
     jl.job[i].out = jobs[i].out;
   }
   PlaneSet ps;
-  ps.base[0] = p->d7_T;
-  ps.base[1] = p->d7_Q;
-  ps.base[2] = p->d7_U;
-  ps.base[3] = p->d7_P;
+  for (int i = 0; i < 4; ++i) ps.base[i] = planes[i];
   const int plane_len = p->nrings * (p->mmax + 1);
   const int batch = ringfft_batch(p);
   const size_t smem = ringfft_smem_for(p, batch);
@@ -427,8 +425,15 @@ static cudaError_t ringfft_t(const tl_plan *p, const MapJob *jobs, int njobs, cu
   return cudaGetLastError();
 }
 
+cudaError_t launch_ringfft_planes(const tl_plan *p, const void *const *planes, const MapJob *jobs, int njobs,
+                                  cudaStream_t s) {
+  return p->precision == TL_FP64 ? ringfft_t<double>(p, planes, jobs, njobs, s)
+                                 : ringfft_t<float>(p, planes, jobs, njobs, s);
+}
+
 cudaError_t launch_ringfft(const tl_plan *p, const MapJob *jobs, int njobs, int, cudaStream_t s) {
-  return p->precision == TL_FP64 ? ringfft_t<double>(p, jobs, njobs, s) : ringfft_t<float>(p, jobs, njobs, s);
+  const void *planes[4] = {p->d7_T, p->d7_Q, p->d7_U, p->d7_P};
+  return launch_ringfft_planes(p, planes, jobs, njobs, s);
 }
 
 // double-precision twiddles for the setup kernel live in a temporary buffer

@@ -96,3 +96,35 @@ def test_lens_mixed_fp32(nside, lmax, order):
     out = api.lens(nside, lmax, order, d["T"], d["E"], d["B"], d["phi"], api.MIXED_FP32).cpu().numpy()
     for i, f in enumerate("TQU"):
         assert rel_rms(out[i], ref[f]) < 1e-4, (f, rel_rms(out[i], ref[f]))
+
+
+@pytest.mark.parametrize("precision,tol", [(api.MIXED_TF32x3, 1e-4), (api.MIXED_TF32, 5e-3)])
+@pytest.mark.parametrize("nside,lmax,order", [(32, 64, 4), (64, 128, 3), (16, 40, 1)])
+def test_lens_tensor_core_forms(nside, lmax, order, precision, tol):
+    """Contraction on the tensor cores: 3xTF32 meets the mixed-precision target,
+    plain TF32 is reported with its own (looser) bound."""
+    s = sky(nside, lmax, pol=True, b_scale=0.4)
+    ref = OL.lens(nside, lmax, order, s["T"], s["E"], s["B"], s["phi"])
+    d = to_dev(s)
+    out = api.lens(nside, lmax, order, d["T"], d["E"], d["B"], d["phi"], precision).cpu().numpy()
+    for i, f in enumerate("TQU"):
+        assert rel_rms(out[i], ref[f]) < tol, (f, rel_rms(out[i], ref[f]))
+
+
+@pytest.mark.parametrize("precision", [api.MIXED_TF32x3, api.MIXED_FP32, api.FP64])
+def test_lens_batch_equals_single_calls(precision):
+    """tl_lens_batch over 3 realisations (a shared-basis pair and a single one on
+    tensor-core plans) gives what three tl_lens calls give."""
+    nside, lmax, order = 32, 64, 4
+    skies = [to_dev(sky(nside, lmax, pol=True, seeds=(10 + i, 20 + i, 30 + i), b_scale=0.3)) for i in range(3)]
+    plan = api.Plan(nside, lmax, order, pol=True, precision=precision)
+    try:
+        outs = [o.cpu().numpy() for o in plan.lens_batch(skies)]
+        singles = [plan.lens(sk["T"], sk["E"], sk["B"], sk["phi"]).cpu().numpy() for sk in skies]
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    tol = 1e-13 if precision == api.FP64 else 1e-6
+    for o, s1 in zip(outs, singles):
+        for i in range(3):
+            assert rel_rms(o[i], s1[i]) <= tol
