@@ -171,6 +171,41 @@ tl_status tl_lens_host(tl_plan *plan, const double *alm_T, const double *alm_E,
 tl_status tl_deflection_noalloc(int nside, int lmax, int precision, const double *alm_phi,
                                 void *a_theta, void *a_phi, void *stream);
 
+/*
+ * Batches of realisations of uneven size (different nside / lmax), same order,
+ * fields, precision and flags. The batch groups realisations by geometry and
+ * owns one plan per group.
+ *   tl_batch_create: nreal realisations, nside[i], lmax[i] (host arrays).
+ *   tl_batch_lens modes:
+ *     TL_BATCH_LOOP        one tl_lens call per realisation (the comparison point);
+ *     TL_BATCH_PERSISTENT  tensor-core plans only: waves of realisation pairs, each
+ *                          wave's Legendre stage in one persistent launch whose
+ *                          blocks take (plan, spin, m, ring block) items, sorted
+ *                          by cost, from an atomic counter (no waits between blocks);
+ *     TL_BATCH_GRAPH       the persistent sequence captured once as a CUDA graph per
+ *                          set of buffer pointers and replayed on `stream`.
+ *   The persistent and graph modes need the lensing potential for every realisation
+ *   (else TL_ERR_UNSUPPORTED); on non-tensor-core plans they run the loop.
+ *   Arrays (host) of nreal device pointers, layouts as in tl_lens.
+ *   tl_batch_autotune: times the persistent grid size and the ring-FFT batching
+ *   on the given data (synchronises), keeps the fastest, and appends it to the file
+ *   named by TAYLENS_TUNE_CACHE when set; tl_batch_create reads that file.
+ */
+typedef struct tl_batch tl_batch;
+enum { TL_BATCH_LOOP = 0, TL_BATCH_PERSISTENT = 1, TL_BATCH_GRAPH = 2 };
+tl_status tl_batch_create(int nreal, const int *nside, const int *lmax, int order, int spins, int precision,
+                          int flags, tl_batch **out);
+tl_status tl_batch_destroy(tl_batch *batch);
+tl_status tl_batch_lens(tl_batch *batch, int mode, const double *const *alm_T, const double *const *alm_E,
+                        const double *const *alm_B, const double *const *alm_phi, void *const *T_out,
+                        void *const *Q_out, void *const *U_out, void *stream);
+tl_status tl_batch_autotune(tl_batch *batch, const double *const *alm_T, const double *const *alm_E,
+                            const double *const *alm_B, const double *const *alm_phi, void *const *T_out,
+                            void *const *Q_out, void *const *U_out, void *stream);
+int tl_batch_groups(const tl_batch *batch); /* number of geometry groups */
+int tl_batch_waves(const tl_batch *batch);  /* waves of the persistent mode */
+int tl_batch_grid(const tl_batch *batch);   /* persistent grid size in use */
+
 /* Human-readable text for a status code (static storage). */
 const char *tl_status_string(tl_status status);
 

@@ -12,6 +12,7 @@ TL_OK, TL_ERR_ARG, TL_ERR_NOMEM, TL_ERR_CUDA, TL_ERR_TIMEOUT, TL_ERR_UNSUPPORTED
 TL_SPIN_T, TL_SPIN_QU = 1, 2
 TL_FP64, TL_MIXED_FP32, TL_MIXED_TF32, TL_MIXED_TF32x3, TL_MIXED_BF16x3 = range(5)
 TL_ROTATE = 1
+TL_BATCH_LOOP, TL_BATCH_PERSISTENT, TL_BATCH_GRAPH = 0, 1, 2
 
 # every symbol include/taylens.h declares, with its ctypes signature
 _P = ctypes.c_void_p
@@ -26,6 +27,14 @@ SIGNATURES = {
     "tl_lens_host": (ctypes.c_int, [_P] * 9),
     "tl_lens_batch": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 8),
     "tl_deflection_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "tl_batch_create": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "tl_batch_destroy": (ctypes.c_int, [_P]),
+    "tl_batch_lens": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 8),
+    "tl_batch_autotune": (ctypes.c_int, [_P] * 9),
+    "tl_batch_groups": (ctypes.c_int, [_P]),
+    "tl_batch_waves": (ctypes.c_int, [_P]),
+    "tl_batch_grid": (ctypes.c_int, [_P]),
     "tl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tl_last_stage_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
 }

@@ -172,3 +172,70 @@ def deflection(nside, lmax, alm_phi, precision=FP64):
     finally:
         torch.cuda.synchronize()
         p.close()
+
+
+class Batch:
+    """Realisations of uneven geometry (tl_batch_*): grouped by (nside, lmax), each
+    group with its own plan. `lens` modes: loop, persistent, graph."""
+
+    MODES = {"loop": _lib.TL_BATCH_LOOP, "persistent": _lib.TL_BATCH_PERSISTENT, "graph": _lib.TL_BATCH_GRAPH}
+
+    def __init__(self, nsides, lmaxs, order, pol=True, precision=MIXED_TF32x3, rotate=True):
+        L = _lib.lib()
+        n = len(nsides)
+        self.n, self.pol, self.precision = n, pol, precision
+        self.nsides, self.lmaxs = list(nsides), list(lmaxs)
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        ns = (ctypes.c_int * n)(*nsides)
+        lm = (ctypes.c_int * n)(*lmaxs)
+        spins = _lib.TL_SPIN_T | (_lib.TL_SPIN_QU if pol else 0)
+        h = ctypes.c_void_p()
+        check(L.tl_batch_create(n, ns, lm, order, spins, precision, _lib.TL_ROTATE if rotate else 0,
+                                ctypes.byref(h)), "tl_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().tl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def groups(self):
+        return _lib.lib().tl_batch_groups(self._h)
+
+    @property
+    def waves(self):
+        return _lib.lib().tl_batch_waves(self._h)
+
+    @property
+    def grid(self):
+        return _lib.lib().tl_batch_grid(self._h)
+
+    def outputs(self, device="cuda"):
+        nf = 3 if self.pol else 1
+        return [torch.empty((nf, 12 * ns * ns), dtype=self.dtype, device=device) for ns in self.nsides]
+
+    def _args(self, skies, outs):
+        n = self.n
+        arr = lambda xs: (ctypes.c_void_p * n)(*[None if x is None else x.data_ptr() for x in xs])
+        self._keep = [{k: _alm(sk.get(k), k) for k in ("T", "E", "B", "phi")} for sk in skies]
+        k = self._keep
+        return (arr([x["T"] for x in k]), arr([x["E"] for x in k]) if self.pol else None,
+                arr([x["B"] for x in k]) if self.pol else None, arr([x["phi"] for x in k]),
+                arr([o[0] for o in outs]), arr([o[1] for o in outs]) if self.pol else None,
+                arr([o[2] for o in outs]) if self.pol else None)
+
+    def lens(self, skies, outs, mode="graph", stream=None):
+        a = self._args(skies, outs)
+        check(_lib.lib().tl_batch_lens(self._h, self.MODES[mode], *a, _stream(stream)), "tl_batch_lens")
+        return outs
+
+    def autotune(self, skies, outs, stream=None):
+        a = self._args(skies, outs)
+        check(_lib.lib().tl_batch_autotune(self._h, *a, _stream(stream)), "tl_batch_autotune")

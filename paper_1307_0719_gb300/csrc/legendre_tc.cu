@@ -18,6 +18,7 @@
 // ldmatrix (the two 16-byte halves of a row swap for rows 4..7 of each 8, which
 // makes both the stores and ldmatrix conflict-free).
 #include <math.h>
+#include <string.h>
 
 #include "legendre.cuh"
 
@@ -317,25 +318,31 @@ __device__ __forceinline__ void acc_to_smem(float *xch, int warp, int lane, cons
 }
 
 // ---------------------------------------------------------------------------
-// spin 2 (block = 2 warps: north rings, then their mirrors)
+// kernel bodies: one (m, ring block) unit of work for a 64-thread block
 
+struct TcDesc {
+  RingTable rt;
+  const double *lnorm0;
+  int nside, lmax, mmax, nrings, nreal;
+  const long long *blk;  // first block of each m
+  const float *step;     // step factors per block
+  const float4 *b;       // coefficient fragments (spin 0: the field; spin 2: E, B)
+  const float4 *bp;      // spin 0: the lensing potential's fragments (or NULL)
+  float2 *d7a, *d7b;     // spin 0: field, potential planes; spin 2: Q, U planes
+  long long rstride, rstride_p;
+};
+
+// spin 2: block = 2 warps: 32 north rings (rblk * 32 ..) then their mirrors
 template <int NDER, int MODE>
-__global__ void __launch_bounds__(64) legendre_spin2_tc(RingTable rt, const double *__restrict__ lnorm0, int nside,
-                                                        int lmax, int mmax, int nrings, int nreal,
-                                                        const long long *__restrict__ blkofs,
-                                                        const float *__restrict__ tcstep,
-                                                        const float4 *__restrict__ tcb, float2 *__restrict__ d7q,
-                                                        float2 *__restrict__ d7u, long long rstride) {
+__device__ __forceinline__ void tc2_body(const TcDesc &D, int m, int rblk, float *smem) {
   constexpr int NJ = NDER + 1;
-  // tiles: [warp][hi/lo][j][32 x 8 floats]; reused as xch[64][NJ][8] afterwards
-  __shared__ __align__(128) float smem[2 * 2 * NJ * 256];
-  const int m = blockIdx.y;
+  const RingTable &rt = D.rt;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rn = blockIdx.x * 32 + lane;
-  const bool active = rn < 2 * nside;
+  const int rn = rblk * 32 + lane;
+  const bool active = rn < 2 * D.nside;
   const bool mirror = warp == 1;
-  const int r = active ? (mirror ? nrings - 1 - rn : rn) : 0;
-  const double invL = 1.0 / (double)(lmax + 1);
+  const int r = active ? (mirror ? D.nrings - 1 - rn : rn) : 0;
+  const double invL = 1.0 / (double)(D.lmax + 1);
   float *tile_hi = smem + (warp * 2 + 0) * NJ * 256;
   float *tile_lo = smem + (warp * 2 + 1) * NJ * 256;
 
@@ -350,7 +357,8 @@ __global__ void __launch_bounds__(64) legendre_spin2_tc(RingTable rt, const doub
     double E, ea, eb;
     if (m >= 2) {
       const double md = (double)m;
-      E = lnorm0[m] + 0.5 * log2(md * (md - 1.0) / ((md + 1.0) * (md + 2.0))) + (md + 2.0) * lsh + (md - 2.0) * lch;
+      E = D.lnorm0[m] + 0.5 * log2(md * (md - 1.0) / ((md + 1.0) * (md + 2.0))) + (md + 2.0) * lsh +
+          (md - 2.0) * lch;
       ea = md + 2.0;
       eb = md - 2.0;
     } else {
@@ -374,14 +382,14 @@ __global__ void __launch_bounds__(64) legendre_spin2_tc(RingTable rt, const doub
 #pragma unroll
       for (int i = 0; i < 4; ++i) acc[j][mt][i] = 0.0f;
 
-  const int nblk = (lmax >= l0) ? (lmax - l0 + 8) / 8 : 0;
-  const long long b0 = blkofs[m];
+  const int nblk = (D.lmax >= l0) ? (D.lmax - l0 + 8) / 8 : 0;
+  const long long b0 = D.blk[m];
   for (int blk = 0; blk < nblk; ++blk) {
-    const float4 *stp = (const float4 *)(tcstep + (b0 + blk) * 16);
+    const float4 *stp = (const float4 *)(D.step + (b0 + blk) * 16);
     const float4 A0 = stp[0], A1 = stp[1], C0 = stp[2], C1 = stp[3];
     const float Av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
     const float Cv[8] = {C0.x, C0.y, C0.z, C0.w, C1.x, C1.y, C1.z, C1.w};
-    const float4 bf = tcb[(b0 + blk) * 32 + lane];
+    const float4 bf = D.b[(b0 + blk) * 32 + lane];
     if (__all_sync(0xffffffffu, sc == 0))
       eight_steps<NDER, MODE, false, true>(a, b, sc, e, X, Av, Cv, tile_hi, tile_lo, lane);
     else
@@ -394,11 +402,11 @@ __global__ void __launch_bounds__(64) legendre_spin2_tc(RingTable rt, const doub
   float *xch = smem;  // [64 rings][NJ][8]
   acc_to_smem<NDER>(xch, warp, lane, acc, NJ);
   __syncthreads();
-  if (!active || m > mmax) return;
-  if (mirror && rn == nrings - 1 - rn) return;  // equator: the north thread writes it
+  if (!active || m > D.mmax) return;
+  if (mirror && rn == D.nrings - 1 - rn) return;  // equator: the north thread writes it
   const int me = warp * 32 + lane, partner = (1 - warp) * 32 + lane;
-  const size_t ld = (size_t)(mmax + 1);
-  for (int rho = 0; rho < nreal; ++rho) {
+  const size_t ld = (size_t)(D.mmax + 1);
+  for (int rho = 0; rho < D.nreal; ++rho) {
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const float s1r = xch[(me * NJ + j) * 8 + 4 * rho], s1i = xch[(me * NJ + j) * 8 + 4 * rho + 1];
@@ -406,36 +414,24 @@ __global__ void __launch_bounds__(64) legendre_spin2_tc(RingTable rt, const doub
       const float sg = (j & 1) ? -1.0f : 1.0f;
       const float ar = s1r + sg * s2r, ai = s1i + sg * s2i;
       const float br = s1r - sg * s2r, bi = s1i - sg * s2i;
-      const size_t o = (size_t)rho * rstride + ((size_t)j * nrings + r) * ld + m;
-      d7q[o] = make_float2(-0.5f * ar, -0.5f * ai);
-      d7u[o] = make_float2(-0.5f * bi, 0.5f * br);
+      const size_t o = (size_t)rho * D.rstride + ((size_t)j * D.nrings + r) * ld + m;
+      D.d7a[o] = make_float2(-0.5f * ar, -0.5f * ai);
+      D.d7b[o] = make_float2(-0.5f * bi, 0.5f * br);
     }
   }
 }
 
-// ---------------------------------------------------------------------------
-// spin 0 (block = 2 warps of north rings incl. the equator; south by parity).
-// With PHI the potential's fragments are contracted for j <= 1 as well.
-
+// spin 0: block = 2 warps of north rings incl. the equator (rblk * 64 ..); south
+// by parity. With PHI the potential's fragments are contracted for j <= 1 as well.
 template <int NDER, int MODE, bool PHI>
-__global__ void __launch_bounds__(64) legendre_spin0_tc(RingTable rt, const double *__restrict__ lnorm0, int nside,
-                                                        int lmax, int mmax, int nrings, int nreal,
-                                                        const long long *__restrict__ blkofs,
-                                                        const float *__restrict__ tcstep,
-                                                        const float4 *__restrict__ tcb,
-                                                        const float4 *__restrict__ tcbp, float2 *__restrict__ d7,
-                                                        float2 *__restrict__ d7p, long long rstride,
-                                                        long long rstride_p) {
+__device__ __forceinline__ void tc0_body(const TcDesc &D, int m, int rblk, float *smem, float *xchp) {
   constexpr int NJ = NDER + 1;
-  constexpr int NPJ = PHI ? 2 : 0;
-  __shared__ __align__(128) float smem[2 * 2 * NJ * 256];
-  __shared__ float xchp[PHI ? 64 * 2 * 8 : 1];
-  const int m = blockIdx.y;
+  const RingTable &rt = D.rt;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r0 = blockIdx.x * 64 + threadIdx.x;  // north ring 0 .. 2N-1
-  const bool active = r0 < 2 * nside;
+  const int r0 = rblk * 64 + threadIdx.x;  // north ring 0 .. 2N-1
+  const bool active = r0 < 2 * D.nside;
   const int r = active ? r0 : 0;
-  const double invL = 1.0 / (double)(lmax + 1);
+  const double invL = 1.0 / (double)(D.lmax + 1);
   float *tile_hi = smem + (warp * 2 + 0) * NJ * 256;
   float *tile_lo = smem + (warp * 2 + 1) * NJ * 256;
 
@@ -445,7 +441,7 @@ __global__ void __launch_bounds__(64) legendre_spin0_tc(RingTable rt, const doub
   {
     const double x = rt.z[r], st = rt.sint[r];
     leib_f32<NDER>(x, st, invL, e);
-    const double E = lnorm0[m] + (double)m * (rt.log2_sh[r] + rt.log2_ch[r]);
+    const double E = D.lnorm0[m] + (double)m * (rt.log2_sh[r] + rt.log2_ch[r]);
     seed_f32<NDER>(rt, r, E, (double)m, (double)m, (m & 1) ? -1.0 : 1.0, invL, b, sc);
     if (!active) sc = -1000000;
   }
@@ -467,15 +463,15 @@ __global__ void __launch_bounds__(64) legendre_spin0_tc(RingTable rt, const doub
 #pragma unroll
       for (int i = 0; i < 4; ++i) accp[j][mt][i] = 0.0f;
 
-  const int nblk = (lmax - m + 8) / 8;
-  const long long b0 = blkofs[m];
+  const int nblk = (D.lmax - m + 8) / 8;
+  const long long b0 = D.blk[m];
   for (int blk = 0; blk < nblk; ++blk) {
-    const float4 *stp = (const float4 *)(tcstep + (b0 + blk) * 16);
+    const float4 *stp = (const float4 *)(D.step + (b0 + blk) * 16);
     const float4 A0 = stp[0], A1 = stp[1];
     const float Av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
-    const float4 bf = tcb[(b0 + blk) * 32 + lane];
+    const float4 bf = D.b[(b0 + blk) * 32 + lane];
     float4 bp;
-    if (PHI) bp = tcbp[(b0 + blk) * 32 + lane];
+    if (PHI) bp = D.bp[(b0 + blk) * 32 + lane];
     const float Cv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (__all_sync(0xffffffffu, sc == 0))
       eight_steps<NDER, MODE, false, false>(a, b, sc, e, X, Av, Cv, tile_hi, tile_lo, lane);
@@ -483,7 +479,7 @@ __global__ void __launch_bounds__(64) legendre_spin0_tc(RingTable rt, const doub
       eight_steps<NDER, MODE, true, false>(a, b, sc, e, X, Av, Cv, tile_hi, tile_lo, lane);
     __syncwarp();
     contract<NDER, NJ, MODE>(tile_hi, tile_lo, lane, bf, acc);
-    if (PHI) contract<1, NPJ, MODE>(tile_hi, tile_lo, lane, bp, accp);
+    if (PHI) contract<1, 2, MODE>(tile_hi, tile_lo, lane, bp, accp);
     __syncwarp();
   }
   __syncthreads();
@@ -491,29 +487,73 @@ __global__ void __launch_bounds__(64) legendre_spin0_tc(RingTable rt, const doub
   acc_to_smem<NDER>(xch, warp, lane, acc, NJ);
   if (PHI) acc_to_smem<1>(xchp, warp, lane, accp, 2);
   __syncthreads();
-  if (!active || m > mmax) return;
+  if (!active || m > D.mmax) return;
   const int me = warp * 32 + lane;
-  const int rs = nrings - 1 - r;
-  const size_t ld = (size_t)(mmax + 1);
-  for (int rho = 0; rho < nreal; ++rho) {
+  const int rs = D.nrings - 1 - r;
+  const size_t ld = (size_t)(D.mmax + 1);
+  for (int rho = 0; rho < D.nreal; ++rho) {
 #pragma unroll
     for (int j = 0; j < NJ; ++j) {
       const float *x = xch + (me * NJ + j) * 8 + 4 * rho;
       const float sg = (j & 1) ? -1.0f : 1.0f;
-      const size_t o = (size_t)rho * rstride + (size_t)j * nrings * ld + m;
-      d7[o + (size_t)r * ld] = make_float2(x[0], x[1]);
-      if (rs != r) d7[o + (size_t)rs * ld] = make_float2(sg * x[2], sg * x[3]);
+      const size_t o = (size_t)rho * D.rstride + (size_t)j * D.nrings * ld + m;
+      D.d7a[o + (size_t)r * ld] = make_float2(x[0], x[1]);
+      if (rs != r) D.d7a[o + (size_t)rs * ld] = make_float2(sg * x[2], sg * x[3]);
     }
     if (PHI) {
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const float *x = xchp + (me * 2 + j) * 8 + 4 * rho;
         const float sg = (j & 1) ? -1.0f : 1.0f;
-        const size_t o = (size_t)rho * rstride_p + (size_t)j * nrings * ld + m;
-        d7p[o + (size_t)r * ld] = make_float2(x[0], x[1]);
-        if (rs != r) d7p[o + (size_t)rs * ld] = make_float2(sg * x[2], sg * x[3]);
+        const size_t o = (size_t)rho * D.rstride_p + (size_t)j * D.nrings * ld + m;
+        D.d7b[o + (size_t)r * ld] = make_float2(x[0], x[1]);
+        if (rs != r) D.d7b[o + (size_t)rs * ld] = make_float2(sg * x[2], sg * x[3]);
       }
     }
+  }
+}
+
+template <int NDER, int MODE>
+__global__ void __launch_bounds__(64) legendre_spin2_tc(TcDesc D) {
+  __shared__ __align__(128) float smem[2 * 2 * (NDER + 1) * 256];
+  tc2_body<NDER, MODE>(D, blockIdx.y, blockIdx.x, smem);
+}
+
+template <int NDER, int MODE, bool PHI>
+__global__ void __launch_bounds__(64) legendre_spin0_tc(TcDesc D) {
+  __shared__ __align__(128) float smem[2 * 2 * (NDER + 1) * 256];
+  __shared__ float xchp[PHI ? 64 * 2 * 8 : 1];
+  tc0_body<NDER, MODE, PHI>(D, blockIdx.y, blockIdx.x, smem, xchp);
+}
+
+// ---------------------------------------------------------------------------
+// persistent form: one launch covers the spin-0 and spin-2 work of several
+// plans (geometries). Items (descriptor, kind, m, ring block) are pre-sorted by
+// cost; blocks take them in order from an atomic counter until none is left.
+// kind: 0 spin 0, 1 spin 0 with the potential, 2 spin 2.
+
+template <int NDER, int MODE>
+__global__ void __launch_bounds__(64) legendre_tc_persistent(const TcDesc *__restrict__ descs,
+                                                             const int4 *__restrict__ items, int nitems,
+                                                             int *__restrict__ counter) {
+  __shared__ __align__(128) float smem[2 * 2 * (NDER + 1) * 256];
+  __shared__ float xchp[64 * 2 * 8];
+  __shared__ int cur;
+  for (;;) {
+    __syncthreads();  // the previous item's shared-memory readers are done
+    if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= nitems) return;
+    const int4 w = items[it];
+    const TcDesc D = descs[w.x & 0xffff];
+    const int kind = w.x >> 16;
+    if (kind == 2)
+      tc2_body<NDER, MODE>(D, w.y, w.z, smem);
+    else if (kind == 1)
+      tc0_body<NDER, MODE, true>(D, w.y, w.z, smem, xchp);
+    else
+      tc0_body<NDER, MODE, false>(D, w.y, w.z, smem, xchp);
   }
 }
 
@@ -541,12 +581,38 @@ cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *cons
   return cudaGetLastError();
 }
 
+static TcDesc make_desc(const tl_plan *p, int spin, int nreal, void *d7a, void *d7b, long long rstride,
+                        long long rstride_p) {
+  TcDesc D;
+  D.rt = p->ring;
+  D.lnorm0 = p->lnorm0;
+  D.nside = p->nside;
+  D.lmax = p->lmax;
+  D.mmax = p->mmax;
+  D.nrings = p->nrings;
+  D.nreal = nreal;
+  D.blk = spin == 2 ? p->tc_blk2 : p->tc_blk0;
+  D.step = spin == 2 ? p->tc_step2 : p->tc_step0;
+  D.b = (const float4 *)(spin == 2 ? p->tc_b2 : p->tc_b0);
+  D.bp = (const float4 *)p->tc_bp;
+  D.d7a = (float2 *)d7a;
+  D.d7b = (float2 *)d7b;
+  D.rstride = rstride;
+  D.rstride_p = rstride_p;
+  return D;
+}
+
+// Write the descriptor of a plan's spin-0 or spin-2 work (nreal realisations) to dst.
+void tc_desc_write(const tl_plan *p, int spin, int nreal, void *dst) {
+  const TcDesc d = spin == 2 ? make_desc(p, 2, nreal, p->d7_Q, p->d7_U, p->d7_rstride, 0)
+                             : make_desc(p, 0, nreal, p->d7_T, p->d7_P, p->d7_rstride, p->d7p_rstride);
+  memcpy(dst, &d, sizeof d);
+}
+
 template <int NDER, int MODE>
 static cudaError_t tc2(const tl_plan *p, int nreal, void *dq, void *du, long long rstride, cudaStream_t s) {
   dim3 grid((2 * p->nside + 31) / 32, p->mmax + 1);
-  legendre_spin2_tc<NDER, MODE><<<grid, 64, 0, s>>>(p->ring, p->lnorm0, p->nside, p->lmax, p->mmax, p->nrings, nreal,
-                                                   p->tc_blk2, p->tc_step2, (const float4 *)p->tc_b2,
-                                                   (float2 *)dq, (float2 *)du, rstride);
+  legendre_spin2_tc<NDER, MODE><<<grid, 64, 0, s>>>(make_desc(p, 2, nreal, dq, du, rstride, 0));
   return cudaGetLastError();
 }
 
@@ -554,11 +620,29 @@ template <int NDER, int MODE, bool PHI>
 static cudaError_t tc0(const tl_plan *p, int nreal, void *d7, void *d7p, long long rstride, long long rstride_p,
                        cudaStream_t s) {
   dim3 grid((2 * p->nside + 63) / 64, p->mmax + 1);
-  legendre_spin0_tc<NDER, MODE, PHI><<<grid, 64, 0, s>>>(
-      p->ring, p->lnorm0, p->nside, p->lmax, p->mmax, p->nrings, nreal, p->tc_blk0, p->tc_step0,
-      (const float4 *)p->tc_b0, (const float4 *)p->tc_bp, (float2 *)d7, (float2 *)d7p, rstride, rstride_p);
+  legendre_spin0_tc<NDER, MODE, PHI><<<grid, 64, 0, s>>>(make_desc(p, 0, nreal, d7, d7p, rstride, rstride_p));
   return cudaGetLastError();
 }
+
+template <int NDER, int MODE>
+static cudaError_t tcp(const void *descs, const void *items, int nitems, int *counter, int grid, cudaStream_t s) {
+  legendre_tc_persistent<NDER, MODE><<<grid, 64, 0, s>>>((const TcDesc *)descs, (const int4 *)items, nitems, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_legendre_tc_persistent(int nder, int precision, const void *descs, const void *items, int nitems,
+                                          int *counter, int grid, cudaStream_t s) {
+  const bool x3 = precision == TL_MIXED_TF32x3;
+  switch (nder) {
+#define CASE(n) \
+  case n: return x3 ? tcp<n, 3>(descs, items, nitems, counter, grid, s) : tcp<n, 1>(descs, items, nitems, counter, grid, s);
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t tc_desc_bytes() { return sizeof(TcDesc); }
 
 #define TL_TC_ORDERS(X) X(1) X(2) X(3) X(4) X(5) X(6)
 

@@ -343,6 +343,34 @@ static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s)
   return TL_OK;
 }
 
+namespace tl {
+// After the tensor-core Legendre stage of nreal realisations: per realisation the
+// deflection's and the fields' ring FFTs, then the gather into the outputs.
+tl_status lens_stage_after_legendre(tl_plan *p, int nreal, bool phi, void *const *To, void *const *Qo,
+                                    void *const *Uo, cudaStream_t s) {
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  const size_t mapb = (size_t)p->elem * p->npix;
+  const size_t t2 = 2 * (size_t)p->elem;
+  void *ath = p->alpha, *aph = (char *)p->alpha + mapb;
+  for (int r = 0; r < nreal; ++r) {
+      const size_t off = (size_t)r * p->d7_rstride * t2, offp = (size_t)r * p->d7p_rstride * t2;
+      const void *planes[4] = {(char *)p->d7_T + off, pol ? (char *)p->d7_Q + off : nullptr,
+                               pol ? (char *)p->d7_U + off : nullptr, (char *)p->d7_P + offp};
+      if (phi) {
+        const double L = deriv_norm(p);
+        MapJob jobs[2] = {{3, 1, 0, 0, L, ath}, {3, 0, 1, 1, L, aph}};
+        TRY_CUDA(launch_ringfft_planes(p, planes, jobs, 2, s));
+      } else {
+        TRY_CUDA(cudaMemsetAsync(p->alpha, 0, 2 * mapb, s));
+      }
+      tl_status st = lens_fft(p, planes, s);
+      if (st != TL_OK) return st;
+      TRY_CUDA(launch_gather(p, p->alpha, p->d3, To[r], pol ? Qo[r] : nullptr, pol ? Uo[r] : nullptr, s));
+    }
+  return TL_OK;
+}
+}  // namespace tl
+
 // Lens nreal <= p->batch realisations that share one Legendre launch.
 static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, const double *const *aE,
                             const double *const *aB, const double *const *aP, void *const *To, void *const *Qo,
@@ -368,20 +396,9 @@ static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, cons
     mark(p, 4, s);
     if (pol) TRY_CUDA(launch_legendre_spin2_tc(p, p->tc_nder, nreal, p->d7_Q, p->d7_U, p->d7_rstride, s));
     mark(p, 5, s);
-    for (int r = 0; r < nreal; ++r) {
-      const size_t off = (size_t)r * p->d7_rstride * t2, offp = (size_t)r * p->d7p_rstride * t2;
-      const void *planes[4] = {(char *)p->d7_T + off, pol ? (char *)p->d7_Q + off : nullptr,
-                               pol ? (char *)p->d7_U + off : nullptr, (char *)p->d7_P + offp};
-      if (phi) {
-        const double L = deriv_norm(p);
-        MapJob jobs[2] = {{3, 1, 0, 0, L, ath}, {3, 0, 1, 1, L, aph}};
-        TRY_CUDA(launch_ringfft_planes(p, planes, jobs, 2, s));
-      } else {
-        TRY_CUDA(cudaMemsetAsync(p->alpha, 0, 2 * mapb, s));
-      }
-      tl_status st = lens_fft(p, planes, s);
+    {
+      tl_status st = lens_stage_after_legendre(p, nreal, phi, To, Qo, Uo, s);
       if (st != TL_OK) return st;
-      TRY_CUDA(launch_gather(p, p->alpha, p->d3, To[r], pol ? Qo[r] : nullptr, pol ? Uo[r] : nullptr, s));
     }
     mark(p, 6, s);
     mark(p, 7, s);

@@ -1,0 +1,74 @@
+"""Batched lensing of realisations of uneven size (tl_batch_*): the persistent
+launch and its CUDA-graph replay give what one tl_lens call per realisation gives,
+and one realisation agrees with the FP64 oracle (Naess & Louis 2013, Eq. 4 + R)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle.lens as OL
+from gpu_util import rel_rms, sky, to_dev
+
+pytestmark = pytest.mark.gpu
+api = pytest.importorskip("paper_1307_0719_gb300.api")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+NSIDES = [8, 16, 8, 32, 16, 8, 32]
+LMAXS = [16, 40, 16, 64, 40, 16, 100]
+
+
+def _skies():
+    return [to_dev(sky(ns, lm, pol=True, seeds=(200 + i, 300 + i, 400 + i), b_scale=0.3))
+            for i, (ns, lm) in enumerate(zip(NSIDES, LMAXS))]
+
+
+def test_batch_modes_agree_and_match_oracle():
+    order = 3
+    b = api.Batch(NSIDES, LMAXS, order, pol=True, precision=api.MIXED_TF32x3)
+    try:
+        assert b.groups == 4 and b.waves == 2
+        skies = _skies()
+        res = {}
+        for mode in ("loop", "persistent", "graph", "graph"):
+            outs = b.outputs()
+            b.lens(skies, outs, mode)
+            torch.cuda.synchronize()
+            res.setdefault(mode, []).append([o.cpu().numpy() for o in outs])
+        for mode in ("persistent", "graph"):
+            for run in res[mode]:
+                for i in range(len(NSIDES)):
+                    for f in range(3):
+                        assert rel_rms(run[i][f], res["loop"][0][i][f]) < 1e-6, (mode, i, f)
+        i = 3
+        ref = OL.lens(NSIDES[i], LMAXS[i], order, *(skies[i][k].cpu().numpy() for k in ("T", "E", "B", "phi")))
+        for f, name in enumerate("TQU"):
+            assert rel_rms(res["graph"][1][i][f], ref[name]) < 1e-4
+    finally:
+        torch.cuda.synchronize()
+        b.close()
+
+
+def test_batch_autotune_keeps_results():
+    order = 2
+    b = api.Batch(NSIDES[:4], LMAXS[:4], order, pol=True, precision=api.MIXED_TF32x3)
+    try:
+        skies = _skies()[:4]
+        outs = b.outputs()
+        b.lens(skies, outs, "loop")
+        ref = [o.cpu().numpy() for o in outs]
+        outs2 = b.outputs()
+        b.autotune(skies, outs2)
+        assert b.grid > 0
+        b.lens(skies, outs2, "graph")
+        torch.cuda.synchronize()
+        for o, r in zip(outs2, ref):
+            for f in range(3):
+                assert rel_rms(o[f].cpu().numpy(), r[f]) < 1e-6
+    finally:
+        torch.cuda.synchronize()
+        b.close()
