@@ -238,3 +238,77 @@ void orc_point_sum(int mmax, int nder, int npts, const double *F, const double *
     out[p] = acc;
   }
 }
+
+/*
+ * Transpose of orc_ring_coeffs: given per-ring coefficient gradients
+ * Fb*[r][j][m] (complex, dL/dRe + i dL/dIm of F^{s,j}_m(theta_r)), accumulate the
+ * coefficient gradients (dL/dRe + i dL/dIm of the stored a_lm, m >= 0):
+ *   Tbar_lm = sum_{r,j} d^j 0lambda_lm(theta_r) FbT^j_m(r)
+ *   Ebar_lm = sum_{r,j} [ -lam+^(j) FbQ^j_m - i lam-^(j) FbU^j_m ]
+ *   Bbar_lm = sum_{r,j} [  i lam-^(j) FbQ^j_m - lam+^(j) FbU^j_m ]
+ * (for F = kappa a with complex kappa the gradient of a is conj(kappa) Fbar).
+ * The m = 0 imaginary parts, which the forward map ignores, are returned as 0.
+ * Parallel over m. Outputs are overwritten.
+ */
+void orc_ring_adjoint(int lmax, int mmax, int nder, int nth, const double *theta, const double *FbT,
+                      const double *FbQ, const double *FbU, double *aT, double *aE, double *aB, int nthreads) {
+  size_t na = (size_t)(lmax + 1) * (lmax + 2) / 2;
+  if (aT) memset(aT, 0, sizeof(double) * 2 * na);
+  if (aE) memset(aE, 0, sizeof(double) * 2 * na);
+  if (aB) memset(aB, 0, sizeof(double) * 2 * na);
+  int pol = (FbQ != NULL);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+  {
+    size_t L1 = (size_t)lmax + 1;
+    double *d0 = (double *)malloc(sizeof(double) * (nder + 1) * L1);
+    double *dp = (double *)malloc(sizeof(double) * (nder + 1) * L1);
+    double *dm = (double *)malloc(sizeof(double) * (nder + 1) * L1);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+    for (int m = 0; m <= mmax; ++m) {
+      size_t base = (size_t)m * (2 * lmax + 1 - m) / 2;
+      for (int r = 0; r < nth; ++r) {
+        if (FbT) orc_spin_lambda_derivs(lmax, m, 0, nder, theta[r], d0);
+        if (pol) {
+          orc_spin_lambda_derivs(lmax, m, 2, nder, theta[r], dp);
+          orc_spin_lambda_derivs(lmax, m, -2, nder, theta[r], dm);
+        }
+        for (int j = 0; j <= nder; ++j) {
+          size_t o = (((size_t)r * (nder + 1) + j) * (mmax + 1) + m) * 2;
+          if (FbT) {
+            double fr = FbT[o], fi = FbT[o + 1];
+            for (int l = m; l <= lmax; ++l) {
+              double lam = d0[j * L1 + l];
+              aT[2 * (base + l)] += lam * fr;
+              aT[2 * (base + l) + 1] += lam * fi;
+            }
+          }
+          if (pol) {
+            double qr = FbQ[o], qi = FbQ[o + 1], ur = FbU[o], ui = FbU[o + 1];
+            for (int l = (m > 2 ? m : 2); l <= lmax; ++l) {
+              double lp = 0.5 * (dp[j * L1 + l] + dm[j * L1 + l]);
+              double lmn = 0.5 * (dp[j * L1 + l] - dm[j * L1 + l]);
+              /* Ebar += -lp Qb - i lmn Ub ; Bbar += i lmn Qb - lp Ub */
+              aE[2 * (base + l)] += -lp * qr + lmn * ui;
+              aE[2 * (base + l) + 1] += -lp * qi - lmn * ur;
+              aB[2 * (base + l)] += -lmn * qi - lp * ur;
+              aB[2 * (base + l) + 1] += lmn * qr - lp * ui;
+            }
+          }
+        }
+      }
+      if (m == 0) {
+        for (int l = 0; l <= lmax; ++l) {
+          if (aT) aT[2 * (base + l) + 1] = 0.0;
+          if (aE) aE[2 * (base + l) + 1] = 0.0;
+          if (aB) aB[2 * (base + l) + 1] = 0.0;
+        }
+      }
+    }
+    free(d0); free(dp); free(dm);
+  }
+}

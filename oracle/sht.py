@@ -35,6 +35,9 @@ def lib():
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         L.orc_point_sum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
                                     ctypes.c_int, dp, ctypes.c_int]
+        L.orc_ring_adjoint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -98,4 +101,30 @@ def point_sum(F: np.ndarray, phi, j: int, k: int, nthreads: int | None = None) -
     out = np.zeros(npts)
     lib().orc_point_sum(m1 - 1, nd1 - 1, npts, _p(F.view(np.float64)), _p(phi), j, k, _p(out),
                         nthreads or _threads())
+    return out
+
+
+def ring_adjoint(lmax: int, nder: int, theta, FbT=None, FbQ=None, FbU=None, nthreads: int | None = None):
+    """Transpose of ring_coeffs: coefficient gradients (dL/dRe + i dL/dIm) from the
+    per-ring gradients Fb[r, j, m] (complex). Returns dict with keys among T, E, B."""
+    theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).ravel())
+    any_f = FbT if FbT is not None else FbQ
+    nth, nd1, m1 = any_f.shape
+    na = (lmax + 1) * (lmax + 2) // 2
+    out = {}
+    aT = np.zeros(na, dtype=np.complex128) if FbT is not None else None
+    aE = np.zeros(na, dtype=np.complex128) if FbQ is not None else None
+    aB = np.zeros(na, dtype=np.complex128) if FbQ is not None else None
+    c = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.complex128)
+    fT, fQ, fU = c(FbT), c(FbQ), c(FbU)
+    lib().orc_ring_adjoint(lmax, m1 - 1, nd1 - 1, nth, _p(theta), _vp(None if fT is None else fT.view(np.float64)),
+                           _vp(None if fQ is None else fQ.view(np.float64)),
+                           _vp(None if fU is None else fU.view(np.float64)),
+                           _vp(None if aT is None else aT.view(np.float64)),
+                           _vp(None if aE is None else aE.view(np.float64)),
+                           _vp(None if aB is None else aB.view(np.float64)), nthreads or _threads())
+    if aT is not None:
+        out["T"] = aT
+    if aE is not None:
+        out["E"], out["B"] = aE, aB
     return out
