@@ -23,145 +23,9 @@
 // above 0.02 rad use the double form.
 #include <math.h>
 
-#include "legendre.cuh"
+#include "geometry.cuh"
 
 namespace tl {
-
-static constexpr double kPiD = 3.14159265358979323846;
-
-struct PixLoc {
-  int ring;  // 0-based ring index
-  int idx;   // index within the ring
-};
-
-// ring and in-ring index of a RING-scheme pixel
-__device__ __forceinline__ PixLoc pix2loc(long long p, int nside, long long npix) {
-  const long long ncap = 2LL * nside * (nside - 1);
-  PixLoc L;
-  if (p < ncap) {
-    long long i = (long long)((1.0 + sqrt(1.0 + 2.0 * (double)p)) * 0.5);
-    if (2 * i * (i - 1) > p) --i;
-    if (2 * (i + 1) * i <= p) ++i;
-    L.ring = (int)i - 1;
-    L.idx = (int)(p - 2 * i * (i - 1));
-  } else if (p < npix - ncap) {
-    long long q = p - ncap;
-    long long i = q / (4LL * nside) + nside;
-    L.ring = (int)i - 1;
-    L.idx = (int)(q - (i - nside) * 4LL * nside);
-  } else {
-    long long q = npix - 1 - p;
-    long long i = (long long)((1.0 + sqrt(1.0 + 2.0 * (double)q)) * 0.5);
-    if (2 * i * (i - 1) > q) --i;
-    if (2 * (i + 1) * i <= q) ++i;
-    L.ring = (int)(4LL * nside - i) - 1;
-    L.idx = (int)(4 * i - 1 - (q - 2 * i * (i - 1)));
-  }
-  return L;
-}
-
-__device__ __forceinline__ long long floordiv2(long long a) { return (a >= 0) ? a / 2 : -((1 - a) / 2); }
-
-// HEALPix ang2pix (RING) from z = cos(theta), omz = 1 - |z| and phi in [0, 2pi):
-// belt cells are bounded by the lines N(t + 1/2) -+ (3/4) N z in Z (t = 2 phi / pi);
-// cap cells by tp * tmp and (1 - tp) * tmp in Z with tmp = N sqrt(3 (1 - |z|)),
-// tp = frac(t) (Gorski et al. 2005).
-__device__ __forceinline__ PixLoc ang2loc(double z, double omz, double phi, int nside) {
-  const double N = (double)nside;
-  double t = phi * (2.0 / kPiD);
-  if (t >= 4.0) t -= 4.0;
-  if (t < 0.0) t += 4.0;
-  const double za = fabs(z);
-  PixLoc L;
-  if (za <= 2.0 / 3.0) {
-    const double a = N * (0.5 + t), b = 0.75 * N * z;
-    const long long jp = (long long)floor(a - b);
-    const long long jm = (long long)floor(a + b);
-    long long ir = nside + 1 + jp - jm;  // 1 .. 2N+1
-    if (ir < 1) ir = 1;                   // rounding exactly at |z| = 2/3
-    if (ir > 2LL * nside + 1) ir = 2LL * nside + 1;
-    const long long kshift = 1 - (ir & 1);
-    long long ip = floordiv2(jp + jm - nside + kshift + 1);
-    const long long n4 = 4LL * nside;
-    ip %= n4;
-    if (ip < 0) ip += n4;
-    L.ring = (int)(nside - 2 + ir);
-    L.idx = (int)ip;
-  } else {
-    const double tp = t - floor(t);
-    const double tmp = N * sqrt(3.0 * (omz > 0.0 ? omz : 0.0));
-    long long jp = (long long)floor(tp * tmp);
-    long long jm = (long long)floor((1.0 - tp) * tmp);
-    long long ir = jp + jm + 1;
-    if (ir > nside) ir = nside;  // guards rounding exactly at |z| = 2/3
-    long long ip = (long long)floor(t * (double)ir);
-    ip %= 4 * ir;
-    if (ip < 0) ip += 4 * ir;
-    L.ring = (z > 0.0) ? (int)ir - 1 : (int)(4LL * nside - ir) - 1;
-    L.idx = (int)ip;
-  }
-  return L;
-}
-
-__device__ __forceinline__ double ring_phi(const RingTable &rt, int ring, int idx) {
-  return rt.phi0[ring] + 2.0 * kPiD * (double)idx / (double)rt.nphi[ring];
-}
-
-struct Geo {
-  long long q;
-  double dth, dph;  // offsets to the expansion centre
-  double c2b, s2b;  // cos 2 beta, sin 2 beta
-};
-
-// Double-precision geometry (any pixel, any deflection).
-__device__ __forceinline__ void geo64(const RingTable &rt, int nside, double z, double s, double phi, double ath,
-                                      double aph, bool rot, Geo &g) {
-  const double d = hypot(ath, aph);
-  double sp, cp;
-  sincos(phi, &sp, &cp);
-  double sd, cd;
-  sincos(d, &sd, &cd);
-  const double sinc = sd / d;
-  // n = (s cp, s sp, z), e_th = (z cp, z sp, -s), e_ph = (-sp, cp, 0)
-  const double ux = ath * z * cp - aph * sp, uy = ath * z * sp + aph * cp, uz = -ath * s;
-  const double nx = cd * s * cp + sinc * ux;
-  const double ny = cd * s * sp + sinc * uy;
-  const double nz = cd * z + sinc * uz;
-  const double s2 = hypot(nx, ny);
-  double phi2 = atan2(ny, nx);
-  if (phi2 < 0.0) phi2 += 2.0 * kPiD;
-  const double th2 = atan2(s2, nz);
-  const PixLoc lq = ang2loc(nz, s2 * s2 / (1.0 + fabs(nz)), phi2, nside);
-  g.q = rt.first[lq.ring] + lq.idx;
-  g.dth = th2 - rt.theta[lq.ring];
-  double dph = phi2 - ring_phi(rt, lq.ring, lq.idx);
-  if (dph >= kPiD) dph -= 2.0 * kPiD;
-  if (dph < -kPiD) dph += 2.0 * kPiD;
-  g.dph = dph;
-  g.c2b = 1.0;
-  g.s2b = 0.0;
-  if (rot) {
-    // e_theta(x) transported to x' (rotation about n x u by d):
-    // t = (1 - cos^2(delta) omc) e_th - sin(delta) cos(delta) omc e_ph - sin(d) cos(delta) n
-    const double cdl = ath / d, sdl = aph / d;
-    const double sh = sin(0.5 * d);
-    const double omc = 2.0 * sh * sh;
-    const double ct = 1.0 - cdl * cdl * omc, cph = -sdl * cdl * omc, cn = -sd * cdl;
-    const double tx = ct * z * cp + cph * (-sp) + cn * s * cp;
-    const double ty = ct * z * sp + cph * cp + cn * s * sp;
-    const double tz = ct * (-s) + cn * z;
-    double cp2 = 1.0, sp2 = 0.0;
-    if (s2 > 0.0) {
-      cp2 = nx / s2;
-      sp2 = ny / s2;
-    }
-    const double cb = tx * nz * cp2 + ty * nz * sp2 - tz * s2;  // t . e_theta'
-    const double sb = -tx * sp2 + ty * cp2;                      // t . e_phi'
-    const double nrm = cb * cb + sb * sb;
-    g.c2b = (cb * cb - sb * sb) / nrm;
-    g.s2b = 2.0 * cb * sb / nrm;
-  }
-}
 
 // Increment-form geometry in float (see the header comment); pixel lookup in double.
 __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, double z, double s, double phi,

@@ -55,4 +55,97 @@ template <typename T> struct __align__(4 * sizeof(T)) Rec2 {
   T A, cterm, pad0, pad1;
 };
 
+// ---------------------------------------------------------------------------
+// recurrence pieces shared by the forward and adjoint Legendre kernels
+
+// Binomial coefficient for small arguments; a plain loop, so that with the
+// unrolled (constant) arguments of the kernels below it folds to a constant.
+__host__ __device__ __forceinline__ constexpr int binom(int n, int k) {
+  int r = 1;
+  for (int t = 1; t <= k; ++t) r = r * (n - k + t) / t;
+  return r;
+}
+
+// Seed mantissas (normalised derivatives) of s_lambda_{l0,m} at ring r.
+// E = log2 |lambda|, exponents (a, b) of sin(th/2), cos(th/2), sign.
+template <typename T, int NDER>
+__device__ __forceinline__ void seed_values(const RingTable &rt, int r, double E, double a, double b,
+                                            double sign, double invL, T (&cur)[NDER + 1], int &sc) {
+  typedef RealTraits<T> RT;
+  // scale: E - SB*sc in (H - SB, H]
+  int s0 = (int)ceil((E - RT::H) / (double)RT::SB);
+  if (s0 > 0) s0 = 0;
+  sc = s0;
+  const double mant = sign * exp2(E - (double)RT::SB * s0);
+  // d^j/dth^j f = f * B_j with B_{j+1} = sum_i C(j,i) g_{i+1} B_{j-i},
+  // g_k = d^k/dth^k ln f = a d^k ln sin(th/2) + b d^k ln cos(th/2)
+  double g[NDER + 1];
+  const double *dls = rt.dls + (size_t)r * (TL_MAX_NDER + 1);
+  const double *dlc = rt.dlc + (size_t)r * (TL_MAX_NDER + 1);
+#pragma unroll
+  for (int k = 1; k <= NDER; ++k) g[k] = a * dls[k - 1] + b * dlc[k - 1];
+  double B[NDER + 1];
+  B[0] = 1.0;
+#pragma unroll
+  for (int j = 0; j < NDER; ++j) {
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i <= j; ++i) acc += (double)binom(j, i) * g[i + 1] * B[j - i];
+    B[j + 1] = acc;
+  }
+  double p = 1.0;
+#pragma unroll
+  for (int j = 0; j <= NDER; ++j) {
+    cur[j] = (T)(mant * B[j] * p);
+    p *= invL;
+  }
+}
+
+// Leibniz coefficients e[j][i] = C(j, i) cos^(i)(theta) / L^i, i = 1..j, once per thread.
+template <typename T, int NDER> struct Leib {
+  T e[NDER + 1][NDER + 1];
+};
+template <typename T, int NDER>
+__device__ __forceinline__ void leibniz_coefs(double x, double st, double invL, Leib<T, NDER> &L) {
+  double p = 1.0, dc[NDER + 1];
+#pragma unroll
+  for (int i = 0; i <= NDER; ++i) {
+    const double v = (i % 4 == 0) ? x : (i % 4 == 1) ? -st : (i % 4 == 2) ? -x : st;
+    dc[i] = v * p;
+    p *= invL;
+  }
+#pragma unroll
+  for (int j = 0; j <= NDER; ++j)
+#pragma unroll
+    for (int i = 0; i <= NDER; ++i) L.e[j][i] = (i >= 1 && i <= j) ? (T)(binom(j, i) * dc[i]) : (T)0;
+}
+
+// In-place step: old (mu_{l-1}) becomes mu_{l+1} from cur (mu_l):
+//   old^(j) = A (X cur^(j) + sum_{i>=1} e[j][i] cur^(j-i)) - old^(j)
+template <typename T, int NDER>
+__device__ __forceinline__ void step_into(T (&old)[NDER + 1], const T (&cur)[NDER + 1], const Leib<T, NDER> &L,
+                                          T X, T A) {
+#pragma unroll
+  for (int j = NDER; j >= 0; --j) {
+    T acc = X * cur[j];
+#pragma unroll
+    for (int i = 1; i <= j; ++i) acc = fma(L.e[j][i], cur[j - i], acc);
+    old[j] = fma(A, acc, -old[j]);
+  }
+}
+
+// Exponent rescaling while the values are below the representable range.
+template <typename T, int NDER>
+__device__ __forceinline__ void rescale(T (&a)[NDER + 1], T (&b)[NDER + 1], const T lead, int &sc) {
+  typedef RealTraits<T> RT;
+  if (sc < 0 && fabs(lead) > RT::THR) {
+#pragma unroll
+    for (int j = 0; j <= NDER; ++j) {
+      a[j] *= RT::STEP;
+      b[j] *= RT::STEP;
+    }
+    ++sc;
+  }
+}
+
 }  // namespace tl
