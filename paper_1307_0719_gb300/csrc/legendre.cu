@@ -139,10 +139,7 @@ __global__ void __launch_bounds__(128) legendre_spin0_kernel(RingTable rt, const
 
   T a[NDER + 1], b[NDER + 1];  // alternately mu_{l-1} and mu_l
   int sc;
-  {
-    const double E = lnorm0[m] + (double)m * (rt.log2_sh[r] + rt.log2_ch[r]);
-    seed_values<T, NDER>(rt, r, E, (double)m, (double)m, (m & 1) ? -1.0 : 1.0, invL, b, sc);
-  }
+  seed_spin0<T, NDER>(rt, lnorm0, r, m, invL, b, sc);
 #pragma unroll
   for (int j = 0; j <= NDER; ++j) a[j] = (T)0;
 
@@ -284,26 +281,8 @@ __global__ void __launch_bounds__(2 * RP) legendre_spin2_kernel(RingTable rt, co
     Leib<T, NDER> LC;
     leibniz_coefs<T, NDER>(x, st, invL, LC);
     T a[NDER + 1], b[NDER + 1];
-    int sc, l0;
-    {
-      const double lsh = rt.log2_sh[r], lch = rt.log2_ch[r];
-      double E, ea, eb;
-      if (m >= 2) {
-        l0 = m;
-        const double md = (double)m;
-        E = lnorm0[m] + 0.5 * log2(md * (md - 1.0) / ((md + 1.0) * (md + 2.0))) + (md + 2.0) * lsh +
-            (md - 2.0) * lch;
-        ea = md + 2.0;
-        eb = md - 2.0;
-      } else {
-        l0 = 2;
-        const double c4 = (m == 0) ? 6.0 : 4.0;  // C(4, 2+m)
-        E = log2(sqrt(5.0 / (4.0 * 3.14159265358979323846)) * sqrt(c4)) + (2.0 + m) * lsh + (2.0 - m) * lch;
-        ea = 2.0 + m;
-        eb = 2.0 - m;
-      }
-      seed_values<T, NDER>(rt, r, E, ea, eb, (m & 1) ? -1.0 : 1.0, invL, b, sc);
-    }
+    int sc;
+    const int l0 = seed_spin2<T, NDER>(rt, lnorm0, r, m, invL, b, sc);
 #pragma unroll
     for (int j = 0; j <= NDER; ++j) a[j] = (T)0;
     const Rec2<T> *rm = rec + (long long)m * (2 * lmax + 1 - m) / 2;

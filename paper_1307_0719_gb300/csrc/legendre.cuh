@@ -101,6 +101,40 @@ __device__ __forceinline__ void seed_values(const RingTable &rt, int r, double E
   }
 }
 
+// Seed of the spin-0 recurrence at l0 = m: N_m sin^m(th/2) cos^m(th/2) (-1)^m.
+template <typename T, int NDER>
+__device__ __forceinline__ void seed_spin0(const RingTable &rt, const double *__restrict__ lnorm0, int r, int m,
+                                           double invL, T (&cur)[NDER + 1], int &sc) {
+  const double E = lnorm0[m] + (double)m * (rt.log2_sh[r] + rt.log2_ch[r]);
+  seed_values<T, NDER>(rt, r, E, (double)m, (double)m, (m & 1) ? -1.0 : 1.0, invL, cur, sc);
+}
+
+// Seed of the spin-2 recurrence at l0 = max(m, 2); returns l0. For m >= 2 the
+// seed is N_m sqrt(m(m-1)/((m+1)(m+2))) sin^(m+2)(th/2) cos^(m-2)(th/2); for
+// m < 2, sqrt(5/4pi) sqrt(C(4, 2+m)) sin^(2+m)(th/2) cos^(2-m)(th/2); sign (-1)^m.
+template <typename T, int NDER>
+__device__ __forceinline__ int seed_spin2(const RingTable &rt, const double *__restrict__ lnorm0, int r, int m,
+                                          double invL, T (&cur)[NDER + 1], int &sc) {
+  const double lsh = rt.log2_sh[r], lch = rt.log2_ch[r];
+  double E, ea, eb;
+  int l0;
+  if (m >= 2) {
+    l0 = m;
+    const double md = (double)m;
+    E = lnorm0[m] + 0.5 * log2(md * (md - 1.0) / ((md + 1.0) * (md + 2.0))) + (md + 2.0) * lsh + (md - 2.0) * lch;
+    ea = md + 2.0;
+    eb = md - 2.0;
+  } else {
+    l0 = 2;
+    const double c4 = (m == 0) ? 6.0 : 4.0;  // C(4, 2+m)
+    E = log2(sqrt(5.0 / (4.0 * 3.14159265358979323846)) * sqrt(c4)) + (2.0 + m) * lsh + (2.0 - m) * lch;
+    ea = 2.0 + m;
+    eb = 2.0 - m;
+  }
+  seed_values<T, NDER>(rt, r, E, ea, eb, (m & 1) ? -1.0 : 1.0, invL, cur, sc);
+  return l0;
+}
+
 // Leibniz coefficients e[j][i] = C(j, i) cos^(i)(theta) / L^i, i = 1..j, once per thread.
 template <typename T, int NDER> struct Leib {
   T e[NDER + 1][NDER + 1];
