@@ -73,3 +73,49 @@ def test_unlensed_gradient_matches_central_differences():
             fd = (lp - lm) / (2 * h)
             an = gr[field][idx].real if part == 0 else gr[field][idx].imag
             assert abs(fd - an) < 1e-8 * max(1.0, abs(fd)), (field, l, m, part, fd, an)
+
+
+def test_geometry_jacobian_accuracy():
+    """The Richardson Jacobian of (theta', phi', beta) against 40-digit central
+    differences of the same construction (displacement along the geodesic,
+    Rodrigues rotation of e_theta about n x u), at points from the pole to the
+    equator; error measured against the largest entry of each row."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+
+    def geo(z, s, phi, ath, aph):
+        z, s, phi, ath, aph = (mp.mpf(v) for v in (z, s, phi, ath, aph))
+        cp, sp = mp.cos(phi), mp.sin(phi)
+        n = [s * cp, s * sp, z]
+        et = [z * cp, z * sp, -s]
+        ep = [-sp, cp, mp.mpf(0)]
+        d = mp.sqrt(ath ** 2 + aph ** 2)
+        u = [(ath * a + aph * b) / d for a, b in zip(et, ep)]
+        n2 = [mp.cos(d) * a + mp.sin(d) * b for a, b in zip(n, u)]
+        ax = [n[1] * u[2] - n[2] * u[1], n[2] * u[0] - n[0] * u[2], n[0] * u[1] - n[1] * u[0]]
+        cr = [ax[1] * et[2] - ax[2] * et[1], ax[2] * et[0] - ax[0] * et[2], ax[0] * et[1] - ax[1] * et[0]]
+        dot = sum(a * b for a, b in zip(ax, et))
+        t = [a * mp.cos(d) + b * mp.sin(d) + c * dot * (1 - mp.cos(d)) for a, b, c in zip(et, cr, ax)]
+        th2 = mp.atan2(mp.sqrt(n2[0] ** 2 + n2[1] ** 2), n2[2])
+        ph2 = mp.atan2(n2[1], n2[0])
+        et2 = [mp.cos(th2) * mp.cos(ph2), mp.cos(th2) * mp.sin(ph2), -mp.sin(th2)]
+        ep2 = [-mp.sin(ph2), mp.cos(ph2), mp.mpf(0)]
+        beta = mp.atan2(sum(a * b for a, b in zip(t, ep2)), sum(a * b for a, b in zip(t, et2)))
+        return th2, ph2, beta
+
+    rng = np.random.default_rng(3)
+    hh = mp.mpf("1e-15")
+    for th, sc in [(0.042, 1e-3), (0.1, 7e-4), (1.0, 7e-4), (3.1, 7e-4), (0.02, 5e-3)]:
+        for _ in range(3):
+            phi = rng.uniform(0, 2 * np.pi)
+            ath, aph = rng.normal(scale=sc, size=2)
+            z, s = np.cos(th), np.sin(th)
+            J = A._jacobian(np.array([z]), np.array([s]), np.array([phi]), np.array([ath]), np.array([aph]),
+                            np.array([0.0]), np.array([0.0]))
+            for comp, (e0, e1) in enumerate(((1, 0), (0, 1))):
+                fp = geo(z, s, phi, ath + hh * e0, aph + hh * e1)
+                fm = geo(z, s, phi, ath - hh * e0, aph - hh * e1)
+                ref = [float((a - b) / (2 * hh)) for a, b in zip(fp, fm)]
+                scale = max(abs(v) for v in ref)
+                for q in range(3):
+                    assert abs(J[comp][q][0] - ref[q]) < 1e-9 * scale, (th, comp, q, J[comp][q][0], ref[q])
