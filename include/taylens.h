@@ -148,6 +148,37 @@ tl_status tl_lens_host(tl_plan *plan, const double *alm_T, const double *alm_E,
                        void *U_out, void *stream);
 
 /*
+ * Reverse mode of tl_lens (the transpose of its linearisation): gradients of a
+ * scalar loss with respect to the coefficients, given its gradients with
+ * respect to the lensed maps. Naess & Louis 2013, Sec. II (Eq. 4 and the
+ * rotation R of Eq. 2), differentiated step by step: the rotation and the Taylor
+ * sum of Eq. 4 at each pixel, the displacement geometry of Sec. II.A, the ring
+ * synthesis of the derivative maps and the spherical-harmonic (Legendre) stage.
+ * The expansion pixel q(p) of every output pixel is held fixed: the lensed map is
+ * piecewise smooth in the deflection and q is constant between its jumps.
+ *   alm_T, alm_E, alm_B, alm_phi   device, as in tl_lens (alm_phi NULL: alpha = 0)
+ *   gT, gQ, gU     device [npix] dL/dT', dL/dQ', dL/dU' in the plan's map type
+ *                  (gQ, gU required for TL_SPIN_QU plans, ignored otherwise)
+ *   galm_T, galm_E, galm_B, galm_phi
+ *                  device [nalm] complex128 outputs, dL/dRe + i dL/dIm per stored
+ *                  coefficient (m >= 0; the imaginary part is 0 at m = 0, where the
+ *                  coefficients are real). Any of them may be NULL to skip it;
+ *                  galm_E and galm_B must be NULL for TL_SPIN_T plans.
+ *   galpha         NULL, or device [2][npix] in the plan's map type: receives
+ *                  dL/da_theta and dL/da_phi per pixel (the deflection gradient)
+ *   stream         cudaStream_t (NULL: legacy default stream)
+ * The forward lens is recomputed inside the call. The displacement geometry and
+ * its Jacobian are evaluated in double precision for every plan precision.
+ * First use allocates the adjoint workspace (the size of the derivative maps
+ * plus, without galpha, 2 npix map elements), counted in tl_plan_workspace_bytes.
+ * Errors: TL_ERR_ARG for NULL required pointers, misaligned buffers or E/B
+ * outputs on a temperature-only plan; TL_ERR_NOMEM, TL_ERR_CUDA as elsewhere.
+ */
+tl_status tl_lens_adjoint(tl_plan *plan, const double *alm_T, const double *alm_E, const double *alm_B,
+                          const double *alm_phi, const void *gT, const void *gQ, const void *gU, double *galm_T,
+                          double *galm_E, double *galm_B, double *galm_phi, void *galpha, void *stream);
+
+/*
  * tl_deflection without any allocation, for callers that cannot allocate device
  * memory while they run (code inside a memory pool or allocator of its own,
  * or a process whose device memory is fixed up front).

@@ -3,4 +3,4 @@
 The computation runs in the CUDA library libtaylens.so (C ABI in include/taylens.h);
 this package only marshals arguments. PyTorch provides device memory and streams.
 """
-from .api import Plan, lens, synth_derivs, deflection, FP64, MIXED_FP32, MIXED_TF32, MIXED_TF32x3  # noqa: F401
+from .api import Plan, LensFunction, lens, synth_derivs, deflection, FP64, MIXED_FP32, MIXED_TF32, MIXED_TF32x3  # noqa: F401

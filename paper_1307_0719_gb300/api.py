@@ -140,6 +140,29 @@ class Plan:
                                       _stream(stream)), "tl_lens_host")
         return out
 
+    def lens_adjoint(self, alm_T, alm_E, alm_B, alm_phi, gT, gQ=None, gU=None, want=("T", "E", "B", "phi"),
+                     galpha=False, stream=None):
+        """tl_lens_adjoint: gradients (complex128 [nalm], dL/dRe + i dL/dIm) of the fields
+        named in `want` from the map gradients gT, gQ, gU (the plan's map dtype). Returns a
+        dict; with galpha=True it also holds "alpha", the [2, Npix] deflection gradient."""
+        aT, aE, aB, aP = (_alm(alm_T, "alm_T"), _alm(alm_E, "alm_E"), _alm(alm_B, "alm_B"),
+                          _alm(alm_phi, "alm_phi"))
+        dev = aT.device
+        for name, g in (("gT", gT), ("gQ", gQ), ("gU", gU)):
+            if g is not None and (g.dtype != self.dtype or not g.is_contiguous() or not g.is_cuda):
+                raise ValueError(f"{name} must be a contiguous CUDA tensor of {self.dtype}")
+        fields = [f for f in ("T", "E", "B", "phi") if f in want and (self.pol or f not in ("E", "B"))]
+        out = {f: torch.zeros(self.nalm, dtype=torch.complex128, device=dev) for f in fields}
+        ga = torch.empty((2, self.npix), dtype=self.dtype, device=dev) if galpha else None
+        o = lambda f: _ptr(torch.view_as_real(out[f])) if f in out else None
+        check(_lib.lib().tl_lens_adjoint(self._h, _ptr(aT), _ptr(aE), _ptr(aB), _ptr(aP), _ptr(gT),
+                                         _ptr(gQ if self.pol else None), _ptr(gU if self.pol else None),
+                                         o("T"), o("E"), o("B"), o("phi"), _ptr(ga), _stream(stream)),
+              "tl_lens_adjoint")
+        if galpha:
+            out["alpha"] = ga
+        return out
+
     def last_stage_ms(self):
         buf = (ctypes.c_float * 8)()
         n = _lib.lib().tl_last_stage_ms(self._h, buf, 8)
@@ -239,3 +262,31 @@ class Batch:
     def autotune(self, skies, outs, stream=None):
         a = self._args(skies, outs)
         check(_lib.lib().tl_batch_autotune(self._h, *a, _stream(stream)), "tl_batch_autotune")
+
+
+class LensFunction(torch.autograd.Function):
+    """Differentiable lensing: lensed maps [3 or 1, Npix] from complex128 coefficients.
+    The backward pass is tl_lens_adjoint (the expansion pixels held fixed). Use as
+    LensFunction.apply(plan, alm_T, alm_E, alm_B, alm_phi); alm_E/alm_B/alm_phi may be None."""
+
+    @staticmethod
+    def forward(ctx, plan, alm_T, alm_E, alm_B, alm_phi):
+        ctx.plan = plan
+        ctx.save_for_backward(alm_T, alm_E, alm_B, alm_phi)
+        return plan.lens(alm_T.detach(), None if alm_E is None else alm_E.detach(),
+                         None if alm_B is None else alm_B.detach(),
+                         None if alm_phi is None else alm_phi.detach())
+
+    @staticmethod
+    def backward(ctx, gout):
+        plan = ctx.plan
+        alm_T, alm_E, alm_B, alm_phi = ctx.saved_tensors
+        g = gout.to(plan.dtype).contiguous()
+        want = []
+        for name, t, i in (("T", alm_T, 1), ("E", alm_E, 2), ("B", alm_B, 3), ("phi", alm_phi, 4)):
+            if t is not None and ctx.needs_input_grad[i]:
+                want.append(name)
+        res = plan.lens_adjoint(alm_T, alm_E, alm_B, alm_phi, g[0].contiguous(),
+                                g[1].contiguous() if plan.pol else None,
+                                g[2].contiguous() if plan.pol else None, want=tuple(want))
+        return (None, res.get("T"), res.get("E"), res.get("B"), res.get("phi"))

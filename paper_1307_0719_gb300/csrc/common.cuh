@@ -69,6 +69,8 @@ struct tl_plan {
   long long d7_rstride, d7p_rstride;  // T2 elements between realisations' D7 planes
   void *d3;            // derivative maps [3*nmaps][npix] (T), Taylor-ready
   void *alpha;         // [2][npix] (T)
+  void *adj_dbar;      // adjoint: gradients of the derivative maps, as d3 (allocated on first use)
+  void *adj_ga;        // adjoint: [2][npix] deflection gradients (allocated on first use)
   void *stage_alm;     // host-path staging: 4 * nalm complex128
   void *stage_out;     // host-path staging: 3 * npix (T)
   size_t bytes;
@@ -105,6 +107,22 @@ cudaError_t launch_ringfft(const tl_plan *p, const MapJob *jobs, int njobs, int 
 // as launch_ringfft with explicit plane bases (T, Q, U, phi) for one realisation
 cudaError_t launch_ringfft_planes(const tl_plan *p, const void *const *planes, const MapJob *jobs, int njobs,
                                   cudaStream_t s);
+// One output plane of the adjoint ring FFT: plane 0..2 (T, Q, U) row j from the
+// maps d_theta^j d_phi^k, k < nk, at in + map_index(j, k) npix; plane 3 (phi) row
+// j from the single map at in (j = 1: the theta deflection, j = 0: the phi one).
+struct AdjMapJob {
+  int plane, j, nk;
+  const void *in;
+};
+cudaError_t launch_ringfft_adjoint(const tl_plan *p, void *const *planes, const AdjMapJob *jobs, int njobs,
+                                   cudaStream_t s);
+cudaError_t launch_legendre_adj0(const tl_plan *p, int nder_T, const void *FT, const void *FP, double *aT,
+                                 double *aP, cudaStream_t s);
+cudaError_t launch_legendre_adj2(const tl_plan *p, int nder, const void *FQ, const void *FU, double *aE, double *aB,
+                                 cudaStream_t s);
+cudaError_t launch_adj_finish(const tl_plan *p, double *gT, double *gP, double *gE, double *gB, cudaStream_t s);
+cudaError_t launch_gather_adjoint(const tl_plan *p, const void *alpha, const void *d3, const void *gT, const void *gQ,
+                                  const void *gU, void *dbar, void *ga, cudaStream_t s);
 cudaError_t launch_tcstep(const tl_plan *p, int s, const long long *blkofs, const void *tab, float *out,
                           cudaStream_t st);
 cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *const *a, const double *const *b,

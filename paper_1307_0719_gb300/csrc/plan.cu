@@ -77,7 +77,8 @@ static void free_plan(tl_plan *p) {
                   p->ring.dls, p->ring.dlc, p->ring.nphi, p->ring.inorth, p->ring.first, p->blue.spec,
                   p->blue.offset, p->blue.mlen, p->lnorm0, p->twiddle, p->tab0, p->tab2, p->rec_T, p->rec_P,
                   p->rec_QU,
-                  p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->stage_alm, p->stage_out,
+                  p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->adj_dbar, p->adj_ga, p->stage_alm,
+                  p->stage_out,
                   p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2};
   for (void *q : ptrs)
     if (q) cudaFree(q);
@@ -481,6 +482,112 @@ extern "C" tl_status tl_lens(tl_plan *p, const double *alm_T, const double *alm_
   const double *aT[1] = {alm_T}, *aE[1] = {alm_E}, *aB[1] = {alm_B}, *aP[1] = {alm_phi};
   void *To[1] = {T_out}, *Qo[1] = {Q_out}, *Uo[1] = {U_out};
   return tl_lens_batch(p, 1, aT, aE, aB, aP, To, Qo, Uo, stream);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint (reverse mode) of tl_lens
+
+// The forward lens of one realisation up to its gather: Taylor-ready maps in d3
+// and the deflection in alpha.
+static tl_status forward_derivs(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,
+                                const double *alm_phi, cudaStream_t s) {
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  const size_t mapb = (size_t)p->elem * p->npix;
+  void *ath = p->alpha, *aph = (char *)p->alpha + mapb;
+  bool defl_done = false;
+  if (p->batch > 1) {
+    const double *aT[1] = {alm_T}, *aE[1] = {alm_E}, *aB[1] = {alm_B}, *aP[1] = {alm_phi};
+    TRY_CUDA(launch_tcprep(p, 0, 1, aT, nullptr, p->tc_blk0, p->tab0, p->tc_b0, s));
+    if (alm_phi) TRY_CUDA(launch_tcprep(p, 0, 1, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
+    TRY_CUDA(launch_legendre_spin0_tc(p, p->tc_nder, 1, alm_phi != nullptr, p->d7_T, p->d7_P, p->d7_rstride,
+                                      p->d7p_rstride, s));
+    if (pol) {
+      TRY_CUDA(launch_tcprep(p, 2, 1, aE, aB, p->tc_blk2, p->tab2, p->tc_b2, s));
+      TRY_CUDA(launch_legendre_spin2_tc(p, p->tc_nder, 1, p->d7_Q, p->d7_U, p->d7_rstride, s));
+    }
+  } else {
+    const bool fuse = alm_phi && p->order >= 1;
+    if (alm_phi && !fuse) {
+      tl_status st = deflection_impl(p, alm_phi, ath, aph, s);
+      if (st != TL_OK) return st;
+      defl_done = true;
+    }
+    TRY_CUDA(launch_prep_spin0(p, alm_T, fuse ? alm_phi : nullptr, s));
+    TRY_CUDA(launch_legendre_spin0(p, p->order, fuse, p->d7_T, p->d7_P, s));
+    if (pol) {
+      TRY_CUDA(launch_prep_spin2(p, alm_E, alm_B, s));
+      TRY_CUDA(launch_legendre_spin2(p, p->order, s));
+    }
+  }
+  if (alm_phi && !defl_done) {
+    tl_status st = deflection_fft(p, ath, aph, s);
+    if (st != TL_OK) return st;
+  } else if (!alm_phi) {
+    TRY_CUDA(cudaMemsetAsync(p->alpha, 0, 2 * mapb, s));
+  }
+  const void *planes[4] = {p->d7_T, p->d7_Q, p->d7_U, p->d7_P};
+  return lens_fft(p, planes, s);
+}
+
+extern "C" tl_status tl_lens_adjoint(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,
+                                     const double *alm_phi, const void *gT, const void *gQ, const void *gU,
+                                     double *galm_T, double *galm_E, double *galm_B, double *galm_phi, void *galpha,
+                                     void *stream) {
+  if (!p || !alm_T || !gT) return TL_ERR_ARG;
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  if (pol && (!alm_E || !gQ || !gU)) return TL_ERR_ARG;
+  if (!pol && (galm_E || galm_B)) return TL_ERR_ARG;
+  const void *ptrs[] = {alm_T, alm_E, alm_B, alm_phi, gT, gQ, gU, galm_T, galm_E, galm_B, galm_phi, galpha};
+  for (const void *q : ptrs)
+    if (q && !aligned16(q)) return TL_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long na = nalm(p->lmax);
+  const size_t mapb = (size_t)p->elem * p->npix;
+  const int nfield = pol ? 3 : 1;
+  const size_t dbar_bytes = mapb * nfield * p->nmaps;
+  if (!p->adj_dbar) TRY_CUDA(dalloc(&p->adj_dbar, dbar_bytes, &p->bytes));
+  if (!galpha && !p->adj_ga) TRY_CUDA(dalloc(&p->adj_ga, 2 * mapb, &p->bytes));
+  void *ga = galpha ? galpha : p->adj_ga;
+
+  // 1. forward quantities: d3 (Taylor-ready maps) and alpha
+  {
+    tl_status st = forward_derivs(p, alm_T, pol ? alm_E : nullptr, pol ? alm_B : nullptr, alm_phi, s);
+    if (st != TL_OK) return st;
+  }
+  // 2. gather + Taylor + rotate, transposed: Dbar and the deflection gradient
+  TRY_CUDA(cudaMemsetAsync(p->adj_dbar, 0, dbar_bytes, s));
+  TRY_CUDA(launch_gather_adjoint(p, p->alpha, p->d3, gT, pol ? gQ : nullptr, pol ? gU : nullptr, p->adj_dbar, ga, s));
+  // 3. ring synthesis, transposed, into the (now free) Legendre planes
+  std::vector<AdjMapJob> jobs;
+  const int n = p->order;
+  for (int f = 0; f < nfield; ++f) {
+    if (f == 0 && !galm_T) continue;
+    if (f > 0 && !galm_E && !galm_B) continue;
+    for (int j = 0; j <= n; ++j)
+      jobs.push_back(AdjMapJob{f, j, n - j + 1, (const char *)p->adj_dbar + mapb * (size_t)f * p->nmaps});
+  }
+  if (galm_phi) {
+    jobs.push_back(AdjMapJob{3, 1, 1, ga});
+    jobs.push_back(AdjMapJob{3, 0, 1, (const char *)ga + mapb});
+  }
+  void *planes[4] = {p->d7_T, p->d7_Q, p->d7_U, p->d7_P};
+  TRY_CUDA(launch_ringfft_adjoint(p, planes, jobs.data(), (int)jobs.size(), s));
+  // 4. Legendre stages, transposed, accumulated straight into the outputs
+  const size_t ab = (size_t)na * 16;
+  double *outs[4] = {galm_T, galm_E, galm_B, galm_phi};
+  for (double *o : outs)
+    if (o) TRY_CUDA(cudaMemsetAsync(o, 0, ab, s));
+  if (galm_T || galm_phi)
+    TRY_CUDA(launch_legendre_adj0(p, galm_T ? n : -1, galm_T ? p->d7_T : nullptr, galm_phi ? p->d7_P : nullptr,
+                                  galm_T, galm_phi, s));
+  if (pol && (galm_E || galm_B)) {
+    // A_{l+1} and m s/(l(l+1)) of the spin-2 step (prepared by the SIMT forward; the
+    // tensor-core forward does not use these records)
+    if (p->batch > 1) TRY_CUDA(launch_prep_spin2(p, alm_E, alm_B, s));
+    TRY_CUDA(launch_legendre_adj2(p, n, p->d7_Q, p->d7_U, galm_E, galm_B, s));
+  }
+  TRY_CUDA(launch_adj_finish(p, galm_T, galm_phi, galm_E, galm_B, s));
+  return TL_OK;
 }
 
 extern "C" tl_status tl_lens_host(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,

@@ -30,6 +30,20 @@ struct JobList {
 struct PlaneSet {
   const void *base[4];  // T, Q, U, phi planes: [j][ring][m]
 };
+// adjoint: one output plane (plane 0..2 = T, Q, U with inputs d_theta^j d_phi^k,
+// k < nk, at base + map_index(j, k) npix; plane 3 = phi with one input map at base)
+struct AdjJobDev {
+  const void *base;
+  int plane, j, nk, pad;
+};
+#define TL_MAX_ADJ_JOBS 32
+struct AdjJobList {
+  int n;
+  AdjJobDev job[TL_MAX_ADJ_JOBS];
+};
+struct PlaneSetOut {
+  void *base[4];
+};
 
 // sum over the aliasing class m = t0 + qN (q >= 0, m <= mmax) of
 //   (-1)^q [shifted rings] * w_m (i m / L)^k F_m,   w_0 = 1, w_m = 2
@@ -225,6 +239,180 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the ring synthesis. For an output plane (field, j) fed by the real
+// maps g_k (k = derivative order in phi, scale c_k, optional 1/sin(theta)), the
+// gradient with respect to the plane's coefficients is
+//     Fbar^j_m = w_m e^{-i m phi0} sum_k c_k (-i m / L)^k X^k_{m mod N},
+//     X^k_t = sum_p g_k(p) e^{-2 pi i t p / N},
+// (the forward map is Re[c w_m (i m/L)^k F_m e^{i m phi_p}], whose gradient in
+// the convention dL/dRe + i dL/dIm is the complex conjugate of the factor).
+// Two maps share one forward DFT: with Z = g_a + i g_b, X^a_t = (Z_t + conj Z_{N-t})/2,
+// X^b_t = (Z_t - conj Z_{N-t})/(2i); the DFT is conj(IDFT(conj Z)), computed by
+// the forward kernel's decimated sub-transforms and an in-place radix-4 pass.
+
+template <typename T>
+__global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax, long long npix, int nmaps,
+                                                          AdjJobList jobs, PlaneSetOut ps, int plane_len,
+                                                          BluesteinTable bt,
+                                                          const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
+                                                          int bbatch, double L_d) {
+  typedef typename RealTraits<T>::T2 T2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int r = blockIdx.x;
+  const AdjJobDev J = jobs.job[blockIdx.y];
+  const int N = rt.nphi[r];
+  const int ni = N >> 2;
+  const long long first = rt.first[r];
+  const int nth = blockDim.x, tid = threadIdx.x;
+  T2 *Y = (T2 *)smem_raw;
+  T2 *W = Y + N;
+  const bool shifted = rt.phi0[r] != 0.0;  // phi0 = pi / N
+  const T invL = (T)(1.0 / L_d);
+  const T inv_s = (T)(1.0 / rt.sint[r]);
+  T2 *F = (T2 *)ps.base[J.plane] + (size_t)J.j * plane_len + (size_t)r * (mmax + 1);
+  // inputs: field planes take k = 0 .. nk-1 with c_k = 1/(j! k!); the deflection's
+  // planes one map each (j = 1: k = 0; j = 0: k = 1 over sin(theta)), c = L
+  const bool defl = J.plane == 3;
+  const int nin = defl ? 1 : J.nk;
+  T jfact = (T)1;
+  for (int i = 2; i <= J.j; ++i) jfact *= (T)i;
+
+  for (int i0 = 0; i0 < nin; i0 += 2) {
+    const bool hasb = i0 + 1 < nin;
+    int ka, kb;
+    const T *ga, *gb;
+    T ca, cb;
+    if (defl) {
+      ka = kb = (J.j == 0) ? 1 : 0;
+      ga = gb = (const T *)J.base;
+      ca = (T)L_d * ((J.j == 0) ? inv_s : (T)1);
+      cb = (T)0;
+    } else {
+      ka = i0;
+      kb = hasb ? i0 + 1 : i0;
+      const int na = (J.j + ka) * (J.j + ka + 1) / 2 + J.j, nb = (J.j + kb) * (J.j + kb + 1) / 2 + J.j;
+      ga = (const T *)J.base + (size_t)na * npix;
+      gb = (const T *)J.base + (size_t)nb * npix;
+      T kfa = (T)1, kfb = (T)1;
+      for (int i = 2; i <= ka; ++i) kfa *= (T)i;
+      for (int i = 2; i <= kb; ++i) kfb *= (T)i;
+      ca = (T)1 / (jfact * kfa);
+      cb = hasb ? (T)1 / (jfact * kfb) : (T)0;
+    }
+    // conj(Z) in decimated order
+    for (int p = tid; p < N; p += nth) {
+      T2 z;
+      z.x = ga[first + p];
+      z.y = hasb ? -gb[first + p] : (T)0;
+      Y[(p & 3) * ni + (p >> 2)] = z;
+    }
+    __syncthreads();
+    if ((ni & (ni - 1)) == 0) {
+      fft_pow2<T2>(Y, ni, 4, +1, tw, TW);
+    } else {
+      const long long off = bt.offset[ni];
+      const int M = bt.mlen[ni];
+      const T2 *bh = (const T2 *)bt.spec + off;
+      const T2 *ch = bh + M;
+      if (bbatch >= 4) {
+        bluestein_batch<T, T2>(Y, ni, M, 4, W, bh, ch, tw, TW);
+      } else {
+        for (int t2 = 0; t2 < 4; ++t2) bluestein_batch<T, T2>(Y + t2 * ni, ni, M, 1, W, bh, ch, tw, TW);
+      }
+    }
+    // radix-4 pass in place (slots p1 + ni t2 are read and written by one thread), then conj
+    for (int p1 = tid; p1 < ni; p1 += nth) {
+      T s, c;
+      sincos_pi<T>((T)(2 * p1) / (T)N, &s, &c);
+      T2 w1;
+      w1.x = c;
+      w1.y = s;
+      const T2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+      T2 y[4];
+      y[0] = Y[p1];
+      y[1] = cmul(Y[ni + p1], w1);
+      y[2] = cmul(Y[2 * ni + p1], w2);
+      y[3] = cmul(Y[3 * ni + p1], w3);
+      const T2 a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
+      const T2 b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
+      T2 ib1;
+      ib1.x = -b1.y;
+      ib1.y = b1.x;
+      T2 X0 = cadd(a0, b0), X2 = csub(a0, b0);
+      T2 X1 = cadd(a1, ib1), X3 = csub(a1, ib1);
+      X0.y = -X0.y;
+      X1.y = -X1.y;
+      X2.y = -X2.y;
+      X3.y = -X3.y;
+      Y[p1] = X0;
+      Y[p1 + ni] = X1;
+      Y[p1 + 2 * ni] = X2;
+      Y[p1 + 3 * ni] = X3;
+    }
+    __syncthreads();
+    // split the packed spectra and accumulate the plane's row
+    for (int m = tid; m <= mmax; m += nth) {
+      const int t = m % N;
+      const int tm = (N - t) % N;
+      const T2 zt = Y[t], zm = Y[tm];
+      // X^a = (Z_t + conj Z_{N-t})/2, X^b = (Z_t - conj Z_{N-t})/(2i)
+      T2 xa, xb;
+      xa.x = (T)0.5 * (zt.x + zm.x);
+      xa.y = (T)0.5 * (zt.y - zm.y);
+      xb.x = (T)0.5 * (zt.y + zm.y);
+      xb.y = (T)-0.5 * (zt.x - zm.x);
+      // c (m/L)^k (-i)^k X
+      const T mm = (T)m * invL;
+      T pa = ca, pb = cb;
+      for (int i = 0; i < ka; ++i) pa *= mm;
+      for (int i = 0; i < kb; ++i) pb *= mm;
+      T2 va, vb;
+      va.x = pa * xa.x;
+      va.y = pa * xa.y;
+      vb.x = pb * xb.x;
+      vb.y = pb * xb.y;
+      T2 v;
+      {
+        T2 ra, rb;  // multiply by (-i)^k
+        switch (ka & 3) {
+          case 0: ra = va; break;
+          case 1: ra.x = va.y; ra.y = -va.x; break;
+          case 2: ra.x = -va.x; ra.y = -va.y; break;
+          default: ra.x = -va.y; ra.y = va.x; break;
+        }
+        switch (kb & 3) {
+          case 0: rb = vb; break;
+          case 1: rb.x = vb.y; rb.y = -vb.x; break;
+          case 2: rb.x = -vb.x; rb.y = -vb.y; break;
+          default: rb.x = -vb.y; rb.y = vb.x; break;
+        }
+        v = cadd(ra, rb);
+      }
+      // w_m e^{-i m phi0}
+      T wm = (m > 0) ? (T)2 : (T)1;
+      if (shifted) {
+        const int m2 = m % (2 * N);
+        T s, c;
+        sincos_pi<T>((T)m2 / (T)N, &s, &c);
+        T2 e;
+        e.x = wm * c;
+        e.y = -wm * s;
+        v = cmul(v, e);
+      } else {
+        v.x *= wm;
+        v.y *= wm;
+      }
+      if (i0 == 0) {
+        F[m] = v;
+      } else {
+        F[m] = cadd(F[m], v);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Bluestein spectra: one block per non-power-of-two length i; computed in double.
 template <typename T>
 __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const long long *__restrict__ offset,
@@ -329,6 +517,39 @@ cudaError_t launch_ringfft_planes(const tl_plan *p, const void *const *planes, c
 cudaError_t launch_ringfft(const tl_plan *p, const MapJob *jobs, int njobs, int, cudaStream_t s) {
   const void *planes[4] = {p->d7_T, p->d7_Q, p->d7_U, p->d7_P};
   return launch_ringfft_planes(p, planes, jobs, njobs, s);
+}
+
+template <typename T>
+static cudaError_t ringfft_adj_t(const tl_plan *p, void *const *planes, const AdjMapJob *jobs, int njobs,
+                                 cudaStream_t s) {
+  if (njobs > TL_MAX_ADJ_JOBS) return cudaErrorInvalidValue;
+  if (njobs == 0) return cudaSuccess;
+  AdjJobList jl;
+  jl.n = njobs;
+  for (int i = 0; i < njobs; ++i) {
+    jl.job[i].base = jobs[i].in;
+    jl.job[i].plane = jobs[i].plane;
+    jl.job[i].j = jobs[i].j;
+    jl.job[i].nk = jobs[i].nk;
+    jl.job[i].pad = 0;
+  }
+  PlaneSetOut ps;
+  for (int i = 0; i < 4; ++i) ps.base[i] = planes[i];
+  const int plane_len = p->nrings * (p->mmax + 1);
+  const int batch = ringfft_batch(p);
+  const size_t smem = ringfft_smem_for(p, batch);
+  TL_CUDA_TRY(cudaFuncSetAttribute(ringfft_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(p->nrings, njobs);
+  ringfft_adj_kernel<T><<<grid, 512, smem, s>>>(p->ring, p->mmax, p->npix, p->nmaps, jl, ps, plane_len, p->blue,
+                                                (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch,
+                                                (double)(p->lmax + 1));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ringfft_adjoint(const tl_plan *p, void *const *planes, const AdjMapJob *jobs, int njobs,
+                                   cudaStream_t s) {
+  return p->precision == TL_FP64 ? ringfft_adj_t<double>(p, planes, jobs, njobs, s)
+                                 : ringfft_adj_t<float>(p, planes, jobs, njobs, s);
 }
 
 // double-precision twiddles for the setup kernel live in a temporary buffer
