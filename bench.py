@@ -2,11 +2,17 @@
 
 One step = one full lensing pass through the C ABI (deflection synthesis, Legendre
 stage of T and Q/U with all derivative orders, ring FFTs into the derivative maps,
-gather + Taylor sum + rotation) for one synthetic sky whose coefficients are
-already resident in HBM. The headline is the mixed-precision form
-(TL_MIXED_FP32); the plain FP64 GPU form is timed on the same GPU beside it.
+gather + Taylor sum + rotation) for the step's synthetic skies, whose coefficients
+are already resident in HBM. The headline form is the 3xTF32 tensor-core
+contraction with two realisations per Legendre launch (--form, --batch); the plain
+FP64 GPU form is timed on the same GPU beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--form fp32|tf32|tf32x3]
+
+Other workloads: batched64_n4_TQU (64 uneven realisations in one batch) and
+adjoint_nside1024_lmax2048_n4_TQU (one gradient evaluation of a quadratic map loss
+per step: forward lens plus tl_lens_adjoint).
 
 Multi-GPU: one process per GPU (torchrun); every rank lenses its own independent
 realisations (weak scaling, no data-path collective); the time is the max over
@@ -129,6 +135,18 @@ def shard(n_units: int, rank: int, world: int):
     return list(range(start, start + base + (1 if rank < extra else 0)))
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of x over all ranks of the default process group (the step
+    time of the slowest rank); x itself without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_sample(w, sky, npix_sample: int, seed: int = 0, nthreads=None):
     """Time the FP64 CPU oracle on a bounded sample of the workload: the pixel-relative
     Taylor lensing of `npix_sample` output pixels (each needs the deflection at its
@@ -227,11 +245,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     ms_per_step = ms / args.steps
     value = world * nb * args.steps / (ms / 1e3)
     stages = stage_sum / args.steps
@@ -335,7 +349,7 @@ def run_ours(args):
                 o[f] = {"rel_rms": float(np.sqrt(np.mean(dlt ** 2) / np.mean(r ** 2))),
                         "max_rel": float(np.max(np.abs(dlt)) / np.sqrt(np.mean(r ** 2)))}
             return o
-        err = {"mixed_fp32": errs(lensed), "npix": int(len(pix))}
+        err = {args.form: errs(lensed), "npix": int(len(pix))}
         if lensed64 is not None:
             err["fp64"] = errs(lensed64)
 
@@ -418,25 +432,165 @@ def run_batched(args):
         print(json.dumps(line), flush=True)
 
 
+ADJ_WORKLOAD = "adjoint_nside1024_lmax2048_n4_TQU"
+ADJ_METRIC = "gradient evaluations/sec of L = sum (s' - s_target)^2 wrt alm_T,E,B,phi @Nside1024 lmax2048 order4"
+
+
+def run_adjoint(args):
+    """One step = forward lens, loss gradient g = 2 (maps - targets), tl_lens_adjoint
+    (which recomputes the derivative maps) for dL/dalm of T, E, B and phi. Targets are
+    the lensed maps of an independent sky (seeds 9000..9002)."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    os.environ["TAYLENS_TIMING"] = "1"
+    from paper_1307_0719_gb300 import api
+    w = skygen.WORKLOADS["nside1024_lmax2048_n4_TQU"]
+    forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3}
+    form = args.form if args.form_given else "fp32"
+    sky = skygen.make_sky(w.nside, w.lmax, True, w.seed_t + 1000 * rank, w.seed_e + 1000 * rank,
+                          w.seed_phi + 1000 * rank, w.damp_t, w.damp_e)
+    tsky = skygen.make_sky(w.nside, w.lmax, True, 9000, 9001, 9002, w.damp_t, w.damp_e)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in sky.items()}
+    dt = {k: torch.from_numpy(v).to(dev) for k, v in tsky.items()}
+    plan = api.Plan(w.nside, w.lmax, w.order, pol=True, precision=forms[form])
+    target = plan.lens(dt["T"], dt["E"], dt["B"], dt["phi"]).clone()
+    del dt
+    out = torch.empty((3, plan.npix), dtype=torch.float32, device=dev)
+    g = torch.empty_like(out)
+    stream = torch.cuda.current_stream()
+
+    def step(alm):
+        plan.lens(alm["T"], alm["E"], alm["B"], alm["phi"], out=out)
+        torch.sub(out, target, out=g)
+        g.mul_(2.0)
+        return plan.lens_adjoint(alm["T"], alm["E"], alm["B"], alm["phi"], g[0], g[1], g[2])
+
+    for _ in range(args.warmup):
+        step(d)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    names = ["forward", "gather_adj", "ringfft_adj", "legendre_T_adj", "legendre_QU_adj", "finish"]
+    stage_sum = np.zeros(len(names))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(d)
+            stage_sum += np.array(plan.last_stage_ms())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    value = world * args.steps / (ms / 1e3)
+    stage_ms = {n: float(v) for n, v in zip(names, stage_sum / args.steps)}
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            peaks = json.load(f)
+    fp32_peak = FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    dom = max(("gather_adj", "ringfft_adj", "legendre_T_adj", "legendre_QU_adj"), key=lambda k: stage_ms[k])
+    if dom.startswith("legendre"):
+        spin = 2 if dom == "legendre_QU_adj" else 0
+        fl = legendre_flops_per_launch(w.nside, w.lmax, w.order, spin)
+        ach = fl / (stage_ms[dom] / 1e3) / 1e12
+        roof = {"kernel": f"legendre_adj{spin}_kernel<float, {w.order}>", "bound": "alu", "achieved": ach,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
+                "counts": "recurrence + transposed contraction (same per-triple count as the forward)"}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": None}
+    # end to end: coefficients and targets from pinned host memory, gradients back
+    e2e = None
+    if not args.no_e2e:
+        hin = {k: torch.from_numpy(v).pin_memory() for k, v in sky.items()}
+        hout = {k: torch.empty(plan.nalm, dtype=torch.complex128).pin_memory() for k in ("T", "E", "B", "phi")}
+        k2 = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            dd = {k: v.to(dev, non_blocking=True) for k, v in hin.items()}
+            gr = step(dd)
+            for k in hout:
+                hout[k].copy_(gr[k], non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / k2
+        e2e = {"value": world / e2e_s, "unit": "gradient evaluations/s", "h2d_bytes_per_step": 4 * plan.nalm * 16,
+               "d2h_bytes_per_step": 4 * plan.nalm * 16}
+    gr = step(d)
+    torch.cuda.synchronize()
+    gnorm = {k: float(v.abs().pow(2).sum().sqrt()) for k, v in gr.items()}
+    plan.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # oracle adjoint on a reduced geometry of the same order; time extrapolated by the
+        # Legendre work (rings x coefficients), which dominates it
+        import oracle.adjoint as OA
+        ns, lm = 32, 64
+        ssk = skygen.make_sky(ns, lm, True, 2, 3, 4, w.damp_t, w.damp_e)
+        rng = np.random.default_rng(0)
+        gg = {f: rng.normal(size=12 * ns * ns) for f in "TQU"}
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        OA.lens_adjoint(ns, lm, w.order, ssk["T"], ssk["E"], ssk["B"], ssk["phi"], gg["T"], gg["Q"], gg["U"],
+                        nthreads=cores)
+        dt_s = time.perf_counter() - t0
+        scale = ((4 * w.nside - 1) * (w.lmax + 1) * (w.lmax + 2)) / ((4 * ns - 1) * (lm + 1) * (lm + 2))
+        cpu = {"value": 1.0 / (dt_s * scale), "unit": "gradient evaluations/s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle adjoint at Nside {ns}, lmax {lm}, order {w.order} in {dt_s:.1f} s, "
+                         f"extrapolated x{scale:.0f} by rings x coefficients"}
+    if rank == 0:
+        line = {
+            "metric": ADJ_METRIC, "value": value, "unit": "gradient evaluations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[form],
+            "data": "synthetic (seeded Gaussian alm, analytic spectra; targets from seeds 9000-9002)",
+            "config": {"workload": ADJ_WORKLOAD, "nside": w.nside, "lmax": w.lmax, "order": w.order,
+                       "fields": "TQU", "form": form + "; FP64 geometry and Jacobian",
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (derivative maps 2.3 GB, their gradients 2.3 GB)"},
+            "stage_ms": stage_ms, "roofline": roof, "clocks": clk.summary(),
+            "gpu_launches": args.steps * 20, "e2e": e2e, "grad_norms": gnorm, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(skygen.WORKLOADS) + ["batched64_n4_TQU"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=sorted(skygen.WORKLOADS) + ["batched64_n4_TQU", ADJ_WORKLOAD])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--form", default="tf32x3", choices=["fp32", "tf32", "tf32x3"])
+    ap.add_argument("--form", default=None, choices=["fp32", "tf32", "tf32x3"])
     ap.add_argument("--batch", type=int, default=0, help="realisations per step (default 2 on tensor cores)")
     ap.add_argument("--sample-pixels", type=int, default=16)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    args.form_given = args.form is not None
+    if args.form is None:
+        args.form = "tf32x3"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64_n4_TQU":
         run_batched(args)
+    elif args.workload == ADJ_WORKLOAD:
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -240,12 +240,14 @@ int tl_batch_grid(const tl_batch *batch);   /* persistent grid size in use */
 /* Human-readable text for a status code (static storage). */
 const char *tl_status_string(tl_status status);
 
-/* Milliseconds of the stages of the most recent tl_lens on this plan, measured
- * with CUDA events on the call's stream when the environment variable
- * TAYLENS_TIMING=1 was set at plan creation (otherwise returns 0). Stage order:
- * prep_T (T and phi coefficients), legendre_T (spin-0 stage, with phi's j <= 1
- * planes), deflection_fft, prep_QU, legendre_QU, ringfft (all T/Q/U maps),
- * gather. Synchronises on the last event.
+/* Milliseconds of the stages of the most recent tl_lens or tl_lens_adjoint on
+ * this plan, measured with CUDA events on the call's stream when the environment
+ * variable TAYLENS_TIMING=1 was set at plan creation (otherwise returns 0).
+ * tl_lens stage order: prep_T (T and phi coefficients), legendre_T (spin-0 stage,
+ * with phi's j <= 1 planes), deflection_fft, prep_QU, legendre_QU, ringfft (all
+ * T/Q/U maps), gather. tl_lens_adjoint: forward (recomputed derivative maps and
+ * deflection), gather (transposed), ringfft (transposed), legendre_T (transposed,
+ * with phi), legendre_QU (transposed), finish. Synchronises on the last event.
  * Returns the number of stages written (<= n). */
 int tl_last_stage_ms(const tl_plan *plan, float *ms, int n);
 

@@ -152,7 +152,7 @@ class Plan:
             if g is not None and (g.dtype != self.dtype or not g.is_contiguous() or not g.is_cuda):
                 raise ValueError(f"{name} must be a contiguous CUDA tensor of {self.dtype}")
         fields = [f for f in ("T", "E", "B", "phi") if f in want and (self.pol or f not in ("E", "B"))]
-        out = {f: torch.zeros(self.nalm, dtype=torch.complex128, device=dev) for f in fields}
+        out = {f: torch.empty(self.nalm, dtype=torch.complex128, device=dev) for f in fields}  # zeroed in the call
         ga = torch.empty((2, self.npix), dtype=self.dtype, device=dev) if galpha else None
         o = lambda f: _ptr(torch.view_as_real(out[f])) if f in out else None
         check(_lib.lib().tl_lens_adjoint(self._h, _ptr(aT), _ptr(aE), _ptr(aB), _ptr(aP), _ptr(gT),

@@ -549,14 +549,19 @@ extern "C" tl_status tl_lens_adjoint(tl_plan *p, const double *alm_T, const doub
   if (!galpha && !p->adj_ga) TRY_CUDA(dalloc(&p->adj_ga, 2 * mapb, &p->bytes));
   void *ga = galpha ? galpha : p->adj_ga;
 
+  // stage marks (TAYLENS_TIMING): forward, gather, ring FFT, Legendre spin 0, spin 2, finish
+  p->nstage = 0;
+  mark(p, 0, s);
   // 1. forward quantities: d3 (Taylor-ready maps) and alpha
   {
     tl_status st = forward_derivs(p, alm_T, pol ? alm_E : nullptr, pol ? alm_B : nullptr, alm_phi, s);
     if (st != TL_OK) return st;
   }
+  mark(p, 1, s);
   // 2. gather + Taylor + rotate, transposed: Dbar and the deflection gradient
   TRY_CUDA(cudaMemsetAsync(p->adj_dbar, 0, dbar_bytes, s));
   TRY_CUDA(launch_gather_adjoint(p, p->alpha, p->d3, gT, pol ? gQ : nullptr, pol ? gU : nullptr, p->adj_dbar, ga, s));
+  mark(p, 2, s);
   // 3. ring synthesis, transposed, into the (now free) Legendre planes
   std::vector<AdjMapJob> jobs;
   const int n = p->order;
@@ -572,6 +577,7 @@ extern "C" tl_status tl_lens_adjoint(tl_plan *p, const double *alm_T, const doub
   }
   void *planes[4] = {p->d7_T, p->d7_Q, p->d7_U, p->d7_P};
   TRY_CUDA(launch_ringfft_adjoint(p, planes, jobs.data(), (int)jobs.size(), s));
+  mark(p, 3, s);
   // 4. Legendre stages, transposed, accumulated straight into the outputs
   const size_t ab = (size_t)na * 16;
   double *outs[4] = {galm_T, galm_E, galm_B, galm_phi};
@@ -580,13 +586,17 @@ extern "C" tl_status tl_lens_adjoint(tl_plan *p, const double *alm_T, const doub
   if (galm_T || galm_phi)
     TRY_CUDA(launch_legendre_adj0(p, galm_T ? n : -1, galm_T ? p->d7_T : nullptr, galm_phi ? p->d7_P : nullptr,
                                   galm_T, galm_phi, s));
+  mark(p, 4, s);
   if (pol && (galm_E || galm_B)) {
     // A_{l+1} and m s/(l(l+1)) of the spin-2 step (prepared by the SIMT forward; the
     // tensor-core forward does not use these records)
     if (p->batch > 1) TRY_CUDA(launch_prep_spin2(p, alm_E, alm_B, s));
     TRY_CUDA(launch_legendre_adj2(p, n, p->d7_Q, p->d7_U, galm_E, galm_B, s));
   }
+  mark(p, 5, s);
   TRY_CUDA(launch_adj_finish(p, galm_T, galm_phi, galm_E, galm_B, s));
+  mark(p, 6, s);
+  p->nstage = p->timing ? 6 : 0;
   return TL_OK;
 }
 
