@@ -4,7 +4,7 @@ One step = one full lensing pass through the C ABI (deflection synthesis, Legend
 stage of T and Q/U with all derivative orders, ring FFTs into the derivative maps,
 gather + Taylor sum + rotation) for the step's synthetic skies, whose coefficients
 are already resident in HBM. The headline form is the 3xTF32 tensor-core
-contraction with two realisations per Legendre launch (--form, --batch); the plain
+contraction (tcgen05) with eight realisations per Legendre launch (--form, --batch); the plain
 FP64 GPU form is timed on the same GPU beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -210,7 +210,7 @@ def run_ours(args):
     w = skygen.WORKLOADS[args.workload]
     forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3}
     prec = forms[args.form]
-    nb = args.batch if args.batch else (2 if args.form != "fp32" else 1)
+    nb = args.batch if args.batch else (8 if args.form != "fp32" else 1)
     # each rank lenses its own realisations (seeds offset by rank and index): weak scaling
     skies = [skygen.make_sky(w.nside, w.lmax, w.pol, w.seed_t + 1000 * rank + 100 * i,
                              w.seed_e + 1000 * rank + 100 * i, w.seed_phi + 1000 * rank + 100 * i,
@@ -253,10 +253,10 @@ def run_ours(args):
     stage_ms = {n: float(v) for n, v in zip(names, stages)}
 
     # roofline of the dominant kernel (stage times are per Legendre launch, which on
-    # tensor-core plans covers two realisations; see the per-step stage sums)
+    # tensor-core plans covers up to eight realisations; see the per-step stage sums)
     tc = args.form != "fp32"
     part = "recurrence" if tc else "all"
-    nr_launch = min(nb, 2) if tc else 1
+    nr_launch = min(nb, 8) if tc else 1
     flops_qu = legendre_flops_per_launch(w.nside, w.lmax, w.order, 2, part=part)
     flops_t = legendre_flops_per_launch(w.nside, w.lmax, w.order, 0, part=part)
     tflops_qu = legendre_flops_per_launch(w.nside, w.lmax, w.order, 2, part="contraction", nreal=nr_launch)
@@ -576,7 +576,7 @@ def main():
                     choices=sorted(skygen.WORKLOADS) + ["batched64_n4_TQU", ADJ_WORKLOAD])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--form", default=None, choices=["fp32", "tf32", "tf32x3"])
-    ap.add_argument("--batch", type=int, default=0, help="realisations per step (default 2 on tensor cores)")
+    ap.add_argument("--batch", type=int, default=0, help="realisations per step (default 8 on tensor cores)")
     ap.add_argument("--sample-pixels", type=int, default=16)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -56,9 +56,10 @@ enum { TL_SPIN_T = 1, TL_SPIN_QU = 2 };
  * TL_MIXED_FP32    float recurrence and contraction with double seeds and
  *                  exponent rescaling; float maps; double pixel lookup.
  * TL_MIXED_TF32    as TL_MIXED_FP32, but tl_lens / tl_lens_batch contract the
- *                  recurrence against the coefficients on the tensor cores in
- *                  TF32 (10-bit mantissas, FP32 accumulation), two realisations
- *                  per Legendre launch.
+ *                  recurrence against the coefficients on the tensor cores
+ *                  (tcgen05, accumulators in tensor memory) in TF32 (10-bit
+ *                  mantissas, FP32 accumulation), up to eight realisations per
+ *                  Legendre launch.
  * TL_MIXED_TF32x3  the same with each operand split into TF32 hi + lo parts and
  *                  three products accumulated (errors close to FP32).
  * TL_MIXED_BF16x3  declared, not built (TL_ERR_UNSUPPORTED).
@@ -129,9 +130,10 @@ tl_status tl_lens(tl_plan *plan, const double *alm_T, const double *alm_E, const
  * device pointers (host arrays); entries as in tl_lens; alm_B may be NULL (all
  * B = 0); alm_phi may be NULL (none lensed), otherwise every entry must be set.
  * On tensor-core plans (TL_MIXED_TF32, TL_MIXED_TF32x3) realisations go through
- * the Legendre stage two at a time, sharing the recurrence (the coefficient sets
- * of both fill the columns of one tensor-core product); ring FFTs and the gather
- * then run per realisation. On other plans this equals nreal calls of tl_lens.
+ * the Legendre stage eight at a time, sharing the recurrence (the coefficient sets
+ * of all eight fill the 32 columns of one tensor-core product); ring FFTs and the
+ * gather then run per realisation. On other plans this equals nreal calls of
+ * tl_lens.
  */
 tl_status tl_lens_batch(tl_plan *plan, int nreal, const double *const *alm_T, const double *const *alm_E,
                         const double *const *alm_B, const double *const *alm_phi, void *const *T_out,
@@ -209,7 +211,7 @@ tl_status tl_deflection_noalloc(int nside, int lmax, int precision, const double
  *   tl_batch_create: nreal realisations, nside[i], lmax[i] (host arrays).
  *   tl_batch_lens modes:
  *     TL_BATCH_LOOP        one tl_lens call per realisation (the comparison point);
- *     TL_BATCH_PERSISTENT  tensor-core plans only: waves of realisation pairs, each
+ *     TL_BATCH_PERSISTENT  tensor-core plans only: waves of up to eight realisations per group, each
  *                          wave's Legendre stage in one persistent launch whose
  *                          blocks take (plan, spin, m, ring block) items, sorted
  *                          by cost, from an atomic counter (no waits between blocks);
@@ -236,6 +238,15 @@ tl_status tl_batch_autotune(tl_batch *batch, const double *const *alm_T, const d
 int tl_batch_groups(const tl_batch *batch); /* number of geometry groups */
 int tl_batch_waves(const tl_batch *batch);  /* waves of the persistent mode */
 int tl_batch_grid(const tl_batch *batch);   /* persistent grid size in use */
+
+/*
+ * Device-side error check: synchronises the device and returns TL_ERR_TIMEOUT if
+ * a kernel of this plan gave up a bounded wait since the last check (the flag is
+ * then cleared), else TL_OK. Kernels that time out record the flag, wait (bounded)
+ * for their own tensor-core work, free their tensor memory and return; their
+ * outputs are then undefined. TL_ERR_CUDA if the device reports an error.
+ */
+tl_status tl_plan_device_error(tl_plan *plan);
 
 /* Human-readable text for a status code (static storage). */
 const char *tl_status_string(tl_status status);

@@ -65,6 +65,10 @@ class Plan:
         except Exception:
             pass
 
+    def check_device_error(self):
+        """Raise TaylensError if a kernel of this plan timed out a bounded wait (synchronises)."""
+        check(_lib.lib().tl_plan_device_error(self._h), "device-side wait")
+
     @property
     def workspace_bytes(self) -> int:
         return _lib.lib().tl_plan_workspace_bytes(self._h)

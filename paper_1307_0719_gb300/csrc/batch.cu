@@ -1,7 +1,7 @@
 // Batched lensing of many realisations of uneven size (tl_batch_*).
 //
 // Realisations are grouped by geometry (nside, lmax); each group owns a plan.
-// On tensor-core plans the work goes in waves: a wave takes the next pair of
+// On tensor-core plans the work goes in waves: a wave takes the next (up to) eight
 // realisations from every group that still has some, prepares their coefficient
 // fragments, and runs the Legendre stage of all of them in ONE persistent
 // launch whose blocks pull (plan, spin, m, ring block) items, pre-sorted by cost,
@@ -176,7 +176,8 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
     std::vector<unsigned char> descs;
     std::vector<const tl_plan *> desc_plan;  // geometry behind each descriptor (for the checks below)
     size_t maxc = 0;
-    for (auto &m : b->members) maxc = std::max(maxc, (m.size() + 1) / 2);
+    const size_t per = (size_t)b->plans[0]->batch;  // realisations per wave and group
+    for (auto &m : b->members) maxc = std::max(maxc, (m.size() + per - 1) / per);
     const bool pol = (spins & TL_SPIN_QU) != 0;
     for (size_t w = 0; w < maxc; ++w) {
       Wave wv;
@@ -188,9 +189,9 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
       };
       std::vector<It> its;
       for (size_t g = 0; g < b->plans.size(); ++g) {
-        const size_t first = 2 * w;
+        const size_t first = per * w;
         if (first >= b->members[g].size()) continue;
-        const int cnt = (int)std::min<size_t>(2, b->members[g].size() - first);
+        const int cnt = (int)std::min<size_t>(per, b->members[g].size() - first);
         const int di = (int)(descs.size() / db);
         for (int spin : {0, 2}) {
           const size_t at = descs.size();
@@ -201,10 +202,10 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
         wv.members.push_back(std::make_pair((int)g, (int)first));
         wv.counts.push_back(cnt);
         const tl_plan *p = b->plans[g];
-        const int nb0 = (2 * p->nside + 63) / 64, nb2 = (2 * p->nside + 31) / 32;
+        const int nb0 = tc_ring_blocks(p, 0), nb2 = tc_ring_blocks(p, 2);
         for (int m = 0; m <= p->mmax; ++m) {
           for (int r = 0; r < nb0; ++r)  // kind 0 or 1 decided per call (phi or not): encode 1, patch below
-            its.push_back({(long long)(p->lmax - m + 1) * 64, make_int4(di | (1 << 16), m, r, 0)});
+            its.push_back({(long long)(p->lmax - m + 1) * 128, make_int4(di | (1 << 16), m, r, 0)});
           if (pol)
             for (int r = 0; r < nb2; ++r)
               its.push_back({(long long)(p->lmax - std::max(m, 2) + 1) * 64 * 2, make_int4((di + 1) | (2 << 16), m, r, 0)});
@@ -223,7 +224,7 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
         return TL_ERR_ARG;
       }
       const tl_plan *q = desc_plan[di];
-      const int nbk = (kind == 2) ? (2 * q->nside + 31) / 32 : (2 * q->nside + 63) / 64;
+      const int nbk = tc_ring_blocks(q, kind == 2 ? 2 : 0);
       if (v.y < 0 || v.y > q->mmax || v.z < 0 || v.z >= nbk || ((kind == 2) != (di % 2 == 1))) {
         batch_free(b);
         return TL_ERR_ARG;
@@ -241,7 +242,7 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = nsm * 8;
+    b->grid = nsm * 2;  // two CTAs per SM (shared memory and tensor memory)
   }
   tune_load(b);
   *out = b;
@@ -276,11 +277,11 @@ static tl_status batch_pass(tl_batch *b, int mode, const double *const *aT, cons
   }
   for (size_t w = 0; w < b->waves.size(); ++w) {
     const Wave &wv = b->waves[w];
-    // coefficient fragments of every member pair
+    // coefficient tiles of every member group
     for (size_t k = 0; k < wv.members.size(); ++k) {
       const int g = wv.members[k].first, first = wv.members[k].second, cnt = wv.counts[k];
       tl_plan *p = b->plans[g];
-      const double *t[2], *e[2], *bb[2], *ph[2];
+      const double *t[8], *e[8], *bb[8], *ph[8];
       for (int r = 0; r < cnt; ++r) {
         const int i = b->members[g][first + r];
         t[r] = aT[i];
@@ -302,7 +303,7 @@ static tl_status batch_pass(tl_batch *b, int mode, const double *const *aT, cons
     // ring FFTs and gather per realisation
     for (size_t k = 0; k < wv.members.size(); ++k) {
       const int g = wv.members[k].first, first = wv.members[k].second, cnt = wv.counts[k];
-      void *T2[2], *Q2[2], *U2[2];
+      void *T2[8], *Q2[8], *U2[8];
       for (int r = 0; r < cnt; ++r) {
         const int i = b->members[g][first + r];
         T2[r] = To[i];
@@ -415,7 +416,7 @@ extern "C" tl_status tl_batch_autotune(tl_batch *b, const double *const *alm_T, 
   // 2. persistent grid size (blocks per SM)
   best = 1e30f;
   int best_grid = b->grid;
-  for (int k : {4, 6, 8, 12, 16}) {
+  for (int k : {1, 2}) {
     b->grid = nsm * k;
     float ms;
     tl_status st = timeit(&ms);

@@ -61,11 +61,12 @@ struct tl_plan {
   void *rec_T, *rec_P, *rec_QU; // coefficient records
   void *d7_T, *d7_Q, *d7_U, *d7_P; // per-ring Fourier coefficients [j][ring][m] (T2)
   // tensor-core Legendre stage (TL_MIXED_TF32, TL_MIXED_TF32x3): blocks of 8 l per m
-  int batch;             // realisations sharing one Legendre launch (1, or 2 on tensor cores)
+  int batch;             // realisations sharing one Legendre launch (1, or 8 on tensor cores)
   int tc_nder;           // derivative orders carried there (max(order, 1))
   long long *tc_blk0, *tc_blk2;   // [lmax+1] first block of each m (spin 0 / spin 2)
   float *tc_step0, *tc_step2;     // [blocks][16]: A_{l+1} x 8, m s/(l(l+1)) x 8
-  void *tc_b0, *tc_bp, *tc_b2;    // [blocks][32 lanes] float4 coefficient fragments
+  void *tc_b0, *tc_bp, *tc_b2;    // [blocks] 2 KB coefficient tiles (TF32 hi, lo; 32 columns x 8 l)
+  int *dev_err;                   // set by a kernel whose bounded wait timed out
   long long d7_rstride, d7p_rstride;  // T2 elements between realisations' D7 planes
   void *d3;            // derivative maps [3*nmaps][npix] (T), Taylor-ready
   void *alpha;         // [2][npix] (T)
@@ -132,6 +133,10 @@ cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void
 cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, bool phi, void *d7, void *d7p,
                                      long long rstride, long long rstride_p, cudaStream_t s);
 cudaError_t launch_bluestein_setup(tl_plan *p, cudaStream_t s);
+// CTAs per m of the tensor-core Legendre kernels (128 rings each) and their dynamic shared memory
+int tc_ring_blocks(const tl_plan *p, int spin);
+int tc_realisations();  // realisations per tensor-core Legendre launch
+size_t tc_persistent_smem(int nder);
 cudaError_t launch_gather(const tl_plan *p, const void *alpha, const void *d3, void *T, void *Q,
                           void *U, cudaStream_t s);
 

@@ -1,0 +1,754 @@
+// Legendre stage with the contraction on the 5th-generation tensor cores
+// (tcgen05, accumulators in tensor memory) (Naess & Louis 2013, Sec. II.B: the
+// derivative maps of Eq. 4).
+//
+// The recurrence runs exactly as in legendre.cu: one thread per ring, FP32 values
+// with FP64 seeds and exponent scaling, normalised step mu_{l+1} = A X mu_l - mu_{l-1},
+// theta-derivatives by Leibniz's rule. A CTA holds 128 rings (spin 2: 64 north
+// rings and their mirrors; spin 0: 128 north rings, south by parity) in four
+// compute warps, plus one warp that issues the tensor-core work. Every 8 values
+// of l the compute warps write the [128 rings x 8 l] tile of mu^(j) of every
+// derivative order j to shared memory, and the issuing warp runs
+//     D^(j)[128 x 32] += Mu^(j)[128 x 8] . C[8 x 32]       (tcgen05.mma, kind::tf32)
+// into tensor memory. The 32 columns hold the coefficient sets of up to eight
+// realisations that share the basis (4 reals each):
+//   spin 2: k_l (E + iB), k_l (-1)^(l+m) (E - iB);   spin 0: k_l a, k_l (-1)^(l+m) a,
+// plus, for spin 0, the lensing potential's set at j <= 1 in its own accumulators.
+// TF32 keeps 10 mantissa bits of each operand; the 3xTF32 form splits both into
+// hi + lo and accumulates hi.hi + hi.lo + lo.hi (errors near FP32).
+//
+// Why 32 columns: with few columns an MMA costs what reading its 4 KB A tile from
+// shared memory costs, so the columns per tile set the tensor work per realisation
+// (and the recurrence and tile stores are shared by all realisations).
+//
+// Pipeline: the tiles are double-buffered. For block g the compute warps run 8
+// steps (step factors and coefficient tiles prefetched one block ahead), wait
+// until the MMAs of block g-2 (same buffer) have completed (mbarrier signalled by
+// tcgen05.commit), store the tiles, fence them into the async proxy and arrive on
+// the buffer's "full" barrier (one arrival per warp). The issuing warp waits for
+// the four arrivals, issues the block's MMAs and commits them to the buffer's
+// "done" barrier, so the MMAs of one block run under the next block's steps.
+//
+// Shared-memory tiles use the K-major layout without swizzle: 8-row x 16-byte
+// core matrices, 128 bytes apart along K and 256 bytes apart along the rows.
+// Every wait is bounded; on time-out the kernel records an error flag, waits
+// (bounded) for its own MMAs, frees its tensor memory and returns.
+#include <math.h>
+#include <string.h>
+
+#include "legendre.cuh"
+
+namespace tl {
+
+constexpr int kUmmaCols = 32;     // accumulator columns per order: 8 realisations x 4 reals
+constexpr int kUmmaReal = 8;      // realisations per launch
+constexpr int kComputeThreads = 128;
+constexpr int kUmmaThreads = 160;  // + the issuing warp
+
+// ---------------------------------------------------------------------------
+// tcgen05 building blocks
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// K-major, no-swizzle tile: byte offset of (row, k) for 4-byte elements
+__host__ __device__ __forceinline__ uint32_t can_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 256 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// shared-memory matrix descriptor: start, leading (K) byte offset 128, stride (row group) 256
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of tcgen05
+  return d;
+}
+
+// instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = 32
+constexpr uint32_t kIdescTf32 =
+    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kUmmaCols >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(kIdescTf32), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
+}
+
+// bounded wait for the completion of the mbarrier phase with the given parity; gives
+// up early when another thread of the CTA has recorded a failure in *abort
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const volatile int *abort = nullptr) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (abort && (it & 255) == 255 && *abort) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// 32 consecutive columns of the calling thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// 3xTF32 split of the basis values: hi = the value with its low 13 mantissa bits
+// cleared (exactly a TF32 number), lo = value - hi (exact; the tensor core reads
+// its top 19 bits), so the pair carries ~21 bits
+__device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+// tensor-memory columns per CTA: (NJ + 2) x 32 (spin 0 with the potential's j <= 1), power of two
+template <int NJ> struct UmmaCols {
+  static constexpr int need = (NJ + 2) * kUmmaCols;
+  static constexpr int value = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+};
+
+// shared memory per tile buffer: NJ x (hi 4 KB + lo 4 KB), then the coefficient
+// tiles: field hi, lo (1 KB each), potential hi, lo
+__host__ __device__ constexpr uint32_t umma_buf_bytes(int nj) { return (uint32_t)nj * 8192u + 4096u; }
+
+// Descriptor of one plan's spin-0 or spin-2 Legendre work.
+struct TcDesc {
+  RingTable rt;
+  const double *lnorm0;
+  int nside, lmax, mmax, nrings, nreal;
+  const long long *blk;          // first 8-l block of each m
+  const float *step;             // per block: A_{l+1} x 8, m s/(l(l+1)) x 8
+  const unsigned char *b;        // per block 2 KB: coefficient tile hi [32 x 8] then lo (spin 0 field / E, B)
+  const unsigned char *bp;       // spin 0: the lensing potential's tiles (or NULL)
+  float2 *d7a, *d7b;             // spin 0: field, potential planes; spin 2: Q, U planes
+  long long rstride, rstride_p;  // T2 elements between realisations' planes
+  int *err;                      // set to 1 when a wait times out
+};
+
+// Per-CTA tcgen05 state (identical in every thread).
+struct UmmaCta {
+  uint32_t tmem;        // accumulator base (lane 0, first column)
+  uint32_t done[2];     // per buffer: MMAs of its last block completed (one arrival: the commit)
+  uint32_t full[2];     // per buffer: tiles written (one arrival per compute warp)
+  uint32_t count;       // blocks so far (the block's buffer is count & 1)
+  volatile int *abort;  // shared: set by a thread whose wait timed out
+  bool failed;
+};
+
+// block g uses buffer g & 1; it is that buffer's (g >> 1)-th phase on both barriers
+__device__ __forceinline__ uint32_t phase_of(uint32_t g) { return (g >> 1) & 1u; }
+
+// ---------------------------------------------------------------------------
+// recurrence steps with the basis values buffered for the tiles
+
+template <int S0, int NDER, bool GATED, bool SPIN2>
+__device__ __forceinline__ void four_steps(float (&a)[NDER + 1], float (&b)[NDER + 1], int &sc,
+                                           const Leib<float, NDER> &LC, float X, const float (&Av)[8],
+                                           const float (&Cv)[8], float (&buf)[NDER + 1][4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int s = S0 + q;
+    const bool on = GATED ? (sc == 0) : true;
+#pragma unroll
+    for (int j = 0; j <= NDER; ++j) buf[j][q] = on ? ((s & 1) ? a[j] : b[j]) : 0.0f;
+    const float Xs = SPIN2 ? X + Cv[s] : X;
+    if (s & 1) {
+      step_into<float, NDER>(b, a, LC, Xs, Av[s]);
+      if (GATED) rescale<float, NDER>(a, b, b[0], sc);
+    } else {
+      step_into<float, NDER>(a, b, LC, Xs, Av[s]);
+      if (GATED) rescale<float, NDER>(a, b, a[0], sc);
+    }
+  }
+}
+
+template <int S0, int NDER, bool SPIN2>
+__device__ __forceinline__ void steps_gated(float (&a)[NDER + 1], float (&b)[NDER + 1], int &sc,
+                                            const Leib<float, NDER> &LC, float X, const float (&Av)[8],
+                                            const float (&Cv)[8], float (&buf)[NDER + 1][4]) {
+  if (__all_sync(0xffffffffu, sc == 0))
+    four_steps<S0, NDER, false, SPIN2>(a, b, sc, LC, X, Av, Cv, buf);
+  else
+    four_steps<S0, NDER, true, SPIN2>(a, b, sc, LC, X, Av, Cv, buf);
+}
+
+// store one 4-column chunk of every order's tile (hi, and lo for 3xTF32)
+template <int NDER, int MODE>
+__device__ __forceinline__ void stash(unsigned char *tiles, int row, int chunk, const float (&buf)[NDER + 1][4]) {
+  const uint32_t off = can_off(row, 4 * chunk);
+#pragma unroll
+  for (int j = 0; j <= NDER; ++j) {
+    float4 h, lo;
+    if (MODE == 3) {
+      h = make_float4(tf32_trunc(buf[j][0]), tf32_trunc(buf[j][1]), tf32_trunc(buf[j][2]), tf32_trunc(buf[j][3]));
+      lo = make_float4(buf[j][0] - h.x, buf[j][1] - h.y, buf[j][2] - h.z, buf[j][3] - h.w);
+      *(float4 *)(tiles + j * 8192 + 4096 + off) = lo;
+    } else {
+      h = make_float4(__uint_as_float(to_tf32(buf[j][0])), __uint_as_float(to_tf32(buf[j][1])),
+                      __uint_as_float(to_tf32(buf[j][2])), __uint_as_float(to_tf32(buf[j][3])));
+    }
+    *(float4 *)(tiles + j * 8192 + off) = h;
+  }
+}
+
+// D_j += A_j . B for j < nj (and the lo terms for 3xTF32); accumulator j at col0 + 32 j.
+// Descriptors differ only in their start-address field: add (byte offset >> 4).
+template <int MODE>
+__device__ __forceinline__ void issue_block(uint64_t dA, uint64_t dB, int nj, uint32_t tmem_col0, bool first) {
+  for (int j = 0; j < nj; ++j)
+    umma_tf32(tmem_col0 + (uint32_t)(kUmmaCols * j), dA + (uint64_t)((uint32_t)j * (8192u >> 4)), dB, first ? 0u : 1u);
+  if (MODE == 3) {
+    const uint64_t bl = dB + (1024u >> 4);
+    for (int j = 0; j < nj; ++j)
+      umma_tf32(tmem_col0 + (uint32_t)(kUmmaCols * j), dA + (uint64_t)((uint32_t)j * (8192u >> 4)), bl, 1u);
+    for (int j = 0; j < nj; ++j)
+      umma_tf32(tmem_col0 + (uint32_t)(kUmmaCols * j), dA + (uint64_t)((uint32_t)j * (8192u >> 4) + (4096u >> 4)),
+                dB, 1u);
+  }
+}
+
+__device__ __forceinline__ int unit_l0(int m, bool spin2) { return spin2 ? (m > 2 ? m : 2) : m; }
+
+// One (m, ring block) unit: recurrence and tiles (compute warps), MMAs (issuing
+// warp). Leaves the accumulators complete in tensor memory (every MMA waited
+// for) and returns the number of 8-l blocks (0: accumulators unset).
+template <int NDER, int MODE, int KIND>
+__device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
+  constexpr bool SPIN2 = KIND == 2;
+  constexpr int NJ = NDER + 1;
+  constexpr uint32_t BUF = umma_buf_bytes(NJ);
+  const int tid = threadIdx.x;
+  const int l0 = unit_l0(m, SPIN2);
+  const int nblk = (D.lmax >= l0) ? (D.lmax - l0 + 8) / 8 : 0;
+  const long long b0 = D.blk[m];
+  const uint32_t g0 = U.count;
+  bool bad = false;
+  if (tid >= kComputeThreads) {
+    // ---- issuing warp: one lane waits for each block's tiles and issues its MMAs
+    if (tid == kComputeThreads) {
+      const uint32_t s0 = smem_u32(sm);
+      for (int blk = 0; blk < nblk; ++blk) {
+        const uint32_t g = g0 + (uint32_t)blk, i = g & 1u;
+        if (!mbar_wait(U.full[i], phase_of(g), U.abort)) {
+          bad = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t dA = umma_desc(s0 + i * BUF), dB = umma_desc(s0 + i * BUF + NJ * 8192u);
+        issue_block<MODE>(dA, dB, NJ, U.tmem, blk == 0);
+        if (KIND == 1) issue_block<MODE>(dA, dB + (2048u >> 4), 2, U.tmem + (uint32_t)(kUmmaCols * NJ), blk == 0);
+        umma_commit(U.done[i]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- compute warps: one ring per thread
+    const RingTable &rt = D.rt;
+    int r;
+    bool active;
+    if (SPIN2) {
+      const int rn = rblk * 64 + (tid & 63);
+      active = rn < 2 * D.nside;
+      r = active ? (tid >= 64 ? D.nrings - 1 - rn : rn) : 0;
+    } else {
+      const int rn = rblk * 128 + tid;
+      active = rn < 2 * D.nside;
+      r = active ? rn : 0;
+    }
+    const double invL = 1.0 / (double)(D.lmax + 1);
+    Leib<float, NDER> LC;
+    leibniz_coefs<float, NDER>(rt.z[r], rt.sint[r], invL, LC);
+    float a[NJ], b[NJ];
+    int sc;
+    if (SPIN2)
+      (void)seed_spin2<float, NDER>(rt, D.lnorm0, r, m, invL, b, sc);
+    else
+      seed_spin0<float, NDER>(rt, D.lnorm0, r, m, invL, b, sc);
+    if (!active) sc = -1000000;  // contributes nothing
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) a[j] = 0.0f;
+    const float X = (float)rt.z[r];
+    // the next block's step factors and coefficient tiles, loaded one block ahead
+    float4 nA0 = make_float4(0.f, 0.f, 0.f, 0.f), nA1 = nA0, nC0 = nA0, nC1 = nA0, nbq = nA0, nbp = nA0;
+    auto prefetch = [&](int blk) {
+      const float4 *stp = (const float4 *)(D.step + (b0 + blk) * 16);
+      nA0 = __ldg(stp);
+      nA1 = __ldg(stp + 1);
+      if (SPIN2) {
+        nC0 = __ldg(stp + 2);
+        nC1 = __ldg(stp + 3);
+      }
+      nbq = __ldg((const float4 *)(D.b + (b0 + blk) * 2048) + tid);
+      if (KIND == 1) nbp = __ldg((const float4 *)(D.bp + (b0 + blk) * 2048) + tid);
+    };
+    if (nblk > 0) prefetch(0);
+    for (int blk = 0; blk < nblk; ++blk) {
+      const uint32_t g = g0 + (uint32_t)blk, i = g & 1u;
+      const float Av[8] = {nA0.x, nA0.y, nA0.z, nA0.w, nA1.x, nA1.y, nA1.z, nA1.w};
+      const float Cv[8] = {nC0.x, nC0.y, nC0.z, nC0.w, nC1.x, nC1.y, nC1.z, nC1.w};
+      const float4 bq = nbq, bp = nbp;
+      if (blk + 1 < nblk) prefetch(blk + 1);
+      float buf0[NJ][4], buf1[NJ][4];
+      steps_gated<0, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf0);
+      steps_gated<4, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf1);
+      // this buffer was last read by the MMAs of block g - 2
+      if (g >= 2 && !mbar_wait(U.done[i], phase_of(g - 2), U.abort)) {
+        bad = true;
+        break;
+      }
+      unsigned char *tiles = sm + i * BUF;
+      stash<NDER, MODE>(tiles, tid, 0, buf0);
+      stash<NDER, MODE>(tiles, tid, 1, buf1);
+      *(float4 *)(tiles + NJ * 8192 + tid * 16) = bq;
+      if (KIND == 1) *(float4 *)(tiles + NJ * 8192 + 2048 + tid * 16) = bp;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(U.full[i]);
+    }
+  }
+  U.count = g0 + (uint32_t)nblk;
+  // the last commit covers every MMA issued before it
+  if (!bad && nblk > 0 && !mbar_wait(U.done[(U.count - 1) & 1u], phase_of(U.count - 1), U.abort)) bad = true;
+  if (bad) *U.abort = 1;
+  if (__syncthreads_or(bad)) {
+    U.failed = true;
+    return 0;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return nblk;
+}
+
+// spin 2: combine each ring's S1 with its mirror's S2 into F^Q, F^U, one order at a time
+template <int NDER, int MODE>
+__device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
+  constexpr int NJ = NDER + 1;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nblk = run_blocks<NDER, MODE, 2>(D, m, rblk, sm, U);
+  if (U.failed) return;
+  const bool compute = tid < kComputeThreads;
+  const int rn = rblk * 64 + (tid & 63);
+  const bool active = compute && rn < 2 * D.nside;
+  const bool mirror = tid >= 64;
+  const int r = active ? (mirror ? D.nrings - 1 - rn : rn) : 0;
+  const bool writer = active && m <= D.mmax && !(mirror && rn == D.nrings - 1 - rn);  // equator: north thread
+  const int partner = tid ^ 64;
+  const size_t ld = (size_t)(D.mmax + 1);
+  float *xch = (float *)sm;  // [128][16]: S2 (4 rho + 2, 3) of every ring, over the (now free) tiles
+#pragma unroll 1
+  for (int j = 0; j < NJ; ++j) {
+    float v[32];
+    if (compute) {
+      tmem_ld32(U.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kUmmaCols * j), v);
+#pragma unroll
+      for (int rho = 0; rho < kUmmaReal; ++rho) {
+        xch[tid * 16 + 2 * rho] = nblk ? v[4 * rho + 2] : 0.f;
+        xch[tid * 16 + 2 * rho + 1] = nblk ? v[4 * rho + 3] : 0.f;
+      }
+    }
+    __syncthreads();
+    if (writer) {
+      const float sg = (j & 1) ? -1.0f : 1.0f;
+#pragma unroll
+      for (int rho = 0; rho < kUmmaReal; ++rho) {
+        if (rho >= D.nreal) break;
+        const float s1r = nblk ? v[4 * rho] : 0.f, s1i = nblk ? v[4 * rho + 1] : 0.f;
+        const float s2r = xch[partner * 16 + 2 * rho], s2i = xch[partner * 16 + 2 * rho + 1];
+        const float ar = s1r + sg * s2r, ai = s1i + sg * s2i;
+        const float br = s1r - sg * s2r, bi = s1i - sg * s2i;
+        const size_t o = (size_t)rho * D.rstride + ((size_t)j * D.nrings + r) * ld + m;
+        D.d7a[o] = make_float2(-0.5f * ar, -0.5f * ai);
+        D.d7b[o] = make_float2(-0.5f * bi, 0.5f * br);
+      }
+    }
+    __syncthreads();  // xch is rewritten for the next order, and is the next unit's tiles
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+// spin 0: north ring r and its mirror by parity; the potential's j <= 1 with KIND 1
+template <int NDER, int MODE, int KIND>
+__device__ __forceinline__ void u0_unit(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
+  constexpr int NJ = NDER + 1;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int nblk = run_blocks<NDER, MODE, KIND>(D, m, rblk, sm, U);
+  if (U.failed) return;
+  if (tid < kComputeThreads) {
+    const int rn = rblk * 128 + tid;
+    const bool active = rn < 2 * D.nside && m <= D.mmax;
+    const int r = active ? rn : 0;
+    const int rs = D.nrings - 1 - r;
+    const size_t ld = (size_t)(D.mmax + 1);
+    const uint32_t lane_base = U.tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int j = 0; j < NJ + (KIND == 1 ? 2 : 0); ++j) {
+      float v[32];
+      tmem_ld32(lane_base + (uint32_t)(kUmmaCols * j), v);
+      if (!active || nblk == 0) continue;
+      const bool pot = j >= NJ;
+      const int jj = pot ? j - NJ : j;
+      float2 *out = pot ? D.d7b : D.d7a;
+      const long long rstr = pot ? D.rstride_p : D.rstride;
+      const float sg = (jj & 1) ? -1.0f : 1.0f;
+#pragma unroll
+      for (int rho = 0; rho < kUmmaReal; ++rho) {
+        if (rho >= D.nreal) break;
+        const size_t o = (size_t)rho * rstr + (size_t)jj * D.nrings * ld + m;
+        out[o + (size_t)r * ld] = make_float2(v[4 * rho], v[4 * rho + 1]);
+        if (rs != r) out[o + (size_t)rs * ld] = make_float2(sg * v[4 * rho + 2], sg * v[4 * rho + 3]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+}
+
+// CTA set-up and tear-down of the barriers and the tensor memory
+template <int NCOLS>
+__device__ __forceinline__ void umma_open(UmmaCta &U, uint64_t *bars, uint32_t *tbase, int *abort) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));  // done[0]: the commit
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));  // done[1]
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars[2])));  // full[0]: 4 warps
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars[3])));  // full[1]
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    *abort = 0;
+  }
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tbase)),
+                 "n"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  U.tmem = *tbase;
+  U.done[0] = smem_u32(&bars[0]);
+  U.done[1] = smem_u32(&bars[1]);
+  U.full[0] = smem_u32(&bars[2]);
+  U.full[1] = smem_u32(&bars[3]);
+  U.count = 0;
+  U.abort = abort;
+  U.failed = false;
+}
+
+template <int NCOLS>
+__device__ __forceinline__ void umma_close(const TcDesc &D, UmmaCta &U) {
+  if (U.failed && threadIdx.x == 0) {
+    atomicExch(D.err, 1);
+    // own MMAs in flight: the last two blocks' commits (bounded)
+    if (U.count > 0) (void)mbar_wait(U.done[(U.count - 1) & 1u], phase_of(U.count - 1));
+    if (U.count > 1) (void)mbar_wait(U.done[(U.count - 2) & 1u], phase_of(U.count - 2));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(U.tmem), "n"(NCOLS));
+}
+
+template <int NDER, int MODE>
+__global__ void __launch_bounds__(kUmmaThreads, 2) legendre_spin2_umma(TcDesc D) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  constexpr int NCOLS = UmmaCols<NDER + 1>::value;
+  UmmaCta U;
+  umma_open<NCOLS>(U, bars, &tbase, &abort_flag);
+  u2_unit<NDER, MODE>(D, blockIdx.y, blockIdx.x, sm, U);
+  umma_close<NCOLS>(D, U);
+}
+
+template <int NDER, int MODE, bool PHI>
+__global__ void __launch_bounds__(kUmmaThreads, 2) legendre_spin0_umma(TcDesc D) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  constexpr int NCOLS = UmmaCols<NDER + 1>::value;
+  UmmaCta U;
+  umma_open<NCOLS>(U, bars, &tbase, &abort_flag);
+  u0_unit<NDER, MODE, PHI ? 1 : 0>(D, blockIdx.y, blockIdx.x, sm, U);
+  umma_close<NCOLS>(D, U);
+}
+
+// Persistent form: one launch covers the spin-0 and spin-2 work of several plans.
+// Items (descriptor, kind, m, ring block) are pre-sorted by cost; each CTA takes
+// them in order from an atomic counter until none is left (no waits between CTAs).
+template <int NDER, int MODE>
+__global__ void __launch_bounds__(kUmmaThreads, 2) legendre_umma_persistent(const TcDesc *__restrict__ descs,
+                                                                           const int4 *__restrict__ items,
+                                                                           int nitems, int *__restrict__ counter) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  __shared__ int cur;
+  constexpr int NCOLS = UmmaCols<NDER + 1>::value;
+  UmmaCta U;
+  umma_open<NCOLS>(U, bars, &tbase, &abort_flag);
+  TcDesc D = descs[0];
+  for (;;) {
+    __syncthreads();  // the previous item's readers of `cur` are done
+    if (threadIdx.x == 0) cur = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    D = descs[w.x & 0xffff];
+    const int kind = w.x >> 16;
+    if (kind == 2)
+      u2_unit<NDER, MODE>(D, w.y, w.z, sm, U);
+    else if (kind == 1)
+      u0_unit<NDER, MODE, 1>(D, w.y, w.z, sm, U);
+    else
+      u0_unit<NDER, MODE, 0>(D, w.y, w.z, sm, U);
+    if (U.failed) break;  // uniform: set after a block-wide vote
+  }
+  umma_close<NCOLS>(D, U);
+}
+
+// ---------------------------------------------------------------------------
+// plan-time and per-call tables
+
+// step factors per block: A_{l+1} (8 floats) then m s/(l(l+1)) (8 floats); 0 past lmax
+__global__ void tcstep_kernel(int lmax, int s, const long long *__restrict__ blkofs,
+                              const float2 *__restrict__ tab, float *__restrict__ out) {
+  const int m = blockIdx.y;
+  const int as = s < 0 ? -s : s;
+  const int l0 = m > as ? m : as;
+  const int nblk = (lmax >= l0) ? (lmax - l0 + 8) / 8 : 0;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (block, slot)
+  if (e >= nblk * 8) return;
+  const int blk = e >> 3, k = e & 7;
+  const int l = l0 + 8 * blk + k;
+  float A = 0.0f, ct = 0.0f;
+  if (l <= lmax) {
+    A = tab[(long long)m * (2 * lmax + 1 - m) / 2 + l].y;
+    ct = (float)((double)m * s / ((double)l * (l + 1.0)));
+  }
+  float *o = out + (blkofs[m] + blk) * 16;
+  o[k] = A;
+  o[8 + k] = ct;
+}
+
+// Coefficient tiles per 8-l block: B[n][k] for column n = 4 rho + c and l = l0 + 8 blk + k,
+// as TF32 hi (first 1 KB) and lo (next 1 KB), K-major without swizzle.
+//   spin 2: c = 0,1: k_l (E + iB) re, im;  c = 2,3: k_l (-1)^(l+m) (E - iB) re, im
+//   spin 0: c = 0,1: k_l a re, im;         c = 2,3: k_l (-1)^(l+m) a re, im
+struct TcAlm {
+  const double *a[kUmmaReal];  // spin 0 field, or E (spin 2)
+  const double *b[kUmmaReal];  // B (spin 2), may be NULL
+};
+
+__global__ void tcprep_kernel(int lmax, int s, int nreal, TcAlm alm, const long long *__restrict__ blkofs,
+                              const float2 *__restrict__ tab, unsigned char *__restrict__ out) {
+  const int m = blockIdx.y;
+  const int as = s < 0 ? -s : s;
+  const int l0 = m > as ? m : as;
+  const int nblk = (lmax >= l0) ? (lmax - l0 + 8) / 8 : 0;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (block, n, k)
+  if (e >= nblk * 256) return;
+  const int blk = e >> 8, n = (e >> 3) & 31, k = e & 7;
+  const int rho = n >> 2, c = n & 3;
+  const int l = l0 + 8 * blk + k;
+  double val = 0.0;
+  if (l <= lmax && rho < nreal) {
+    const long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
+    const double kl = (double)tab[idx].x;
+    const double sg = ((l + m) & 1) ? -1.0 : 1.0;
+    const double *A = alm.a[rho], *Bm = alm.b[rho];
+    const double ar = A[2 * idx], ai = (m > 0) ? A[2 * idx + 1] : 0.0;
+    if (s == 0) {
+      const double re = ar * kl, im = ai * kl;
+      val = (c == 0) ? re : (c == 1) ? im : (c == 2) ? sg * re : sg * im;
+    } else {
+      const double br = Bm ? Bm[2 * idx] : 0.0, bi = (Bm && m > 0) ? Bm[2 * idx + 1] : 0.0;
+      val = (c == 0) ? (ar - bi) * kl : (c == 1) ? (ai + br) * kl : (c == 2) ? sg * kl * (ar + bi) : sg * kl * (ai - br);
+    }
+  }
+  const float v = (float)val;
+  const float hi = __uint_as_float(to_tf32(v));
+  const float lo = __uint_as_float(to_tf32(v - hi));
+  unsigned char *o = out + (blkofs[m] + blk) * 2048;
+  const uint32_t off = can_off(n, k);
+  *(float *)(o + off) = hi;
+  *(float *)(o + 1024 + off) = lo;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+cudaError_t launch_tcstep(const tl_plan *p, int s, const long long *blkofs, const void *tab, float *out,
+                          cudaStream_t st) {
+  const int maxe = ((p->lmax + 8) / 8) * 8;
+  dim3 grid((maxe + 255) / 256, p->lmax + 1);
+  tcstep_kernel<<<grid, 256, 0, st>>>(p->lmax, s, blkofs, (const float2 *)tab, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *const *a, const double *const *b,
+                          const long long *blkofs, const void *tab, void *out, cudaStream_t st) {
+  if (nreal < 1 || nreal > kUmmaReal) return cudaErrorInvalidValue;
+  TcAlm alm;
+  for (int i = 0; i < kUmmaReal; ++i) {
+    alm.a[i] = (i < nreal) ? a[i] : nullptr;
+    alm.b[i] = (i < nreal && b) ? b[i] : nullptr;
+  }
+  const int maxe = ((p->lmax + 8) / 8) * 256;
+  dim3 grid((maxe + 255) / 256, p->lmax + 1);
+  tcprep_kernel<<<grid, 256, 0, st>>>(p->lmax, s, nreal, alm, blkofs, (const float2 *)tab, (unsigned char *)out);
+  return cudaGetLastError();
+}
+
+// Rings per CTA: spin 2 takes 64 north rings with their mirrors, spin 0 128 north rings.
+int tc_realisations() { return kUmmaReal; }
+int tc_ring_blocks(const tl_plan *p, int spin) {
+  return spin == 2 ? (2 * p->nside + 63) / 64 : (2 * p->nside + 127) / 128;
+}
+
+// Dynamic shared memory: two tile buffers of NJ x 8 KB + 4 KB of coefficient tiles,
+// at least the size that keeps the CTAs per SM within the tensor memory
+// (512 columns per SM): 2 CTAs of 256 columns (76 KB) or 1 of 512 (114 KB).
+static size_t umma_smem(int nder) {
+  const int nj = nder + 1;
+  const size_t need = 2 * (size_t)umma_buf_bytes(nj);
+  const int need_cols = (nj + 2) * kUmmaCols;
+  const size_t floor_b = need_cols <= 128 ? 46 * 1024 : need_cols <= 256 ? 76 * 1024 : 114 * 1024;
+  return need > floor_b ? need : floor_b;
+}
+
+static TcDesc make_desc(const tl_plan *p, int spin, int nreal, void *d7a, void *d7b, long long rstride,
+                        long long rstride_p) {
+  TcDesc D;
+  memset(&D, 0, sizeof D);
+  D.rt = p->ring;
+  D.lnorm0 = p->lnorm0;
+  D.nside = p->nside;
+  D.lmax = p->lmax;
+  D.mmax = p->mmax;
+  D.nrings = p->nrings;
+  D.nreal = nreal;
+  D.blk = spin == 2 ? p->tc_blk2 : p->tc_blk0;
+  D.step = spin == 2 ? p->tc_step2 : p->tc_step0;
+  D.b = (const unsigned char *)(spin == 2 ? p->tc_b2 : p->tc_b0);
+  D.bp = (const unsigned char *)p->tc_bp;
+  D.d7a = (float2 *)d7a;
+  D.d7b = (float2 *)d7b;
+  D.rstride = rstride;
+  D.rstride_p = rstride_p;
+  D.err = p->dev_err;
+  return D;
+}
+
+// Write the descriptor of a plan's spin-0 or spin-2 work (nreal realisations) to dst.
+void tc_desc_write(const tl_plan *p, int spin, int nreal, void *dst) {
+  const TcDesc d = spin == 2 ? make_desc(p, 2, nreal, p->d7_Q, p->d7_U, p->d7_rstride, 0)
+                             : make_desc(p, 0, nreal, p->d7_T, p->d7_P, p->d7_rstride, p->d7p_rstride);
+  memcpy(dst, &d, sizeof d);
+}
+size_t tc_desc_bytes() { return sizeof(TcDesc); }
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int NDER, int MODE>
+static cudaError_t u2(const tl_plan *p, int nreal, void *dq, void *du, long long rstride, cudaStream_t s) {
+  const size_t smem = umma_smem(NDER);
+  TL_CUDA_TRY(set_smem(legendre_spin2_umma<NDER, MODE>, smem));
+  dim3 grid(tc_ring_blocks(p, 2), p->mmax + 1);
+  legendre_spin2_umma<NDER, MODE><<<grid, kUmmaThreads, smem, s>>>(make_desc(p, 2, nreal, dq, du, rstride, 0));
+  return cudaGetLastError();
+}
+
+template <int NDER, int MODE, bool PHI>
+static cudaError_t u0(const tl_plan *p, int nreal, void *d7, void *d7p, long long rstride, long long rstride_p,
+                      cudaStream_t s) {
+  const size_t smem = umma_smem(NDER);
+  TL_CUDA_TRY(set_smem(legendre_spin0_umma<NDER, MODE, PHI>, smem));
+  dim3 grid(tc_ring_blocks(p, 0), p->mmax + 1);
+  legendre_spin0_umma<NDER, MODE, PHI><<<grid, kUmmaThreads, smem, s>>>(make_desc(p, 0, nreal, d7, d7p, rstride, rstride_p));
+  return cudaGetLastError();
+}
+
+template <int NDER, int MODE>
+static cudaError_t up(const void *descs, const void *items, int nitems, int *counter, int grid, cudaStream_t s) {
+  const size_t smem = umma_smem(NDER);
+  TL_CUDA_TRY(set_smem(legendre_umma_persistent<NDER, MODE>, smem));
+  legendre_umma_persistent<NDER, MODE><<<grid, kUmmaThreads, smem, s>>>((const TcDesc *)descs, (const int4 *)items, nitems,
+                                                               counter);
+  return cudaGetLastError();
+}
+
+#define TL_TC_ORDERS(X) X(1) X(2) X(3) X(4) X(5) X(6)
+
+cudaError_t launch_legendre_tc_persistent(int nder, int precision, const void *descs, const void *items, int nitems,
+                                          int *counter, int grid, cudaStream_t s) {
+  const bool x3 = precision == TL_MIXED_TF32x3;
+  switch (nder) {
+#define CASE(n) \
+  case n: return x3 ? up<n, 3>(descs, items, nitems, counter, grid, s) : up<n, 1>(descs, items, nitems, counter, grid, s);
+    TL_TC_ORDERS(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void *dq, void *du, long long rstride,
+                                     cudaStream_t s) {
+  const bool x3 = p->precision == TL_MIXED_TF32x3;
+  switch (nder) {
+#define CASE(n) \
+  case n: return x3 ? u2<n, 3>(p, nreal, dq, du, rstride, s) : u2<n, 1>(p, nreal, dq, du, rstride, s);
+    TL_TC_ORDERS(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, bool phi, void *d7, void *d7p,
+                                     long long rstride, long long rstride_p, cudaStream_t s) {
+  const bool x3 = p->precision == TL_MIXED_TF32x3;
+  switch (nder) {
+#define CASE(n)                                                                                   \
+  case n:                                                                                         \
+    if (phi)                                                                                      \
+      return x3 ? u0<n, 3, true>(p, nreal, d7, d7p, rstride, rstride_p, s)                        \
+                : u0<n, 1, true>(p, nreal, d7, d7p, rstride, rstride_p, s);                       \
+    return x3 ? u0<n, 3, false>(p, nreal, d7, d7p, rstride, rstride_p, s)                         \
+              : u0<n, 1, false>(p, nreal, d7, d7p, rstride, rstride_p, s);
+    TL_TC_ORDERS(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+// The persistent kernel's dynamic shared memory (for the grid-size choice).
+size_t tc_persistent_smem(int nder) { return umma_smem(nder); }
+
+}  // namespace tl

@@ -79,7 +79,7 @@ static void free_plan(tl_plan *p) {
                   p->rec_QU,
                   p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->adj_dbar, p->adj_ga, p->stage_alm,
                   p->stage_out,
-                  p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2};
+                  p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2, p->dev_err};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (p->timing)
@@ -150,7 +150,7 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   const size_t plane = (size_t)p->nrings * (p->mmax + 1) * t2;
   const bool pol = (spins & TL_SPIN_QU) != 0;
   const bool tc = (precision == TL_MIXED_TF32 || precision == TL_MIXED_TF32x3);
-  p->batch = tc ? 2 : 1;
+  p->batch = tc ? tc_realisations() : 1;
   p->tc_nder = order > 1 ? order : 1;
   const int nplanes = tc ? p->tc_nder + 1 : order + 1;  // D7 planes per field and realisation
   p->d7_rstride = (long long)nplanes * p->nrings * (p->mmax + 1);
@@ -182,15 +182,17 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
     TRY_CUDA(upload(&p->tc_blk0, b0, B));
     TRY_CUDA(dalloc((void **)&p->tc_step0, 64 * (size_t)n0, B));
     TRY_CUDA(launch_tcstep(p, 0, p->tc_blk0, p->tab0, p->tc_step0, 0));
-    TRY_CUDA(dalloc(&p->tc_b0, 512 * (size_t)n0, B));
-    TRY_CUDA(dalloc(&p->tc_bp, 512 * (size_t)n0, B));
+    TRY_CUDA(dalloc(&p->tc_b0, 2048 * (size_t)n0, B));
+    TRY_CUDA(dalloc(&p->tc_bp, 2048 * (size_t)n0, B));
     if (pol) {
       TRY_CUDA(upload(&p->tc_blk2, b2, B));
       TRY_CUDA(dalloc((void **)&p->tc_step2, 64 * (size_t)(n2 > 0 ? n2 : 1), B));
       TRY_CUDA(launch_tcstep(p, 2, p->tc_blk2, p->tab2, p->tc_step2, 0));
-      TRY_CUDA(dalloc(&p->tc_b2, 512 * (size_t)(n2 > 0 ? n2 : 1), B));
+      TRY_CUDA(dalloc(&p->tc_b2, 2048 * (size_t)(n2 > 0 ? n2 : 1), B));
     }
   }
+  TRY_CUDA(dalloc((void **)&p->dev_err, sizeof(int), B));
+  TRY_CUDA(cudaMemset(p->dev_err, 0, sizeof(int)));
   const int nfield = pol ? 3 : 1;
   TRY_CUDA(dalloc(&p->d3, (size_t)p->elem * nfield * p->nmaps * p->npix, B));
   TRY_CUDA(dalloc(&p->alpha, (size_t)p->elem * 2 * p->npix, B));
@@ -253,6 +255,18 @@ extern "C" tl_status tl_plan_destroy(tl_plan *p) {
 }
 
 extern "C" size_t tl_plan_workspace_bytes(const tl_plan *p) { return p ? p->bytes : 0; }
+
+extern "C" tl_status tl_plan_device_error(tl_plan *p) {
+  if (!p) return TL_ERR_ARG;
+  int h = 0;
+  TRY_CUDA(cudaDeviceSynchronize());
+  TRY_CUDA(cudaMemcpy(&h, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    TRY_CUDA(cudaMemset(p->dev_err, 0, sizeof(int)));
+    return TL_ERR_TIMEOUT;
+  }
+  return TL_OK;
+}
 
 extern "C" int tl_plan_maps_per_field(const tl_plan *p) { return p ? p->nmaps : 0; }
 

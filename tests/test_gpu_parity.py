@@ -99,7 +99,7 @@ def test_lens_mixed_fp32(nside, lmax, order):
 
 
 @pytest.mark.parametrize("precision,tol", [(api.MIXED_TF32x3, 1e-4), (api.MIXED_TF32, 5e-3)])
-@pytest.mark.parametrize("nside,lmax,order", [(32, 64, 4), (64, 128, 3), (16, 40, 1)])
+@pytest.mark.parametrize("nside,lmax,order", [(32, 64, 4), (64, 128, 3), (16, 40, 1), (128, 203, 2), (8, 21, 6)])
 def test_lens_tensor_core_forms(nside, lmax, order, precision, tol):
     """Contraction on the tensor cores: 3xTF32 meets the mixed-precision target,
     plain TF32 is reported with its own (looser) bound."""
@@ -113,10 +113,10 @@ def test_lens_tensor_core_forms(nside, lmax, order, precision, tol):
 
 @pytest.mark.parametrize("precision", [api.MIXED_TF32x3, api.MIXED_FP32, api.FP64])
 def test_lens_batch_equals_single_calls(precision):
-    """tl_lens_batch over 3 realisations (a shared-basis pair and a single one on
-    tensor-core plans) gives what three tl_lens calls give."""
+    """tl_lens_batch over 10 realisations (on tensor-core plans a group of eight that
+    shares one basis, then a group of two) gives what ten tl_lens calls give."""
     nside, lmax, order = 32, 64, 4
-    skies = [to_dev(sky(nside, lmax, pol=True, seeds=(10 + i, 20 + i, 30 + i), b_scale=0.3)) for i in range(3)]
+    skies = [to_dev(sky(nside, lmax, pol=True, seeds=(10 + i, 20 + i, 30 + i), b_scale=0.3)) for i in range(10)]
     plan = api.Plan(nside, lmax, order, pol=True, precision=precision)
     try:
         outs = [o.cpu().numpy() for o in plan.lens_batch(skies)]
