@@ -37,9 +37,48 @@ template <typename T> __device__ __forceinline__ void sincos_pi(T x, T *s, T *c)
 template <> __device__ __forceinline__ void sincos_pi<float>(float x, float *s, float *c) { sincospif(x, s, c); }
 template <> __device__ __forceinline__ void sincos_pi<double>(double x, double *s, double *c) { sincospi(x, s, c); }
 
-// In-place radix-2 DIT FFT on `batch` contiguous arrays of length n (power of two)
-// in shared memory. dir = -1: sum x e^{-2 pi i k t/n}; dir = +1: e^{+...}.
-// tw[k] = e^{-2 pi i k / TW}, k < TW/2. Index arithmetic by shifts and masks.
+// R consecutive radix-2 DIT stages (half-spans 2^sh .. 2^(sh+R-1)) fused into one
+// pass: each thread loads the 2^R elements base + c 2^sh of one group, runs the R
+// levels of butterflies in registers and stores them back. At stage s an element
+// whose bit s is clear pairs with the one 2^s above it, with the twiddle
+// W_{2^(s+1)}^(index mod 2^s).
+template <int R, typename T2>
+__device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int sh, int dir, const T2 *__restrict__ tw,
+                                         int lgtw) {
+  constexpr int P = 1 << R;
+  const int ulg = lg - R;  // groups per array: 2^ulg
+  const int total = batch << ulg;
+  const int h = 1 << sh;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int b = e >> ulg, q = e & ((1 << ulg) - 1);
+    const int pos = q & (h - 1), grp = q >> sh;
+    T2 *base = a + (b << lg) + (grp << (sh + R)) + pos;
+    T2 x[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) x[c] = base[c << sh];
+#pragma unroll
+    for (int lev = 0; lev < R; ++lev) {
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        if ((c >> lev) & 1) continue;
+        const int cc = c & ((1 << lev) - 1);
+        T2 w = tw[(pos + (cc << sh)) << (lgtw - sh - lev - 1)];
+        if (dir > 0) w.y = -w.y;
+        const T2 u = x[c], v = cmul(x[c + (1 << lev)], w);
+        x[c] = cadd(u, v);
+        x[c + (1 << lev)] = csub(u, v);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < P; ++c) base[c << sh] = x[c];
+  }
+  __syncthreads();
+}
+
+// In-place DIT FFT on `batch` contiguous arrays of length n (power of two) in
+// shared memory. dir = -1: sum x e^{-2 pi i k t/n}; dir = +1: e^{+...}.
+// tw[k] = e^{-2 pi i k / TW}, k < TW/2 (TW >= n). A bit-reversal permutation, then
+// the log2 n radix-2 stages in passes of three (eight elements per thread).
 template <typename T2>
 __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict__ tw, int TW) {
   const int nth = blockDim.x, tid = threadIdx.x;
@@ -57,24 +96,11 @@ __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict_
     }
   }
   __syncthreads();
-  const int hn = n >> 1;
-  const int nbf = hn * batch;
   const int lgtw = 31 - __clz(TW);
-  for (int sh = 0; sh < lg; ++sh) {  // len = 2^(sh+1), half = 2^sh
-    const int half = 1 << sh;
-    const int tws = lgtw - sh - 1;  // twiddle stride TW / len = 2^tws
-    for (int e = tid; e < nbf; e += nth) {
-      const int b = e >> (lg - 1), q = e & (hn - 1);
-      const int grp = q >> sh, pos = q & (half - 1);
-      const int i0 = (b << lg) + (grp << (sh + 1)) + pos, i1 = i0 + half;
-      T2 w = tw[pos << tws];
-      if (dir > 0) w.y = -w.y;
-      const T2 u = a[i0], v = cmul(a[i1], w);
-      a[i0] = cadd(u, v);
-      a[i1] = csub(u, v);
-    }
-    __syncthreads();
-  }
+  int sh = 0;
+  for (; sh + 3 <= lg; sh += 3) dit_pass<3, T2>(a, lg, batch, sh, dir, tw, lgtw);
+  if (lg - sh == 2) dit_pass<2, T2>(a, lg, batch, sh, dir, tw, lgtw);
+  if (lg - sh == 1) dit_pass<1, T2>(a, lg, batch, sh, dir, tw, lgtw);
 }
 
 // Bluestein on `batch` contiguous sequences y[b n + t] of length n (n arbitrary),
