@@ -40,6 +40,14 @@ struct BluesteinTable {
 
 struct StageTimer;
 
+// Rings of one ring-FFT launch: the equatorial belt, the power-of-two caps, or
+// the caps whose Bluestein length is M; ring indices fft_rings[first .. first + count),
+// largest first. Each launch gets the shared memory its own rings need.
+struct FftGroup {
+  int first, count, ni_max, ni_min, M;
+};
+#define TL_MAX_FFT_GROUPS 24
+
 }  // namespace tl
 
 struct tl_plan {
@@ -56,6 +64,9 @@ struct tl_plan {
   int tw_len;
   int blue_maxm;        // largest Bluestein FFT length (0 if none)
   int fft_batch;        // Bluestein sub-transforms run together in the ring FFT (1 or 4; 0 = choose)
+  int *fft_rings;       // ring indices grouped by FFT launch (device)
+  int fft_ngroups;
+  tl::FftGroup fft_groups[TL_MAX_FFT_GROUPS];
   // workspace
   void *tab0, *tab2;    // plan-time step tables {k_l, A_{l+1}} for spin 0 and spin 2
   void *rec_T, *rec_P, *rec_QU; // coefficient records
@@ -154,6 +165,9 @@ long long host_bluestein_layout(int nside, long long *off, int *ml, int *maxm);
 int host_twiddle_len(int nside, int maxm);
 void host_twiddles(int TW, double *tw);
 size_t ringfft_smem_bytes(const tl_plan *p);
+// ring-FFT launch groups (no allocation): fills groups[] and order[nrings]; returns
+// the number of groups, or -1 if there are more than TL_MAX_FFT_GROUPS
+int host_fft_groups(int nside, int nrings, const int *nphi, const int *ml, FftGroup *groups, int *order);
 cudaError_t launch_bluestein_setup_impl(tl_plan *p, const double2 *tw64, cudaStream_t s);
 
 // normalisation of theta derivatives inside the Legendre stage: lambda^(j) / L^j

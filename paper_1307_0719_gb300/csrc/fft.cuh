@@ -37,14 +37,38 @@ template <typename T> __device__ __forceinline__ void sincos_pi(T x, T *s, T *c)
 template <> __device__ __forceinline__ void sincos_pi<float>(float x, float *s, float *c) { sincospif(x, s, c); }
 template <> __device__ __forceinline__ void sincos_pi<double>(double x, double *s, double *c) { sincospi(x, s, c); }
 
+// Shared-memory layout of the ring transforms: element i of an array sits at
+// i + i/8 (one pad slot every 8 complex values), which keeps the fused passes below
+// free of bank conflicts for every span.
+__host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 3); }
+__device__ __forceinline__ int brev_bits(int e, int lg) { return lg == 0 ? 0 : (int)(__brev((unsigned)e) >> (32 - lg)); }
+
+// e^{-2 pi i cc / 2^(lev+1)} (conjugated for dir > 0), cc < 2^lev, lev <= 2
+template <typename T, typename T2>
+__device__ __forceinline__ T2 unit_root(int lev, int cc, int dir) {
+  const T h = (T)0.70710678118654752440;
+  T2 r;
+  if (lev == 1) {
+    r.x = (T)0;
+    r.y = (T)-1;
+  } else {  // lev == 2
+    r.x = (cc == 1) ? h : (cc == 2) ? (T)0 : -h;
+    r.y = (cc == 2) ? (T)-1 : -h;
+  }
+  if (dir > 0) r.y = -r.y;
+  return r;
+}
+
 // R consecutive radix-2 DIT stages (half-spans 2^sh .. 2^(sh+R-1)) fused into one
-// pass: each thread loads the 2^R elements base + c 2^sh of one group, runs the R
+// pass: each thread loads the 2^R elements i0 + c 2^sh of one group, runs the R
 // levels of butterflies in registers and stores them back. At stage s an element
 // whose bit s is clear pairs with the one 2^s above it, with the twiddle
-// W_{2^(s+1)}^(index mod 2^s).
-template <int R, typename T2>
-__device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int sh, int dir, const T2 *__restrict__ tw,
-                                         int lgtw) {
+// W_{2^(s+1)}^(index mod 2^s) = W_{2^(s+1)}^pos W_{2^(lev+1)}^cc: one table load
+// per level times a fixed root of unity.
+template <int R, bool PAD, typename T, typename T2>
+__device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, int sh, int dir,
+                                         const T2 *__restrict__ tw, int lgtw) {
   constexpr int P = 1 << R;
   const int ulg = lg - R;  // groups per array: 2^ulg
   const int total = batch << ulg;
@@ -52,42 +76,54 @@ __device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int sh, int d
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int b = e >> ulg, q = e & ((1 << ulg) - 1);
     const int pos = q & (h - 1), grp = q >> sh;
-    T2 *base = a + (b << lg) + (grp << (sh + R)) + pos;
+    T2 *arr = a + (size_t)b * stride;
+    const int i0 = (grp << (sh + R)) + pos;
     T2 x[P];
 #pragma unroll
-    for (int c = 0; c < P; ++c) x[c] = base[c << sh];
+    for (int c = 0; c < P; ++c) x[c] = arr[PAD ? pidx(i0 + (c << sh)) : i0 + (c << sh)];
 #pragma unroll
     for (int lev = 0; lev < R; ++lev) {
+      T2 wl = tw[pos << (lgtw - sh - lev - 1)];
+      if (dir > 0) wl.y = -wl.y;
 #pragma unroll
       for (int c = 0; c < P; ++c) {
         if ((c >> lev) & 1) continue;
         const int cc = c & ((1 << lev) - 1);
-        T2 w = tw[(pos + (cc << sh)) << (lgtw - sh - lev - 1)];
-        if (dir > 0) w.y = -w.y;
+        const T2 w = cc ? cmul(wl, unit_root<T, T2>(lev, cc, dir)) : wl;
         const T2 u = x[c], v = cmul(x[c + (1 << lev)], w);
         x[c] = cadd(u, v);
         x[c + (1 << lev)] = csub(u, v);
       }
     }
 #pragma unroll
-    for (int c = 0; c < P; ++c) base[c << sh] = x[c];
+    for (int c = 0; c < P; ++c) arr[PAD ? pidx(i0 + (c << sh)) : i0 + (c << sh)] = x[c];
   }
   __syncthreads();
 }
 
-// In-place DIT FFT on `batch` contiguous arrays of length n (power of two) in
-// shared memory. dir = -1: sum x e^{-2 pi i k t/n}; dir = +1: e^{+...}.
-// tw[k] = e^{-2 pi i k / TW}, k < TW/2 (TW >= n). A bit-reversal permutation, then
-// the log2 n radix-2 stages in passes of three (eight elements per thread).
-template <typename T2>
-__device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict__ tw, int TW) {
-  const int nth = blockDim.x, tid = threadIdx.x;
+// In-place DIT FFT on `batch` arrays of length n (power of two), `stride` elements
+// apart, whose input is already in bit-reversed order (the writers store it so);
+// output in natural order. dir = -1: sum x e^{-2 pi i k t/n}; dir = +1: e^{+...}.
+// tw[k] = e^{-2 pi i k / TW}, k < TW/2 (TW >= n). Passes of three stages.
+template <bool PAD, typename T, typename T2>
+__device__ void fft_core(T2 *a, int n, int batch, int stride, int dir, const T2 *__restrict__ tw, int TW) {
   if (n <= 1) return;
   const int lg = 31 - __clz(n);
-  const int total = n * batch;
-  for (int e = tid; e < total; e += nth) {
+  const int lgtw = 31 - __clz(TW);
+  int sh = 0;
+  for (; sh + 3 <= lg; sh += 3) dit_pass<3, PAD, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  if (lg - sh == 2) dit_pass<2, PAD, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  if (lg - sh == 1) dit_pass<1, PAD, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+}
+
+// The same for contiguous, unpadded arrays in natural order (bit-reversal first).
+template <typename T, typename T2>
+__device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict__ tw, int TW) {
+  if (n <= 1) return;
+  const int lg = 31 - __clz(n);
+  for (int e = threadIdx.x; e < n * batch; e += blockDim.x) {
     const int k = e & (n - 1);
-    const int r = __brev(k) >> (32 - lg);
+    const int r = brev_bits(k, lg);
     if (k < r) {
       const int base = e - k;
       T2 t = a[base + k];
@@ -96,44 +132,52 @@ __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict_
     }
   }
   __syncthreads();
-  const int lgtw = 31 - __clz(TW);
-  int sh = 0;
-  for (; sh + 3 <= lg; sh += 3) dit_pass<3, T2>(a, lg, batch, sh, dir, tw, lgtw);
-  if (lg - sh == 2) dit_pass<2, T2>(a, lg, batch, sh, dir, tw, lgtw);
-  if (lg - sh == 1) dit_pass<1, T2>(a, lg, batch, sh, dir, tw, lgtw);
+  fft_core<false, T, T2>(a, n, batch, n, dir, tw, TW);
 }
 
-// Bluestein on `batch` contiguous sequences y[b n + t] of length n (n arbitrary),
+// Bluestein on `batch` sequences y (padded, ystride apart) of length n (n arbitrary),
 // in place: y_p <- sum_{t<n} y_t e^{+2 pi i t p / n}. With tp = (t^2 + p^2 - (p-t)^2)/2
-// the DFT is a chirp, a circular convolution of length M >= 2n - 1 (done by two
-// power-of-two FFTs against the tabulated spectrum bh = DFT_M(conj chirp) / M)
-// and a chirp. work holds batch * M entries.
+// the DFT is a chirp, a circular convolution of length M >= 2n - 1 (two power-of-two
+// FFTs against the tabulated spectrum bh = DFT_M(conj chirp) / M) and a chirp.
+// work: batch padded arrays of length M, wstride apart. Each pass writes the next
+// transform's input in bit-reversed order.
 template <typename T, typename T2>
-__device__ void bluestein_batch(T2 *y, int n, int M, int batch, T2 *work, const T2 *__restrict__ bh,
-                                const T2 *__restrict__ chirp, const T2 *__restrict__ tw, int TW) {
+__device__ void bluestein_batch(T2 *y, int n, int ystride, int M, int batch, T2 *work, int wstride,
+                                const T2 *__restrict__ bh, const T2 *__restrict__ chirp,
+                                const T2 *__restrict__ tw, int TW) {
   const int nth = blockDim.x, tid = threadIdx.x;
+  const int lgM = 31 - __clz(M);
   for (int t = tid; t < M; t += nth) {
+    const int d = pidx(brev_bits(t, lgM));
     if (t < n) {
       const T2 w = chirp[t];  // e^{i pi t^2 / n}
-      for (int b = 0; b < batch; ++b) work[b * M + t] = cmul(y[b * n + t], w);
+      for (int b = 0; b < batch; ++b) work[b * wstride + d] = cmul(y[b * ystride + pidx(t)], w);
     } else {
       T2 z;
       z.x = (T)0;
       z.y = (T)0;
-      for (int b = 0; b < batch; ++b) work[b * M + t] = z;
+      for (int b = 0; b < batch; ++b) work[b * wstride + d] = z;
     }
   }
   __syncthreads();
-  fft_pow2<T2>(work, M, batch, -1, tw, TW);
+  fft_core<true, T, T2>(work, M, batch, wstride, -1, tw, TW);
+  // multiply by the spectrum, writing bit-reversed for the inverse transform
   for (int k = tid; k < M; k += nth) {
-    const T2 h = bh[k];
-    for (int b = 0; b < batch; ++b) work[b * M + k] = cmul(work[b * M + k], h);
+    const int r = brev_bits(k, lgM);
+    if (k > r) continue;
+    const T2 hk = bh[k], hr = bh[r];
+    for (int b = 0; b < batch; ++b) {
+      T2 *w = work + b * wstride;
+      const T2 xk = w[pidx(k)], xr = w[pidx(r)];
+      w[pidx(r)] = cmul(xk, hk);
+      w[pidx(k)] = cmul(xr, hr);
+    }
   }
   __syncthreads();
-  fft_pow2<T2>(work, M, batch, +1, tw, TW);
+  fft_core<true, T, T2>(work, M, batch, wstride, +1, tw, TW);
   for (int p = tid; p < n; p += nth) {
     const T2 w = chirp[p];
-    for (int b = 0; b < batch; ++b) y[b * n + p] = cmul(work[b * M + p], w);
+    for (int b = 0; b < batch; ++b) y[b * ystride + pidx(p)] = cmul(work[b * wstride + pidx(p)], w);
   }
   __syncthreads();
 }

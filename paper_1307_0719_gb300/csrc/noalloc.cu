@@ -30,7 +30,7 @@ DevState g_dev[kMaxDev];
 // host staging for the tables, sized for the largest supported plan
 double h_z[kMaxRings], h_sint[kMaxRings], h_theta[kMaxRings], h_phi0[kMaxRings], h_lsh[kMaxRings],
     h_lch[kMaxRings], h_dls[kMaxRings * kK], h_dlc[kMaxRings * kK];
-int h_nphi[kMaxRings], h_inorth[kMaxRings];
+int h_nphi[kMaxRings], h_inorth[kMaxRings], h_fft_order[kMaxRings];
 long long h_first[kMaxRings];
 double h_lnorm0[TL_NOALLOC_MAX_LMAX + 1];
 long long h_off[TL_NOALLOC_MAX_NSIDE + 1];
@@ -76,6 +76,8 @@ tl_status setup(DevState &st, int nside, int lmax, int precision) {
   int maxm = 0;
   const long long tot = tl::host_bluestein_layout(nside, h_off, h_ml, &maxm);
   p.blue_maxm = maxm;
+  p.fft_ngroups = tl::host_fft_groups(nside, p.nrings, h_nphi, h_ml, p.fft_groups, h_fft_order);
+  if (p.fft_ngroups < 0) return TL_ERR_ARG;
   const int TW = tl::host_twiddle_len(nside, maxm);
   p.tw_len = TW;
   tl::host_twiddles(TW, h_tw);
@@ -95,6 +97,7 @@ tl_status setup(DevState &st, int nside, int lmax, int precision) {
       {(void **)&p.ring.first, h_first, 8 * nr},  {(void **)&p.lnorm0, h_lnorm0, 8 * (size_t)(lmax + 1)},
       {(void **)&p.blue.offset, h_off, 8 * (size_t)(nside + 1)},
       {(void **)&p.blue.mlen, h_ml, 4 * (size_t)(nside + 1)},
+      {(void **)&p.fft_rings, h_fft_order, 4 * nr},
       {(void **)&p.twiddle, precision == TL_FP64 ? (const void *)h_tw : (const void *)h_tw32,
        (size_t)(precision == TL_FP64 ? 8 : 4) * TW},
   };

@@ -79,7 +79,8 @@ static void free_plan(tl_plan *p) {
                   p->rec_QU,
                   p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->adj_dbar, p->adj_ga, p->stage_alm,
                   p->stage_out,
-                  p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2, p->dev_err};
+                  p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2, p->dev_err,
+                  p->fft_rings};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   if (p->timing)
@@ -120,6 +121,14 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   TRY_CUDA(upload(&p->blue.mlen, ml, B));
   const size_t e2 = 2 * (size_t)p->elem;
   TRY_CUDA(dalloc(&p->blue.spec, e2 * (size_t)(tot > 0 ? tot : 1), B));
+
+  // ring-FFT launch groups: belt, caps by Bluestein length, power-of-two caps
+  {
+    std::vector<int> order(p->nrings);
+    p->fft_ngroups = host_fft_groups(nside, p->nrings, h.nphi.data(), ml.data(), p->fft_groups, order.data());
+    if (p->fft_ngroups < 0) return TL_ERR_UNSUPPORTED;
+    TRY_CUDA(upload(&p->fft_rings, order, B));
+  }
 
   // twiddles e^{-2 pi i k / TW}, k < TW/2, for every power-of-two length used
   const int TW = host_twiddle_len(nside, maxm);

@@ -81,10 +81,10 @@ template <typename T>
 __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, int mmax, int nrings, PlaneSet ps,
                                                       int plane_len, JobList jobs, BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
-                                                      int bbatch, double invL_d) {
+                                                      int bbatch, double invL_d, const int *__restrict__ rings) {
   typedef typename RealTraits<T>::T2 T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int r = blockIdx.x;
+  const int r = rings[blockIdx.x];
   const int pair = blockIdx.y;
   const int ja = 2 * pair, jb = 2 * pair + 1;
   const bool hasb = jb < jobs.n;
@@ -94,8 +94,14 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   const long long first = rt.first[r];
   const T invL = (T)invL_d;
   const int nth = blockDim.x, tid = threadIdx.x;
-  T2 *Y = (T2 *)smem_raw;  // [4][ni], decimated order
-  T2 *W = Y + N;           // work area
+  // Y: the four decimated sub-sequences Z_{4 t1 + t2}, padded arrays SY apart, stored in
+  // bit-reversed order for power-of-two ni (the input order of the in-place FFT)
+  const int SY = padded_len(ni);
+  T2 *Y = (T2 *)smem_raw;
+  T2 *W = Y + 4 * SY;  // work area
+  const bool pw2 = (ni & (ni - 1)) == 0;
+  const int lgni = 31 - __clz(ni);
+  auto ydst = [&](int t) { return (t & 3) * SY + pidx(pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
   // half-pixel-shifted rings have phi0 = pi / (4 ni) = pi / N: e^{i m phi0} = e^{i t phi0} (-1)^q
   // for m = t + q N
   const bool shifted = rt.phi0[r] != 0.0;
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
 
   // ---- fold m modulo N into the Hermitian spectrum; thread handles classes t and N - t
   // (t = 0 .. N/2): C_t = (B_t + conj(B_{-t}))/2, C_{-t} = conj(C_t), Z = C^a + i C^b.
-  // Z_t is stored at Y[(t % 4) ni + t / 4] (decimated order).
+  // Z_t is stored at sub-sequence t % 4, element t / 4 (see ydst).
   const int ncls = half + 1;
   const int C = (ncls >= nth) ? 1 : nth / ncls;  // threads sharing one class pair
   {
@@ -161,8 +167,8 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
         z.y = ca.y + cb.x;
         zm.x = ca.x + cb.y;  // conj(C^a) + i conj(C^b)
         zm.y = -ca.y + cb.x;
-        Y[(tt & 3) * ni + (tt >> 2)] = z;
-        if (tt != 0 && tt != half) Y[(tm & 3) * ni + (tm >> 2)] = zm;
+        Y[ydst(tt)] = z;
+        if (tt != 0 && tt != half) Y[ydst(tm)] = zm;
       } else {
         W[2 * (c * ncls + tt)] = ca;
         W[2 * (c * ncls + tt) + 1] = cb;
@@ -183,24 +189,25 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
       z.y = ca.y + cb.x;
       zm.x = ca.x + cb.y;
       zm.y = -ca.y + cb.x;
-      Y[(tt & 3) * ni + (tt >> 2)] = z;
-      if (tt != 0 && tt != half) Y[(tm & 3) * ni + (tm >> 2)] = zm;
+      Y[ydst(tt)] = z;
+      if (tt != 0 && tt != half) Y[ydst(tm)] = zm;
     }
   }
   __syncthreads();
 
   // ---- four length-ni inverse DFTs
-  if ((ni & (ni - 1)) == 0) {
-    fft_pow2<T2>(Y, ni, 4, +1, tw, TW);
+  if (pw2) {
+    fft_core<true, T, T2>(Y, ni, 4, SY, +1, tw, TW);
   } else {
     const long long off = bt.offset[ni];
     const int M = bt.mlen[ni];
     const T2 *bh = (const T2 *)bt.spec + off;
     const T2 *ch = bh + M;  // the length's chirp follows its spectrum
+    const int SW = padded_len(M);
     if (bbatch >= 4) {
-      bluestein_batch<T, T2>(Y, ni, M, 4, W, bh, ch, tw, TW);
+      bluestein_batch<T, T2>(Y, ni, SY, M, 4, W, SW, bh, ch, tw, TW);
     } else {
-      for (int t2 = 0; t2 < 4; ++t2) bluestein_batch<T, T2>(Y + t2 * ni, ni, M, 1, W, bh, ch, tw, TW);
+      for (int t2 = 0; t2 < 4; ++t2) bluestein_batch<T, T2>(Y + t2 * SY, ni, SY, M, 1, W, SW, bh, ch, tw, TW);
     }
   }
 
@@ -214,11 +221,12 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
     w1.x = c;
     w1.y = s;
     const T2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+    const int q = pidx(p1);
     T2 y[4];
-    y[0] = Y[p1];
-    y[1] = cmul(Y[ni + p1], w1);
-    y[2] = cmul(Y[2 * ni + p1], w2);
-    y[3] = cmul(Y[3 * ni + p1], w3);
+    y[0] = Y[q];
+    y[1] = cmul(Y[SY + q], w1);
+    y[2] = cmul(Y[2 * SY + q], w2);
+    y[3] = cmul(Y[3 * SY + q], w3);
     const T2 a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
     const T2 b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
     T2 ib1;  // i * b1
@@ -256,17 +264,21 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
                                                           AdjJobList jobs, PlaneSetOut ps, int plane_len,
                                                           BluesteinTable bt,
                                                           const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
-                                                          int bbatch, double L_d) {
+                                                          int bbatch, double L_d, const int *__restrict__ rings) {
   typedef typename RealTraits<T>::T2 T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int r = blockIdx.x;
+  const int r = rings[blockIdx.x];
   const AdjJobDev J = jobs.job[blockIdx.y];
   const int N = rt.nphi[r];
   const int ni = N >> 2;
   const long long first = rt.first[r];
   const int nth = blockDim.x, tid = threadIdx.x;
-  T2 *Y = (T2 *)smem_raw;
-  T2 *W = Y + N;
+  const int SY = padded_len(ni);
+  T2 *Y = (T2 *)smem_raw;  // four padded sub-sequences (see the forward kernel)
+  T2 *W = Y + 4 * SY;
+  const bool pw2 = (ni & (ni - 1)) == 0;
+  const int lgni = 31 - __clz(ni);
+  auto ydst = [&](int t) { return (t & 3) * SY + pidx(pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
   const bool shifted = rt.phi0[r] != 0.0;  // phi0 = pi / N
   const T invL = (T)(1.0 / L_d);
   const T inv_s = (T)(1.0 / rt.sint[r]);
@@ -305,20 +317,21 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
       T2 z;
       z.x = ga[first + p];
       z.y = hasb ? -gb[first + p] : (T)0;
-      Y[(p & 3) * ni + (p >> 2)] = z;
+      Y[ydst(p)] = z;
     }
     __syncthreads();
-    if ((ni & (ni - 1)) == 0) {
-      fft_pow2<T2>(Y, ni, 4, +1, tw, TW);
+    if (pw2) {
+      fft_core<true, T, T2>(Y, ni, 4, SY, +1, tw, TW);
     } else {
       const long long off = bt.offset[ni];
       const int M = bt.mlen[ni];
       const T2 *bh = (const T2 *)bt.spec + off;
       const T2 *ch = bh + M;
+      const int SW = padded_len(M);
       if (bbatch >= 4) {
-        bluestein_batch<T, T2>(Y, ni, M, 4, W, bh, ch, tw, TW);
+        bluestein_batch<T, T2>(Y, ni, SY, M, 4, W, SW, bh, ch, tw, TW);
       } else {
-        for (int t2 = 0; t2 < 4; ++t2) bluestein_batch<T, T2>(Y + t2 * ni, ni, M, 1, W, bh, ch, tw, TW);
+        for (int t2 = 0; t2 < 4; ++t2) bluestein_batch<T, T2>(Y + t2 * SY, ni, SY, M, 1, W, SW, bh, ch, tw, TW);
       }
     }
     // radix-4 pass in place (slots p1 + ni t2 are read and written by one thread), then conj
@@ -329,11 +342,12 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
       w1.x = c;
       w1.y = s;
       const T2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+      const int q = pidx(p1);
       T2 y[4];
-      y[0] = Y[p1];
-      y[1] = cmul(Y[ni + p1], w1);
-      y[2] = cmul(Y[2 * ni + p1], w2);
-      y[3] = cmul(Y[3 * ni + p1], w3);
+      y[0] = Y[q];
+      y[1] = cmul(Y[SY + q], w1);
+      y[2] = cmul(Y[2 * SY + q], w2);
+      y[3] = cmul(Y[3 * SY + q], w3);
       const T2 a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
       const T2 b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
       T2 ib1;
@@ -345,17 +359,17 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
       X1.y = -X1.y;
       X2.y = -X2.y;
       X3.y = -X3.y;
-      Y[p1] = X0;
-      Y[p1 + ni] = X1;
-      Y[p1 + 2 * ni] = X2;
-      Y[p1 + 3 * ni] = X3;
+      Y[q] = X0;
+      Y[SY + q] = X1;
+      Y[2 * SY + q] = X2;
+      Y[3 * SY + q] = X3;
     }
     __syncthreads();
     // split the packed spectra and accumulate the plane's row
     for (int m = tid; m <= mmax; m += nth) {
       const int t = m % N;
       const int tm = (N - t) % N;
-      const T2 zt = Y[t], zm = Y[tm];
+      const T2 zt = Y[(t / ni) * SY + pidx(t % ni)], zm = Y[(tm / ni) * SY + pidx(tm % ni)];
       // X^a = (Z_t + conj Z_{N-t})/2, X^b = (Z_t - conj Z_{N-t})/(2i)
       T2 xa, xb;
       xa.x = (T)0.5 * (zt.x + zm.x);
@@ -441,7 +455,7 @@ __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const l
     w[k] = v;
   }
   __syncthreads();
-  fft_pow2<double2>(w, M, 1, -1, tw, TW);
+  fft_pow2<double, double2>(w, M, 1, -1, tw, TW);
   typedef typename RealTraits<T>::T2 T2;
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
     T2 v;
@@ -463,23 +477,41 @@ __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const l
 
 // ---------------------------------------------------------------------------
 
-// Shared memory of the ring FFT: the ring (<= 4 nside entries) plus a work area
-// for the folding partial sums (2 x 512) and Bluestein: four sub-transforms at
-// once when that fits in 227 KB, else one at a time.
-static size_t ringfft_smem_for(const tl_plan *p, int batch) {
+// Shared memory of a ring-FFT launch: the ring (4 ni entries) plus a work area for
+// the folding partial sums (2 x 512, only when a ring has fewer than 512 classes)
+// and, for Bluestein lengths, `batch` sub-transforms of length M.
+static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch) {
   const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
-  size_t wl = (size_t)batch * (size_t)p->blue_maxm;
+  const size_t fold = (2 * g.ni_min + 1 < 512) ? 1024 : 0;
+  size_t wl = g.M ? (size_t)batch * (size_t)padded_len(g.M) : 0;
+  if (wl < fold) wl = fold;
+  return e2 * ((size_t)4 * padded_len(g.ni_max) + wl);
+}
+// Four sub-transforms at once when two CTAs still fit on an SM (or when asked to and
+// one fits); one at a time otherwise.
+static int group_batch(const tl_plan *p, const FftGroup &g) {
+  if (g.M == 0 || p->fft_batch == 1) return 1;
+  const size_t s4 = group_smem(p, g, 4);
+  if (p->fft_batch == 4) return s4 <= 227 * 1024 ? 4 : 1;
+  return s4 <= 113 * 1024 ? 4 : 1;
+}
+// Upper bound over all rings (plan feasibility check): batch 1.
+size_t ringfft_smem_bytes(const tl_plan *p) {
+  const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
+  size_t wl = (size_t)padded_len(p->blue_maxm);
   if (wl < 1024) wl = 1024;
-  return e2 * ((size_t)4 * p->nside + wl);
+  return e2 * ((size_t)4 * padded_len(p->nside) + wl);
 }
-static int ringfft_batch(const tl_plan *p) {
-  if (p->fft_batch == 1) return 1;
-  const bool fits4 = ringfft_smem_for(p, 4) <= 227 * 1024;
-  if (p->fft_batch == 4) return fits4 ? 4 : 1;
-  // default: batch only while two blocks still fit on an SM
-  return ringfft_smem_for(p, 4) <= 113 * 1024 ? 4 : 1;
+
+template <typename K>
+static cudaError_t set_group_smem(const tl_plan *p, K kernel) {
+  size_t mx = 0;
+  for (int i = 0; i < p->fft_ngroups; ++i) {
+    const size_t sm = group_smem(p, p->fft_groups[i], group_batch(p, p->fft_groups[i]));
+    if (sm > mx) mx = sm;
+  }
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
-size_t ringfft_smem_bytes(const tl_plan *p) { return ringfft_smem_for(p, ringfft_batch(p)); }
 
 template <typename T>
 static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const MapJob *jobs, int njobs,
@@ -498,13 +530,16 @@ static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const 
   PlaneSet ps;
   for (int i = 0; i < 4; ++i) ps.base[i] = planes[i];
   const int plane_len = p->nrings * (p->mmax + 1);
-  const int batch = ringfft_batch(p);
-  const size_t smem = ringfft_smem_for(p, batch);
-  TL_CUDA_TRY(cudaFuncSetAttribute(ringfft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(p->nrings, (njobs + 1) / 2);
-  ringfft_kernel<T><<<grid, 512, smem, s>>>(p->ring, p->nside, p->mmax, p->nrings, ps, plane_len, jl, p->blue,
-                                            (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch,
-                                            1.0 / (double)(p->lmax + 1));
+  TL_CUDA_TRY(set_group_smem(p, ringfft_kernel<T>));
+  for (int gi = 0; gi < p->fft_ngroups; ++gi) {
+    const FftGroup &g = p->fft_groups[gi];
+    const int batch = group_batch(p, g);
+    dim3 grid(g.count, (njobs + 1) / 2);
+    ringfft_kernel<T><<<grid, 512, group_smem(p, g, batch), s>>>(
+        p->ring, p->nside, p->mmax, p->nrings, ps, plane_len, jl, p->blue,
+        (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, 1.0 / (double)(p->lmax + 1),
+        p->fft_rings + g.first);
+  }
   return cudaGetLastError();
 }
 
@@ -536,13 +571,16 @@ static cudaError_t ringfft_adj_t(const tl_plan *p, void *const *planes, const Ad
   PlaneSetOut ps;
   for (int i = 0; i < 4; ++i) ps.base[i] = planes[i];
   const int plane_len = p->nrings * (p->mmax + 1);
-  const int batch = ringfft_batch(p);
-  const size_t smem = ringfft_smem_for(p, batch);
-  TL_CUDA_TRY(cudaFuncSetAttribute(ringfft_adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(p->nrings, njobs);
-  ringfft_adj_kernel<T><<<grid, 512, smem, s>>>(p->ring, p->mmax, p->npix, p->nmaps, jl, ps, plane_len, p->blue,
-                                                (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch,
-                                                (double)(p->lmax + 1));
+  TL_CUDA_TRY(set_group_smem(p, ringfft_adj_kernel<T>));
+  for (int gi = 0; gi < p->fft_ngroups; ++gi) {
+    const FftGroup &g = p->fft_groups[gi];
+    const int batch = group_batch(p, g);
+    dim3 grid(g.count, njobs);
+    ringfft_adj_kernel<T><<<grid, 512, group_smem(p, g, batch), s>>>(
+        p->ring, p->mmax, p->npix, p->nmaps, jl, ps, plane_len, p->blue,
+        (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (double)(p->lmax + 1),
+        p->fft_rings + g.first);
+  }
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // Host-side geometry and transform tables (written into caller-provided arrays,
 // no allocation). Used by plan creation.
+#include <algorithm>
 #include <math.h>
 
 #include "common.cuh"
@@ -119,6 +120,37 @@ long long host_bluestein_layout(int nside, long long *off, int *ml, int *maxm) {
   }
   *maxm = mx;
   return tot;
+}
+
+// Rings of each ring-FFT launch: the equatorial belt, then the caps by Bluestein
+// length M (largest first), then the power-of-two caps; each group's rings are
+// ordered by decreasing length. No allocation.
+int host_fft_groups(int nside, int nrings, const int *nphi, const int *ml, FftGroup *groups, int *order) {
+  int ng = 0, n = 0;
+  auto key_of = [&](int r) {
+    const int ni = nphi[r] / 4;
+    return (ni == nside) ? -1 : ((ni & (ni - 1)) == 0 ? 0 : ml[ni]);
+  };
+  auto add = [&](int key) {
+    const int first = n;
+    for (int r = 0; r < nrings; ++r)
+      if (key_of(r) == key) order[n++] = r;
+    if (n == first) return true;
+    std::sort(order + first, order + n, [&](int a, int b) { return nphi[a] != nphi[b] ? nphi[a] > nphi[b] : a < b; });
+    if (ng == TL_MAX_FFT_GROUPS) return false;
+    groups[ng].first = first;
+    groups[ng].count = n - first;
+    groups[ng].ni_max = nphi[order[first]] / 4;
+    groups[ng].ni_min = nphi[order[n - 1]] / 4;
+    groups[ng].M = key > 0 ? key : 0;
+    ++ng;
+    return true;
+  };
+  if (!add(-1)) return -1;
+  for (int M = 1 << 30; M >= 2; M >>= 1)
+    if (M <= 4 * nside && !add(M)) return -1;
+  if (!add(0)) return -1;
+  return n == nrings ? ng : -1;
 }
 
 int host_twiddle_len(int nside, int maxm) {
