@@ -249,18 +249,17 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = world * nb * args.steps / (ms / 1e3)
     stages = stage_sum / args.steps
-    names = ["prep_T", "legendre_T", "deflection_fft", "prep_QU", "legendre_QU", "ringfft", "gather"]
+    names = ["prep_T", "legendre_T", "deflection_fft", "prep_QU", "legendre_QU", "ringfft", "gather",
+             "fft_total", "gather_total"]
     stage_ms = {n: float(v) for n, v in zip(names, stages)}
 
-    # roofline of the dominant kernel (stage times are per Legendre launch, which on
-    # tensor-core plans covers up to eight realisations; see the per-step stage sums)
+    # rooflines per stage: the Legendre kernels against the FP32 pipe (tensor-core forms
+    # count the recurrence, the contraction runs on the tensor cores), the ring FFTs and
+    # the gather against HBM (algorithmic bytes: every input read once, every output
+    # written once). The dominant stage (largest time per step) is `roofline`.
     tc = args.form != "fp32"
     part = "recurrence" if tc else "all"
     nr_launch = min(nb, 8) if tc else 1
-    flops_qu = legendre_flops_per_launch(w.nside, w.lmax, w.order, 2, part=part)
-    flops_t = legendre_flops_per_launch(w.nside, w.lmax, w.order, 0, part=part)
-    tflops_qu = legendre_flops_per_launch(w.nside, w.lmax, w.order, 2, part="contraction", nreal=nr_launch)
-    dom = max(("legendre_QU", "legendre_T", "ringfft", "gather"), key=lambda k: stage_ms[k])
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         with open(PEAKS_FILE) as f:
@@ -268,20 +267,38 @@ def run_ours(args):
     clocks = clk.summary()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    if dom in ("legendre_QU", "legendre_T"):
-        fl = flops_qu if dom == "legendre_QU" else flops_t
-        achieved = fl / (stage_ms[dom] / 1e3) / 1e12
-        kname = f"legendre_spin{'2' if dom == 'legendre_QU' else '0'}_{'tc' if tc else 'kernel'}<{w.order}>"
-        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
-                "counts": "recurrence only; the contraction runs on the tensor cores" if tc else
-                          "recurrence + contraction"}
-        if tc and dom == "legendre_QU":
-            roof["tensor_tflops_contraction"] = tflops_qu / (stage_ms[dom] / 1e3) / 1e12
-    else:
-        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": None, "traffic": None}
+    hbm = peaks.get("hbm_gbs")
+    # stage times are those of the step's last tl_lens_batch chunk: one Legendre launch of
+    # up to 8 realisations on tensor cores, one realisation otherwise
+    launches = 1
+    nchunk = min(nb, 8) if tc else 1
+    rl = {}
+    for st, spin in (("legendre_QU", 2), ("legendre_T", 0)):
+        fl = legendre_flops_per_launch(w.nside, w.lmax, w.order, spin, part=part) * launches
+        ach = fl / (stage_ms[st] / 1e3) / 1e12
+        e = {"kernel": f"legendre_spin{spin}_{'umma' if tc else 'kernel'}<{w.order}>", "bound": "alu",
+             "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
+             "counts": "recurrence only (contraction on the tensor cores)" if tc else "recurrence + contraction"}
+        if tc:
+            cf = legendre_flops_per_launch(w.nside, w.lmax, w.order, spin, part="contraction", nreal=nr_launch)
+            e["tensor_tflops_contraction"] = cf / (stage_ms[st] / 1e3) / 1e12
+        rl[st] = e
+    nplanes = 3 * (w.order + 1) + 2  # D7 planes read once: T, Q, U (j <= n) and phi (j <= 1)
+    nmaps = 3 * (w.order + 1) * (w.order + 2) // 2 + 2  # derivative maps and the deflection
+    nrings = 4 * w.nside - 1
+    npix = 12 * w.nside * w.nside
+    fft_bytes = nchunk * (nplanes * nrings * (w.lmax + 1) * 8 + nmaps * npix * 4)
+    gat_bytes = nchunk * npix * (3 * (w.order + 1) * (w.order + 2) // 2 * 4 + 2 * 4 + 3 * 4)
+    for st, byt, kname in (("fft_total", fft_bytes, "ringfft_kernel<float> (all ring groups)"),
+                           ("gather_total", gat_bytes, f"gather_kernel<float, {w.order}, 1>")):
+        ach = byt / (stage_ms[st] / 1e3) / 1e9 if stage_ms.get(st) else None
+        rl[st] = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                  "frac": (ach / hbm) if (ach and hbm) else None, "traffic": None,
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
+                  "algorithmic_bytes": byt}
+    dom = max(rl, key=lambda k: stage_ms.get(k, 0.0))
+    roof = dict(rl[dom], stage=dom)
 
     # end to end through the public API: every step copies its coefficients in from pinned
     # host memory, lenses them (Plan.lens_batch) and copies the maps back, inside the timed region
@@ -377,7 +394,7 @@ def run_ours(args):
                        + "; FP64 seeds and rescaling; double pixel lookup", "realisations_per_step": nb,
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (alm 537 MB, "
                        "derivative maps 9 GB per step)"},
-            "stage_ms": stage_ms, "roofline": roof, "clocks": clocks,
+            "stage_ms": stage_ms, "roofline": roof, "roofline_stages": rl, "clocks": clocks,
             "gpu_launches": args.steps * ((8 * nb) if not tc else (5 + 5 * nb)), "e2e": e2e, "fp64": fp64, "err_vs_oracle": err,
             "cpu_baseline": cpu,
         }

@@ -256,7 +256,10 @@ const char *tl_status_string(tl_status status);
  * variable TAYLENS_TIMING=1 was set at plan creation (otherwise returns 0).
  * tl_lens stage order: prep_T (T and phi coefficients), legendre_T (spin-0 stage,
  * with phi's j <= 1 planes), deflection_fft, prep_QU, legendre_QU, ringfft (all
- * T/Q/U maps), gather. tl_lens_adjoint: forward (recomputed derivative maps and
+ * T/Q/U maps), gather, then two totals: all ring FFTs and all gathers of the call
+ * (on tensor-core plans the ringfft stage spans every realisation's ring FFTs and
+ * gathers, and the deflection_fft and gather stages are empty; the totals
+ * separate them). tl_lens_adjoint: forward (recomputed derivative maps and
  * deflection), gather (transposed), ringfft (transposed), legendre_T (transposed,
  * with phi), legendre_QU (transposed), finish. Synchronises on the last event.
  * Returns the number of stages written (<= n). */

@@ -168,8 +168,8 @@ class Plan:
         return out
 
     def last_stage_ms(self):
-        buf = (ctypes.c_float * 8)()
-        n = _lib.lib().tl_last_stage_ms(self._h, buf, 8)
+        buf = (ctypes.c_float * 16)()
+        n = _lib.lib().tl_last_stage_ms(self._h, buf, 16)
         return list(buf[:n])
 
 

@@ -22,6 +22,8 @@ struct RingTable {
   double *sint;    // sin(theta)
   double *theta;   // colatitude
   double *phi0;    // longitude of the ring's first pixel
+  double *dphi;    // 2 pi / nphi: longitude step between the ring's pixels
+  double *omza;    // 1 - |cos(theta)|, formed without cancellation
   double *log2_sh; // log2 sin(theta/2)
   double *log2_ch; // log2 cos(theta/2)
   double *dls;     // [ring][k], k = 1..TL_MAX_NDER+1: d^k/dtheta^k ln sin(theta/2)
@@ -91,6 +93,10 @@ struct tl_plan {
   cudaEvent_t ev[8];
   float stage_ms[7];
   int nstage;
+  // per realisation of a tensor-core chunk: before its ring FFTs, after them (before
+  // the gather), after the gather; summed into the FFT and gather totals
+  cudaEvent_t evr[3 * 8];
+  int nevr;
 };
 
 namespace tl {
@@ -155,7 +161,7 @@ cudaError_t launch_gather(const tl_plan *p, const void *alpha, const void *d3, v
 // rings: 4 nside - 1 entries (dls, dlc: (4 nside - 1) * (TL_MAX_NDER + 1)),
 // lnorm0: lmax + 1, Bluestein off/ml: nside + 1, twiddles: TW doubles
 struct RingHostView {
-  double *z, *sint, *theta, *phi0, *lsh, *lch, *dls, *dlc;
+  double *z, *sint, *theta, *phi0, *lsh, *lch, *dls, *dlc, *dphi, *omza;
   int *nphi, *inorth;
   long long *first;
 };

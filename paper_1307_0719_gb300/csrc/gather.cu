@@ -47,7 +47,7 @@ __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, 
   const float dphp = atan2f(Y, X);                                        // phi' - phi_p
   // pixel lookup in double on the accurate increments
   const double z2 = z + (double)dz;
-  const double omz_p = s * s / (1.0 + fabs(z));
+  const double omz_p = rt.omza[ring];  // 1 - |z| of the pixel's ring
   const double omz2 = omz_p - (z >= 0.0 ? (double)dz : -(double)dz);
   double phi2 = phi + (double)dphp;
   if (phi2 >= 2.0 * kPiD) phi2 -= 2.0 * kPiD;

@@ -16,12 +16,13 @@ struct PixLoc {
   int idx;   // index within the ring
 };
 
-// ring and in-ring index of a RING-scheme pixel
+// ring and in-ring index of a RING-scheme pixel (the ring from a float square-root
+// estimate, off by at most one, then corrected in integers)
 __device__ __forceinline__ PixLoc pix2loc(long long p, int nside, long long npix) {
   const long long ncap = 2LL * nside * (nside - 1);
   PixLoc L;
   if (p < ncap) {
-    long long i = (long long)((1.0 + sqrt(1.0 + 2.0 * (double)p)) * 0.5);
+    long long i = (long long)((1.0f + sqrtf(1.0f + 2.0f * (float)p)) * 0.5f);
     if (2 * i * (i - 1) > p) --i;
     if (2 * (i + 1) * i <= p) ++i;
     L.ring = (int)i - 1;
@@ -33,7 +34,7 @@ __device__ __forceinline__ PixLoc pix2loc(long long p, int nside, long long npix
     L.idx = (int)(q - (i - nside) * 4LL * nside);
   } else {
     long long q = npix - 1 - p;
-    long long i = (long long)((1.0 + sqrt(1.0 + 2.0 * (double)q)) * 0.5);
+    long long i = (long long)((1.0f + sqrtf(1.0f + 2.0f * (float)q)) * 0.5f);
     if (2 * i * (i - 1) > q) --i;
     if (2 * (i + 1) * i <= q) ++i;
     L.ring = (int)(4LL * nside - i) - 1;
@@ -86,7 +87,7 @@ __device__ __forceinline__ PixLoc ang2loc(double z, double omz, double phi, int 
 }
 
 __device__ __forceinline__ double ring_phi(const RingTable &rt, int ring, int idx) {
-  return rt.phi0[ring] + 2.0 * kPiD * (double)idx / (double)rt.nphi[ring];
+  return fma((double)idx, rt.dphi[ring], rt.phi0[ring]);
 }
 
 struct Geo {

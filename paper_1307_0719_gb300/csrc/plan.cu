@@ -40,7 +40,7 @@ extern "C" const char *tl_status_string(tl_status s) {
 // host tables (tables.cu) gathered into vectors
 
 struct HostRings {
-  std::vector<double> z, sint, theta, phi0, lsh, lch, dls, dlc;
+  std::vector<double> z, sint, theta, phi0, lsh, lch, dls, dlc, dphi, omza;
   std::vector<int> nphi, inorth;
   std::vector<long long> first;
 };
@@ -49,9 +49,11 @@ static void build_rings(int N, HostRings &h) {
   const size_t nr = 4 * (size_t)N - 1, K = TL_MAX_NDER + 1;
   h.z.resize(nr); h.sint.resize(nr); h.theta.resize(nr); h.phi0.resize(nr);
   h.lsh.resize(nr); h.lch.resize(nr); h.dls.resize(nr * K); h.dlc.resize(nr * K);
+  h.dphi.resize(nr); h.omza.resize(nr);
   h.nphi.resize(nr); h.inorth.resize(nr); h.first.resize(nr);
   RingHostView v{h.z.data(), h.sint.data(), h.theta.data(), h.phi0.data(), h.lsh.data(), h.lch.data(),
-                 h.dls.data(), h.dlc.data(), h.nphi.data(), h.inorth.data(), h.first.data()};
+                 h.dls.data(), h.dlc.data(), h.dphi.data(), h.omza.data(), h.nphi.data(), h.inorth.data(),
+                 h.first.data()};
   host_ring_tables(N, v);
 }
 
@@ -73,7 +75,8 @@ static cudaError_t dalloc(void **p, size_t b, size_t *bytes) {
 
 static void free_plan(tl_plan *p) {
   if (!p) return;
-  void *ptrs[] = {p->ring.z, p->ring.sint, p->ring.theta, p->ring.phi0, p->ring.log2_sh, p->ring.log2_ch,
+  void *ptrs[] = {p->ring.z, p->ring.sint, p->ring.theta, p->ring.phi0, p->ring.dphi, p->ring.omza,
+                  p->ring.log2_sh, p->ring.log2_ch,
                   p->ring.dls, p->ring.dlc, p->ring.nphi, p->ring.inorth, p->ring.first, p->blue.spec,
                   p->blue.offset, p->blue.mlen, p->lnorm0, p->twiddle, p->tab0, p->tab2, p->rec_T, p->rec_P,
                   p->rec_QU,
@@ -86,6 +89,9 @@ static void free_plan(tl_plan *p) {
   if (p->timing)
     for (int i = 0; i < 8; ++i)
       if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  if (p->timing)
+    for (int i = 0; i < 3 * 8; ++i)
+      if (p->evr[i]) cudaEventDestroy(p->evr[i]);
   free(p);
 }
 
@@ -105,6 +111,7 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   TRY_CUDA(upload(&p->ring.theta, h.theta, B)); TRY_CUDA(upload(&p->ring.phi0, h.phi0, B));
   TRY_CUDA(upload(&p->ring.log2_sh, h.lsh, B)); TRY_CUDA(upload(&p->ring.log2_ch, h.lch, B));
   TRY_CUDA(upload(&p->ring.dls, h.dls, B)); TRY_CUDA(upload(&p->ring.dlc, h.dlc, B));
+  TRY_CUDA(upload(&p->ring.dphi, h.dphi, B)); TRY_CUDA(upload(&p->ring.omza, h.omza, B));
   TRY_CUDA(upload(&p->ring.nphi, h.nphi, B)); TRY_CUDA(upload(&p->ring.inorth, h.inorth, B));
   TRY_CUDA(upload(&p->ring.first, h.first, B));
 
@@ -213,6 +220,8 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   p->timing = (env && env[0] == '1') ? 1 : 0;
   if (p->timing)
     for (int i = 0; i < 8; ++i) TRY_CUDA(cudaEventCreate(&p->ev[i]));
+  if (p->timing)
+    for (int i = 0; i < 3 * 8; ++i) TRY_CUDA(cudaEventCreate(&p->evr[i]));
   return TL_OK;
 }
 
@@ -376,7 +385,10 @@ tl_status lens_stage_after_legendre(tl_plan *p, int nreal, bool phi, void *const
   const size_t mapb = (size_t)p->elem * p->npix;
   const size_t t2 = 2 * (size_t)p->elem;
   void *ath = p->alpha, *aph = (char *)p->alpha + mapb;
+  p->nevr = 0;
   for (int r = 0; r < nreal; ++r) {
+      const bool tm = p->timing && r < 8;
+      if (tm) cudaEventRecord(p->evr[3 * r], s);
       const size_t off = (size_t)r * p->d7_rstride * t2, offp = (size_t)r * p->d7p_rstride * t2;
       const void *planes[4] = {(char *)p->d7_T + off, pol ? (char *)p->d7_Q + off : nullptr,
                                pol ? (char *)p->d7_U + off : nullptr, (char *)p->d7_P + offp};
@@ -389,7 +401,12 @@ tl_status lens_stage_after_legendre(tl_plan *p, int nreal, bool phi, void *const
       }
       tl_status st = lens_fft(p, planes, s);
       if (st != TL_OK) return st;
+      if (tm) cudaEventRecord(p->evr[3 * r + 1], s);
       TRY_CUDA(launch_gather(p, p->alpha, p->d3, To[r], pol ? Qo[r] : nullptr, pol ? Uo[r] : nullptr, s));
+      if (tm) {
+        cudaEventRecord(p->evr[3 * r + 2], s);
+        p->nevr = r + 1;
+      }
     }
   return TL_OK;
 }
@@ -658,5 +675,23 @@ extern "C" int tl_last_stage_ms(const tl_plan *p, float *ms, int n) {
   if (cudaEventSynchronize(q->ev[p->nstage]) != cudaSuccess) return 0;
   int k = 0;
   for (int i = 0; i < p->nstage && k < n; ++i, ++k) cudaEventElapsedTime(&ms[k], q->ev[i], q->ev[i + 1]);
+  if (p->nstage == 7 && k + 2 <= n) {
+    // ring FFTs and gathers of the call
+    float fft = 0.f, gat = 0.f;
+    if (p->batch > 1) {
+      for (int r = 0; r < p->nevr; ++r) {
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, q->evr[3 * r], q->evr[3 * r + 1]);
+        cudaEventElapsedTime(&b, q->evr[3 * r + 1], q->evr[3 * r + 2]);
+        fft += a;
+        gat += b;
+      }
+    } else {
+      fft = ms[2] + ms[5];
+      gat = ms[6];
+    }
+    ms[k++] = fft;
+    ms[k++] = gat;
+  }
   return k;
 }
