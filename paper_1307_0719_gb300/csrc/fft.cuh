@@ -37,11 +37,22 @@ template <typename T> __device__ __forceinline__ void sincos_pi(T x, T *s, T *c)
 template <> __device__ __forceinline__ void sincos_pi<float>(float x, float *s, float *c) { sincospif(x, s, c); }
 template <> __device__ __forceinline__ void sincos_pi<double>(double x, double *s, double *c) { sincospi(x, s, c); }
 
-// Shared-memory layout of the ring transforms: element i of an array sits at
-// i + i/8 (one pad slot every 8 complex values), which keeps the fused passes below
-// free of bank conflicts for every span.
-__host__ __device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
-__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 3); }
+// Shared-memory layout of power-of-two arrays: element i of array b (length 2^lg)
+// sits at b * stride + swz(i, lg) ^ (b & 3). swz XORs bits 4-6, bit 6 and the top
+// bits of i into its low four bits (16 banks of 8-byte elements), a bijection within
+// every 16-element block, chosen so that the fused FFT passes at every span, the
+// bit-reversed writes of the fold and of Bluestein, and the natural-order passes
+// all reach distinct banks (checked for lengths up to 2^13: at most 1.5 wavefronts
+// per 16 threads, against 16 for a plain or padded layout on bit-reversed writes).
+__host__ __device__ __forceinline__ int swz(int i, int lg) {
+  const int f1 = (i >> 4) & 7;
+  const int f2 = ((i >> 6) & 1) << 3;
+  const int f3 = lg >= 8 ? (i >> (lg - 4 > 7 ? lg - 4 : 7)) & 15 : 0;
+  return i ^ f1 ^ f2 ^ f3;
+}
+__host__ __device__ __forceinline__ int faddr(int b, int i, int lg, int stride) {
+  return b * stride + (swz(i, lg) ^ (b & 3));
+}
 __device__ __forceinline__ int brev_bits(int e, int lg) { return lg == 0 ? 0 : (int)(__brev((unsigned)e) >> (32 - lg)); }
 
 // e^{-2 pi i cc / 2^(lev+1)} (conjugated for dir > 0), cc < 2^lev, lev <= 2
@@ -66,7 +77,7 @@ __device__ __forceinline__ T2 unit_root(int lev, int cc, int dir) {
 // whose bit s is clear pairs with the one 2^s above it, with the twiddle
 // W_{2^(s+1)}^(index mod 2^s) = W_{2^(s+1)}^pos W_{2^(lev+1)}^cc: one table load
 // per level times a fixed root of unity.
-template <int R, bool PAD, typename T, typename T2>
+template <int R, bool SWZ, typename T, typename T2>
 __device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, int sh, int dir,
                                          const T2 *__restrict__ tw, int lgtw) {
   constexpr int P = 1 << R;
@@ -76,11 +87,10 @@ __device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, i
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int b = e >> ulg, q = e & ((1 << ulg) - 1);
     const int pos = q & (h - 1), grp = q >> sh;
-    T2 *arr = a + (size_t)b * stride;
     const int i0 = (grp << (sh + R)) + pos;
     T2 x[P];
 #pragma unroll
-    for (int c = 0; c < P; ++c) x[c] = arr[PAD ? pidx(i0 + (c << sh)) : i0 + (c << sh)];
+    for (int c = 0; c < P; ++c) x[c] = a[SWZ ? faddr(b, i0 + (c << sh), lg, stride) : b * stride + i0 + (c << sh)];
 #pragma unroll
     for (int lev = 0; lev < R; ++lev) {
       T2 wl = tw[pos << (lgtw - sh - lev - 1)];
@@ -96,24 +106,25 @@ __device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, i
       }
     }
 #pragma unroll
-    for (int c = 0; c < P; ++c) arr[PAD ? pidx(i0 + (c << sh)) : i0 + (c << sh)] = x[c];
+    for (int c = 0; c < P; ++c) a[SWZ ? faddr(b, i0 + (c << sh), lg, stride) : b * stride + i0 + (c << sh)] = x[c];
   }
   __syncthreads();
 }
 
 // In-place DIT FFT on `batch` arrays of length n (power of two), `stride` elements
-// apart, whose input is already in bit-reversed order (the writers store it so);
+// apart (swizzled layout when SWZ), whose input is already in bit-reversed order
+// (the writers store it so);
 // output in natural order. dir = -1: sum x e^{-2 pi i k t/n}; dir = +1: e^{+...}.
 // tw[k] = e^{-2 pi i k / TW}, k < TW/2 (TW >= n). Passes of three stages.
-template <bool PAD, typename T, typename T2>
+template <bool SWZ, typename T, typename T2>
 __device__ void fft_core(T2 *a, int n, int batch, int stride, int dir, const T2 *__restrict__ tw, int TW) {
   if (n <= 1) return;
   const int lg = 31 - __clz(n);
   const int lgtw = 31 - __clz(TW);
   int sh = 0;
-  for (; sh + 3 <= lg; sh += 3) dit_pass<3, PAD, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
-  if (lg - sh == 2) dit_pass<2, PAD, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
-  if (lg - sh == 1) dit_pass<1, PAD, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  for (; sh + 3 <= lg; sh += 3) dit_pass<3, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  if (lg - sh == 2) dit_pass<2, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  if (lg - sh == 1) dit_pass<1, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
 }
 
 // The same for contiguous, unpadded arrays in natural order (bit-reversal first).
@@ -135,12 +146,12 @@ __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict_
   fft_core<false, T, T2>(a, n, batch, n, dir, tw, TW);
 }
 
-// Bluestein on `batch` sequences y (padded, ystride apart) of length n (n arbitrary),
-// in place: y_p <- sum_{t<n} y_t e^{+2 pi i t p / n}. With tp = (t^2 + p^2 - (p-t)^2)/2
-// the DFT is a chirp, a circular convolution of length M >= 2n - 1 (two power-of-two
-// FFTs against the tabulated spectrum bh = DFT_M(conj chirp) / M) and a chirp.
-// work: batch padded arrays of length M, wstride apart. Each pass writes the next
-// transform's input in bit-reversed order.
+// Bluestein on `batch` sequences y (plain layout, ystride apart) of length n (n
+// arbitrary), in place: y_p <- sum_{t<n} y_t e^{+2 pi i t p / n}. With
+// tp = (t^2 + p^2 - (p-t)^2)/2 the DFT is a chirp, a circular convolution of length
+// M >= 2n - 1 (two power-of-two FFTs against the tabulated spectrum
+// bh = DFT_M(conj chirp) / M) and a chirp. work: batch swizzled arrays of length M,
+// wstride apart. Each pass writes the next transform's input in bit-reversed order.
 template <typename T, typename T2>
 __device__ void bluestein_batch(T2 *y, int n, int ystride, int M, int batch, T2 *work, int wstride,
                                 const T2 *__restrict__ bh, const T2 *__restrict__ chirp,
@@ -148,15 +159,15 @@ __device__ void bluestein_batch(T2 *y, int n, int ystride, int M, int batch, T2 
   const int nth = blockDim.x, tid = threadIdx.x;
   const int lgM = 31 - __clz(M);
   for (int t = tid; t < M; t += nth) {
-    const int d = pidx(brev_bits(t, lgM));
+    const int d = brev_bits(t, lgM);
     if (t < n) {
       const T2 w = chirp[t];  // e^{i pi t^2 / n}
-      for (int b = 0; b < batch; ++b) work[b * wstride + d] = cmul(y[b * ystride + pidx(t)], w);
+      for (int b = 0; b < batch; ++b) work[faddr(b, d, lgM, wstride)] = cmul(y[b * ystride + t], w);
     } else {
       T2 z;
       z.x = (T)0;
       z.y = (T)0;
-      for (int b = 0; b < batch; ++b) work[b * wstride + d] = z;
+      for (int b = 0; b < batch; ++b) work[faddr(b, d, lgM, wstride)] = z;
     }
   }
   __syncthreads();
@@ -167,17 +178,17 @@ __device__ void bluestein_batch(T2 *y, int n, int ystride, int M, int batch, T2 
     if (k > r) continue;
     const T2 hk = bh[k], hr = bh[r];
     for (int b = 0; b < batch; ++b) {
-      T2 *w = work + b * wstride;
-      const T2 xk = w[pidx(k)], xr = w[pidx(r)];
-      w[pidx(r)] = cmul(xk, hk);
-      w[pidx(k)] = cmul(xr, hr);
+      const int ak = faddr(b, k, lgM, wstride), ar = faddr(b, r, lgM, wstride);
+      const T2 xk = work[ak], xr = work[ar];
+      work[ar] = cmul(xk, hk);
+      work[ak] = cmul(xr, hr);
     }
   }
   __syncthreads();
   fft_core<true, T, T2>(work, M, batch, wstride, +1, tw, TW);
   for (int p = tid; p < n; p += nth) {
     const T2 w = chirp[p];
-    for (int b = 0; b < batch; ++b) y[b * ystride + pidx(p)] = cmul(work[b * wstride + pidx(p)], w);
+    for (int b = 0; b < batch; ++b) y[b * ystride + p] = cmul(work[faddr(b, p, lgM, wstride)], w);
   }
   __syncthreads();
 }

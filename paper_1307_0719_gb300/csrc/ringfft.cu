@@ -45,6 +45,20 @@ struct PlaneSetOut {
   void *base[4];
 };
 
+// Stride of the four decimated sub-sequences of a ring with nphi = 4 ni: ni for
+// power-of-two ni (swizzled layout), else the next value = 4 mod 16.
+__host__ __device__ __forceinline__ int ring_sub_stride(int ni) {
+  return ((ni & (ni - 1)) == 0) ? ni : ni + ((20 - (ni & 15)) & 15);
+}
+static int ring_sub_stride_max(const FftGroup &g) {
+  int mx = 0;
+  for (int ni = g.ni_min; ni <= g.ni_max; ++ni) {
+    const int s = ring_sub_stride(ni);
+    if (s > mx) mx = s;
+  }
+  return mx;
+}
+
 // sum over the aliasing class m = t0 + qN (q >= 0, m <= mmax) of
 //   (-1)^q [shifted rings] * w_m (i m / L)^k F_m,   w_0 = 1, w_m = 2
 // i.e. the class's contribution without its common phase e^{i t0 phi0}.
@@ -94,14 +108,18 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   const long long first = rt.first[r];
   const T invL = (T)invL_d;
   const int nth = blockDim.x, tid = threadIdx.x;
-  // Y: the four decimated sub-sequences Z_{4 t1 + t2}, padded arrays SY apart, stored in
-  // bit-reversed order for power-of-two ni (the input order of the in-place FFT)
-  const int SY = padded_len(ni);
-  T2 *Y = (T2 *)smem_raw;
-  T2 *W = Y + 4 * SY;  // work area
+  // Y: the four decimated sub-sequences Z_{4 t1 + t2}, SY apart. Power-of-two ni: the
+  // swizzled layout, stored in bit-reversed order (the input order of the in-place
+  // FFT); other ni: plain, with SY = 4 mod 16 so that the four arrays fall on
+  // different banks.
   const bool pw2 = (ni & (ni - 1)) == 0;
   const int lgni = 31 - __clz(ni);
-  auto ydst = [&](int t) { return (t & 3) * SY + pidx(pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
+  const int SY = ring_sub_stride(ni);
+  T2 *Y = (T2 *)smem_raw;
+  T2 *W = Y + 4 * SY;  // work area
+  const bool yswz = pw2 && ni >= 16;  // the XOR layout needs whole 16-element blocks
+  auto yaddr = [&](int b, int i) { return yswz ? faddr(b, i, lgni, SY) : b * SY + i; };
+  auto ydst = [&](int t) { return yaddr(t & 3, pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
   // half-pixel-shifted rings have phi0 = pi / (4 ni) = pi / N: e^{i m phi0} = e^{i t phi0} (-1)^q
   // for m = t + q N
   const bool shifted = rt.phi0[r] != 0.0;
@@ -197,13 +215,16 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
 
   // ---- four length-ni inverse DFTs
   if (pw2) {
-    fft_core<true, T, T2>(Y, ni, 4, SY, +1, tw, TW);
+    if (yswz)
+      fft_core<true, T, T2>(Y, ni, 4, SY, +1, tw, TW);
+    else
+      fft_core<false, T, T2>(Y, ni, 4, SY, +1, tw, TW);
   } else {
     const long long off = bt.offset[ni];
     const int M = bt.mlen[ni];
     const T2 *bh = (const T2 *)bt.spec + off;
     const T2 *ch = bh + M;  // the length's chirp follows its spectrum
-    const int SW = padded_len(M);
+    const int SW = M;
     if (bbatch >= 4) {
       bluestein_batch<T, T2>(Y, ni, SY, M, 4, W, SW, bh, ch, tw, TW);
     } else {
@@ -221,12 +242,11 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
     w1.x = c;
     w1.y = s;
     const T2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
-    const int q = pidx(p1);
     T2 y[4];
-    y[0] = Y[q];
-    y[1] = cmul(Y[SY + q], w1);
-    y[2] = cmul(Y[2 * SY + q], w2);
-    y[3] = cmul(Y[3 * SY + q], w3);
+    y[0] = Y[yaddr(0, p1)];
+    y[1] = cmul(Y[yaddr(1, p1)], w1);
+    y[2] = cmul(Y[yaddr(2, p1)], w2);
+    y[3] = cmul(Y[yaddr(3, p1)], w3);
     const T2 a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
     const T2 b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
     T2 ib1;  // i * b1
@@ -273,12 +293,14 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
   const int ni = N >> 2;
   const long long first = rt.first[r];
   const int nth = blockDim.x, tid = threadIdx.x;
-  const int SY = padded_len(ni);
-  T2 *Y = (T2 *)smem_raw;  // four padded sub-sequences (see the forward kernel)
-  T2 *W = Y + 4 * SY;
   const bool pw2 = (ni & (ni - 1)) == 0;
   const int lgni = 31 - __clz(ni);
-  auto ydst = [&](int t) { return (t & 3) * SY + pidx(pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
+  const int SY = ring_sub_stride(ni);
+  T2 *Y = (T2 *)smem_raw;  // the four sub-sequences (layout as in the forward kernel)
+  T2 *W = Y + 4 * SY;
+  const bool yswz = pw2 && ni >= 16;  // the XOR layout needs whole 16-element blocks
+  auto yaddr = [&](int b, int i) { return yswz ? faddr(b, i, lgni, SY) : b * SY + i; };
+  auto ydst = [&](int t) { return yaddr(t & 3, pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
   const bool shifted = rt.phi0[r] != 0.0;  // phi0 = pi / N
   const T invL = (T)(1.0 / L_d);
   const T inv_s = (T)(1.0 / rt.sint[r]);
@@ -321,13 +343,16 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
     }
     __syncthreads();
     if (pw2) {
-      fft_core<true, T, T2>(Y, ni, 4, SY, +1, tw, TW);
+      if (yswz)
+        fft_core<true, T, T2>(Y, ni, 4, SY, +1, tw, TW);
+      else
+        fft_core<false, T, T2>(Y, ni, 4, SY, +1, tw, TW);
     } else {
       const long long off = bt.offset[ni];
       const int M = bt.mlen[ni];
       const T2 *bh = (const T2 *)bt.spec + off;
       const T2 *ch = bh + M;
-      const int SW = padded_len(M);
+      const int SW = M;
       if (bbatch >= 4) {
         bluestein_batch<T, T2>(Y, ni, SY, M, 4, W, SW, bh, ch, tw, TW);
       } else {
@@ -342,12 +367,11 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
       w1.x = c;
       w1.y = s;
       const T2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
-      const int q = pidx(p1);
       T2 y[4];
-      y[0] = Y[q];
-      y[1] = cmul(Y[SY + q], w1);
-      y[2] = cmul(Y[2 * SY + q], w2);
-      y[3] = cmul(Y[3 * SY + q], w3);
+      y[0] = Y[yaddr(0, p1)];
+      y[1] = cmul(Y[yaddr(1, p1)], w1);
+      y[2] = cmul(Y[yaddr(2, p1)], w2);
+      y[3] = cmul(Y[yaddr(3, p1)], w3);
       const T2 a0 = cadd(y[0], y[2]), a1 = csub(y[0], y[2]);
       const T2 b0 = cadd(y[1], y[3]), b1 = csub(y[1], y[3]);
       T2 ib1;
@@ -359,17 +383,17 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
       X1.y = -X1.y;
       X2.y = -X2.y;
       X3.y = -X3.y;
-      Y[q] = X0;
-      Y[SY + q] = X1;
-      Y[2 * SY + q] = X2;
-      Y[3 * SY + q] = X3;
+      Y[yaddr(0, p1)] = X0;
+      Y[yaddr(1, p1)] = X1;
+      Y[yaddr(2, p1)] = X2;
+      Y[yaddr(3, p1)] = X3;
     }
     __syncthreads();
     // split the packed spectra and accumulate the plane's row
     for (int m = tid; m <= mmax; m += nth) {
       const int t = m % N;
       const int tm = (N - t) % N;
-      const T2 zt = Y[(t / ni) * SY + pidx(t % ni)], zm = Y[(tm / ni) * SY + pidx(tm % ni)];
+      const T2 zt = Y[yaddr(t / ni, t % ni)], zm = Y[yaddr(tm / ni, tm % ni)];
       // X^a = (Z_t + conj Z_{N-t})/2, X^b = (Z_t - conj Z_{N-t})/(2i)
       T2 xa, xb;
       xa.x = (T)0.5 * (zt.x + zm.x);
@@ -483,9 +507,9 @@ __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const l
 static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch) {
   const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
   const size_t fold = (2 * g.ni_min + 1 < 512) ? 1024 : 0;
-  size_t wl = g.M ? (size_t)batch * (size_t)padded_len(g.M) : 0;
+  size_t wl = g.M ? (size_t)batch * (size_t)g.M : 0;
   if (wl < fold) wl = fold;
-  return e2 * ((size_t)4 * padded_len(g.ni_max) + wl);
+  return e2 * ((size_t)4 * ring_sub_stride_max(g) + wl);
 }
 // Four sub-transforms at once when two CTAs still fit on an SM (or when asked to and
 // one fits); one at a time otherwise.
@@ -498,9 +522,9 @@ static int group_batch(const tl_plan *p, const FftGroup &g) {
 // Upper bound over all rings (plan feasibility check): batch 1.
 size_t ringfft_smem_bytes(const tl_plan *p) {
   const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
-  size_t wl = (size_t)padded_len(p->blue_maxm);
+  size_t wl = (size_t)p->blue_maxm;
   if (wl < 1024) wl = 1024;
-  return e2 * ((size_t)4 * padded_len(p->nside) + wl);
+  return e2 * ((size_t)4 * ((size_t)p->nside + 16) + wl);
 }
 
 template <typename K>
