@@ -84,13 +84,19 @@ __device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, i
   const int ulg = lg - R;  // groups per array: 2^ulg
   const int total = batch << ulg;
   const int h = 1 << sh;
+  // swz is linear over XOR and i0 has bits sh .. sh+R-1 clear, so the element
+  // addresses are faddr(b, i0) ^ swz(c << sh): offsets d[c] shared by every group
+  int d[P];
+#pragma unroll
+  for (int c = 0; c < P; ++c) d[c] = SWZ ? swz(c << sh, lg) : (c << sh);
   for (int e = threadIdx.x; e < total; e += blockDim.x) {
     const int b = e >> ulg, q = e & ((1 << ulg) - 1);
     const int pos = q & (h - 1), grp = q >> sh;
     const int i0 = (grp << (sh + R)) + pos;
+    const int base = SWZ ? faddr(b, i0, lg, stride) : b * stride + i0;
     T2 x[P];
 #pragma unroll
-    for (int c = 0; c < P; ++c) x[c] = a[SWZ ? faddr(b, i0 + (c << sh), lg, stride) : b * stride + i0 + (c << sh)];
+    for (int c = 0; c < P; ++c) x[c] = a[SWZ ? (base ^ d[c]) : base + d[c]];
 #pragma unroll
     for (int lev = 0; lev < R; ++lev) {
       T2 wl = tw[pos << (lgtw - sh - lev - 1)];
@@ -106,7 +112,7 @@ __device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, i
       }
     }
 #pragma unroll
-    for (int c = 0; c < P; ++c) a[SWZ ? faddr(b, i0 + (c << sh), lg, stride) : b * stride + i0 + (c << sh)] = x[c];
+    for (int c = 0; c < P; ++c) a[SWZ ? (base ^ d[c]) : base + d[c]] = x[c];
   }
   __syncthreads();
 }

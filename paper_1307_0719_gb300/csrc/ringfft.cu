@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   // both packed maps are transformed in the normalised units of the Legendre stage
   // (similar magnitudes, so the shared transform's rounding does not leak from a
   // large map into a small one); each job's scale is applied on output
-  const T wa = (T)(JA.div_sint ? 1.0 / rt.sint[r] : 1.0);
-  const T wb = hasb ? (T)(JB.div_sint ? 1.0 / rt.sint[r] : 1.0) : (T)0;
+  const T inv_s = (T)1 / (T)rt.sint[r];  // in the map type: a double divide per thread costs the FP64 pipe
+  const T wa = JA.div_sint ? inv_s : (T)1;
+  const T wb = hasb ? (JB.div_sint ? inv_s : (T)1) : (T)0;
   const T sa = (T)JA.scale, sb = (T)JB.scale;
 
   // ---- fold m modulo N into the Hermitian spectrum; thread handles classes t and N - t
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
   auto ydst = [&](int t) { return yaddr(t & 3, pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
   const bool shifted = rt.phi0[r] != 0.0;  // phi0 = pi / N
   const T invL = (T)(1.0 / L_d);
-  const T inv_s = (T)(1.0 / rt.sint[r]);
+  const T inv_s = (T)1 / (T)rt.sint[r];
   T2 *F = (T2 *)ps.base[J.plane] + (size_t)J.j * plane_len + (size_t)r * (mmax + 1);
   // inputs: field planes take k = 0 .. nk-1 with c_k = 1/(j! k!); the deflection's
   // planes one map each (j = 1: k = 0; j = 0: k = 1 over sin(theta)), c = L
