@@ -24,6 +24,7 @@ struct RingTable {
   double *phi0;    // longitude of the ring's first pixel
   double *dphi;    // 2 pi / nphi: longitude step between the ring's pixels
   double *omza;    // 1 - |cos(theta)|, formed without cancellation
+  float *rsinf;    // 1 / sin(theta), rounded to float (single-precision kernels)
   double *log2_sh; // log2 sin(theta/2)
   double *log2_ch; // log2 cos(theta/2)
   double *dls;     // [ring][k], k = 1..TL_MAX_NDER+1: d^k/dtheta^k ln sin(theta/2)
@@ -77,6 +78,7 @@ struct tl_plan {
   int batch;             // realisations sharing one Legendre launch (1, or 8 on tensor cores)
   int tc_nder;           // derivative orders carried there (max(order, 1))
   long long *tc_blk0, *tc_blk2;   // [lmax+1] first block of each m (spin 0 / spin 2)
+  long long tc_nblk0, tc_nblk2;   // blocks in all
   float *tc_step0, *tc_step2;     // [blocks][16]: A_{l+1} x 8, m s/(l(l+1)) x 8
   void *tc_b0, *tc_bp, *tc_b2;    // [blocks] 2 KB coefficient tiles (TF32 hi, lo; 32 columns x 8 l)
   int *dev_err;                   // set by a kernel whose bounded wait timed out
@@ -162,6 +164,7 @@ cudaError_t launch_gather(const tl_plan *p, const void *alpha, const void *d3, v
 // lnorm0: lmax + 1, Bluestein off/ml: nside + 1, twiddles: TW doubles
 struct RingHostView {
   double *z, *sint, *theta, *phi0, *lsh, *lch, *dls, *dlc, *dphi, *omza;
+  float *rsinf;
   int *nphi, *inorth;
   long long *first;
 };

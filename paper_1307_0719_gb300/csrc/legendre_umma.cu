@@ -150,14 +150,21 @@ struct TcDesc {
 };
 
 // Per-CTA tcgen05 state (identical in every thread).
+// The four mbarriers are adjacent 8-byte words: done[0], done[1], full[0], full[1];
+// their addresses are formed arithmetically (a runtime-indexed array member would
+// place the whole struct in local memory).
 struct UmmaCta {
   uint32_t tmem;        // accumulator base (lane 0, first column)
-  uint32_t done[2];     // per buffer: MMAs of its last block completed (one arrival: the commit)
-  uint32_t full[2];     // per buffer: tiles written (one arrival per compute warp)
+  uint32_t bars;        // shared address of done[0]
   uint32_t count;       // blocks so far (the block's buffer is count & 1)
   volatile int *abort;  // shared: set by a thread whose wait timed out
   bool failed;
 };
+
+// per buffer i: MMAs of its last block completed (one arrival: the commit)
+__device__ __forceinline__ uint32_t bar_done(const UmmaCta &U, uint32_t i) { return U.bars + 8u * i; }
+// per buffer i: tiles written (one arrival per compute warp)
+__device__ __forceinline__ uint32_t bar_full(const UmmaCta &U, uint32_t i) { return U.bars + 16u + 8u * i; }
 
 // block g uses buffer g & 1; it is that buffer's (g >> 1)-th phase on both barriers
 __device__ __forceinline__ uint32_t phase_of(uint32_t g) { return (g >> 1) & 1u; }
@@ -253,7 +260,7 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       const uint32_t s0 = smem_u32(sm);
       for (int blk = 0; blk < nblk; ++blk) {
         const uint32_t g = g0 + (uint32_t)blk, i = g & 1u;
-        if (!mbar_wait(U.full[i], phase_of(g), U.abort)) {
+        if (!mbar_wait(bar_full(U, i), phase_of(g), U.abort)) {
           bad = true;
           break;
         }
@@ -261,7 +268,7 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
         const uint64_t dA = umma_desc(s0 + i * BUF), dB = umma_desc(s0 + i * BUF + NJ * 8192u);
         issue_block<MODE>(dA, dB, NJ, U.tmem, blk == 0);
         if (KIND == 1) issue_block<MODE>(dA, dB + (2048u >> 4), 2, U.tmem + (uint32_t)(kUmmaCols * NJ), blk == 0);
-        umma_commit(U.done[i]);
+        umma_commit(bar_done(U, i));
       }
     }
     __syncwarp();
@@ -316,7 +323,7 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       steps_gated<0, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf0);
       steps_gated<4, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf1);
       // this buffer was last read by the MMAs of block g - 2
-      if (g >= 2 && !mbar_wait(U.done[i], phase_of(g - 2), U.abort)) {
+      if (g >= 2 && !mbar_wait(bar_done(U, i), phase_of(g - 2), U.abort)) {
         bad = true;
         break;
       }
@@ -327,12 +334,12 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       if (KIND == 1) *(float4 *)(tiles + NJ * 8192 + 2048 + tid * 16) = bp;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(U.full[i]);
+      if ((tid & 31) == 0) mbar_arrive(bar_full(U, i));
     }
   }
   U.count = g0 + (uint32_t)nblk;
   // the last commit covers every MMA issued before it
-  if (!bad && nblk > 0 && !mbar_wait(U.done[(U.count - 1) & 1u], phase_of(U.count - 1), U.abort)) bad = true;
+  if (!bad && nblk > 0 && !mbar_wait(bar_done(U, (U.count - 1) & 1u), phase_of(U.count - 1), U.abort)) bad = true;
   if (bad) *U.abort = 1;
   if (__syncthreads_or(bad)) {
     U.failed = true;
@@ -446,10 +453,7 @@ __device__ __forceinline__ void umma_open(UmmaCta &U, uint64_t *bars, uint32_t *
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   U.tmem = *tbase;
-  U.done[0] = smem_u32(&bars[0]);
-  U.done[1] = smem_u32(&bars[1]);
-  U.full[0] = smem_u32(&bars[2]);
-  U.full[1] = smem_u32(&bars[3]);
+  U.bars = smem_u32(&bars[0]);
   U.count = 0;
   U.abort = abort;
   U.failed = false;
@@ -460,8 +464,8 @@ __device__ __forceinline__ void umma_close(const TcDesc &D, UmmaCta &U) {
   if (U.failed && threadIdx.x == 0) {
     atomicExch(D.err, 1);
     // own MMAs in flight: the last two blocks' commits (bounded)
-    if (U.count > 0) (void)mbar_wait(U.done[(U.count - 1) & 1u], phase_of(U.count - 1));
-    if (U.count > 1) (void)mbar_wait(U.done[(U.count - 2) & 1u], phase_of(U.count - 2));
+    if (U.count > 0) (void)mbar_wait(bar_done(U, (U.count - 1) & 1u), phase_of(U.count - 1));
+    if (U.count > 1) (void)mbar_wait(bar_done(U, (U.count - 2) & 1u), phase_of(U.count - 2));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -564,39 +568,54 @@ struct TcAlm {
   const double *b[kUmmaReal];  // B (spin 2), may be NULL
 };
 
-__global__ void tcprep_kernel(int lmax, int s, int nreal, TcAlm alm, const long long *__restrict__ blkofs,
-                              const float2 *__restrict__ tab, unsigned char *__restrict__ out) {
-  const int m = blockIdx.y;
+// One warp per 8-l block (blocks of all m numbered contiguously; the block's m by
+// binary search in blkofs); lane n owns column n: it forms the column's 8 values
+// and writes their hi and lo parts as 16-byte vectors.
+__global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal, TcAlm alm,
+                                                     const long long *__restrict__ blkofs, long long nblocks,
+                                                     const float2 *__restrict__ tab, unsigned char *__restrict__ out) {
+  const long long B = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (B >= nblocks) return;
+  const int n = threadIdx.x & 31;
+  int lo_m = 0, hi_m = lmax;  // largest m with blkofs[m] <= B
+  while (lo_m < hi_m) {
+    const int mid = (lo_m + hi_m + 1) >> 1;
+    if (blkofs[mid] <= B) lo_m = mid;
+    else hi_m = mid - 1;
+  }
+  const int m = lo_m;
+  const int blk = (int)(B - blkofs[m]);
   const int as = s < 0 ? -s : s;
   const int l0 = m > as ? m : as;
-  const int nblk = (lmax >= l0) ? (lmax - l0 + 8) / 8 : 0;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;  // (block, n, k)
-  if (e >= nblk * 256) return;
-  const int blk = e >> 8, n = (e >> 3) & 31, k = e & 7;
   const int rho = n >> 2, c = n & 3;
-  const int l = l0 + 8 * blk + k;
-  double val = 0.0;
-  if (l <= lmax && rho < nreal) {
-    const long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
-    const double kl = (double)tab[idx].x;
-    const double sg = ((l + m) & 1) ? -1.0 : 1.0;
-    const double *A = alm.a[rho], *Bm = alm.b[rho];
-    const double ar = A[2 * idx], ai = (m > 0) ? A[2 * idx + 1] : 0.0;
-    if (s == 0) {
-      const double re = ar * kl, im = ai * kl;
-      val = (c == 0) ? re : (c == 1) ? im : (c == 2) ? sg * re : sg * im;
-    } else {
-      const double br = Bm ? Bm[2 * idx] : 0.0, bi = (Bm && m > 0) ? Bm[2 * idx + 1] : 0.0;
-      val = (c == 0) ? (ar - bi) * kl : (c == 1) ? (ai + br) * kl : (c == 2) ? sg * kl * (ar + bi) : sg * kl * (ai - br);
+  float hv[8], lv[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int l = l0 + 8 * blk + k;
+    double val = 0.0;
+    if (l <= lmax && rho < nreal) {
+      const long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
+      const double kl = (double)tab[idx].x;
+      const double sg = ((l + m) & 1) ? -1.0 : 1.0;
+      const double *A = alm.a[rho], *Bm = alm.b[rho];
+      const double ar = A[2 * idx], ai = (m > 0) ? A[2 * idx + 1] : 0.0;
+      if (s == 0) {
+        const double re = ar * kl, im = ai * kl;
+        val = (c == 0) ? re : (c == 1) ? im : (c == 2) ? sg * re : sg * im;
+      } else {
+        const double br = Bm ? Bm[2 * idx] : 0.0, bi = (Bm && m > 0) ? Bm[2 * idx + 1] : 0.0;
+        val = (c == 0) ? (ar - bi) * kl : (c == 1) ? (ai + br) * kl : (c == 2) ? sg * kl * (ar + bi) : sg * kl * (ai - br);
+      }
     }
+    const float v = (float)val;
+    hv[k] = __uint_as_float(to_tf32(v));
+    lv[k] = __uint_as_float(to_tf32(v - hv[k]));
   }
-  const float v = (float)val;
-  const float hi = __uint_as_float(to_tf32(v));
-  const float lo = __uint_as_float(to_tf32(v - hi));
-  unsigned char *o = out + (blkofs[m] + blk) * 2048;
-  const uint32_t off = can_off(n, k);
-  *(float *)(o + off) = hi;
-  *(float *)(o + 1024 + off) = lo;
+  unsigned char *o = out + B * 2048;
+  *(float4 *)(o + can_off(n, 0)) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+  *(float4 *)(o + can_off(n, 4)) = make_float4(hv[4], hv[5], hv[6], hv[7]);
+  *(float4 *)(o + 1024 + can_off(n, 0)) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+  *(float4 *)(o + 1024 + can_off(n, 4)) = make_float4(lv[4], lv[5], lv[6], lv[7]);
 }
 
 // ---------------------------------------------------------------------------
@@ -618,9 +637,10 @@ cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *cons
     alm.a[i] = (i < nreal) ? a[i] : nullptr;
     alm.b[i] = (i < nreal && b) ? b[i] : nullptr;
   }
-  const int maxe = ((p->lmax + 8) / 8) * 256;
-  dim3 grid((maxe + 255) / 256, p->lmax + 1);
-  tcprep_kernel<<<grid, 256, 0, st>>>(p->lmax, s, nreal, alm, blkofs, (const float2 *)tab, (unsigned char *)out);
+  const long long nblocks = (s == 2) ? p->tc_nblk2 : p->tc_nblk0;
+  if (nblocks == 0) return cudaSuccess;
+  tcprep_kernel<<<(unsigned)((nblocks + 7) / 8), 256, 0, st>>>(p->lmax, s, nreal, alm, blkofs, nblocks,
+                                                               (const float2 *)tab, (unsigned char *)out);
   return cudaGetLastError();
 }
 

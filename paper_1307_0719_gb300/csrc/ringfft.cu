@@ -17,32 +17,33 @@
 
 namespace tl {
 
+// One output map: its coefficient plane's first ring (T2 [ring][m], chosen on the
+// host, so that the kernel indexes no parameter array at run time), phi-derivative
+// order k, 1/sin(theta) weight and output scale (double, and rounded to float).
 struct JobDev {
-  int plane, j, k, div_sint;
-  double scale;
+  const void *in;
   void *out;
+  double scale;
+  float scalef;
+  int k, div_sint;
 };
 #define TL_MAX_JOBS 96
 struct JobList {
   int n;
   JobDev job[TL_MAX_JOBS];
 };
-struct PlaneSet {
-  const void *base[4];  // T, Q, U, phi planes: [j][ring][m]
-};
 // adjoint: one output plane (plane 0..2 = T, Q, U with inputs d_theta^j d_phi^k,
-// k < nk, at base + map_index(j, k) npix; plane 3 = phi with one input map at base)
+// k < nk, at base + map_index(j, k) npix; plane 3 = phi with one input map at base),
+// written at fout (T2 [ring][m], its first ring)
 struct AdjJobDev {
   const void *base;
+  void *fout;
   int plane, j, nk, pad;
 };
 #define TL_MAX_ADJ_JOBS 32
 struct AdjJobList {
   int n;
   AdjJobDev job[TL_MAX_ADJ_JOBS];
-};
-struct PlaneSetOut {
-  void *base[4];
 };
 
 // Stride of the four decimated sub-sequences of a ring with nphi = 4 ni: ni for
@@ -92,10 +93,10 @@ __device__ __forceinline__ T2 fold_class(const T2 *__restrict__ F, int t0, int N
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, int mmax, int nrings, PlaneSet ps,
-                                                      int plane_len, JobList jobs, BluesteinTable bt,
+__global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
+                                                      BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
-                                                      int bbatch, double invL_d, const int *__restrict__ rings) {
+                                                      int bbatch, T invL, const int *__restrict__ rings) {
   typedef typename RealTraits<T>::T2 T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = rings[blockIdx.x];
@@ -106,7 +107,6 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   const int ni = N >> 2;
   const int half = N >> 1;
   const long long first = rt.first[r];
-  const T invL = (T)invL_d;
   const int nth = blockDim.x, tid = threadIdx.x;
   // Y: the four decimated sub-sequences Z_{4 t1 + t2}, SY apart. Power-of-two ni: the
   // swizzled layout, stored in bit-reversed order (the input order of the in-place
@@ -122,19 +122,23 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   auto ydst = [&](int t) { return yaddr(t & 3, pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
   // half-pixel-shifted rings have phi0 = pi / (4 ni) = pi / N: e^{i m phi0} = e^{i t phi0} (-1)^q
   // for m = t + q N
-  const bool shifted = rt.phi0[r] != 0.0;
+  const bool shifted = __double_as_longlong(rt.phi0[r]) != 0;  // phi0 >= 0: an integer test
 
   const JobDev JA = jobs.job[ja];
   const JobDev JB = hasb ? jobs.job[jb] : jobs.job[ja];
-  const T2 *FA = (const T2 *)ps.base[JA.plane] + (size_t)JA.j * plane_len + (size_t)r * (mmax + 1);
-  const T2 *FB = (const T2 *)ps.base[JB.plane] + (size_t)JB.j * plane_len + (size_t)r * (mmax + 1);
+  const T2 *FA = (const T2 *)JA.in + (size_t)r * (mmax + 1);
+  const T2 *FB = (const T2 *)JB.in + (size_t)r * (mmax + 1);
   // both packed maps are transformed in the normalised units of the Legendre stage
   // (similar magnitudes, so the shared transform's rounding does not leak from a
   // large map into a small one); each job's scale is applied on output
-  const T inv_s = (T)1 / (T)rt.sint[r];  // in the map type: a double divide per thread costs the FP64 pipe
+  // single precision takes its per-ring and per-job factors from float tables: a
+  // double operation per thread would queue on the FP64 pipe
+  constexpr bool F32 = sizeof(T) == 4;
+  const T inv_s = F32 ? (T)rt.rsinf[r] : (T)(1.0 / rt.sint[r]);
   const T wa = JA.div_sint ? inv_s : (T)1;
   const T wb = hasb ? (JB.div_sint ? inv_s : (T)1) : (T)0;
-  const T sa = (T)JA.scale, sb = (T)JB.scale;
+  const T sa = F32 ? (T)JA.scalef : (T)JA.scale, sb = F32 ? (T)JB.scalef : (T)JB.scale;
+  const T invN = (T)1 / (T)N;
 
   // ---- fold m modulo N into the Hermitian spectrum; thread handles classes t and N - t
   // (t = 0 .. N/2): C_t = (B_t + conj(B_{-t}))/2, C_{-t} = conj(C_t), Z = C^a + i C^b.
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   {
     const int c = tid / ncls, t = tid - (tid / ncls) * ncls;
     for (int tt = (C == 1 ? tid : t); tt < ncls && c < C; tt += (C == 1 ? nth : ncls)) {
-      const int tm = (N - tt) % N;
+      const int tm = tt ? N - tt : 0;
       const int m0 = tt + c * N, m1 = tm + c * N, step = C * N;
       T2 Ba = fold_class<T, T2>(FA, m0, N, step, mmax, JA.k, invL, shifted, C);
       T2 Bam = fold_class<T, T2>(FA, m1, N, step, mmax, JA.k, invL, shifted, C);
@@ -161,7 +165,7 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
       if (shifted) {
         // class phases e^{i t phi0} and e^{i (N-t) phi0} = -conj(e^{i t phi0}) (t > 0)
         T s, co;
-        sincos_pi<T>((T)tt / (T)N, &s, &co);
+        sincos_pi<T>((T)tt * invN, &s, &co);
         T2 e, em;
         e.x = co;
         e.y = s;
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
         ca = cadd(ca, W[2 * (c * ncls + tt)]);
         cb = cadd(cb, W[2 * (c * ncls + tt) + 1]);
       }
-      const int tm = (N - tt) % N;
+      const int tm = tt ? N - tt : 0;
       T2 z, zm;
       z.x = ca.x - cb.y;
       z.y = ca.y + cb.x;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   T *outB = hasb ? (T *)JB.out + first : nullptr;
   for (int p1 = tid; p1 < ni; p1 += nth) {
     T s, c;
-    sincos_pi<T>((T)(2 * p1) / (T)N, &s, &c);
+    sincos_pi<T>((T)(2 * p1) * invN, &s, &c);
     T2 w1;
     w1.x = c;
     w1.y = s;
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
 
 template <typename T>
 __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax, long long npix, int nmaps,
-                                                          AdjJobList jobs, PlaneSetOut ps, int plane_len,
+                                                          AdjJobList jobs,
                                                           BluesteinTable bt,
                                                           const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
                                                           int bbatch, double L_d, const int *__restrict__ rings) {
@@ -302,10 +306,10 @@ __global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax
   const bool yswz = pw2 && ni >= 16;  // the XOR layout needs whole 16-element blocks
   auto yaddr = [&](int b, int i) { return yswz ? faddr(b, i, lgni, SY) : b * SY + i; };
   auto ydst = [&](int t) { return yaddr(t & 3, pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
-  const bool shifted = rt.phi0[r] != 0.0;  // phi0 = pi / N
+  const bool shifted = __double_as_longlong(rt.phi0[r]) != 0;  // phi0 = pi / N
   const T invL = (T)(1.0 / L_d);
   const T inv_s = (T)1 / (T)rt.sint[r];
-  T2 *F = (T2 *)ps.base[J.plane] + (size_t)J.j * plane_len + (size_t)r * (mmax + 1);
+  T2 *F = (T2 *)J.fout + (size_t)r * (mmax + 1);
   // inputs: field planes take k = 0 .. nk-1 with c_k = 1/(j! k!); the deflection's
   // planes one map each (j = 1: k = 0; j = 0: k = 1 over sin(theta)), c = L
   const bool defl = J.plane == 3;
@@ -544,25 +548,24 @@ static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const 
   JobList jl;
   if (njobs > TL_MAX_JOBS) return cudaErrorInvalidValue;
   jl.n = njobs;
+  const size_t plane_len = (size_t)p->nrings * (p->mmax + 1);
   for (int i = 0; i < njobs; ++i) {
-    jl.job[i].plane = jobs[i].plane;
-    jl.job[i].j = jobs[i].j;
+    if (jobs[i].plane < 0 || jobs[i].plane > 3) return cudaErrorInvalidValue;
+    jl.job[i].in = (const typename RealTraits<T>::T2 *)planes[jobs[i].plane] + (size_t)jobs[i].j * plane_len;
     jl.job[i].k = jobs[i].k;
     jl.job[i].div_sint = jobs[i].div_sint;
     jl.job[i].scale = jobs[i].scale;
+    jl.job[i].scalef = (float)jobs[i].scale;
     jl.job[i].out = jobs[i].out;
   }
-  PlaneSet ps;
-  for (int i = 0; i < 4; ++i) ps.base[i] = planes[i];
-  const int plane_len = p->nrings * (p->mmax + 1);
   TL_CUDA_TRY(set_group_smem(p, ringfft_kernel<T>));
   for (int gi = 0; gi < p->fft_ngroups; ++gi) {
     const FftGroup &g = p->fft_groups[gi];
     const int batch = group_batch(p, g);
     dim3 grid(g.count, (njobs + 1) / 2);
     ringfft_kernel<T><<<grid, 512, group_smem(p, g, batch), s>>>(
-        p->ring, p->nside, p->mmax, p->nrings, ps, plane_len, jl, p->blue,
-        (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, 1.0 / (double)(p->lmax + 1),
+        p->ring, p->nside, p->mmax, jl, p->blue,
+        (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (T)(1.0 / (double)(p->lmax + 1)),
         p->fft_rings + g.first);
   }
   return cudaGetLastError();
@@ -586,23 +589,23 @@ static cudaError_t ringfft_adj_t(const tl_plan *p, void *const *planes, const Ad
   if (njobs == 0) return cudaSuccess;
   AdjJobList jl;
   jl.n = njobs;
+  const size_t plane_len = (size_t)p->nrings * (p->mmax + 1);
   for (int i = 0; i < njobs; ++i) {
+    if (jobs[i].plane < 0 || jobs[i].plane > 3) return cudaErrorInvalidValue;
     jl.job[i].base = jobs[i].in;
+    jl.job[i].fout = (typename RealTraits<T>::T2 *)planes[jobs[i].plane] + (size_t)jobs[i].j * plane_len;
     jl.job[i].plane = jobs[i].plane;
     jl.job[i].j = jobs[i].j;
     jl.job[i].nk = jobs[i].nk;
     jl.job[i].pad = 0;
   }
-  PlaneSetOut ps;
-  for (int i = 0; i < 4; ++i) ps.base[i] = planes[i];
-  const int plane_len = p->nrings * (p->mmax + 1);
   TL_CUDA_TRY(set_group_smem(p, ringfft_adj_kernel<T>));
   for (int gi = 0; gi < p->fft_ngroups; ++gi) {
     const FftGroup &g = p->fft_groups[gi];
     const int batch = group_batch(p, g);
     dim3 grid(g.count, njobs);
     ringfft_adj_kernel<T><<<grid, 512, group_smem(p, g, batch), s>>>(
-        p->ring, p->mmax, p->npix, p->nmaps, jl, ps, plane_len, p->blue,
+        p->ring, p->mmax, p->npix, p->nmaps, jl, p->blue,
         (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (double)(p->lmax + 1),
         p->fft_rings + g.first);
   }

@@ -78,6 +78,7 @@ void host_ring_tables(int N, const RingHostView &h) {
     h.dphi[r] = 2.0 * kPiH / (double)h.nphi[r];
     h.omza[r] = omz_m < omz_p ? omz_m : omz_p;
     h.sint[r] = sqrt(omz_m * omz_p);
+    h.rsinf[r] = (float)(1.0 / h.sint[r]);
     h.theta[r] = (z >= 0.0) ? 2.0 * asin(sqrt(0.5 * omz_m)) : kPiH - 2.0 * asin(sqrt(0.5 * omz_p));
     h.lsh[r] = 0.5 * log2(0.5 * omz_m);
     h.lch[r] = 0.5 * log2(0.5 * omz_p);
