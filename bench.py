@@ -4,7 +4,7 @@ One step = one full lensing pass through the C ABI (deflection synthesis, Legend
 stage of T and Q/U with all derivative orders, ring FFTs into the derivative maps,
 gather + Taylor sum + rotation) for the step's synthetic skies, whose coefficients
 are already resident in HBM. The headline form is the 3xTF32 tensor-core
-contraction (tcgen05) with eight realisations per Legendre launch (--form, --batch); the plain
+contraction (tcgen05) with sixteen realisations per Legendre launch (--form, --batch); the plain
 FP64 GPU form is timed on the same GPU beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -210,7 +210,9 @@ def run_ours(args):
     w = skygen.WORKLOADS[args.workload]
     forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3}
     prec = forms[args.form]
-    nb = args.batch if args.batch else (8 if args.form != "fp32" else 1)
+    plan = api.Plan(w.nside, w.lmax, w.order, pol=w.pol, precision=prec)
+    # one Legendre launch's worth of realisations per step (16 on the tensor cores)
+    nb = args.batch if args.batch else plan.batch
     # each rank lenses its own realisations (seeds offset by rank and index): weak scaling
     skies = [skygen.make_sky(w.nside, w.lmax, w.pol, w.seed_t + 1000 * rank + 100 * i,
                              w.seed_e + 1000 * rank + 100 * i, w.seed_phi + 1000 * rank + 100 * i,
@@ -218,7 +220,6 @@ def run_ours(args):
     sky = skies[0]
     dl = [{k: torch.from_numpy(v).to(dev) for k, v in sk.items()} for sk in skies]
     d = dl[0]
-    plan = api.Plan(w.nside, w.lmax, w.order, pol=w.pol, precision=prec)
     outs = [torch.empty((3, plan.npix), dtype=torch.float32, device=dev) for _ in range(nb)]
     out = outs[0]
     stream = torch.cuda.current_stream()
@@ -259,7 +260,7 @@ def run_ours(args):
     # written once). The dominant stage (largest time per step) is `roofline`.
     tc = args.form != "fp32"
     part = "recurrence" if tc else "all"
-    nr_launch = min(nb, 8) if tc else 1
+    nr_launch = min(nb, plan.batch) if tc else 1
     peaks = {}
     if os.path.exists(PEAKS_FILE):
         with open(PEAKS_FILE) as f:
@@ -269,9 +270,9 @@ def run_ours(args):
     fp32_peak = FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     hbm = peaks.get("hbm_gbs")
     # stage times are those of the step's last tl_lens_batch chunk: one Legendre launch of
-    # up to 8 realisations on tensor cores, one realisation otherwise
+    # up to 16 realisations on tensor cores, one realisation otherwise
     launches = 1
-    nchunk = min(nb, 8) if tc else 1
+    nchunk = min(nb, plan.batch) if tc else 1
     rl = {}
     for st, spin in (("legendre_QU", 2), ("legendre_T", 0)):
         fl = legendre_flops_per_launch(w.nside, w.lmax, w.order, spin, part=part) * launches
@@ -329,6 +330,7 @@ def run_ours(args):
         del hin, hout, dbuf
 
     lensed = out.cpu().numpy()
+    launches_per_step = plan.batch_launches(nb)
     plan.close()
     del plan
     torch.cuda.empty_cache()
@@ -395,7 +397,7 @@ def run_ours(args):
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (alm 537 MB, "
                        "derivative maps 9 GB per step)"},
             "stage_ms": stage_ms, "roofline": roof, "roofline_stages": rl, "clocks": clocks,
-            "gpu_launches": args.steps * ((8 * nb) if not tc else (5 + 5 * nb)), "e2e": e2e, "fp64": fp64, "err_vs_oracle": err,
+            "gpu_launches": args.steps * launches_per_step, "e2e": e2e, "fp64": fp64, "err_vs_oracle": err,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -604,7 +606,8 @@ def main():
                     choices=sorted(skygen.WORKLOADS) + ["batched64_n4_TQU", ADJ_WORKLOAD])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--form", default=None, choices=["fp32", "tf32", "tf32x3"])
-    ap.add_argument("--batch", type=int, default=0, help="realisations per step (default 8 on tensor cores)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="realisations per step (default: the plan's Legendre batch, 16 on tensor cores)")
     ap.add_argument("--sample-pixels", type=int, default=16)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

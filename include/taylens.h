@@ -93,6 +93,16 @@ size_t tl_plan_workspace_bytes(const tl_plan *plan);
 /* Number of derivative maps per field, (order+1)(order+2)/2. */
 int tl_plan_maps_per_field(const tl_plan *plan);
 
+/* Realisations that share one Legendre launch in tl_lens_batch: 16 on the
+ * tensor-core precisions up to order 5 (8 at order 6), 1 otherwise. Batches of
+ * this size use the contraction best. 0 for NULL. */
+int tl_plan_batch(const tl_plan *plan);
+
+/* Kernel launches that tl_lens_batch makes for nreal realisations (with the
+ * lensing potential when with_phi != 0): the Legendre stage per batch, the ring
+ * FFTs (one launch per ring group) and the gather per realisation. -1 for NULL. */
+long long tl_plan_batch_launches(const tl_plan *plan, int nreal, int with_phi);
+
 /*
  * Derivative maps of one field (Sec. II.B, Eq. 4: the maps d_theta^j d_phi^k s
  * evaluated at every pixel centre), in natural units.

@@ -21,6 +21,8 @@ SIGNATURES = {
     "tl_plan_destroy": (ctypes.c_int, [_P]),
     "tl_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
     "tl_plan_maps_per_field": (ctypes.c_int, [_P]),
+    "tl_plan_batch": (ctypes.c_int, [_P]),
+    "tl_plan_batch_launches": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int]),
     "tl_plan_device_error": (ctypes.c_int, [_P]),
     "tl_synth_derivs": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "tl_deflection": (ctypes.c_int, [_P, _P, _P, _P, _P]),

@@ -53,6 +53,11 @@ class Plan:
               "tl_plan_create")
         self._h = h
         self.nmaps = L.tl_plan_maps_per_field(h)
+        self.batch = L.tl_plan_batch(h)  # realisations per Legendre launch in lens_batch
+
+    def batch_launches(self, nreal, with_phi=True):
+        """Kernel launches lens_batch makes for nreal realisations."""
+        return int(_lib.lib().tl_plan_batch_launches(self._h, int(nreal), 1 if with_phi else 0))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -24,7 +24,7 @@
 #include "legendre.cuh"
 
 namespace tl {
-void tc_desc_write(const tl_plan *p, int spin, int nreal, void *dst);
+void tc_desc_write(const tl_plan *p, int which, int nreal, void *dst);
 size_t tc_desc_bytes();
 cudaError_t launch_legendre_tc_persistent(int nder, int precision, const void *descs, const void *items, int nitems,
                                           int *counter, int grid, cudaStream_t s);
@@ -39,7 +39,7 @@ struct Wave {
   std::vector<int> counts;                   // realisations of each member in this wave (1 or 2)
   long long item_off;                        // into the device item array
   int nitems;
-  long long desc_off;                        // into the device descriptor array (2 per member)
+  long long desc_off;                        // into the device descriptor array (3 per member)
 };
 
 struct tl_batch {
@@ -170,7 +170,8 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
   }
   b->persistent_ok = b->plans[0]->batch > 1;
   if (b->persistent_ok) {
-    // waves and their cost-sorted item lists; descriptors (spin 0, spin 2) per member
+    // waves and their cost-sorted item lists; descriptors (temperature, potential,
+    // polarisation) per member
     const size_t db = tc_desc_bytes();
     std::vector<int4> items;
     std::vector<unsigned char> descs;
@@ -193,22 +194,26 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
         if (first >= b->members[g].size()) continue;
         const int cnt = (int)std::min<size_t>(per, b->members[g].size() - first);
         const int di = (int)(descs.size() / db);
-        for (int spin : {0, 2}) {
+        for (int which : {0, 1, 2}) {
           const size_t at = descs.size();
           descs.resize(at + db);
-          tc_desc_write(b->plans[g], spin, cnt, descs.data() + at);
+          tc_desc_write(b->plans[g], which, cnt, descs.data() + at);
           desc_plan.push_back(b->plans[g]);
         }
         wv.members.push_back(std::make_pair((int)g, (int)first));
         wv.counts.push_back(cnt);
         const tl_plan *p = b->plans[g];
         const int nb0 = tc_ring_blocks(p, 0), nb2 = tc_ring_blocks(p, 2);
+        // cost ~ blocks x (recurrence + tiles of NDER + 1 orders); the potential carries 2
+        const long long wt = p->tc_nder + 1, wp = 2;
         for (int m = 0; m <= p->mmax; ++m) {
-          for (int r = 0; r < nb0; ++r)  // kind 0 or 1 decided per call (phi or not): encode 1, patch below
-            its.push_back({(long long)(p->lmax - m + 1) * 128, make_int4(di | (1 << 16), m, r, 0)});
+          for (int r = 0; r < nb0; ++r) {
+            its.push_back({(long long)(p->lmax - m + 1) * wt, make_int4(di | (0 << 16), m, r, 0)});
+            its.push_back({(long long)(p->lmax - m + 1) * wp, make_int4((di + 1) | (1 << 16), m, r, 0)});
+          }
           if (pol)
             for (int r = 0; r < nb2; ++r)
-              its.push_back({(long long)(p->lmax - std::max(m, 2) + 1) * 64 * 2, make_int4((di + 1) | (2 << 16), m, r, 0)});
+              its.push_back({(long long)(p->lmax - std::max(m, 2) + 1) * wt, make_int4((di + 2) | (2 << 16), m, r, 0)});
         }
       }
       std::stable_sort(its.begin(), its.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
@@ -225,7 +230,7 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
       }
       const tl_plan *q = desc_plan[di];
       const int nbk = tc_ring_blocks(q, kind == 2 ? 2 : 0);
-      if (v.y < 0 || v.y > q->mmax || v.z < 0 || v.z >= nbk || ((kind == 2) != (di % 2 == 1))) {
+      if (v.y < 0 || v.y > q->mmax || v.z < 0 || v.z >= nbk || di % 3 != kind) {
         batch_free(b);
         return TL_ERR_ARG;
       }
@@ -242,7 +247,7 @@ extern "C" tl_status tl_batch_create(int nreal, const int *nside, const int *lma
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = nsm * 2;  // two CTAs per SM (shared memory and tensor memory)
+    b->grid = nsm * tc_persistent_ctas(b->plans[0]->tc_nder, precision);  // as the tensor memory allows
   }
   tune_load(b);
   *out = b;
@@ -281,7 +286,7 @@ static tl_status batch_pass(tl_batch *b, int mode, const double *const *aT, cons
     for (size_t k = 0; k < wv.members.size(); ++k) {
       const int g = wv.members[k].first, first = wv.members[k].second, cnt = wv.counts[k];
       tl_plan *p = b->plans[g];
-      const double *t[8], *e[8], *bb[8], *ph[8];
+      const double *t[TL_MAX_BATCH], *e[TL_MAX_BATCH], *bb[TL_MAX_BATCH], *ph[TL_MAX_BATCH];
       for (int r = 0; r < cnt; ++r) {
         const int i = b->members[g][first + r];
         t[r] = aT[i];
@@ -303,7 +308,7 @@ static tl_status batch_pass(tl_batch *b, int mode, const double *const *aT, cons
     // ring FFTs and gather per realisation
     for (size_t k = 0; k < wv.members.size(); ++k) {
       const int g = wv.members[k].first, first = wv.members[k].second, cnt = wv.counts[k];
-      void *T2[8], *Q2[8], *U2[8];
+      void *T2[TL_MAX_BATCH], *Q2[TL_MAX_BATCH], *U2[TL_MAX_BATCH];
       for (int r = 0; r < cnt; ++r) {
         const int i = b->members[g][first + r];
         T2[r] = To[i];
@@ -416,7 +421,8 @@ extern "C" tl_status tl_batch_autotune(tl_batch *b, const double *const *alm_T, 
   // 2. persistent grid size (blocks per SM)
   best = 1e30f;
   int best_grid = b->grid;
-  for (int k : {1, 2}) {
+  const int ctas = tc_persistent_ctas(b->plans[0]->tc_nder, b->precision);
+  for (int k : {ctas > 1 ? ctas / 2 : 1, ctas}) {
     b->grid = nsm * k;
     float ms;
     tl_status st = timeit(&ms);

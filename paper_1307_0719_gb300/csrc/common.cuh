@@ -10,7 +10,8 @@
 // largest plan tl_deflection_noalloc serves from its fixed device array
 #define TL_NOALLOC_MAX_NSIDE 128
 #define TL_NOALLOC_MAX_LMAX 256
-#define TL_MAX_NDER 6  // highest theta-derivative order a Legendre kernel carries
+#define TL_MAX_NDER 6
+#define TL_MAX_BATCH 16  // realisations per tensor-core Legendre launch at most  // highest theta-derivative order a Legendre kernel carries
 
 namespace tl {
 
@@ -97,7 +98,7 @@ struct tl_plan {
   int nstage;
   // per realisation of a tensor-core chunk: before its ring FFTs, after them (before
   // the gather), after the gather; summed into the FFT and gather totals
-  cudaEvent_t evr[3 * 8];
+  cudaEvent_t evr[3 * TL_MAX_BATCH];
   int nevr;
 };
 
@@ -149,13 +150,17 @@ cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *cons
                           const long long *blkofs, const void *tab, void *out, cudaStream_t st);
 cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void *dq, void *du, long long rstride,
                                      cudaStream_t s);
-cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, bool phi, void *d7, void *d7p,
-                                     long long rstride, long long rstride_p, cudaStream_t s);
+// spin-0 field (temperature at nder = tc_nder, the lensing potential at nder = 1)
+// from its coefficient tiles btiles into the planes d7
+cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, const void *btiles, void *d7,
+                                     long long rstride, cudaStream_t s);
 cudaError_t launch_bluestein_setup(tl_plan *p, cudaStream_t s);
-// CTAs per m of the tensor-core Legendre kernels (128 rings each) and their dynamic shared memory
+// CTAs per m of the tensor-core Legendre kernels (128 rings each), and the CTAs per
+// SM that the persistent kernel's tensor memory allows
 int tc_ring_blocks(const tl_plan *p, int spin);
-int tc_realisations();  // realisations per tensor-core Legendre launch
-size_t tc_persistent_smem(int nder);
+int tc_realisations(int nder);  // realisations per tensor-core Legendre launch at tc_nder
+size_t tc_btile_bytes(int nder);  // coefficient-tile bytes per 8-l block
+int tc_persistent_ctas(int nder, int precision);
 cudaError_t launch_gather(const tl_plan *p, const void *alpha, const void *d3, void *T, void *Q,
                           void *U, cudaStream_t s);
 

@@ -1,6 +1,6 @@
 // Legendre stage with the contraction on the 5th-generation tensor cores
-// (tcgen05, accumulators in tensor memory) (Naess & Louis 2013, Sec. II.B: the
-// derivative maps of Eq. 4).
+// (tcgen05, operands and accumulators in tensor memory) (Naess & Louis 2013,
+// Sec. II.B: the derivative maps of Eq. 4).
 //
 // The recurrence runs exactly as in legendre.cu: one thread per ring, FP32 values
 // with FP64 seeds and exponent scaling, normalised step mu_{l+1} = A X mu_l - mu_{l-1},
@@ -8,31 +8,37 @@
 // rings and their mirrors; spin 0: 128 north rings, south by parity) in four
 // compute warps, plus one warp that issues the tensor-core work. Every 8 values
 // of l the compute warps write the [128 rings x 8 l] tile of mu^(j) of every
-// derivative order j to shared memory, and the issuing warp runs
-//     D^(j)[128 x 32] += Mu^(j)[128 x 8] . C[8 x 32]       (tcgen05.mma, kind::tf32)
-// into tensor memory. The 32 columns hold the coefficient sets of up to eight
-// realisations that share the basis (4 reals each):
-//   spin 2: k_l (E + iB), k_l (-1)^(l+m) (E - iB);   spin 0: k_l a, k_l (-1)^(l+m) a,
-// plus, for spin 0, the lensing potential's set at j <= 1 in its own accumulators.
+// derivative order j into tensor memory (thread t owns lane t, the tile's row t),
+// and the issuing warp runs
+//     D^(j)[128 x NC] += Mu^(j)[128 x 8] . C[8 x NC]       (tcgen05.mma, kind::tf32)
+// with Mu^(j) read from tensor memory and the coefficient tile C from shared
+// memory. The NC columns (64, or 32 at the highest order) hold the coefficient
+// sets of up to NC/4 realisations that share the basis (4 reals each):
+//   spin 2: k_l (E + iB), k_l (-1)^(l+m) (E - iB);   spin 0: k_l a, k_l (-1)^(l+m) a.
 // TF32 keeps 10 mantissa bits of each operand; the 3xTF32 form splits both into
 // hi + lo and accumulates hi.hi + hi.lo + lo.hi (errors near FP32).
 //
-// Why 32 columns: with few columns an MMA costs what reading its 4 KB A tile from
-// shared memory costs, so the columns per tile set the tensor work per realisation
-// (and the recurrence and tile stores are shared by all realisations).
+// Why 64 columns and the basis in tensor memory: measured on GB300, one CTA's
+// chain of these small MMAs advances at ~50 cycles per instruction whatever N is
+// up to 128, so the MMA side of a block costs the same for 64 columns as for 32
+// and the columns per tile set the realisations served per recurrence. The
+// accumulators of 16 realisations (5 orders x 64 columns) and two sets of basis
+// tiles then fill the 512 columns of tensor memory (one CTA per SM).
 //
-// Pipeline: the tiles are double-buffered. For block g the compute warps run 8
-// steps (step factors and coefficient tiles prefetched one block ahead), wait
-// until the MMAs of block g-2 (same buffer) have completed (mbarrier signalled by
-// tcgen05.commit), store the tiles, fence them into the async proxy and arrive on
-// the buffer's "full" barrier (one arrival per warp). The issuing warp waits for
-// the four arrivals, issues the block's MMAs and commits them to the buffer's
-// "done" barrier, so the MMAs of one block run under the next block's steps.
+// Pipeline: the basis tiles (tensor memory) and the coefficient tiles (shared
+// memory) are double-buffered where the columns allow. For block g the compute
+// warps run 8 steps in registers (step factors and coefficient tiles prefetched
+// one block ahead), wait until the MMAs of the block that last used the buffer
+// have completed (mbarrier "done" of the buffer, signalled by tcgen05.commit),
+// store the basis tiles (tcgen05.st) and the coefficient tile, and arrive on the
+// buffer's "full" barrier (one arrival per warp). The issuing warp waits for the
+// four arrivals, issues the block's MMAs and commits them to the buffer's "done",
+// so the tensor core works on one buffer while the other is being filled.
 //
-// Shared-memory tiles use the K-major layout without swizzle: 8-row x 16-byte
-// core matrices, 128 bytes apart along K and 256 bytes apart along the rows.
-// Every wait is bounded; on time-out the kernel records an error flag, waits
-// (bounded) for its own MMAs, frees its tensor memory and returns.
+// The coefficient tile uses the K-major shared-memory layout without swizzle:
+// 8-row x 16-byte core matrices, 128 bytes apart along K and 256 bytes apart along
+// the rows. Every wait is bounded; on time-out the kernel records an error flag,
+// waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include <math.h>
 #include <string.h>
 
@@ -40,10 +46,16 @@
 
 namespace tl {
 
-constexpr int kUmmaCols = 32;     // accumulator columns per order: 8 realisations x 4 reals
-constexpr int kUmmaReal = 8;      // realisations per launch
+constexpr int kMaxReal = TL_MAX_BATCH;  // realisations per launch at most (64 columns)
 constexpr int kComputeThreads = 128;
 constexpr int kUmmaThreads = 160;  // + the issuing warp
+constexpr uint32_t kXchBytes = 128 * 16 * 4;  // spin-2 epilogue exchange [128][16] floats
+
+// accumulator columns per order for NDER theta-derivatives: 64 (16 realisations)
+// up to NDER = 5, 32 (8) at NDER = 6, where 64 would not fit tensor memory
+__host__ __device__ constexpr int tc_cols(int nder) { return nder <= 5 ? 64 : 32; }
+// coefficient tile of NC columns in shared memory: hi [NC x 8] then lo, TF32
+__host__ __device__ constexpr uint32_t btile_bytes(int nc) { return (uint32_t)nc * 64u; }
 
 // ---------------------------------------------------------------------------
 // tcgen05 building blocks
@@ -64,15 +76,19 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = 32
-constexpr uint32_t kIdescTf32 =
-    (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kUmmaCols >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = NC
+template <int NC> struct Idesc {
+  static constexpr uint32_t value =
+      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NC >> 3) << 17) | ((128u >> 4) << 24);
+};
 
-__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate) {
+// D (tensor memory) += A (tensor memory: row i in lane i, K along 8 columns) . B (shared memory)
+template <int NC>
+__device__ __forceinline__ void umma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(da), "l"(db), "r"(kIdescTf32), "r"(accumulate));
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(db), "n"(Idesc<NC>::value), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
@@ -115,6 +131,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 8 or 16 consecutive columns of the calling thread's lane
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -125,49 +156,54 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 // its top 19 bits), so the pair carries ~21 bits
 __device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
 
-// tensor-memory columns per CTA: (NJ + 2) x 32 (spin 0 with the potential's j <= 1), power of two
-template <int NJ> struct UmmaCols {
-  static constexpr int need = (NJ + 2) * kUmmaCols;
-  static constexpr int value = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+// Tensor-memory map of a CTA: accumulators D^(j) at columns NC j (j < NJ), then
+// NB sets of basis tiles: Mu^(j) of buffer i at A0 + i ASET + AW j (hi in 8
+// columns, then lo for 3xTF32). Two buffers where they fit the 512 columns, else
+// one. The allocation is the next power of two; `ctas` is how many CTAs of that
+// size fit the SM (at most 4).
+template <int NJ, int MODE, int NC> struct TmemMap {
+  static constexpr int AW = MODE == 3 ? 16 : 8;
+  static constexpr int A0 = NJ * NC;
+  static constexpr int ASET = NJ * AW;
+  static constexpr int NB = A0 + 2 * ASET <= 512 ? 2 : 1;
+  static constexpr int need = A0 + NB * ASET;
+  static constexpr int cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+  static constexpr int ctas = 512 / cols > 4 ? 4 : 512 / cols;
+  static_assert(need <= 512, "tensor memory");
 };
 
-// shared memory per tile buffer: NJ x (hi 4 KB + lo 4 KB), then the coefficient
-// tiles: field hi, lo (1 KB each), potential hi, lo
-__host__ __device__ constexpr uint32_t umma_buf_bytes(int nj) { return (uint32_t)nj * 8192u + 4096u; }
-
-// Descriptor of one plan's spin-0 or spin-2 Legendre work.
+// Descriptor of one plan's Legendre work for one coefficient set: a spin-0 field
+// (the temperature, or the lensing potential at NDER = 1) or the spin-2 pair (E, B).
 struct TcDesc {
   RingTable rt;
   const double *lnorm0;
   int nside, lmax, mmax, nrings, nreal;
   const long long *blk;          // first 8-l block of each m
   const float *step;             // per block: A_{l+1} x 8, m s/(l(l+1)) x 8
-  const unsigned char *b;        // per block 2 KB: coefficient tile hi [32 x 8] then lo (spin 0 field / E, B)
-  const unsigned char *bp;       // spin 0: the lensing potential's tiles (or NULL)
-  float2 *d7a, *d7b;             // spin 0: field, potential planes; spin 2: Q, U planes
-  long long rstride, rstride_p;  // T2 elements between realisations' planes
+  const unsigned char *b;        // per block 2 KB: coefficient tile hi [32 x 8] then lo
+  float2 *d7a, *d7b;             // spin 0: the field's planes; spin 2: Q, U planes
+  long long rstride;             // T2 elements between realisations' planes
   int *err;                      // set to 1 when a wait times out
 };
 
-// Per-CTA tcgen05 state (identical in every thread).
-// The four mbarriers are adjacent 8-byte words: done[0], done[1], full[0], full[1];
-// their addresses are formed arithmetically (a runtime-indexed array member would
-// place the whole struct in local memory).
+// Per-CTA tcgen05 state (identical in every thread). The four mbarriers are
+// adjacent 8-byte words: done[0], done[1] (MMAs of the buffer's last block
+// completed; one arrival, the commit), full[0], full[1] (the block's tiles
+// written; one arrival per compute warp). Their addresses are formed
+// arithmetically: a runtime-indexed array member would put the struct in local memory.
 struct UmmaCta {
-  uint32_t tmem;        // accumulator base (lane 0, first column)
+  uint32_t tmem;        // tensor-memory base (lane 0, first column)
   uint32_t bars;        // shared address of done[0]
-  uint32_t count;       // blocks so far (the block's buffer is count & 1)
+  uint32_t count;       // blocks so far
   volatile int *abort;  // shared: set by a thread whose wait timed out
   bool failed;
 };
-
-// per buffer i: MMAs of its last block completed (one arrival: the commit)
 __device__ __forceinline__ uint32_t bar_done(const UmmaCta &U, uint32_t i) { return U.bars + 8u * i; }
-// per buffer i: tiles written (one arrival per compute warp)
 __device__ __forceinline__ uint32_t bar_full(const UmmaCta &U, uint32_t i) { return U.bars + 16u + 8u * i; }
-
-// block g uses buffer g & 1; it is that buffer's (g >> 1)-th phase on both barriers
-__device__ __forceinline__ uint32_t phase_of(uint32_t g) { return (g >> 1) & 1u; }
+// Block g uses buffer g % NB; it is that buffer's (g / NB)-th use, i.e. phase
+// g / NB of both of its barriers.
+template <int NB> __device__ __forceinline__ uint32_t buf_of(uint32_t g) { return NB == 2 ? (g & 1u) : 0u; }
+template <int NB> __device__ __forceinline__ uint32_t phase_of(uint32_t g) { return (NB == 2 ? (g >> 1) : g) & 1u; }
 
 // ---------------------------------------------------------------------------
 // recurrence steps with the basis values buffered for the tiles
@@ -203,51 +239,61 @@ __device__ __forceinline__ void steps_gated(float (&a)[NDER + 1], float (&b)[NDE
     four_steps<S0, NDER, true, SPIN2>(a, b, sc, LC, X, Av, Cv, buf);
 }
 
-// store one 4-column chunk of every order's tile (hi, and lo for 3xTF32)
+// the block's basis values of every order into the calling thread's lane: hi (and
+// lo for 3xTF32) of l = l0 + 8 blk + 0..7, at column a0 + AW j
 template <int NDER, int MODE>
-__device__ __forceinline__ void stash(unsigned char *tiles, int row, int chunk, const float (&buf)[NDER + 1][4]) {
-  const uint32_t off = can_off(row, 4 * chunk);
+__device__ __forceinline__ void store_tiles(uint32_t a0, const float (&buf0)[NDER + 1][4],
+                                            const float (&buf1)[NDER + 1][4]) {
+  constexpr int AW = MODE == 3 ? 16 : 8;
 #pragma unroll
   for (int j = 0; j <= NDER; ++j) {
-    float4 h, lo;
-    if (MODE == 3) {
-      h = make_float4(tf32_trunc(buf[j][0]), tf32_trunc(buf[j][1]), tf32_trunc(buf[j][2]), tf32_trunc(buf[j][3]));
-      lo = make_float4(buf[j][0] - h.x, buf[j][1] - h.y, buf[j][2] - h.z, buf[j][3] - h.w);
-      *(float4 *)(tiles + j * 8192 + 4096 + off) = lo;
-    } else {
-      h = make_float4(__uint_as_float(to_tf32(buf[j][0])), __uint_as_float(to_tf32(buf[j][1])),
-                      __uint_as_float(to_tf32(buf[j][2])), __uint_as_float(to_tf32(buf[j][3])));
+    float v[16];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float x = k < 4 ? buf0[j][k] : buf1[j][k - 4];
+      if (MODE == 3) {
+        v[k] = tf32_trunc(x);
+        v[8 + k] = x - v[k];
+      } else {
+        v[k] = __uint_as_float(to_tf32(x));
+      }
     }
-    *(float4 *)(tiles + j * 8192 + off) = h;
+    if (MODE == 3)
+      tmem_st16(a0 + (uint32_t)(AW * j), v);
+    else
+      tmem_st8(a0 + (uint32_t)(AW * j), v);
   }
 }
 
-// D_j += A_j . B for j < nj (and the lo terms for 3xTF32); accumulator j at col0 + 32 j.
-// Descriptors differ only in their start-address field: add (byte offset >> 4).
-template <int MODE>
-__device__ __forceinline__ void issue_block(uint64_t dA, uint64_t dB, int nj, uint32_t tmem_col0, bool first) {
-  for (int j = 0; j < nj; ++j)
-    umma_tf32(tmem_col0 + (uint32_t)(kUmmaCols * j), dA + (uint64_t)((uint32_t)j * (8192u >> 4)), dB, first ? 0u : 1u);
-  if (MODE == 3) {
-    const uint64_t bl = dB + (1024u >> 4);
-    for (int j = 0; j < nj; ++j)
-      umma_tf32(tmem_col0 + (uint32_t)(kUmmaCols * j), dA + (uint64_t)((uint32_t)j * (8192u >> 4)), bl, 1u);
-    for (int j = 0; j < nj; ++j)
-      umma_tf32(tmem_col0 + (uint32_t)(kUmmaCols * j), dA + (uint64_t)((uint32_t)j * (8192u >> 4) + (4096u >> 4)),
-                dB, 1u);
+// D^(j) += Mu^(j) . C for j < NJ (and the lo terms for 3xTF32), basis tiles at
+// column aset, coefficient tile at descriptor dB (its lo half btile/2 bytes on)
+template <int NJ, int MODE, int NC>
+__device__ __forceinline__ void issue_block(uint32_t tmem, uint32_t aset, uint64_t dB, bool first) {
+  typedef TmemMap<NJ, MODE, NC> TM;
+#pragma unroll
+  for (int j = 0; j < NJ; ++j) {
+    const uint32_t d = tmem + (uint32_t)(NC * j), a = tmem + aset + (uint32_t)(TM::AW * j);
+    umma_tf32_ts<NC>(d, a, dB, first ? 0u : 1u);
+    if (MODE == 3) {
+      umma_tf32_ts<NC>(d, a, dB + ((btile_bytes(NC) / 2) >> 4), 1u);  // hi . lo
+      umma_tf32_ts<NC>(d, a + 8u, dB, 1u);                             // lo . hi
+    }
   }
 }
 
 __device__ __forceinline__ int unit_l0(int m, bool spin2) { return spin2 ? (m > 2 ? m : 2) : m; }
 
 // One (m, ring block) unit: recurrence and tiles (compute warps), MMAs (issuing
-// warp). Leaves the accumulators complete in tensor memory (every MMA waited
-// for) and returns the number of 8-l blocks (0: accumulators unset).
-template <int NDER, int MODE, int KIND>
+// warp). NB: the kernel's buffer count (the same for every unit a CTA runs, so
+// that the barriers' phases follow one block count). Leaves the accumulators
+// complete in tensor memory (every MMA waited for) and returns the number of 8-l
+// blocks (0: accumulators unset).
+template <int NDER, int MODE, int NC, int NB, bool SPIN2>
 __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
-  constexpr bool SPIN2 = KIND == 2;
   constexpr int NJ = NDER + 1;
-  constexpr uint32_t BUF = umma_buf_bytes(NJ);
+  typedef TmemMap<NJ, MODE, NC> TM;
+  static_assert(NB <= TM::NB, "buffers fit");
+  constexpr uint32_t BT = btile_bytes(NC);
   const int tid = threadIdx.x;
   const int l0 = unit_l0(m, SPIN2);
   const int nblk = (D.lmax >= l0) ? (D.lmax - l0 + 8) / 8 : 0;
@@ -257,23 +303,21 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
   if (tid >= kComputeThreads) {
     // ---- issuing warp: one lane waits for each block's tiles and issues its MMAs
     if (tid == kComputeThreads) {
-      const uint32_t s0 = smem_u32(sm);
+      const uint64_t dB0 = umma_desc(smem_u32(sm));
       for (int blk = 0; blk < nblk; ++blk) {
-        const uint32_t g = g0 + (uint32_t)blk, i = g & 1u;
-        if (!mbar_wait(bar_full(U, i), phase_of(g), U.abort)) {
+        const uint32_t g = g0 + (uint32_t)blk, i = buf_of<NB>(g);
+        if (!mbar_wait(bar_full(U, i), phase_of<NB>(g), U.abort)) {
           bad = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t dA = umma_desc(s0 + i * BUF), dB = umma_desc(s0 + i * BUF + NJ * 8192u);
-        issue_block<MODE>(dA, dB, NJ, U.tmem, blk == 0);
-        if (KIND == 1) issue_block<MODE>(dA, dB + (2048u >> 4), 2, U.tmem + (uint32_t)(kUmmaCols * NJ), blk == 0);
+        issue_block<NJ, MODE, NC>(U.tmem, (uint32_t)(TM::A0 + TM::ASET * i), dB0 + ((i * BT) >> 4), blk == 0);
         umma_commit(bar_done(U, i));
       }
     }
     __syncwarp();
   } else {
-    // ---- compute warps: one ring per thread
+    // ---- compute warps: one ring per thread (tensor-memory lane tid)
     const RingTable &rt = D.rt;
     int r;
     bool active;
@@ -286,6 +330,7 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       active = rn < 2 * D.nside;
       r = active ? rn : 0;
     }
+    const uint32_t lane = U.tmem + ((uint32_t)((tid >> 5) * 32) << 16);
     const double invL = 1.0 / (double)(D.lmax + 1);
     Leib<float, NDER> LC;
     leibniz_coefs<float, NDER>(rt.z[r], rt.sint[r], invL, LC);
@@ -299,8 +344,12 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
 #pragma unroll
     for (int j = 0; j < NJ; ++j) a[j] = 0.0f;
     const float X = (float)rt.z[r];
-    // the next block's step factors and coefficient tiles, loaded one block ahead
-    float4 nA0 = make_float4(0.f, 0.f, 0.f, 0.f), nA1 = nA0, nC0 = nA0, nC1 = nA0, nbq = nA0, nbp = nA0;
+    // the next block's step factors and coefficient tile (BT / 128 bytes per
+    // thread), loaded one block ahead
+    constexpr int QV = (int)(BT / 16 / kComputeThreads);  // float4 per thread: 1 or 2
+    float4 nA0 = make_float4(0.f, 0.f, 0.f, 0.f), nA1 = nA0, nC0 = nA0, nC1 = nA0, nbq[QV];
+#pragma unroll
+    for (int q = 0; q < QV; ++q) nbq[q] = nA0;
     auto prefetch = [&](int blk) {
       const float4 *stp = (const float4 *)(D.step + (b0 + blk) * 16);
       nA0 = __ldg(stp);
@@ -309,37 +358,43 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
         nC0 = __ldg(stp + 2);
         nC1 = __ldg(stp + 3);
       }
-      nbq = __ldg((const float4 *)(D.b + (b0 + blk) * 2048) + tid);
-      if (KIND == 1) nbp = __ldg((const float4 *)(D.bp + (b0 + blk) * 2048) + tid);
+      const float4 *bt = (const float4 *)(D.b + (b0 + blk) * BT);
+#pragma unroll
+      for (int q = 0; q < QV; ++q) nbq[q] = __ldg(bt + q * kComputeThreads + tid);
     };
     if (nblk > 0) prefetch(0);
     for (int blk = 0; blk < nblk; ++blk) {
-      const uint32_t g = g0 + (uint32_t)blk, i = g & 1u;
+      const uint32_t g = g0 + (uint32_t)blk, i = buf_of<NB>(g);
       const float Av[8] = {nA0.x, nA0.y, nA0.z, nA0.w, nA1.x, nA1.y, nA1.z, nA1.w};
       const float Cv[8] = {nC0.x, nC0.y, nC0.z, nC0.w, nC1.x, nC1.y, nC1.z, nC1.w};
-      const float4 bq = nbq, bp = nbp;
+      float4 bq[QV];
+#pragma unroll
+      for (int q = 0; q < QV; ++q) bq[q] = nbq[q];
       if (blk + 1 < nblk) prefetch(blk + 1);
       float buf0[NJ][4], buf1[NJ][4];
       steps_gated<0, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf0);
       steps_gated<4, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf1);
-      // this buffer was last read by the MMAs of block g - 2
-      if (g >= 2 && !mbar_wait(bar_done(U, i), phase_of(g - 2), U.abort)) {
+      // the buffer was last read by the MMAs of block g - NB
+      if (g >= (uint32_t)NB && !mbar_wait(bar_done(U, i), phase_of<NB>(g - NB), U.abort)) {
         bad = true;
         break;
       }
-      unsigned char *tiles = sm + i * BUF;
-      stash<NDER, MODE>(tiles, tid, 0, buf0);
-      stash<NDER, MODE>(tiles, tid, 1, buf1);
-      *(float4 *)(tiles + NJ * 8192 + tid * 16) = bq;
-      if (KIND == 1) *(float4 *)(tiles + NJ * 8192 + 2048 + tid * 16) = bp;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < QV; ++q) *(float4 *)(sm + i * BT + (q * kComputeThreads + tid) * 16) = bq[q];
+      store_tiles<NDER, MODE>(lane + (uint32_t)(TM::A0 + TM::ASET * i), buf0, buf1);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(bar_full(U, i));
     }
   }
   U.count = g0 + (uint32_t)nblk;
   // the last commit covers every MMA issued before it
-  if (!bad && nblk > 0 && !mbar_wait(bar_done(U, (U.count - 1) & 1u), phase_of(U.count - 1), U.abort)) bad = true;
+  if (!bad && nblk > 0 &&
+      !mbar_wait(bar_done(U, buf_of<NB>(U.count - 1)), phase_of<NB>(U.count - 1), U.abort))
+    bad = true;
   if (bad) *U.abort = 1;
   if (__syncthreads_or(bad)) {
     U.failed = true;
@@ -349,12 +404,17 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
   return nblk;
 }
 
-// spin 2: combine each ring's S1 with its mirror's S2 into F^Q, F^U, one order at a time
-template <int NDER, int MODE>
+// Dynamic shared memory of a CTA: two coefficient tile buffers, then the spin-2
+// exchange area.
+template <int NC> __host__ __device__ constexpr uint32_t xch_offset() { return 2 * btile_bytes(NC); }
+
+// spin 2: combine each ring's S1 with its mirror's S2 into F^Q, F^U, one order and
+// one group of 8 realisations (32 columns) at a time
+template <int NDER, int MODE, int NC, int NB>
 __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
   constexpr int NJ = NDER + 1;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int nblk = run_blocks<NDER, MODE, 2>(D, m, rblk, sm, U);
+  const int nblk = run_blocks<NDER, MODE, NC, NB, true>(D, m, rblk, sm, U);
   if (U.failed) return;
   const bool compute = tid < kComputeThreads;
   const int rn = rblk * 64 + (tid & 63);
@@ -364,44 +424,47 @@ __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsign
   const bool writer = active && m <= D.mmax && !(mirror && rn == D.nrings - 1 - rn);  // equator: north thread
   const int partner = tid ^ 64;
   const size_t ld = (size_t)(D.mmax + 1);
-  float *xch = (float *)sm;  // [128][16]: S2 (4 rho + 2, 3) of every ring, over the (now free) tiles
+  float *xch = (float *)(sm + xch_offset<NC>());  // [128][16]: S2 (4 rho + 2, 3) of every ring
 #pragma unroll 1
   for (int j = 0; j < NJ; ++j) {
-    float v[32];
-    if (compute) {
-      tmem_ld32(U.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kUmmaCols * j), v);
+#pragma unroll 1
+    for (int h = 0; h < NC / 32; ++h) {
+      float v[32];
+      if (compute) {
+        tmem_ld32(U.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(NC * j + 32 * h), v);
 #pragma unroll
-      for (int rho = 0; rho < kUmmaReal; ++rho) {
-        xch[tid * 16 + 2 * rho] = nblk ? v[4 * rho + 2] : 0.f;
-        xch[tid * 16 + 2 * rho + 1] = nblk ? v[4 * rho + 3] : 0.f;
+        for (int rho = 0; rho < 8; ++rho) {
+          xch[tid * 16 + 2 * rho] = nblk ? v[4 * rho + 2] : 0.f;
+          xch[tid * 16 + 2 * rho + 1] = nblk ? v[4 * rho + 3] : 0.f;
+        }
       }
-    }
-    __syncthreads();
-    if (writer) {
-      const float sg = (j & 1) ? -1.0f : 1.0f;
+      __syncthreads();
+      if (writer) {
+        const float sg = (j & 1) ? -1.0f : 1.0f;
 #pragma unroll
-      for (int rho = 0; rho < kUmmaReal; ++rho) {
-        if (rho >= D.nreal) break;
-        const float s1r = nblk ? v[4 * rho] : 0.f, s1i = nblk ? v[4 * rho + 1] : 0.f;
-        const float s2r = xch[partner * 16 + 2 * rho], s2i = xch[partner * 16 + 2 * rho + 1];
-        const float ar = s1r + sg * s2r, ai = s1i + sg * s2i;
-        const float br = s1r - sg * s2r, bi = s1i - sg * s2i;
-        const size_t o = (size_t)rho * D.rstride + ((size_t)j * D.nrings + r) * ld + m;
-        D.d7a[o] = make_float2(-0.5f * ar, -0.5f * ai);
-        D.d7b[o] = make_float2(-0.5f * bi, 0.5f * br);
+        for (int rho = 0; rho < 8; ++rho) {
+          if (8 * h + rho >= D.nreal) break;
+          const float s1r = nblk ? v[4 * rho] : 0.f, s1i = nblk ? v[4 * rho + 1] : 0.f;
+          const float s2r = xch[partner * 16 + 2 * rho], s2i = xch[partner * 16 + 2 * rho + 1];
+          const float ar = s1r + sg * s2r, ai = s1i + sg * s2i;
+          const float br = s1r - sg * s2r, bi = s1i - sg * s2i;
+          const size_t o = (size_t)(8 * h + rho) * D.rstride + ((size_t)j * D.nrings + r) * ld + m;
+          D.d7a[o] = make_float2(-0.5f * ar, -0.5f * ai);
+          D.d7b[o] = make_float2(-0.5f * bi, 0.5f * br);
+        }
       }
+      __syncthreads();  // xch is rewritten next
     }
-    __syncthreads();  // xch is rewritten for the next order, and is the next unit's tiles
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 
-// spin 0: north ring r and its mirror by parity; the potential's j <= 1 with KIND 1
-template <int NDER, int MODE, int KIND>
+// spin 0: north ring r and its mirror by parity
+template <int NDER, int MODE, int NC, int NB>
 __device__ __forceinline__ void u0_unit(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
   constexpr int NJ = NDER + 1;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int nblk = run_blocks<NDER, MODE, KIND>(D, m, rblk, sm, U);
+  const int nblk = run_blocks<NDER, MODE, NC, NB, false>(D, m, rblk, sm, U);
   if (U.failed) return;
   if (tid < kComputeThreads) {
     const int rn = rblk * 128 + tid;
@@ -410,22 +473,21 @@ __device__ __forceinline__ void u0_unit(const TcDesc &D, int m, int rblk, unsign
     const int rs = D.nrings - 1 - r;
     const size_t ld = (size_t)(D.mmax + 1);
     const uint32_t lane_base = U.tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int j = 0; j < NJ; ++j) {
+      const float sg = (j & 1) ? -1.0f : 1.0f;
+#pragma unroll 1
+      for (int h = 0; h < NC / 32; ++h) {
+        float v[32];
+        tmem_ld32(lane_base + (uint32_t)(NC * j + 32 * h), v);
+        if (!active || nblk == 0) continue;
 #pragma unroll
-    for (int j = 0; j < NJ + (KIND == 1 ? 2 : 0); ++j) {
-      float v[32];
-      tmem_ld32(lane_base + (uint32_t)(kUmmaCols * j), v);
-      if (!active || nblk == 0) continue;
-      const bool pot = j >= NJ;
-      const int jj = pot ? j - NJ : j;
-      float2 *out = pot ? D.d7b : D.d7a;
-      const long long rstr = pot ? D.rstride_p : D.rstride;
-      const float sg = (jj & 1) ? -1.0f : 1.0f;
-#pragma unroll
-      for (int rho = 0; rho < kUmmaReal; ++rho) {
-        if (rho >= D.nreal) break;
-        const size_t o = (size_t)rho * rstr + (size_t)jj * D.nrings * ld + m;
-        out[o + (size_t)r * ld] = make_float2(v[4 * rho], v[4 * rho + 1]);
-        if (rs != r) out[o + (size_t)rs * ld] = make_float2(sg * v[4 * rho + 2], sg * v[4 * rho + 3]);
+        for (int rho = 0; rho < 8; ++rho) {
+          if (8 * h + rho >= D.nreal) break;
+          const size_t o = (size_t)(8 * h + rho) * D.rstride + (size_t)j * D.nrings * ld + m;
+          D.d7a[o + (size_t)r * ld] = make_float2(v[4 * rho], v[4 * rho + 1]);
+          if (rs != r) D.d7a[o + (size_t)rs * ld] = make_float2(sg * v[4 * rho + 2], sg * v[4 * rho + 3]);
+        }
       }
     }
   }
@@ -459,13 +521,14 @@ __device__ __forceinline__ void umma_open(UmmaCta &U, uint64_t *bars, uint32_t *
   U.failed = false;
 }
 
-template <int NCOLS>
+// NB: the buffers of the kernel's main unit type; the last block's commit covers
+// every MMA issued before it.
+template <int NCOLS, int NB>
 __device__ __forceinline__ void umma_close(const TcDesc &D, UmmaCta &U) {
   if (U.failed && threadIdx.x == 0) {
     atomicExch(D.err, 1);
-    // own MMAs in flight: the last two blocks' commits (bounded)
-    if (U.count > 0) (void)mbar_wait(bar_done(U, (U.count - 1) & 1u), phase_of(U.count - 1));
-    if (U.count > 1) (void)mbar_wait(bar_done(U, (U.count - 2) & 1u), phase_of(U.count - 2));
+    // own MMAs in flight (bounded)
+    if (U.count > 0) (void)mbar_wait(bar_done(U, buf_of<NB>(U.count - 1)), phase_of<NB>(U.count - 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -474,46 +537,59 @@ __device__ __forceinline__ void umma_close(const TcDesc &D, UmmaCta &U) {
 }
 
 template <int NDER, int MODE>
-__global__ void __launch_bounds__(kUmmaThreads, 2) legendre_spin2_umma(TcDesc D) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bars[4];
-  __shared__ uint32_t tbase;
-  __shared__ int abort_flag;
-  constexpr int NCOLS = UmmaCols<NDER + 1>::value;
-  UmmaCta U;
-  umma_open<NCOLS>(U, bars, &tbase, &abort_flag);
-  u2_unit<NDER, MODE>(D, blockIdx.y, blockIdx.x, sm, U);
-  umma_close<NCOLS>(D, U);
-}
+struct Tc {
+  static constexpr int NC = tc_cols(NDER);
+  typedef TmemMap<NDER + 1, MODE, NC> TM;
+};
 
-template <int NDER, int MODE, bool PHI>
-__global__ void __launch_bounds__(kUmmaThreads, 2) legendre_spin0_umma(TcDesc D) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bars[4];
-  __shared__ uint32_t tbase;
-  __shared__ int abort_flag;
-  constexpr int NCOLS = UmmaCols<NDER + 1>::value;
-  UmmaCta U;
-  umma_open<NCOLS>(U, bars, &tbase, &abort_flag);
-  u0_unit<NDER, MODE, PHI ? 1 : 0>(D, blockIdx.y, blockIdx.x, sm, U);
-  umma_close<NCOLS>(D, U);
-}
-
-// Persistent form: one launch covers the spin-0 and spin-2 work of several plans.
-// Items (descriptor, kind, m, ring block) are pre-sorted by cost; each CTA takes
-// them in order from an atomic counter until none is left (no waits between CTAs).
 template <int NDER, int MODE>
-__global__ void __launch_bounds__(kUmmaThreads, 2) legendre_umma_persistent(const TcDesc *__restrict__ descs,
-                                                                           const int4 *__restrict__ items,
-                                                                           int nitems, int *__restrict__ counter) {
+__global__ void __launch_bounds__(kUmmaThreads, (Tc<NDER, MODE>::TM::ctas)) legendre_spin2_umma(TcDesc D) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  typedef typename Tc<NDER, MODE>::TM TM;
+  UmmaCta U;
+  umma_open<TM::cols>(U, bars, &tbase, &abort_flag);
+  u2_unit<NDER, MODE, Tc<NDER, MODE>::NC, TM::NB>(D, blockIdx.y, blockIdx.x, sm, U);
+  umma_close<TM::cols, TM::NB>(D, U);
+}
+
+// spin 0 at NDER with the column count CNC (the potential runs at NDER = 1 with the
+// columns of the plan's order)
+template <int NDER, int MODE, int CNC>
+__global__ void __launch_bounds__(kUmmaThreads, (TmemMap<NDER + 1, MODE, CNC>::ctas)) legendre_spin0_umma(TcDesc D) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  typedef TmemMap<NDER + 1, MODE, CNC> TM;
+  UmmaCta U;
+  umma_open<TM::cols>(U, bars, &tbase, &abort_flag);
+  u0_unit<NDER, MODE, CNC, TM::NB>(D, blockIdx.y, blockIdx.x, sm, U);
+  umma_close<TM::cols, TM::NB>(D, U);
+}
+
+// Persistent form: one launch covers the Legendre work of several plans. Items
+// (descriptor, kind, m, ring block) are pre-sorted by cost; each CTA takes them in
+// order from an atomic counter until none is left (no waits between CTAs). Kinds:
+// 0 a spin-0 field at NDER, 1 the lensing potential (spin 0, NDER = 1), 2 spin 2.
+// Every kind's tensor-memory map fits the allocation of NDER's.
+template <int NDER, int MODE>
+__global__ void __launch_bounds__(kUmmaThreads, (Tc<NDER, MODE>::TM::ctas))
+    legendre_umma_persistent(const TcDesc *__restrict__ descs, const int4 *__restrict__ items, int nitems,
+                             int *__restrict__ counter) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t bars[4];
   __shared__ uint32_t tbase;
   __shared__ int abort_flag;
   __shared__ int cur;
-  constexpr int NCOLS = UmmaCols<NDER + 1>::value;
+  constexpr int NC = Tc<NDER, MODE>::NC;
+  typedef typename Tc<NDER, MODE>::TM TM;
+  typedef TmemMap<2, MODE, NC> TM1;
+  static_assert(TM1::A0 + TM::NB * TM1::ASET <= TM::cols, "potential units fit the allocation");
   UmmaCta U;
-  umma_open<NCOLS>(U, bars, &tbase, &abort_flag);
+  umma_open<TM::cols>(U, bars, &tbase, &abort_flag);
   TcDesc D = descs[0];
   for (;;) {
     __syncthreads();  // the previous item's readers of `cur` are done
@@ -525,14 +601,14 @@ __global__ void __launch_bounds__(kUmmaThreads, 2) legendre_umma_persistent(cons
     D = descs[w.x & 0xffff];
     const int kind = w.x >> 16;
     if (kind == 2)
-      u2_unit<NDER, MODE>(D, w.y, w.z, sm, U);
+      u2_unit<NDER, MODE, NC, TM::NB>(D, w.y, w.z, sm, U);
     else if (kind == 1)
-      u0_unit<NDER, MODE, 1>(D, w.y, w.z, sm, U);
+      u0_unit<1, MODE, NC, TM::NB>(D, w.y, w.z, sm, U);
     else
-      u0_unit<NDER, MODE, 0>(D, w.y, w.z, sm, U);
+      u0_unit<NDER, MODE, NC, TM::NB>(D, w.y, w.z, sm, U);
     if (U.failed) break;  // uniform: set after a block-wide vote
   }
-  umma_close<NCOLS>(D, U);
+  umma_close<TM::cols, TM::NB>(D, U);
 }
 
 // ---------------------------------------------------------------------------
@@ -559,24 +635,27 @@ __global__ void tcstep_kernel(int lmax, int s, const long long *__restrict__ blk
   o[8 + k] = ct;
 }
 
-// Coefficient tiles per 8-l block: B[n][k] for column n = 4 rho + c and l = l0 + 8 blk + k,
-// as TF32 hi (first 1 KB) and lo (next 1 KB), K-major without swizzle.
+// Coefficient tiles per 8-l block: B[n][k] for column n = 4 rho + c (n < NC) and
+// l = l0 + 8 blk + k, as TF32 hi (first NC x 32 bytes) and lo (next), K-major
+// without swizzle.
 //   spin 2: c = 0,1: k_l (E + iB) re, im;  c = 2,3: k_l (-1)^(l+m) (E - iB) re, im
 //   spin 0: c = 0,1: k_l a re, im;         c = 2,3: k_l (-1)^(l+m) a re, im
 struct TcAlm {
-  const double *a[kUmmaReal];  // spin 0 field, or E (spin 2)
-  const double *b[kUmmaReal];  // B (spin 2), may be NULL
+  const double *a[kMaxReal];  // spin 0 field, or E (spin 2)
+  const double *b[kMaxReal];  // B (spin 2), may be NULL
 };
 
-// One warp per 8-l block (blocks of all m numbered contiguously; the block's m by
-// binary search in blkofs); lane n owns column n: it forms the column's 8 values
-// and writes their hi and lo parts as 16-byte vectors.
-__global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal, TcAlm alm,
+// One warp per (8-l block, 32 columns) (blocks of all m numbered contiguously; the
+// block's m by binary search in blkofs); lane n owns column 32 h + n: it forms the
+// column's 8 values and writes their hi and lo parts as 16-byte vectors.
+__global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal, int nc, TcAlm alm,
                                                      const long long *__restrict__ blkofs, long long nblocks,
                                                      const float2 *__restrict__ tab, unsigned char *__restrict__ out) {
-  const long long B = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int groups = nc >> 5;
+  const long long W = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const long long B = W / groups;
   if (B >= nblocks) return;
-  const int n = threadIdx.x & 31;
+  const int n = (int)(W - B * groups) * 32 + (threadIdx.x & 31);
   int lo_m = 0, hi_m = lmax;  // largest m with blkofs[m] <= B
   while (lo_m < hi_m) {
     const int mid = (lo_m + hi_m + 1) >> 1;
@@ -611,11 +690,12 @@ __global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal,
     hv[k] = __uint_as_float(to_tf32(v));
     lv[k] = __uint_as_float(to_tf32(v - hv[k]));
   }
-  unsigned char *o = out + B * 2048;
+  const uint32_t half = btile_bytes(nc) / 2;
+  unsigned char *o = out + B * (2 * half);
   *(float4 *)(o + can_off(n, 0)) = make_float4(hv[0], hv[1], hv[2], hv[3]);
   *(float4 *)(o + can_off(n, 4)) = make_float4(hv[4], hv[5], hv[6], hv[7]);
-  *(float4 *)(o + 1024 + can_off(n, 0)) = make_float4(lv[0], lv[1], lv[2], lv[3]);
-  *(float4 *)(o + 1024 + can_off(n, 4)) = make_float4(lv[4], lv[5], lv[6], lv[7]);
+  *(float4 *)(o + half + can_off(n, 0)) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+  *(float4 *)(o + half + can_off(n, 4)) = make_float4(lv[4], lv[5], lv[6], lv[7]);
 }
 
 // ---------------------------------------------------------------------------
@@ -631,38 +711,40 @@ cudaError_t launch_tcstep(const tl_plan *p, int s, const long long *blkofs, cons
 
 cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *const *a, const double *const *b,
                           const long long *blkofs, const void *tab, void *out, cudaStream_t st) {
-  if (nreal < 1 || nreal > kUmmaReal) return cudaErrorInvalidValue;
+  const int nc = tc_cols(p->tc_nder);
+  if (nreal < 1 || nreal > nc / 4) return cudaErrorInvalidValue;
   TcAlm alm;
-  for (int i = 0; i < kUmmaReal; ++i) {
+  for (int i = 0; i < kMaxReal; ++i) {
     alm.a[i] = (i < nreal) ? a[i] : nullptr;
     alm.b[i] = (i < nreal && b) ? b[i] : nullptr;
   }
   const long long nblocks = (s == 2) ? p->tc_nblk2 : p->tc_nblk0;
   if (nblocks == 0) return cudaSuccess;
-  tcprep_kernel<<<(unsigned)((nblocks + 7) / 8), 256, 0, st>>>(p->lmax, s, nreal, alm, blkofs, nblocks,
-                                                               (const float2 *)tab, (unsigned char *)out);
+  const long long warps = nblocks * (nc / 32);
+  tcprep_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(p->lmax, s, nreal, nc, alm, blkofs, nblocks,
+                                                             (const float2 *)tab, (unsigned char *)out);
   return cudaGetLastError();
 }
 
+// Realisations per launch and coefficient-tile bytes per block at a plan's order.
+int tc_realisations(int nder) { return tc_cols(nder) / 4; }
+size_t tc_btile_bytes(int nder) { return btile_bytes(tc_cols(nder)); }
 // Rings per CTA: spin 2 takes 64 north rings with their mirrors, spin 0 128 north rings.
-int tc_realisations() { return kUmmaReal; }
 int tc_ring_blocks(const tl_plan *p, int spin) {
   return spin == 2 ? (2 * p->nside + 63) / 64 : (2 * p->nside + 127) / 128;
 }
 
-// Dynamic shared memory: two tile buffers of NJ x 8 KB + 4 KB of coefficient tiles,
-// at least the size that keeps the CTAs per SM within the tensor memory
-// (512 columns per SM): 2 CTAs of 256 columns (76 KB) or 1 of 512 (114 KB).
-static size_t umma_smem(int nder) {
-  const int nj = nder + 1;
-  const size_t need = 2 * (size_t)umma_buf_bytes(nj);
-  const int need_cols = (nj + 2) * kUmmaCols;
-  const size_t floor_b = need_cols <= 128 ? 46 * 1024 : need_cols <= 256 ? 76 * 1024 : 114 * 1024;
+// Dynamic shared memory: two coefficient tiles and the spin-2 exchange area, raised
+// to the size that keeps the CTAs per SM within the tensor memory (512 columns per
+// SM): 4 CTAs (46 KB), 2 (76 KB) or 1 (114 KB).
+template <int CTAS, int NC> static size_t umma_smem() {
+  const size_t floor_b = CTAS >= 4 ? 46 * 1024 : CTAS == 2 ? 76 * 1024 : 114 * 1024;
+  const size_t need = 2 * btile_bytes(NC) + kXchBytes;
   return need > floor_b ? need : floor_b;
 }
 
-static TcDesc make_desc(const tl_plan *p, int spin, int nreal, void *d7a, void *d7b, long long rstride,
-                        long long rstride_p) {
+static TcDesc make_desc(const tl_plan *p, int spin, int nreal, const void *btiles, void *d7a, void *d7b,
+                        long long rstride) {
   TcDesc D;
   memset(&D, 0, sizeof D);
   D.rt = p->ring;
@@ -674,20 +756,20 @@ static TcDesc make_desc(const tl_plan *p, int spin, int nreal, void *d7a, void *
   D.nreal = nreal;
   D.blk = spin == 2 ? p->tc_blk2 : p->tc_blk0;
   D.step = spin == 2 ? p->tc_step2 : p->tc_step0;
-  D.b = (const unsigned char *)(spin == 2 ? p->tc_b2 : p->tc_b0);
-  D.bp = (const unsigned char *)p->tc_bp;
+  D.b = (const unsigned char *)btiles;
   D.d7a = (float2 *)d7a;
   D.d7b = (float2 *)d7b;
   D.rstride = rstride;
-  D.rstride_p = rstride_p;
   D.err = p->dev_err;
   return D;
 }
 
-// Write the descriptor of a plan's spin-0 or spin-2 work (nreal realisations) to dst.
-void tc_desc_write(const tl_plan *p, int spin, int nreal, void *dst) {
-  const TcDesc d = spin == 2 ? make_desc(p, 2, nreal, p->d7_Q, p->d7_U, p->d7_rstride, 0)
-                             : make_desc(p, 0, nreal, p->d7_T, p->d7_P, p->d7_rstride, p->d7p_rstride);
+// Write the descriptor of a plan's work for nreal realisations to dst: which = 0
+// temperature, 1 lensing potential, 2 polarisation.
+void tc_desc_write(const tl_plan *p, int which, int nreal, void *dst) {
+  const TcDesc d = which == 2   ? make_desc(p, 2, nreal, p->tc_b2, p->d7_Q, p->d7_U, p->d7_rstride)
+                   : which == 1 ? make_desc(p, 0, nreal, p->tc_bp, p->d7_P, nullptr, p->d7p_rstride)
+                                : make_desc(p, 0, nreal, p->tc_b0, p->d7_T, nullptr, p->d7_rstride);
   memcpy(dst, &d, sizeof d);
 }
 size_t tc_desc_bytes() { return sizeof(TcDesc); }
@@ -699,29 +781,34 @@ static cudaError_t set_smem(K kernel, size_t smem) {
 
 template <int NDER, int MODE>
 static cudaError_t u2(const tl_plan *p, int nreal, void *dq, void *du, long long rstride, cudaStream_t s) {
-  const size_t smem = umma_smem(NDER);
+  typedef typename Tc<NDER, MODE>::TM TM;
+  const size_t smem = umma_smem<TM::ctas, Tc<NDER, MODE>::NC>();
   TL_CUDA_TRY(set_smem(legendre_spin2_umma<NDER, MODE>, smem));
   dim3 grid(tc_ring_blocks(p, 2), p->mmax + 1);
-  legendre_spin2_umma<NDER, MODE><<<grid, kUmmaThreads, smem, s>>>(make_desc(p, 2, nreal, dq, du, rstride, 0));
+  legendre_spin2_umma<NDER, MODE>
+      <<<grid, kUmmaThreads, smem, s>>>(make_desc(p, 2, nreal, p->tc_b2, dq, du, rstride));
   return cudaGetLastError();
 }
 
-template <int NDER, int MODE, bool PHI>
-static cudaError_t u0(const tl_plan *p, int nreal, void *d7, void *d7p, long long rstride, long long rstride_p,
+template <int NDER, int MODE, int CNC>
+static cudaError_t u0(const tl_plan *p, int nreal, const void *btiles, void *d7, long long rstride,
                       cudaStream_t s) {
-  const size_t smem = umma_smem(NDER);
-  TL_CUDA_TRY(set_smem(legendre_spin0_umma<NDER, MODE, PHI>, smem));
+  typedef TmemMap<NDER + 1, MODE, CNC> TM;
+  const size_t smem = umma_smem<TM::ctas, CNC>();
+  TL_CUDA_TRY(set_smem(legendre_spin0_umma<NDER, MODE, CNC>, smem));
   dim3 grid(tc_ring_blocks(p, 0), p->mmax + 1);
-  legendre_spin0_umma<NDER, MODE, PHI><<<grid, kUmmaThreads, smem, s>>>(make_desc(p, 0, nreal, d7, d7p, rstride, rstride_p));
+  legendre_spin0_umma<NDER, MODE, CNC>
+      <<<grid, kUmmaThreads, smem, s>>>(make_desc(p, 0, nreal, btiles, d7, nullptr, rstride));
   return cudaGetLastError();
 }
 
 template <int NDER, int MODE>
 static cudaError_t up(const void *descs, const void *items, int nitems, int *counter, int grid, cudaStream_t s) {
-  const size_t smem = umma_smem(NDER);
+  typedef typename Tc<NDER, MODE>::TM TM;
+  const size_t smem = umma_smem<TM::ctas, Tc<NDER, MODE>::NC>();
   TL_CUDA_TRY(set_smem(legendre_umma_persistent<NDER, MODE>, smem));
-  legendre_umma_persistent<NDER, MODE><<<grid, kUmmaThreads, smem, s>>>((const TcDesc *)descs, (const int4 *)items, nitems,
-                                                               counter);
+  legendre_umma_persistent<NDER, MODE>
+      <<<grid, kUmmaThreads, smem, s>>>((const TcDesc *)descs, (const int4 *)items, nitems, counter);
   return cudaGetLastError();
 }
 
@@ -741,6 +828,7 @@ cudaError_t launch_legendre_tc_persistent(int nder, int precision, const void *d
 
 cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void *dq, void *du, long long rstride,
                                      cudaStream_t s) {
+  if (nder != p->tc_nder) return cudaErrorInvalidValue;
   const bool x3 = p->precision == TL_MIXED_TF32x3;
   switch (nder) {
 #define CASE(n) \
@@ -751,24 +839,38 @@ cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, bool phi, void *d7, void *d7p,
-                                     long long rstride, long long rstride_p, cudaStream_t s) {
+// nder: the plan's tc_nder (a field) or 1 (the lensing potential); the columns are
+// the plan's either way (its coefficient tiles have that width)
+cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, const void *btiles, void *d7,
+                                     long long rstride, cudaStream_t s) {
   const bool x3 = p->precision == TL_MIXED_TF32x3;
+  const int nc = tc_cols(p->tc_nder);
+  if (nder != p->tc_nder && nder != 1) return cudaErrorInvalidValue;
+  if (nder == 1) {
+    if (nc == 64) return x3 ? u0<1, 3, 64>(p, nreal, btiles, d7, rstride, s) : u0<1, 1, 64>(p, nreal, btiles, d7, rstride, s);
+    return x3 ? u0<1, 3, 32>(p, nreal, btiles, d7, rstride, s) : u0<1, 1, 32>(p, nreal, btiles, d7, rstride, s);
+  }
   switch (nder) {
-#define CASE(n)                                                                                   \
-  case n:                                                                                         \
-    if (phi)                                                                                      \
-      return x3 ? u0<n, 3, true>(p, nreal, d7, d7p, rstride, rstride_p, s)                        \
-                : u0<n, 1, true>(p, nreal, d7, d7p, rstride, rstride_p, s);                       \
-    return x3 ? u0<n, 3, false>(p, nreal, d7, d7p, rstride, rstride_p, s)                         \
-              : u0<n, 1, false>(p, nreal, d7, d7p, rstride, rstride_p, s);
+#define CASE(n)                                                                         \
+  case n:                                                                               \
+    return x3 ? u0<n, 3, tc_cols(n)>(p, nreal, btiles, d7, rstride, s)                  \
+              : u0<n, 1, tc_cols(n)>(p, nreal, btiles, d7, rstride, s);
     TL_TC_ORDERS(CASE)
 #undef CASE
   }
   return cudaErrorInvalidValue;
 }
 
-// The persistent kernel's dynamic shared memory (for the grid-size choice).
-size_t tc_persistent_smem(int nder) { return umma_smem(nder); }
+// CTAs per SM that the persistent kernel's tensor memory allows (for the grid size).
+int tc_persistent_ctas(int nder, int precision) {
+  const bool x3 = precision == TL_MIXED_TF32x3;
+  switch (nder) {
+#define CASE(n) \
+  case n: return x3 ? Tc<n, 3>::TM::ctas : Tc<n, 1>::TM::ctas;
+    TL_TC_ORDERS(CASE)
+#undef CASE
+  }
+  return 1;
+}
 
 }  // namespace tl

@@ -91,7 +91,7 @@ static void free_plan(tl_plan *p) {
     for (int i = 0; i < 8; ++i)
       if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   if (p->timing)
-    for (int i = 0; i < 3 * 8; ++i)
+    for (int i = 0; i < 3 * TL_MAX_BATCH; ++i)
       if (p->evr[i]) cudaEventDestroy(p->evr[i]);
   free(p);
 }
@@ -168,8 +168,8 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   const size_t plane = (size_t)p->nrings * (p->mmax + 1) * t2;
   const bool pol = (spins & TL_SPIN_QU) != 0;
   const bool tc = (precision == TL_MIXED_TF32 || precision == TL_MIXED_TF32x3);
-  p->batch = tc ? tc_realisations() : 1;
   p->tc_nder = order > 1 ? order : 1;
+  p->batch = tc ? tc_realisations(p->tc_nder) : 1;
   const int nplanes = tc ? p->tc_nder + 1 : order + 1;  // D7 planes per field and realisation
   p->d7_rstride = (long long)nplanes * p->nrings * (p->mmax + 1);
   p->d7p_rstride = 2LL * p->nrings * (p->mmax + 1);
@@ -202,13 +202,14 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
     TRY_CUDA(upload(&p->tc_blk0, b0, B));
     TRY_CUDA(dalloc((void **)&p->tc_step0, 64 * (size_t)n0, B));
     TRY_CUDA(launch_tcstep(p, 0, p->tc_blk0, p->tab0, p->tc_step0, 0));
-    TRY_CUDA(dalloc(&p->tc_b0, 2048 * (size_t)n0, B));
-    TRY_CUDA(dalloc(&p->tc_bp, 2048 * (size_t)n0, B));
+    const size_t bt = tc_btile_bytes(p->tc_nder);
+    TRY_CUDA(dalloc(&p->tc_b0, bt * (size_t)n0, B));
+    TRY_CUDA(dalloc(&p->tc_bp, bt * (size_t)n0, B));
     if (pol) {
       TRY_CUDA(upload(&p->tc_blk2, b2, B));
       TRY_CUDA(dalloc((void **)&p->tc_step2, 64 * (size_t)(n2 > 0 ? n2 : 1), B));
       TRY_CUDA(launch_tcstep(p, 2, p->tc_blk2, p->tab2, p->tc_step2, 0));
-      TRY_CUDA(dalloc(&p->tc_b2, 2048 * (size_t)(n2 > 0 ? n2 : 1), B));
+      TRY_CUDA(dalloc(&p->tc_b2, bt * (size_t)(n2 > 0 ? n2 : 1), B));
     }
   }
   TRY_CUDA(dalloc((void **)&p->dev_err, sizeof(int), B));
@@ -225,7 +226,7 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   if (p->timing)
     for (int i = 0; i < 8; ++i) TRY_CUDA(cudaEventCreate(&p->ev[i]));
   if (p->timing)
-    for (int i = 0; i < 3 * 8; ++i) TRY_CUDA(cudaEventCreate(&p->evr[i]));
+    for (int i = 0; i < 3 * TL_MAX_BATCH; ++i) TRY_CUDA(cudaEventCreate(&p->evr[i]));
   return TL_OK;
 }
 
@@ -291,6 +292,28 @@ extern "C" tl_status tl_plan_device_error(tl_plan *p) {
 }
 
 extern "C" int tl_plan_maps_per_field(const tl_plan *p) { return p ? p->nmaps : 0; }
+extern "C" int tl_plan_batch(const tl_plan *p) { return p ? p->batch : 0; }
+
+extern "C" long long tl_plan_batch_launches(const tl_plan *p, int nreal, int with_phi) {
+  if (!p || nreal < 0) return -1;
+  const bool pol = (p->spins & TL_SPIN_QU) != 0, phi = with_phi != 0;
+  const long long G = p->fft_ngroups;  // one ring-FFT launch per ring group
+  if (p->batch > 1) {
+    // per batch: coefficient tiles and Legendre launch of T, the potential and Q/U
+    const long long chunks = (nreal + p->batch - 1) / p->batch;
+    const long long per_chunk = 2 + (phi ? 2 : 0) + (pol ? 2 : 0);
+    // per realisation: deflection FFT, derivative-map FFT, gather
+    return chunks * per_chunk + (long long)nreal * ((phi ? G : 0) + G + 1);
+  }
+  const bool fuse = phi && p->order >= 1;
+  long long per = 0;
+  if (phi && !fuse) per += 2 + G;  // stand-alone deflection: prep, Legendre, FFT
+  per += 2 + (fuse ? 1 : 0);       // spin-0 prep (T, and phi when fused), Legendre
+  if (fuse) per += G;              // deflection FFT
+  if (pol) per += 2;               // spin-2 prep, Legendre
+  per += G + 1;                    // derivative-map FFT, gather
+  return (long long)nreal * per;
+}
 
 // ---------------------------------------------------------------------------
 // stages
@@ -391,7 +414,7 @@ tl_status lens_stage_after_legendre(tl_plan *p, int nreal, bool phi, void *const
   void *ath = p->alpha, *aph = (char *)p->alpha + mapb;
   p->nevr = 0;
   for (int r = 0; r < nreal; ++r) {
-      const bool tm = p->timing && r < 8;
+      const bool tm = p->timing && r < TL_MAX_BATCH;
       if (tm) cudaEventRecord(p->evr[3 * r], s);
       const size_t off = (size_t)r * p->d7_rstride * t2, offp = (size_t)r * p->d7p_rstride * t2;
       const void *planes[4] = {(char *)p->d7_T + off, pol ? (char *)p->d7_Q + off : nullptr,
@@ -429,12 +452,12 @@ static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, cons
   mark(p, 0, s);
   if (p->batch > 1) {
     // ---- tensor-core Legendre stage for all realisations of the chunk
-    const bool fuse = phi;  // tc_nder >= 1 always
+    // the temperature at all orders, the lensing potential at j <= 1 (its own launch)
     TRY_CUDA(launch_tcprep(p, 0, nreal, aT, nullptr, p->tc_blk0, p->tab0, p->tc_b0, s));
-    if (fuse) TRY_CUDA(launch_tcprep(p, 0, nreal, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
+    if (phi) TRY_CUDA(launch_tcprep(p, 0, nreal, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
     mark(p, 1, s);
-    TRY_CUDA(launch_legendre_spin0_tc(p, p->tc_nder, nreal, fuse, p->d7_T, p->d7_P, p->d7_rstride,
-                                      p->d7p_rstride, s));
+    TRY_CUDA(launch_legendre_spin0_tc(p, p->tc_nder, nreal, p->tc_b0, p->d7_T, p->d7_rstride, s));
+    if (phi) TRY_CUDA(launch_legendre_spin0_tc(p, 1, nreal, p->tc_bp, p->d7_P, p->d7p_rstride, s));
     mark(p, 2, s);
     mark(p, 3, s);
     if (pol) TRY_CUDA(launch_tcprep(p, 2, nreal, aE, aB, p->tc_blk2, p->tab2, p->tc_b2, s));
@@ -543,8 +566,8 @@ static tl_status forward_derivs(tl_plan *p, const double *alm_T, const double *a
     const double *aT[1] = {alm_T}, *aE[1] = {alm_E}, *aB[1] = {alm_B}, *aP[1] = {alm_phi};
     TRY_CUDA(launch_tcprep(p, 0, 1, aT, nullptr, p->tc_blk0, p->tab0, p->tc_b0, s));
     if (alm_phi) TRY_CUDA(launch_tcprep(p, 0, 1, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
-    TRY_CUDA(launch_legendre_spin0_tc(p, p->tc_nder, 1, alm_phi != nullptr, p->d7_T, p->d7_P, p->d7_rstride,
-                                      p->d7p_rstride, s));
+    TRY_CUDA(launch_legendre_spin0_tc(p, p->tc_nder, 1, p->tc_b0, p->d7_T, p->d7_rstride, s));
+    if (alm_phi) TRY_CUDA(launch_legendre_spin0_tc(p, 1, 1, p->tc_bp, p->d7_P, p->d7p_rstride, s));
     if (pol) {
       TRY_CUDA(launch_tcprep(p, 2, 1, aE, aB, p->tc_blk2, p->tab2, p->tc_b2, s));
       TRY_CUDA(launch_legendre_spin2_tc(p, p->tc_nder, 1, p->d7_Q, p->d7_U, p->d7_rstride, s));

@@ -18,9 +18,9 @@ def _gpu():
         pytest.skip("no GPU")
 
 
-# groups: (8, 16) x 10, (16, 40) x 2, (32, 64), (32, 100): two waves of up to eight per group
-NSIDES = [8, 16, 8, 32, 16, 8, 32, 8, 8, 8, 8, 8, 8, 8]
-LMAXS = [16, 40, 16, 64, 40, 16, 100, 16, 16, 16, 16, 16, 16, 16]
+# groups: (8, 16) x 18, (16, 40) x 2, (32, 64), (32, 100): two waves of up to sixteen per group
+NSIDES = [8, 16, 8, 32, 16, 8, 32] + [8] * 15
+LMAXS = [16, 40, 16, 64, 40, 16, 100] + [16] * 15
 
 
 def _skies():

@@ -113,10 +113,10 @@ def test_lens_tensor_core_forms(nside, lmax, order, precision, tol):
 
 @pytest.mark.parametrize("precision", [api.MIXED_TF32x3, api.MIXED_FP32, api.FP64])
 def test_lens_batch_equals_single_calls(precision):
-    """tl_lens_batch over 10 realisations (on tensor-core plans a group of eight that
-    shares one basis, then a group of two) gives what ten tl_lens calls give."""
+    """tl_lens_batch over 20 realisations (on tensor-core plans a group of sixteen
+    that shares one basis, then a group of four) gives what twenty tl_lens calls give."""
     nside, lmax, order = 32, 64, 4
-    skies = [to_dev(sky(nside, lmax, pol=True, seeds=(10 + i, 20 + i, 30 + i), b_scale=0.3)) for i in range(10)]
+    skies = [to_dev(sky(nside, lmax, pol=True, seeds=(10 + i, 20 + i, 30 + i), b_scale=0.3)) for i in range(20)]
     plan = api.Plan(nside, lmax, order, pol=True, precision=precision)
     try:
         outs = [o.cpu().numpy() for o in plan.lens_batch(skies)]
