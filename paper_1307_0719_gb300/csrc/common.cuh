@@ -80,6 +80,10 @@ struct tl_plan {
   int tc_nder;           // derivative orders carried there (max(order, 1))
   long long *tc_blk0, *tc_blk2;   // [lmax+1] first block of each m (spin 0 / spin 2)
   long long tc_nblk0, tc_nblk2;   // blocks in all
+  // start tables (T, potential, Q/U): first contributing block per unit and the
+  // recurrence state there
+  int *tc_bs0, *tc_bsp, *tc_bs2;
+  float *tc_st0, *tc_stp, *tc_st2;
   float *tc_step0, *tc_step2;     // [blocks][16]: A_{l+1} x 8, m s/(l(l+1)) x 8
   void *tc_b0, *tc_bp, *tc_b2;    // [blocks] 2 KB coefficient tiles (TF32 hi, lo; 32 columns x 8 l)
   int *dev_err;                   // set by a kernel whose bounded wait timed out
@@ -150,10 +154,14 @@ cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *cons
                           const long long *blkofs, const void *tab, void *out, cudaStream_t st);
 cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void *dq, void *du, long long rstride,
                                      cudaStream_t s);
-// spin-0 field (temperature at nder = tc_nder, the lensing potential at nder = 1)
-// from its coefficient tiles btiles into the planes d7
-cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, const void *btiles, void *d7,
-                                     long long rstride, cudaStream_t s);
+// spin-0 field (which = 0: temperature at tc_nder, 1: the lensing potential at
+// nder = 1) from its coefficient tiles into the planes d7
+cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int which, int nreal, void *d7, long long rstride,
+                                     cudaStream_t s);
+// start tables of the tensor-core Legendre stage (which: 0 T, 1 potential, 2 Q/U)
+cudaError_t launch_tcstart(const tl_plan *p, int which, int *bstart, float *state, cudaStream_t s);
+size_t tc_start_state_bytes(const tl_plan *p, int which);
+size_t tc_start_units(const tl_plan *p, int which);
 cudaError_t launch_bluestein_setup(tl_plan *p, cudaStream_t s);
 // CTAs per m of the tensor-core Legendre kernels (128 rings each), and the CTAs per
 // SM that the persistent kernel's tensor memory allows

@@ -180,10 +180,16 @@ struct TcDesc {
   int nside, lmax, mmax, nrings, nreal;
   const long long *blk;          // first 8-l block of each m
   const float *step;             // per block: A_{l+1} x 8, m s/(l(l+1)) x 8
-  const unsigned char *b;        // per block 2 KB: coefficient tile hi [32 x 8] then lo
+  const unsigned char *b;        // per block: coefficient tile hi [NC x 8] then lo
   float2 *d7a, *d7b;             // spin 0: the field's planes; spin 2: Q, U planes
   long long rstride;             // T2 elements between realisations' planes
   int *err;                      // set to 1 when a wait times out
+  // start table (plan-time, tcstart_kernel): per unit m * nrblk + rblk the first
+  // 8-l block in which one of its rings contributes, and every ring's recurrence
+  // state at the start of that block: [unit][2 NJ + 1][128] (a, b, scale)
+  const int *bstart;
+  const float *state;
+  int nrblk;
 };
 
 // Per-CTA tcgen05 state (identical in every thread). The four mbarriers are
@@ -283,6 +289,31 @@ __device__ __forceinline__ void issue_block(uint32_t tmem, uint32_t aset, uint64
 
 __device__ __forceinline__ int unit_l0(int m, bool spin2) { return spin2 ? (m > 2 ? m : 2) : m; }
 
+// ring of compute thread tid in ring block rblk (spin 2: 64 north rings, then
+// their mirrors; spin 0: 128 north rings); inactive threads past the equator
+// take ring 0 and contribute nothing
+template <bool SPIN2>
+__device__ __forceinline__ int unit_ring(const TcDesc &D, int rblk, int tid, bool &active) {
+  const int rn = SPIN2 ? rblk * 64 + (tid & 63) : rblk * 128 + tid;
+  active = rn < 2 * D.nside;
+  if (!active) return 0;
+  return (SPIN2 && tid >= 64) ? D.nrings - 1 - rn : rn;
+}
+
+// recurrence state at l0: mu_{l0} in b, mu_{l0-1} = 0 in a, scale sc
+template <int NDER, bool SPIN2>
+__device__ __forceinline__ void unit_seed(const TcDesc &D, int r, int m, bool active, float (&a)[NDER + 1],
+                                          float (&b)[NDER + 1], int &sc) {
+  const double invL = 1.0 / (double)(D.lmax + 1);
+  if (SPIN2)
+    (void)seed_spin2<float, NDER>(D.rt, D.lnorm0, r, m, invL, b, sc);
+  else
+    seed_spin0<float, NDER>(D.rt, D.lnorm0, r, m, invL, b, sc);
+  if (!active) sc = -1000000;  // contributes nothing
+#pragma unroll
+  for (int j = 0; j <= NDER; ++j) a[j] = 0.0f;
+}
+
 // One (m, ring block) unit: recurrence and tiles (compute warps), MMAs (issuing
 // warp). NB: the kernel's buffer count (the same for every unit a CTA runs, so
 // that the barriers' phases follow one block count). Leaves the accumulators
@@ -298,13 +329,17 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
   const int l0 = unit_l0(m, SPIN2);
   const int nblk = (D.lmax >= l0) ? (D.lmax - l0 + 8) / 8 : 0;
   const long long b0 = D.blk[m];
+  const long long unit = (long long)m * D.nrblk + rblk;
+  // blocks before bs contribute nothing for any ring of the unit (start table)
+  const int bs = D.bstart ? D.bstart[unit] : 0;
+  const int nrun = nblk - bs;
   const uint32_t g0 = U.count;
   bool bad = false;
   if (tid >= kComputeThreads) {
     // ---- issuing warp: one lane waits for each block's tiles and issues its MMAs
     if (tid == kComputeThreads) {
       const uint64_t dB0 = umma_desc(smem_u32(sm));
-      for (int blk = 0; blk < nblk; ++blk) {
+      for (int blk = 0; blk < nrun; ++blk) {
         const uint32_t g = g0 + (uint32_t)blk, i = buf_of<NB>(g);
         if (!mbar_wait(bar_full(U, i), phase_of<NB>(g), U.abort)) {
           bad = true;
@@ -319,30 +354,25 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
   } else {
     // ---- compute warps: one ring per thread (tensor-memory lane tid)
     const RingTable &rt = D.rt;
-    int r;
     bool active;
-    if (SPIN2) {
-      const int rn = rblk * 64 + (tid & 63);
-      active = rn < 2 * D.nside;
-      r = active ? (tid >= 64 ? D.nrings - 1 - rn : rn) : 0;
-    } else {
-      const int rn = rblk * 128 + tid;
-      active = rn < 2 * D.nside;
-      r = active ? rn : 0;
-    }
+    const int r = unit_ring<SPIN2>(D, rblk, tid, active);
     const uint32_t lane = U.tmem + ((uint32_t)((tid >> 5) * 32) << 16);
-    const double invL = 1.0 / (double)(D.lmax + 1);
     Leib<float, NDER> LC;
-    leibniz_coefs<float, NDER>(rt.z[r], rt.sint[r], invL, LC);
+    leibniz_coefs<float, NDER>(rt.z[r], rt.sint[r], 1.0 / (double)(D.lmax + 1), LC);
     float a[NJ], b[NJ];
     int sc;
-    if (SPIN2)
-      (void)seed_spin2<float, NDER>(rt, D.lnorm0, r, m, invL, b, sc);
-    else
-      seed_spin0<float, NDER>(rt, D.lnorm0, r, m, invL, b, sc);
-    if (!active) sc = -1000000;  // contributes nothing
+    if (D.bstart) {
+      // the state at block bs, as the recurrence from l0 leaves it
+      const float *st = D.state + unit * (2 * NJ + 1) * kComputeThreads + tid;
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) a[j] = 0.0f;
+      for (int j = 0; j < NJ; ++j) {
+        a[j] = __ldg(st + j * kComputeThreads);
+        b[j] = __ldg(st + (NJ + j) * kComputeThreads);
+      }
+      sc = __float_as_int(__ldg(st + 2 * NJ * kComputeThreads));
+    } else {
+      unit_seed<NDER, SPIN2>(D, r, m, active, a, b, sc);
+    }
     const float X = (float)rt.z[r];
     // the next block's step factors and coefficient tile (BT / 128 bytes per
     // thread), loaded one block ahead
@@ -362,9 +392,10 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
 #pragma unroll
       for (int q = 0; q < QV; ++q) nbq[q] = __ldg(bt + q * kComputeThreads + tid);
     };
-    if (nblk > 0) prefetch(0);
-    for (int blk = 0; blk < nblk; ++blk) {
-      const uint32_t g = g0 + (uint32_t)blk, i = buf_of<NB>(g);
+    if (nrun > 0) prefetch(bs);
+    for (int k = 0; k < nrun; ++k) {
+      const int blk = bs + k;
+      const uint32_t g = g0 + (uint32_t)k, i = buf_of<NB>(g);
       const float Av[8] = {nA0.x, nA0.y, nA0.z, nA0.w, nA1.x, nA1.y, nA1.z, nA1.w};
       const float Cv[8] = {nC0.x, nC0.y, nC0.z, nC0.w, nC1.x, nC1.y, nC1.z, nC1.w};
       float4 bq[QV];
@@ -390,9 +421,9 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       if ((tid & 31) == 0) mbar_arrive(bar_full(U, i));
     }
   }
-  U.count = g0 + (uint32_t)nblk;
+  U.count = g0 + (uint32_t)nrun;
   // the last commit covers every MMA issued before it
-  if (!bad && nblk > 0 &&
+  if (!bad && nrun > 0 &&
       !mbar_wait(bar_done(U, buf_of<NB>(U.count - 1)), phase_of<NB>(U.count - 1), U.abort))
     bad = true;
   if (bad) *U.abort = 1;
@@ -401,7 +432,7 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
     return 0;
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return nblk;
+  return nrun;
 }
 
 // Dynamic shared memory of a CTA: two coefficient tile buffers, then the spin-2
@@ -480,7 +511,11 @@ __device__ __forceinline__ void u0_unit(const TcDesc &D, int m, int rblk, unsign
       for (int h = 0; h < NC / 32; ++h) {
         float v[32];
         tmem_ld32(lane_base + (uint32_t)(NC * j + 32 * h), v);
-        if (!active || nblk == 0) continue;
+        if (!active) continue;
+        if (nblk == 0) {  // nothing contributed: the accumulators were not written
+#pragma unroll
+          for (int c = 0; c < 32; ++c) v[c] = 0.f;
+        }
 #pragma unroll
         for (int rho = 0; rho < 8; ++rho) {
           if (8 * h + rho >= D.nreal) break;
@@ -609,6 +644,66 @@ __global__ void __launch_bounds__(kUmmaThreads, (Tc<NDER, MODE>::TM::ctas))
     if (U.failed) break;  // uniform: set after a block-wide vote
   }
   umma_close<TM::cols, TM::NB>(D, U);
+}
+
+// Plan-time start table (see TcDesc): one CTA of 128 threads per unit runs the
+// recurrence block by block, without the contraction, until one of its rings has
+// reached scale 0 (a basis value that is not gated off), and records every ring's
+// state at the start of that block. The launch kernels resume from it with the
+// same arithmetic, so their results are those of a run from l0. Units in which no
+// ring contributes get bstart = their block count.
+template <int NDER, bool SPIN2>
+__global__ void __launch_bounds__(kComputeThreads) tcstart_kernel(TcDesc D, int *__restrict__ bstart,
+                                                                   float *__restrict__ state) {
+  constexpr int NJ = NDER + 1;
+  const int rblk = blockIdx.x, m = blockIdx.y, tid = threadIdx.x;
+  const int l0 = unit_l0(m, SPIN2);
+  const int nblk = (D.lmax >= l0) ? (D.lmax - l0 + 8) / 8 : 0;
+  const long long b0 = D.blk[m];
+  const long long unit = (long long)m * D.nrblk + rblk;
+  bool active;
+  const int r = unit_ring<SPIN2>(D, rblk, tid, active);
+  Leib<float, NDER> LC;
+  leibniz_coefs<float, NDER>(D.rt.z[r], D.rt.sint[r], 1.0 / (double)(D.lmax + 1), LC);
+  float a[NJ], b[NJ];
+  int sc;
+  unit_seed<NDER, SPIN2>(D, r, m, active, a, b, sc);
+  const float X = (float)D.rt.z[r];
+  float *st = state + unit * (2 * NJ + 1) * kComputeThreads + tid;
+  int first = nblk;
+  for (int blk = 0; blk < nblk; ++blk) {
+    const float4 *stp = (const float4 *)(D.step + (b0 + blk) * 16);
+    const float4 A0 = __ldg(stp), A1 = __ldg(stp + 1);
+    float4 C0 = make_float4(0.f, 0.f, 0.f, 0.f), C1 = C0;
+    if (SPIN2) {
+      C0 = __ldg(stp + 2);
+      C1 = __ldg(stp + 3);
+    }
+    const float Av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
+    const float Cv[8] = {C0.x, C0.y, C0.z, C0.w, C1.x, C1.y, C1.z, C1.w};
+    float sa[NJ], sb[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      sa[j] = a[j];
+      sb[j] = b[j];
+    }
+    const int ssc = sc;
+    float buf0[NJ][4], buf1[NJ][4];
+    steps_gated<0, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf0);
+    steps_gated<4, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf1);
+    // a ring can have contributed in this block only if its scale is 0 at the end
+    if (__syncthreads_or(sc == 0)) {
+      first = blk;
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        st[j * kComputeThreads] = sa[j];
+        st[(NJ + j) * kComputeThreads] = sb[j];
+      }
+      st[2 * NJ * kComputeThreads] = __int_as_float(ssc);
+      break;
+    }
+  }
+  if (tid == 0) bstart[unit] = first;
 }
 
 // ---------------------------------------------------------------------------
@@ -743,8 +838,10 @@ template <int CTAS, int NC> static size_t umma_smem() {
   return need > floor_b ? need : floor_b;
 }
 
-static TcDesc make_desc(const tl_plan *p, int spin, int nreal, const void *btiles, void *d7a, void *d7b,
+// which: 0 temperature, 1 lensing potential, 2 polarisation (its start table)
+static TcDesc make_desc(const tl_plan *p, int which, int nreal, const void *btiles, void *d7a, void *d7b,
                         long long rstride) {
+  const int spin = which == 2 ? 2 : 0;
   TcDesc D;
   memset(&D, 0, sizeof D);
   D.rt = p->ring;
@@ -761,6 +858,10 @@ static TcDesc make_desc(const tl_plan *p, int spin, int nreal, const void *btile
   D.d7b = (float2 *)d7b;
   D.rstride = rstride;
   D.err = p->dev_err;
+  D.nrblk = tc_ring_blocks(p, spin);
+  D.bstart = which == 2 ? p->tc_bs2 : which == 1 ? p->tc_bsp : p->tc_bs0;
+  D.state = which == 2 ? p->tc_st2 : which == 1 ? p->tc_stp : p->tc_st0;
+  if (!D.state) D.bstart = nullptr;  // no table: every unit starts at l0
   return D;
 }
 
@@ -768,7 +869,7 @@ static TcDesc make_desc(const tl_plan *p, int spin, int nreal, const void *btile
 // temperature, 1 lensing potential, 2 polarisation.
 void tc_desc_write(const tl_plan *p, int which, int nreal, void *dst) {
   const TcDesc d = which == 2   ? make_desc(p, 2, nreal, p->tc_b2, p->d7_Q, p->d7_U, p->d7_rstride)
-                   : which == 1 ? make_desc(p, 0, nreal, p->tc_bp, p->d7_P, nullptr, p->d7p_rstride)
+                   : which == 1 ? make_desc(p, 1, nreal, p->tc_bp, p->d7_P, nullptr, p->d7p_rstride)
                                 : make_desc(p, 0, nreal, p->tc_b0, p->d7_T, nullptr, p->d7_rstride);
   memcpy(dst, &d, sizeof d);
 }
@@ -791,14 +892,13 @@ static cudaError_t u2(const tl_plan *p, int nreal, void *dq, void *du, long long
 }
 
 template <int NDER, int MODE, int CNC>
-static cudaError_t u0(const tl_plan *p, int nreal, const void *btiles, void *d7, long long rstride,
-                      cudaStream_t s) {
+static cudaError_t u0(const tl_plan *p, int which, int nreal, void *d7, long long rstride, cudaStream_t s) {
   typedef TmemMap<NDER + 1, MODE, CNC> TM;
   const size_t smem = umma_smem<TM::ctas, CNC>();
   TL_CUDA_TRY(set_smem(legendre_spin0_umma<NDER, MODE, CNC>, smem));
   dim3 grid(tc_ring_blocks(p, 0), p->mmax + 1);
-  legendre_spin0_umma<NDER, MODE, CNC>
-      <<<grid, kUmmaThreads, smem, s>>>(make_desc(p, 0, nreal, btiles, d7, nullptr, rstride));
+  legendre_spin0_umma<NDER, MODE, CNC><<<grid, kUmmaThreads, smem, s>>>(
+      make_desc(p, which, nreal, which == 1 ? p->tc_bp : p->tc_b0, d7, nullptr, rstride));
   return cudaGetLastError();
 }
 
@@ -839,26 +939,58 @@ cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void
   return cudaErrorInvalidValue;
 }
 
-// nder: the plan's tc_nder (a field) or 1 (the lensing potential); the columns are
-// the plan's either way (its coefficient tiles have that width)
-cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int nder, int nreal, const void *btiles, void *d7,
-                                     long long rstride, cudaStream_t s) {
+// which = 0: the temperature at the plan's tc_nder; 1: the lensing potential at
+// NDER = 1. The columns are the plan's either way (its coefficient tiles have that width).
+cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int which, int nreal, void *d7, long long rstride,
+                                     cudaStream_t s) {
   const bool x3 = p->precision == TL_MIXED_TF32x3;
   const int nc = tc_cols(p->tc_nder);
-  if (nder != p->tc_nder && nder != 1) return cudaErrorInvalidValue;
-  if (nder == 1) {
-    if (nc == 64) return x3 ? u0<1, 3, 64>(p, nreal, btiles, d7, rstride, s) : u0<1, 1, 64>(p, nreal, btiles, d7, rstride, s);
-    return x3 ? u0<1, 3, 32>(p, nreal, btiles, d7, rstride, s) : u0<1, 1, 32>(p, nreal, btiles, d7, rstride, s);
+  if (which == 1) {
+    if (nc == 64) return x3 ? u0<1, 3, 64>(p, 1, nreal, d7, rstride, s) : u0<1, 1, 64>(p, 1, nreal, d7, rstride, s);
+    return x3 ? u0<1, 3, 32>(p, 1, nreal, d7, rstride, s) : u0<1, 1, 32>(p, 1, nreal, d7, rstride, s);
   }
-  switch (nder) {
+  if (which != 0) return cudaErrorInvalidValue;
+  switch (p->tc_nder) {
 #define CASE(n)                                                                         \
   case n:                                                                               \
-    return x3 ? u0<n, 3, tc_cols(n)>(p, nreal, btiles, d7, rstride, s)                  \
-              : u0<n, 1, tc_cols(n)>(p, nreal, btiles, d7, rstride, s);
+    return x3 ? u0<n, 3, tc_cols(n)>(p, 0, nreal, d7, rstride, s)                      \
+              : u0<n, 1, tc_cols(n)>(p, 0, nreal, d7, rstride, s);
     TL_TC_ORDERS(CASE)
 #undef CASE
   }
   return cudaErrorInvalidValue;
+}
+
+// Fill a start table (plan time): which as in make_desc; units of that spin.
+cudaError_t launch_tcstart(const tl_plan *p, int which, int *bstart, float *state, cudaStream_t s) {
+  TcDesc D = make_desc(p, which, 1, nullptr, nullptr, nullptr, 0);
+  D.bstart = nullptr;
+  D.state = nullptr;
+  const int spin = which == 2 ? 2 : 0;
+  const int nder = which == 1 ? 1 : p->tc_nder;
+  dim3 grid(tc_ring_blocks(p, spin), p->mmax + 1);
+  switch (nder) {
+#define CASE(n)                                                                                      \
+  case n:                                                                                            \
+    if (spin == 2)                                                                                   \
+      tcstart_kernel<n, true><<<grid, kComputeThreads, 0, s>>>(D, bstart, state);                    \
+    else                                                                                             \
+      tcstart_kernel<n, false><<<grid, kComputeThreads, 0, s>>>(D, bstart, state);                   \
+    return cudaGetLastError();
+    TL_TC_ORDERS(CASE)
+#undef CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Start-table bytes: the state of 128 rings (2 NJ + 1 words each) per unit.
+size_t tc_start_state_bytes(const tl_plan *p, int which) {
+  const int nj = (which == 1 ? 1 : p->tc_nder) + 1;
+  const size_t units = (size_t)(p->mmax + 1) * tc_ring_blocks(p, which == 2 ? 2 : 0);
+  return units * (2 * nj + 1) * kComputeThreads * sizeof(float);
+}
+size_t tc_start_units(const tl_plan *p, int which) {
+  return (size_t)(p->mmax + 1) * tc_ring_blocks(p, which == 2 ? 2 : 0);
 }
 
 // CTAs per SM that the persistent kernel's tensor memory allows (for the grid size).

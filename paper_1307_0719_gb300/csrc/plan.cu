@@ -84,6 +84,7 @@ static void free_plan(tl_plan *p) {
                   p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->adj_dbar, p->adj_ga, p->stage_alm,
                   p->stage_out,
                   p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2, p->dev_err,
+                  p->tc_bs0, p->tc_bsp, p->tc_bs2, p->tc_st0, p->tc_stp, p->tc_st2,
                   p->fft_rings};
   for (void *q : ptrs)
     if (q) cudaFree(q);
@@ -211,6 +212,15 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
       TRY_CUDA(launch_tcstep(p, 2, p->tc_blk2, p->tab2, p->tc_step2, 0));
       TRY_CUDA(dalloc(&p->tc_b2, bt * (size_t)(n2 > 0 ? n2 : 1), B));
     }
+    // start tables: where each unit's first contribution begins (identical results)
+    for (int which = 0; which < (pol ? 3 : 2); ++which) {
+      int **bs = which == 0 ? &p->tc_bs0 : which == 1 ? &p->tc_bsp : &p->tc_bs2;
+      float **st = which == 0 ? &p->tc_st0 : which == 1 ? &p->tc_stp : &p->tc_st2;
+      TRY_CUDA(dalloc((void **)bs, sizeof(int) * tc_start_units(p, which), B));
+      TRY_CUDA(dalloc((void **)st, tc_start_state_bytes(p, which), B));
+      TRY_CUDA(launch_tcstart(p, which, *bs, *st, 0));
+    }
+    TRY_CUDA(cudaDeviceSynchronize());
   }
   TRY_CUDA(dalloc((void **)&p->dev_err, sizeof(int), B));
   TRY_CUDA(cudaMemset(p->dev_err, 0, sizeof(int)));
@@ -456,8 +466,8 @@ static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, cons
     TRY_CUDA(launch_tcprep(p, 0, nreal, aT, nullptr, p->tc_blk0, p->tab0, p->tc_b0, s));
     if (phi) TRY_CUDA(launch_tcprep(p, 0, nreal, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
     mark(p, 1, s);
-    TRY_CUDA(launch_legendre_spin0_tc(p, p->tc_nder, nreal, p->tc_b0, p->d7_T, p->d7_rstride, s));
-    if (phi) TRY_CUDA(launch_legendre_spin0_tc(p, 1, nreal, p->tc_bp, p->d7_P, p->d7p_rstride, s));
+    TRY_CUDA(launch_legendre_spin0_tc(p, 0, nreal, p->d7_T, p->d7_rstride, s));
+    if (phi) TRY_CUDA(launch_legendre_spin0_tc(p, 1, nreal, p->d7_P, p->d7p_rstride, s));
     mark(p, 2, s);
     mark(p, 3, s);
     if (pol) TRY_CUDA(launch_tcprep(p, 2, nreal, aE, aB, p->tc_blk2, p->tab2, p->tc_b2, s));
@@ -566,8 +576,8 @@ static tl_status forward_derivs(tl_plan *p, const double *alm_T, const double *a
     const double *aT[1] = {alm_T}, *aE[1] = {alm_E}, *aB[1] = {alm_B}, *aP[1] = {alm_phi};
     TRY_CUDA(launch_tcprep(p, 0, 1, aT, nullptr, p->tc_blk0, p->tab0, p->tc_b0, s));
     if (alm_phi) TRY_CUDA(launch_tcprep(p, 0, 1, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
-    TRY_CUDA(launch_legendre_spin0_tc(p, p->tc_nder, 1, p->tc_b0, p->d7_T, p->d7_rstride, s));
-    if (alm_phi) TRY_CUDA(launch_legendre_spin0_tc(p, 1, 1, p->tc_bp, p->d7_P, p->d7p_rstride, s));
+    TRY_CUDA(launch_legendre_spin0_tc(p, 0, 1, p->d7_T, p->d7_rstride, s));
+    if (alm_phi) TRY_CUDA(launch_legendre_spin0_tc(p, 1, 1, p->d7_P, p->d7p_rstride, s));
     if (pol) {
       TRY_CUDA(launch_tcprep(p, 2, 1, aE, aB, p->tc_blk2, p->tab2, p->tc_b2, s));
       TRY_CUDA(launch_legendre_spin2_tc(p, p->tc_nder, 1, p->d7_Q, p->d7_U, p->d7_rstride, s));
