@@ -28,8 +28,14 @@
 namespace tl {
 
 // Increment-form geometry in float (see the header comment); pixel lookup in double.
+// Returns the expansion pixel q and, in float, the scaled offsets x = L dth,
+// y = L dph and cos 2 beta, sin 2 beta (no round trip through double).
+struct Geo32 {
+  long long q;
+  float x, y, c2b, s2b;
+};
 __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, double z, double s, double phi,
-                                      float ath, float aph, bool rot, Geo &g) {
+                                      float ath, float aph, bool rot, float Lf, Geo32 &g) {
   const float d2 = ath * ath + aph * aph;
   const float d = sqrtf(d2);
   float sh, ch;
@@ -54,16 +60,16 @@ __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, 
   if (phi2 < 0.0) phi2 += 2.0 * kPiD;
   const PixLoc lq = ang2loc(z2, omz2, phi2, nside);
   g.q = rt.first[lq.ring] + lq.idx;
-  g.dth = (double)(dthp - (float)(rt.theta[lq.ring] - rt.theta[ring]));
+  g.x = Lf * (dthp - (float)(rt.theta[lq.ring] - rt.theta[ring]));
   double dc = ring_phi(rt, lq.ring, lq.idx) - phi;  // centre offset, wrapped
   if (dc >= kPiD) dc -= 2.0 * kPiD;
   if (dc < -kPiD) dc += 2.0 * kPiD;
   float dph = dphp - (float)dc;
   if (dph >= (float)kPiD) dph -= 2.0f * (float)kPiD;
   if (dph < -(float)kPiD) dph += 2.0f * (float)kPiD;
-  g.dph = (double)dph;
-  g.c2b = 1.0;
-  g.s2b = 0.0;
+  g.y = Lf * dph;
+  g.c2b = 1.0f;
+  g.s2b = 0.0f;
   if (rot) {
     // t = (1 - a_th^2 h) e_th - a_ph a_th h e_ph - a_th sinc n, h = (1 - cos d)/d^2,
     // in the frame turned to phi_p: e_th = (z, 0, -s), e_ph = (0, 1, 0), n = (s, 0, z)
@@ -76,8 +82,8 @@ __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, 
     const float cb = Z * (tx * X + ty * Y) / rho - tz * rho;  // t . e_theta'
     const float sb = (-tx * Y + ty * X) / rho;                // t . e_phi'
     const float nrm = cb * cb + sb * sb;
-    g.c2b = (double)((cb * cb - sb * sb) / nrm);
-    g.s2b = (double)(2.0f * cb * sb / nrm);
+    g.c2b = (cb * cb - sb * sb) / nrm;
+    g.s2b = 2.0f * cb * sb / nrm;
   }
 }
 
@@ -114,23 +120,31 @@ __global__ void __launch_bounds__(256) gather_kernel(RingTable rt, int nside, lo
   const T ath = a_th[p], aph = a_ph[p];
   const bool rot = POL && rotate;
 
-  Geo g;
-  g.q = p;
-  g.dth = g.dph = 0.0;
-  g.c2b = 1.0;
-  g.s2b = 0.0;
+  long long q = p;
+  T x = (T)0, y = (T)0, c2 = (T)1, s2 = (T)0;
   if (ath != (T)0 || aph != (T)0) {
-    if (FAST && s >= 0.1 && (float)(ath * ath + aph * aph) < 4e-4f)
-      geo32(rt, nside, loc.ring, z, s, phi, (float)ath, (float)aph, rot, g);
-    else
+    if (FAST && s >= 0.1 && (float)(ath * ath + aph * aph) < 4e-4f) {
+      Geo32 g;
+      geo32(rt, nside, loc.ring, z, s, phi, (float)ath, (float)aph, rot, (float)Lnorm, g);
+      q = g.q;
+      x = (T)g.x;
+      y = (T)g.y;
+      c2 = (T)g.c2b;
+      s2 = (T)g.s2b;
+    } else {
+      Geo g;
       geo64(rt, nside, z, s, phi, (double)ath, (double)aph, rot, g);
+      q = g.q;
+      x = (T)(Lnorm * g.dth);
+      y = (T)(Lnorm * g.dph);
+      c2 = (T)g.c2b;
+      s2 = (T)g.s2b;
+    }
   }
-  const T x = (T)(Lnorm * g.dth), y = (T)(Lnorm * g.dph);
-  Tout[p] = taylor_eval<T, ORDER>(d3, npix, g.q, x, y);
+  Tout[p] = taylor_eval<T, ORDER>(d3, npix, q, x, y);
   if (POL) {
-    const T qv = taylor_eval<T, ORDER>(d3 + (long long)NM * npix, npix, g.q, x, y);
-    const T uv = taylor_eval<T, ORDER>(d3 + 2LL * NM * npix, npix, g.q, x, y);
-    const T c2 = (T)g.c2b, s2 = (T)g.s2b;
+    const T qv = taylor_eval<T, ORDER>(d3 + (long long)NM * npix, npix, q, x, y);
+    const T uv = taylor_eval<T, ORDER>(d3 + 2LL * NM * npix, npix, q, x, y);
     Qout[p] = c2 * qv + s2 * uv;
     Uout[p] = -s2 * qv + c2 * uv;
   }
