@@ -117,6 +117,48 @@ __device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, i
   __syncthreads();
 }
 
+// The top DIT pass of the inverse transform in Bluestein: as dit_pass (dir +1), but
+// each output p < n is multiplied by the chirp e^{i pi p^2/n} and written to y;
+// the rest (p >= n) are not needed.
+template <int R, typename T, typename T2>
+__device__ __forceinline__ void dit_last(const T2 *a, int lg, int batch, int stride, int sh,
+                                         const T2 *__restrict__ tw, int lgtw, T2 *y, int n, int ystride,
+                                         const T2 *__restrict__ chirp) {
+  constexpr int P = 1 << R;
+  const int ulg = lg - R;
+  const int total = batch << ulg;
+  const int h = 1 << sh;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int b = e >> ulg, q = e & ((1 << ulg) - 1);
+    const int pos = q & (h - 1), grp = q >> sh;
+    const int i0 = (grp << (sh + R)) + pos;
+    const int base = faddr(b, i0, lg, stride);
+    T2 x[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) x[c] = a[base ^ swz(c << sh, lg)];
+#pragma unroll
+    for (int lev = 0; lev < R; ++lev) {
+      T2 wl = tw[pos << (lgtw - sh - lev - 1)];
+      wl.y = -wl.y;
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        if ((c >> lev) & 1) continue;
+        const int cc = c & ((1 << lev) - 1);
+        const T2 w = cc ? cmul(wl, unit_root<T, T2>(lev, cc, +1)) : wl;
+        const T2 u = x[c], v = cmul(x[c + (1 << lev)], w);
+        x[c] = cadd(u, v);
+        x[c + (1 << lev)] = csub(u, v);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      const int p = i0 + (c << sh);
+      if (p < n) y[b * ystride + p] = cmul(x[c], chirp[p]);
+    }
+  }
+  __syncthreads();
+}
+
 // In-place DIT FFT on `batch` arrays of length n (power of two), `stride` elements
 // apart (swizzled layout when SWZ), whose input is already in bit-reversed order
 // (the writers store it so);
@@ -152,51 +194,110 @@ __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict_
   fft_core<false, T, T2>(a, n, batch, n, dir, tw, TW);
 }
 
+// R fused radix-2 decimation-in-frequency stages (half-spans 2^(sh+R-1) down to
+// 2^sh) on the swizzled work arrays: each thread takes the 2^R elements
+// i0 + c 2^sh of one group, and at each level pairs c with c + 2^lev:
+// (u, v) -> (u + v, (u - v) W), W = W_{2^(sh+lev+1)}^(index mod 2^(sh+lev)) (the same
+// twiddles as dit_pass). DIF takes natural order in; after all passes the output is
+// in bit-reversed order.
+//   FIRST: the inputs are y_t e^{i pi t^2/n} read from y (t < n, zero from n on;
+//          n <= 2^(lg-1), so the upper half of the first level is zero);
+//   LAST:  each output is multiplied by the tabulated spectrum (bit-reversed order)
+//          as it is stored.
+template <int R, bool FIRST, bool LAST, typename T, typename T2>
+__device__ __forceinline__ void bs_dif_pass(T2 *w, int lg, int batch, int wstride, int sh, const T2 *__restrict__ tw,
+                                            int lgtw, const T2 *y, int n, int ystride, const T2 *__restrict__ chirp,
+                                            const T2 *__restrict__ bhr) {
+  constexpr int P = 1 << R;
+  const int ulg = lg - R;
+  const int total = batch << ulg;
+  const int h = 1 << sh;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int b = e >> ulg, q = e & ((1 << ulg) - 1);
+    const int pos = q & (h - 1), grp = q >> sh;
+    const int i0 = (grp << (sh + R)) + pos;
+    const int base = faddr(b, i0, lg, wstride);
+    T2 x[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      if (FIRST) {
+        const int t = i0 + (c << sh);
+        T2 v;
+        v.x = (T)0;
+        v.y = (T)0;
+        if (c < P / 2 && t < n) v = cmul(y[b * ystride + t], chirp[t]);
+        x[c] = v;
+      } else {
+        x[c] = w[base ^ swz(c << sh, lg)];
+      }
+    }
+#pragma unroll
+    for (int lev = R - 1; lev >= 0; --lev) {
+      const T2 wl = tw[pos << (lgtw - sh - lev - 1)];
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        if ((c >> lev) & 1) continue;
+        const int cc = c & ((1 << lev) - 1);
+        const T2 wt = cc ? cmul(wl, unit_root<T, T2>(lev, cc, -1)) : wl;
+        const T2 u = x[c], v = x[c + (1 << lev)];
+        if (FIRST && lev == R - 1) {  // v is zero (upper half of the first level)
+          x[c + (1 << lev)] = cmul(u, wt);
+        } else {
+          x[c] = cadd(u, v);
+          x[c + (1 << lev)] = cmul(csub(u, v), wt);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      const int off = swz(c << sh, lg);
+      w[base ^ off] = LAST ? cmul(x[c], bhr[i0 + (c << sh)]) : x[c];
+    }
+  }
+  __syncthreads();
+}
+
 // Bluestein on `batch` sequences y (plain layout, ystride apart) of length n (n
 // arbitrary), in place: y_p <- sum_{t<n} y_t e^{+2 pi i t p / n}. With
 // tp = (t^2 + p^2 - (p-t)^2)/2 the DFT is a chirp, a circular convolution of length
-// M >= 2n - 1 (two power-of-two FFTs against the tabulated spectrum
-// bh = DFT_M(conj chirp) / M) and a chirp. work: batch swizzled arrays of length M,
-// wstride apart. Each pass writes the next transform's input in bit-reversed order.
+// M >= 2n (powers of two) against the spectrum of the conjugate chirp, and a chirp:
+// a forward DIF transform of the chirped input (natural order in, bit-reversed out;
+// the chirp applied as its first pass loads), the product with the tabulated
+// spectrum bhr (stored in bit-reversed order, 1/M included; applied as the last DIF
+// pass stores), the inverse DIT transform (bit-reversed in, natural out), whose last
+// pass multiplies by the chirp and writes the n outputs back to y. No bit-reversal
+// pass, no scatter: work holds batch swizzled arrays of length M, wstride apart.
 template <typename T, typename T2>
 __device__ void bluestein_batch(T2 *y, int n, int ystride, int M, int batch, T2 *work, int wstride,
-                                const T2 *__restrict__ bh, const T2 *__restrict__ chirp,
+                                const T2 *__restrict__ bhr, const T2 *__restrict__ chirp,
                                 const T2 *__restrict__ tw, int TW) {
-  const int nth = blockDim.x, tid = threadIdx.x;
-  const int lgM = 31 - __clz(M);
-  for (int t = tid; t < M; t += nth) {
-    const int d = brev_bits(t, lgM);
-    if (t < n) {
-      const T2 w = chirp[t];  // e^{i pi t^2 / n}
-      for (int b = 0; b < batch; ++b) work[faddr(b, d, lgM, wstride)] = cmul(y[b * ystride + t], w);
-    } else {
-      T2 z;
-      z.x = (T)0;
-      z.y = (T)0;
-      for (int b = 0; b < batch; ++b) work[faddr(b, d, lgM, wstride)] = z;
+  const int lg = 31 - __clz(M);
+  const int lgtw = 31 - __clz(TW);
+  // ---- forward DIF: passes of three stages from the top, then the remainder
+  const int r = lg % 3;
+  int sh = lg - 3;
+  if (sh < 0) return;  // M >= 2n >= 8 for every Bluestein length
+  if (sh == 0 && r == 0) {
+    bs_dif_pass<3, true, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+  } else {
+    bs_dif_pass<3, true, false, T, T2>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
+    for (sh -= 3; sh >= 0; sh -= 3) {
+      if (sh == 0 && r == 0)
+        bs_dif_pass<3, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+      else
+        bs_dif_pass<3, false, false, T, T2>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
     }
+    if (r == 2) bs_dif_pass<2, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+    if (r == 1) bs_dif_pass<1, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
   }
-  __syncthreads();
-  fft_core<true, T, T2>(work, M, batch, wstride, -1, tw, TW);
-  // multiply by the spectrum, writing bit-reversed for the inverse transform
-  for (int k = tid; k < M; k += nth) {
-    const int r = brev_bits(k, lgM);
-    if (k > r) continue;
-    const T2 hk = bh[k], hr = bh[r];
-    for (int b = 0; b < batch; ++b) {
-      const int ak = faddr(b, k, lgM, wstride), ar = faddr(b, r, lgM, wstride);
-      const T2 xk = work[ak], xr = work[ar];
-      work[ar] = cmul(xk, hk);
-      work[ak] = cmul(xr, hr);
-    }
-  }
-  __syncthreads();
-  fft_core<true, T, T2>(work, M, batch, wstride, +1, tw, TW);
-  for (int p = tid; p < n; p += nth) {
-    const T2 w = chirp[p];
-    for (int b = 0; b < batch; ++b) y[b * ystride + p] = cmul(work[faddr(b, p, lgM, wstride)], w);
-  }
-  __syncthreads();
+  // ---- inverse DIT, natural order out: passes of three stages from the bottom; the
+  // top pass (the remaining 1, 2 or 3 stages) writes the chirped outputs p < n to y
+  int s0 = 0;
+  for (; s0 + 3 < lg; s0 += 3) dit_pass<3, true, T, T2>(work, lg, batch, wstride, s0, +1, tw, lgtw);
+  const int R = lg - s0;
+  if (R == 3) dit_last<3, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
+  if (R == 2) dit_last<2, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
+  if (R == 1) dit_last<1, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
 }
 
 }  // namespace tl

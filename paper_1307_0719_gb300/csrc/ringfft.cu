@@ -486,10 +486,13 @@ __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const l
   __syncthreads();
   fft_pow2<double, double2>(w, M, 1, -1, tw, TW);
   typedef typename RealTraits<T>::T2 T2;
+  // stored in bit-reversed order, the order in which the DIF transform leaves its output
+  const int lgM = 31 - __clz(M);
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const int kr = brev_bits(k, lgM);
     T2 v;
-    v.x = (T)(w[k].x / M);
-    v.y = (T)(w[k].y / M);
+    v.x = (T)(w[kr].x / M);
+    v.y = (T)(w[kr].y / M);
     spec[off + k] = v;
   }
   // then the chirp e^{i pi t^2 / n}, t < n
