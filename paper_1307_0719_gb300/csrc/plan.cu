@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <utility>
 #include <vector>
 
 #include "legendre.cuh"
@@ -359,6 +360,23 @@ static double fact(int n) {
   return r;
 }
 
+// (j, k), j + k <= order, in the order the ring FFT pairs them (jobs 2i and 2i+1
+// share a transform): pairs within each plane j first, the left-overs of odd
+// planes paired with each other at the end
+static std::vector<std::pair<int, int>> paired_order(int order) {
+  std::vector<std::pair<int, int>> out, rest;
+  for (int j = 0; j <= order; ++j) {
+    const int nk = order - j + 1;
+    for (int k = 0; k + 1 < nk; k += 2) {
+      out.push_back({j, k});
+      out.push_back({j, k + 1});
+    }
+    if (nk & 1) rest.push_back({j, nk - 1});
+  }
+  out.insert(out.end(), rest.begin(), rest.end());
+  return out;
+}
+
 extern "C" tl_status tl_synth_derivs(tl_plan *p, const double *alm, int spin, void *maps, void *stream) {
   if (!p || !alm || !maps) return TL_ERR_ARG;
   if (!aligned16(alm) || !aligned16(maps)) return TL_ERR_ARG;
@@ -373,11 +391,10 @@ extern "C" tl_status tl_synth_derivs(tl_plan *p, const double *alm, int spin, vo
   if (spin == 0) {
     TRY_CUDA(launch_prep_spin0(p, alm, nullptr, s));
     TRY_CUDA(launch_legendre_spin0(p, p->order, false, p->d7_T, nullptr, s));
-    for (int n = 0; n <= p->order; ++n)
-      for (int j = 0; j <= n; ++j) {
-        int k = n - j;
-        jobs.push_back(MapJob{0, j, k, 0, pow(L, n), base + mapb * (n * (n + 1) / 2 + j)});
-      }
+    for (const std::pair<int, int> &jk : paired_order(p->order)) {
+      const int j = jk.first, k = jk.second, n = j + k;
+      jobs.push_back(MapJob{0, j, k, 0, pow(L, n), base + mapb * (n * (n + 1) / 2 + j)});
+    }
   } else {
     TRY_CUDA(launch_prep_spin2(p, alm, alm + 2 * na, s));
     TRY_CUDA(launch_legendre_spin2(p, p->order, s));
@@ -399,12 +416,16 @@ static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s)
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
   const size_t mapb = (size_t)p->elem * p->npix;
   std::vector<MapJob> jobs;
-  const int nf = pol ? 3 : 1;
-  // T maps pair among themselves in (j, k) order; Q and U of the same (j, k) pair
-  for (int f = 0; f < nf; f += (f == 0 ? 1 : 2))
+  // T maps pair within one coefficient plane j (the fold reads the row once for
+  // both), left-overs pair across planes; Q and U of the same (j, k) pair
+  for (const std::pair<int, int> &jk : paired_order(p->order))
+    jobs.push_back(MapJob{0, jk.first, jk.second, 0, 1.0 / (fact(jk.first) * fact(jk.second)),
+                          (char *)p->d3 + mapb * ((jk.first + jk.second) * (jk.first + jk.second + 1) / 2 +
+                                                  jk.first)});
+  if (pol)
     for (int n = 0; n <= p->order; ++n)
       for (int j = 0; j <= n; ++j)
-        for (int g = f; g < (f == 0 ? 1 : 3); ++g) {
+        for (int g = 1; g < 3; ++g) {
           int k = n - j;
           jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)),
                                 (char *)p->d3 + mapb * (g * p->nmaps + n * (n + 1) / 2 + j)});

@@ -92,8 +92,55 @@ __device__ __forceinline__ T2 fold_class(const T2 *__restrict__ F, int t0, int N
   return g;
 }
 
+// (i)^k g
+template <typename T2>
+__device__ __forceinline__ T2 rot_ik(T2 a, int k) {
+  T2 g;
+  switch (k & 3) {
+    case 0: g = a; break;
+    case 1: g.x = -a.y; g.y = a.x; break;
+    case 2: g.x = -a.x; g.y = -a.y; break;
+    default: g.x = a.y; g.y = -a.x; break;
+  }
+  return g;
+}
+
+// fold_class for the two jobs of a transform in one pass over the class's m: the
+// weight, the sign and the power (m/L)^k (built once up to the larger k) are
+// shared, and the coefficient row is read once when both jobs read the same
+// plane (`same`). Values equal fold_class's (the factors 2 and -1 are exact).
+template <typename T, typename T2>
+__device__ __forceinline__ void fold_pair(const T2 *__restrict__ FA, const T2 *__restrict__ FB, bool same,
+                                          bool hasb, int t0, int mstep, int mmax, int kA, int kB, T invL,
+                                          bool shifted, int qstep_odd, T2 &ga, T2 &gb) {
+  T2 aa, ab;
+  aa.x = aa.y = ab.x = ab.y = (T)0;
+  const int kmax = (hasb && kB > kA) ? kB : kA;
+  int q = 0;
+  for (int m = t0; m <= mmax; m += mstep, q += 1) {
+    const T2 fa = FA[m];
+    T2 fb = fa;
+    if (hasb && !same) fb = FB[m];
+    const T mm = (T)m * invL;
+    T w = (m > 0) ? (T)2 : (T)1;
+    if (shifted && ((q * qstep_odd) & 1)) w = -w;
+    T pa = w, pb = w, pw = w;
+    for (int r = 1; r <= kmax; ++r) {
+      pw *= mm;
+      if (r == kA) pa = pw;
+      if (r == kB) pb = pw;
+    }
+    aa.x = fma(fa.x, pa, aa.x);
+    aa.y = fma(fa.y, pa, aa.y);
+    ab.x = fma(fb.x, pb, ab.x);
+    ab.y = fma(fb.y, pb, ab.y);
+  }
+  ga = rot_ik(aa, kA);
+  gb = hasb ? rot_ik(ab, kB) : ab;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
+__global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
                                                       BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
                                                       int bbatch, T invL, const int *__restrict__ rings) {
@@ -128,6 +175,7 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
   const JobDev JB = hasb ? jobs.job[jb] : jobs.job[ja];
   const T2 *FA = (const T2 *)JA.in + (size_t)r * (mmax + 1);
   const T2 *FB = (const T2 *)JB.in + (size_t)r * (mmax + 1);
+  const bool same = JA.in == JB.in;  // both maps from one coefficient plane (different k)
   // both packed maps are transformed in the normalised units of the Legendre stage
   // (similar magnitudes, so the shared transform's rounding does not leak from a
   // large map into a small one); each job's scale is applied on output
@@ -150,13 +198,10 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
     for (int tt = (C == 1 ? tid : t); tt < ncls && c < C; tt += (C == 1 ? nth : ncls)) {
       const int tm = tt ? N - tt : 0;
       const int m0 = tt + c * N, m1 = tm + c * N, step = C * N;
-      T2 Ba = fold_class<T, T2>(FA, m0, N, step, mmax, JA.k, invL, shifted, C);
-      T2 Bam = fold_class<T, T2>(FA, m1, N, step, mmax, JA.k, invL, shifted, C);
-      T2 Bb = {0, 0}, Bbm = {0, 0};
-      if (hasb) {
-        Bb = fold_class<T, T2>(FB, m0, N, step, mmax, JB.k, invL, shifted, C);
-        Bbm = fold_class<T, T2>(FB, m1, N, step, mmax, JB.k, invL, shifted, C);
-      }
+      T2 Ba, Bb, Bam, Bbm;
+      fold_pair<T, T2>(FA, FB, same, hasb, m0, step, mmax, JA.k, JB.k, invL, shifted, C, Ba, Bb);
+      fold_pair<T, T2>(FA, FB, same, hasb, m1, step, mmax, JA.k, JB.k, invL, shifted, C, Bam, Bbm);
+      if (!hasb) Bb.x = Bb.y = Bbm.x = Bbm.y = (T)0;
       // chunk c starts at q = c: its first sign is (-1)^c on shifted rings
       if (shifted && (c & 1)) {
         Ba.x = -Ba.x; Ba.y = -Ba.y; Bam.x = -Bam.x; Bam.y = -Bam.y;
@@ -285,7 +330,7 @@ __global__ void __launch_bounds__(512) ringfft_kernel(RingTable rt, int nside, i
 // the forward kernel's decimated sub-transforms and an in-place radix-4 pass.
 
 template <typename T>
-__global__ void __launch_bounds__(512) ringfft_adj_kernel(RingTable rt, int mmax, long long npix, int nmaps,
+__global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_adj_kernel(RingTable rt, int mmax, long long npix, int nmaps,
                                                           AdjJobList jobs,
                                                           BluesteinTable bt,
                                                           const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
