@@ -28,8 +28,8 @@ def _skies():
             for i, (ns, lm) in enumerate(zip(NSIDES, LMAXS))]
 
 
-def test_batch_modes_agree_and_match_oracle():
-    order = 3
+@pytest.mark.parametrize("order", [3, 5])
+def test_batch_modes_agree_and_match_oracle(order):
     b = api.Batch(NSIDES, LMAXS, order, pol=True, precision=api.MIXED_TF32x3)
     try:
         assert b.groups == 4 and b.waves == 2
