@@ -193,7 +193,98 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
   // Z_t is stored at sub-sequence t % 4, element t / 4 (see ydst).
   const int ncls = half + 1;
   const int C = (ncls >= nth) ? 1 : nth / ncls;  // threads sharing one class pair
-  {
+  // class pair (t, N - t) from its sums Ba, Bam (map a) and Bb, Bbm (map b) over
+  // chunk c of the aliasing terms: class phases, Hermitian combination, store
+  auto finish = [&](int tt, int c, T2 Ba, T2 Bam, T2 Bb, T2 Bbm) {
+    const int tm = tt ? N - tt : 0;
+    // chunk c starts at q = c: its first sign is (-1)^c on shifted rings
+    if (shifted && (c & 1)) {
+      Ba.x = -Ba.x; Ba.y = -Ba.y; Bam.x = -Bam.x; Bam.y = -Bam.y;
+      Bb.x = -Bb.x; Bb.y = -Bb.y; Bbm.x = -Bbm.x; Bbm.y = -Bbm.y;
+    }
+    if (shifted) {
+      // class phases e^{i t phi0} and e^{i (N-t) phi0} = -conj(e^{i t phi0}) (t > 0)
+      T s, co;
+      sincos_pi<T>((T)tt * invN, &s, &co);
+      T2 e, em;
+      e.x = co;
+      e.y = s;
+      if (tt == 0) em = e;
+      else {
+        em.x = -co;
+        em.y = s;
+      }
+      Ba = cmul(Ba, e);
+      Bb = cmul(Bb, e);
+      Bam = cmul(Bam, em);
+      Bbm = cmul(Bbm, em);
+    }
+    T2 ca, cb;  // C^a_t, C^b_t (weights of the maps included)
+    ca.x = (T)0.5 * wa * (Ba.x + Bam.x);
+    ca.y = (T)0.5 * wa * (Ba.y - Bam.y);
+    cb.x = (T)0.5 * wb * (Bb.x + Bbm.x);
+    cb.y = (T)0.5 * wb * (Bb.y - Bbm.y);
+    if (C == 1) {
+      T2 z, zm;
+      z.x = ca.x - cb.y;
+      z.y = ca.y + cb.x;
+      zm.x = ca.x + cb.y;  // conj(C^a) + i conj(C^b)
+      zm.y = -ca.y + cb.x;
+      Y[ydst(tt)] = z;
+      if (tt != 0 && tt != half) Y[ydst(tm)] = zm;
+    } else {
+      W[2 * (c * ncls + tt)] = ca;
+      W[2 * (c * ncls + tt) + 1] = cb;
+    }
+  };
+  if (C == 1 && N > mmax) {
+    // no aliasing: class t has at most the term m = t, class N - t the term
+    // m = N - t (q = 0). A chunk of classes' coefficients is loaded first, then
+    // weighed (as fold_pair does, with the same roundings) and stored.
+    constexpr int U = 4;
+    const int kmax = (hasb && JB.k > JA.k) ? JB.k : JA.k;
+    T2 zero;
+    zero.x = zero.y = (T)0;
+    auto weigh = [&](T2 fa, T2 fb, int m, T2 &ga, T2 &gb) {
+      const T mm = (T)m * invL;
+      const T w = (m > 0) ? (T)2 : (T)1;
+      T pa = w, pb = w, pw = w;
+      for (int r = 1; r <= kmax; ++r) {
+        pw *= mm;
+        if (r == JA.k) pa = pw;
+        if (r == JB.k) pb = pw;
+      }
+      T2 x, y;
+      x.x = fa.x * pa;
+      x.y = fa.y * pa;
+      y.x = fb.x * pb;
+      y.y = fb.y * pb;
+      ga = rot_ik(x, JA.k);
+      gb = hasb ? rot_ik(y, JB.k) : zero;
+    };
+    for (int t0 = tid; t0 < ncls; t0 += U * nth) {
+      T2 fa[U], fb[U], fam[U], fbm[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int tt = t0 + u * nth;
+        const int tm = tt ? N - tt : 0;
+        const bool lo = tt < ncls && tt <= mmax, hi = tt < ncls && tm <= mmax;
+        fa[u] = lo ? FA[tt] : zero;
+        fam[u] = hi ? FA[tm] : zero;
+        fb[u] = (hasb && !same && lo) ? FB[tt] : fa[u];
+        fbm[u] = (hasb && !same && hi) ? FB[tm] : fam[u];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int tt = t0 + u * nth;
+        if (tt >= ncls) break;
+        T2 Ba, Bb, Bam, Bbm;
+        weigh(fa[u], fb[u], tt, Ba, Bb);
+        weigh(fam[u], fbm[u], tt ? N - tt : 0, Bam, Bbm);
+        finish(tt, 0, Ba, Bam, Bb, Bbm);
+      }
+    }
+  } else {
     const int c = tid / ncls, t = tid - (tid / ncls) * ncls;
     for (int tt = (C == 1 ? tid : t); tt < ncls && c < C; tt += (C == 1 ? nth : ncls)) {
       const int tm = tt ? N - tt : 0;
@@ -202,45 +293,7 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
       fold_pair<T, T2>(FA, FB, same, hasb, m0, step, mmax, JA.k, JB.k, invL, shifted, C, Ba, Bb);
       fold_pair<T, T2>(FA, FB, same, hasb, m1, step, mmax, JA.k, JB.k, invL, shifted, C, Bam, Bbm);
       if (!hasb) Bb.x = Bb.y = Bbm.x = Bbm.y = (T)0;
-      // chunk c starts at q = c: its first sign is (-1)^c on shifted rings
-      if (shifted && (c & 1)) {
-        Ba.x = -Ba.x; Ba.y = -Ba.y; Bam.x = -Bam.x; Bam.y = -Bam.y;
-        Bb.x = -Bb.x; Bb.y = -Bb.y; Bbm.x = -Bbm.x; Bbm.y = -Bbm.y;
-      }
-      if (shifted) {
-        // class phases e^{i t phi0} and e^{i (N-t) phi0} = -conj(e^{i t phi0}) (t > 0)
-        T s, co;
-        sincos_pi<T>((T)tt * invN, &s, &co);
-        T2 e, em;
-        e.x = co;
-        e.y = s;
-        if (tt == 0) em = e;
-        else {
-          em.x = -co;
-          em.y = s;
-        }
-        Ba = cmul(Ba, e);
-        Bb = cmul(Bb, e);
-        Bam = cmul(Bam, em);
-        Bbm = cmul(Bbm, em);
-      }
-      T2 ca, cb;  // C^a_t, C^b_t (weights of the maps included)
-      ca.x = (T)0.5 * wa * (Ba.x + Bam.x);
-      ca.y = (T)0.5 * wa * (Ba.y - Bam.y);
-      cb.x = (T)0.5 * wb * (Bb.x + Bbm.x);
-      cb.y = (T)0.5 * wb * (Bb.y - Bbm.y);
-      if (C == 1) {
-        T2 z, zm;
-        z.x = ca.x - cb.y;
-        z.y = ca.y + cb.x;
-        zm.x = ca.x + cb.y;  // conj(C^a) + i conj(C^b)
-        zm.y = -ca.y + cb.x;
-        Y[ydst(tt)] = z;
-        if (tt != 0 && tt != half) Y[ydst(tm)] = zm;
-      } else {
-        W[2 * (c * ncls + tt)] = ca;
-        W[2 * (c * ncls + tt) + 1] = cb;
-      }
+      finish(tt, c, Ba, Bam, Bb, Bbm);
     }
   }
   if (C > 1) {
