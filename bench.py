@@ -22,6 +22,7 @@ same workload on the host cores (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -41,6 +42,33 @@ METRIC = "lensed TQU maps/sec @Nside2048 lmax4096 order4 (mixed vs FP64 GPU, err
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
 FP32_LANES = 152 * 128
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
+# `bench.py --workload nside512_lmax1024_n4_TQU --steps 1 --warmup 1` (3xTF32, 16
+# realisations per launch; profiles/traffic_nside512_lmax1024_n4_tf32x3.md): bytes per
+# realisation (ring FFTs, gather) or per Legendre launch, with the sha256 prefix of the
+# kernel sources it was taken at. The full-size workload scales them by its pixel count
+# (rings x m grows the same way); a changed source, another order or form gives null.
+TRAFFIC_NSIDE512 = {
+    "fft_total": (838.7e6, ["ringfft.cu", "fft.cuh"], "02a7c2ad575b8e4b"),
+    "gather_total": (624.7e6, ["gather.cu", "geometry.cuh"], "0da694ee9a9fee8b"),
+    "legendre_QU": (7.520e9, ["legendre_umma.cu", "legendre.cuh"], "2bde86836b1401f0"),
+    "legendre_T": (4.230e9, ["legendre_umma.cu", "legendre.cuh"], "2bde86836b1401f0"),
+}
+
+
+def captured_traffic(stage, w, per_step_units):
+    """Scaled DRAM bytes of a stage for workload w, or None (see TRAFFIC_NSIDE512)."""
+    if stage not in TRAFFIC_NSIDE512 or w.order != 4:
+        return None
+    byt, files, sha = TRAFFIC_NSIDE512[stage]
+    m = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1307_0719_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    if m.hexdigest()[:16] != sha:
+        return None
+    return byt * (w.nside / 512) ** 2 * per_step_units
 
 
 def legendre_flops_per_launch(nside: int, lmax: int, order: int, spin: int, phi: bool = True,
@@ -278,7 +306,8 @@ def run_ours(args):
         fl = legendre_flops_per_launch(w.nside, w.lmax, w.order, spin, part=part) * launches
         ach = fl / (stage_ms[st] / 1e3) / 1e12
         e = {"kernel": f"legendre_spin{spin}_{'umma' if tc else 'kernel'}<{w.order}>", "bound": "alu",
-             "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+             "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+             "traffic": captured_traffic(st, w, 1) if (tc and args.form == "tf32x3" and nb == 16) else None,
              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
              "counts": "recurrence only (contraction on the tensor cores)" if tc else "recurrence + contraction"}
         if tc:
@@ -295,7 +324,8 @@ def run_ours(args):
                            ("gather_total", gat_bytes, f"gather_kernel<float, {w.order}, 1>")):
         ach = byt / (stage_ms[st] / 1e3) / 1e9 if stage_ms.get(st) else None
         rl[st] = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                  "frac": (ach / hbm) if (ach and hbm) else None, "traffic": None,
+                  "frac": (ach / hbm) if (ach and hbm) else None,
+                  "traffic": captured_traffic(st, w, nchunk) if (tc and args.form == "tf32x3") else None,
                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
                   "algorithmic_bytes": byt}
     dom = max(rl, key=lambda k: stage_ms.get(k, 0.0))
