@@ -60,37 +60,10 @@ static int ring_sub_stride_max(const FftGroup &g) {
   return mx;
 }
 
-// sum over the aliasing class m = t0 + qN (q >= 0, m <= mmax) of
-//   (-1)^q [shifted rings] * w_m (i m / L)^k F_m,   w_0 = 1, w_m = 2
+// The fold sums, over the aliasing class m = t0 + qN (q >= 0, m <= mmax) of a
+// ring of N pixels,
+//   (-1)^q [shifted rings] * w_m (i m / L)^k F_m,   w_0 = 1, w_m = 2,
 // i.e. the class's contribution without its common phase e^{i t0 phi0}.
-template <typename T, typename T2>
-__device__ __forceinline__ T2 fold_class(const T2 *__restrict__ F, int t0, int N, int mstep, int mmax, int k,
-                                         T invL, bool shifted, int qstep_odd) {
-  T2 acc;
-  acc.x = (T)0;
-  acc.y = (T)0;
-  int q = 0;
-  for (int m = t0; m <= mmax; m += mstep, q += 1) {
-    const T2 f = F[m];
-    T mk = (T)1;
-    const T mm = (T)m * invL;
-    for (int r = 0; r < k; ++r) mk *= mm;
-    if (m > 0) mk *= (T)2;
-    if (shifted && ((q * qstep_odd) & 1)) mk = -mk;
-    acc.x = fma(f.x, mk, acc.x);
-    acc.y = fma(f.y, mk, acc.y);
-  }
-  // (i)^k
-  T2 g;
-  switch (k & 3) {
-    case 0: g = acc; break;
-    case 1: g.x = -acc.y; g.y = acc.x; break;
-    case 2: g.x = -acc.x; g.y = -acc.y; break;
-    default: g.x = acc.y; g.y = -acc.x; break;
-  }
-  (void)N;
-  return g;
-}
 
 // (i)^k g
 template <typename T2>
@@ -105,10 +78,11 @@ __device__ __forceinline__ T2 rot_ik(T2 a, int k) {
   return g;
 }
 
-// fold_class for the two jobs of a transform in one pass over the class's m: the
+// The class sum for the two jobs of a transform in one pass over the class's m: the
 // weight, the sign and the power (m/L)^k (built once up to the larger k) are
 // shared, and the coefficient row is read once when both jobs read the same
-// plane (`same`). Values equal fold_class's (the factors 2 and -1 are exact).
+// plane (`same`). The factors 2 and -1 are exact, so the order of the products
+// does not change the values.
 template <typename T, typename T2>
 __device__ __forceinline__ void fold_pair(const T2 *__restrict__ FA, const T2 *__restrict__ FB, bool same,
                                           bool hasb, int t0, int mstep, int mmax, int kA, int kB, T invL,

@@ -130,3 +130,34 @@ def test_lens_batch_equals_single_calls(precision, order):
     for o, s1 in zip(outs, singles):
         for i in range(3):
             assert rel_rms(o[i], s1[i]) <= tol
+
+
+def test_plan_batch_and_launch_count():
+    """tl_plan_batch: 16 realisations per Legendre launch on the tensor-core forms up to
+    order 5, 8 at order 6, 1 otherwise; tl_plan_batch_launches matches the kernels a
+    tl_lens_batch call launches (counted by the CUDA profiler when it is available)."""
+    plans = {(api.MIXED_TF32x3, 4): 16, (api.MIXED_TF32x3, 6): 8, (api.MIXED_FP32, 4): 1, (api.FP64, 3): 1}
+    for (prec, order), want in plans.items():
+        p = api.Plan(16, 32, order, pol=True, precision=prec)
+        try:
+            assert p.batch == want, (prec, order, p.batch)
+        finally:
+            p.close()
+    nside, lmax, order = 32, 64, 4
+    skies = [to_dev(sky(nside, lmax, pol=True, seeds=(50 + i, 60 + i, 70 + i), b_scale=0.3)) for i in range(18)]
+    plan = api.Plan(nside, lmax, order, pol=True, precision=api.MIXED_TF32x3)
+    try:
+        plan.lens_batch(skies)  # warm: plan-time work is done
+        torch.cuda.synchronize()
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            plan.lens_batch(skies)
+            torch.cuda.synchronize()
+        names = [e.name for e in prof.events() if e.device_type.name == "CUDA"]
+        ours = [n for n in names if any(k in n for k in ("ringfft", "legendre", "gather", "tcprep"))]
+        if not ours:
+            pytest.skip("the CUDA profiler recorded no kernels here")
+        assert len(ours) == plan.batch_launches(18), (len(ours), plan.batch_launches(18))
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
