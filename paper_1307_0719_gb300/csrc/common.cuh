@@ -26,6 +26,7 @@ struct RingTable {
   double *dphi;    // 2 pi / nphi: longitude step between the ring's pixels
   double *omza;    // 1 - |cos(theta)|, formed without cancellation
   float *rsinf;    // 1 / sin(theta), rounded to float (single-precision kernels)
+  float *ringf;    // [ring][8] for the float gather: z, sin, 1 - |z|, theta hi, theta lo (hi + lo = theta)
   double *log2_sh; // log2 sin(theta/2)
   double *log2_ch; // log2 cos(theta/2)
   double *dls;     // [ring][k], k = 1..TL_MAX_NDER+1: d^k/dtheta^k ln sin(theta/2)
@@ -177,7 +178,7 @@ cudaError_t launch_gather(const tl_plan *p, const void *alpha, const void *d3, v
 // lnorm0: lmax + 1, Bluestein off/ml: nside + 1, twiddles: TW doubles
 struct RingHostView {
   double *z, *sint, *theta, *phi0, *lsh, *lch, *dls, *dlc, *dphi, *omza;
-  float *rsinf;
+  float *rsinf, *ringf;
   int *nphi, *inorth;
   long long *first;
 };

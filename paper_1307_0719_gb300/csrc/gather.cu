@@ -27,14 +27,17 @@
 
 namespace tl {
 
-// Increment-form geometry in float (see the header comment); pixel lookup in double.
+// Increment-form geometry in float (see the header comment); pixel lookup in float
+// with a double fallback near cell boundaries.
 // Returns the expansion pixel q and, in float, the scaled offsets x = L dth,
 // y = L dph and cos 2 beta, sin 2 beta (no round trip through double).
 struct Geo32 {
   long long q;
   float x, y, c2b, s2b;
 };
-__device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, double z, double s, double phi,
+// The pixel is (ring, idx), fr its float ring record (z, sin theta, 1 - |z|, theta
+// hi, theta lo). No double arithmetic except in the rare fallback of the lookup.
+__device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, int idx, float4 fr, float th_lo,
                                       float ath, float aph, bool rot, float Lf, Geo32 &g) {
   const float d2 = ath * ath + aph * aph;
   const float d = sqrtf(d2);
@@ -43,7 +46,7 @@ __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, 
   const float hsinc = (d > 0.0f) ? sh / (0.5f * d) : 1.0f;  // sinc(d/2)
   const float sinc = hsinc * ch;                             // sin(d)/d
   const float omc = 2.0f * sh * sh;                          // 1 - cos d
-  const float zf = (float)z, sf = (float)s;
+  const float zf = fr.x, sf = fr.y;
   const float X = sf * (1.0f - omc) + zf * ath * sinc;
   const float Y = aph * sinc;
   const float dz = -zf * omc - sf * ath * sinc;
@@ -51,20 +54,40 @@ __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, 
   const float w = Y * Y / (rho + X);
   const float dthp = atan2f(ath * sinc + zf * w, (1.0f - omc) + sf * w);  // th' - th_p
   const float dphp = atan2f(Y, X);                                        // phi' - phi_p
-  // pixel lookup in double on the accurate increments
-  const double z2 = z + (double)dz;
-  const double omz_p = rt.omza[ring];  // 1 - |z| of the pixel's ring
-  const double omz2 = omz_p - (z >= 0.0 ? (double)dz : -(double)dz);
-  double phi2 = phi + (double)dphp;
-  if (phi2 >= 2.0 * kPiD) phi2 -= 2.0 * kPiD;
-  if (phi2 < 0.0) phi2 += 2.0 * kPiD;
-  const PixLoc lq = ang2loc(z2, omz2, phi2, nside);
+  // pixel lookup: in float where every decision clears its error bound (ang2loc_f),
+  // else in double on the accurate increments; both give ang2loc's cell.
+  // Pixel centres: phi = 2 pi (idx + sh/2) / nphi, sh = 1 on half-pixel-shifted rings.
+  const int np = rt.nphi[ring];
+  const int shp = __double_as_longlong(rt.phi0[ring]) != 0;  // phi0 >= 0: an integer test
+  const float tf = (float)(4 * idx + 2 * shp) / (float)np + dphp * (float)(2.0 / kPiD);  // 2 phi' / pi
+  bool ok;
+  PixLoc lq = ang2loc_f(zf + dz, fr.z - (zf >= 0.0f ? dz : -dz), tf, nside, ok);
+  if (!ok) {
+    const double z = rt.z[ring], phi = ring_phi(rt, ring, idx);
+    const double z2 = z + (double)dz;
+    const double omz2 = rt.omza[ring] - (z >= 0.0 ? (double)dz : -(double)dz);
+    double phi2 = phi + (double)dphp;
+    if (phi2 >= 2.0 * kPiD) phi2 -= 2.0 * kPiD;
+    if (phi2 < 0.0) phi2 += 2.0 * kPiD;
+    lq = ang2loc(z2, omz2, phi2, nside);
+  }
   g.q = rt.first[lq.ring] + lq.idx;
-  g.x = Lf * (dthp - (float)(rt.theta[lq.ring] - rt.theta[ring]));
-  double dc = ring_phi(rt, lq.ring, lq.idx) - phi;  // centre offset, wrapped
-  if (dc >= kPiD) dc -= 2.0 * kPiD;
-  if (dc < -kPiD) dc += 2.0 * kPiD;
-  float dph = dphp - (float)dc;
+  // theta_q - theta_p from the hi/lo parts: the hi difference is exact (nearby
+  // rings, Sterbenz), so this is the double difference rounded once
+  const float4 fq = __ldg((const float4 *)(rt.ringf + 8 * (size_t)lq.ring));
+  const float thq_lo = __ldg(rt.ringf + 8 * (size_t)lq.ring + 4);
+  g.x = Lf * (dthp - ((fq.w - fr.w) + (thq_lo - th_lo)));
+  // centre offset phi_q - phi_p = 2 pi [(2 idx_q + sh_q) nphi_p - (2 idx_p + sh_p) nphi_q] / (2 nphi_q nphi_p),
+  // the numerator an exact integer, wrapped to [-pi, pi) exactly
+  const int nq = rt.nphi[lq.ring];
+  const int shq = __double_as_longlong(rt.phi0[lq.ring]) != 0;
+  const long long den = 2LL * nq * np;
+  long long num = (long long)(2 * lq.idx + shq) * np - (long long)(2 * idx + shp) * nq;
+  num %= den;
+  if (num >= den / 2) num -= den;
+  if (num < -den / 2) num += den;
+  const float dc = (float)num * ((float)(2.0 * kPiD) / (float)den);
+  float dph = dphp - dc;
   if (dph >= (float)kPiD) dph -= 2.0f * (float)kPiD;
   if (dph < -(float)kPiD) dph += 2.0f * (float)kPiD;
   g.y = Lf * dph;
@@ -115,17 +138,18 @@ __global__ void __launch_bounds__(256) gather_kernel(RingTable rt, int nside, lo
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npix) return;
   const PixLoc loc = pix2loc(p, nside, npix);
-  const double z = rt.z[loc.ring], s = rt.sint[loc.ring];
-  const double phi = ring_phi(rt, loc.ring, loc.idx);
   const T ath = a_th[p], aph = a_ph[p];
   const bool rot = POL && rotate;
 
   long long q = p;
   T x = (T)0, y = (T)0, c2 = (T)1, s2 = (T)0;
   if (ath != (T)0 || aph != (T)0) {
-    if (FAST && s >= 0.1 && (float)(ath * ath + aph * aph) < 4e-4f) {
+    float4 fr = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (FAST) fr = __ldg((const float4 *)(rt.ringf + 8 * (size_t)loc.ring));
+    if (FAST && fr.y >= 0.1f && (float)(ath * ath + aph * aph) < 4e-4f) {
       Geo32 g;
-      geo32(rt, nside, loc.ring, z, s, phi, (float)ath, (float)aph, rot, (float)Lnorm, g);
+      geo32(rt, nside, loc.ring, loc.idx, fr, __ldg(rt.ringf + 8 * (size_t)loc.ring + 4), (float)ath, (float)aph, rot,
+            (float)Lnorm, g);
       q = g.q;
       x = (T)g.x;
       y = (T)g.y;
@@ -133,7 +157,8 @@ __global__ void __launch_bounds__(256) gather_kernel(RingTable rt, int nside, lo
       s2 = (T)g.s2b;
     } else {
       Geo g;
-      geo64(rt, nside, z, s, phi, (double)ath, (double)aph, rot, g);
+      const double z = rt.z[loc.ring], s = rt.sint[loc.ring];
+      geo64(rt, nside, z, s, ring_phi(rt, loc.ring, loc.idx), (double)ath, (double)aph, rot, g);
       q = g.q;
       x = (T)(Lnorm * g.dth);
       y = (T)(Lnorm * g.dph);

@@ -86,6 +86,56 @@ __device__ __forceinline__ PixLoc ang2loc(double z, double omz, double phi, int 
   return L;
 }
 
+// ang2loc in single precision, for the float gather. z, omz = 1 - |z| and
+// t = 2 phi / pi come rounded to float (|z| <= 1, t in [0, 4)), so every floor
+// argument below carries an absolute error under N * 1e-6 (input rounding of t,
+// z and omz times at most 4N, plus the products' own rounding). When one lies
+// within eps = N * 2.5e-6 of an integer, or |z| within 1e-6 of 2/3, or t within
+// 1e-6 of an integer, `ok` is false and the caller takes ang2loc in double;
+// otherwise both make the same decisions, so the cell is ang2loc's.
+__device__ __forceinline__ PixLoc ang2loc_f(float z, float omz, float t, int nside, bool &ok) {
+  const float N = (float)nside, eps = N * 2.5e-6f;
+  if (t >= 4.0f) t -= 4.0f;
+  if (t < 0.0f) t += 4.0f;
+  const float za = fabsf(z);
+  ok = fabsf(za - (2.0f / 3.0f)) >= 1e-6f;
+  PixLoc L;
+  if (za <= 2.0f / 3.0f) {
+    const float a = N * (0.5f + t), b = 0.75f * N * z;
+    const float x1 = a - b, x2 = a + b;
+    ok = ok && fabsf(x1 - rintf(x1)) >= eps && fabsf(x2 - rintf(x2)) >= eps;
+    const int jp = (int)floorf(x1), jm = (int)floorf(x2);
+    int ir = nside + 1 + jp - jm;
+    if (ir < 1) ir = 1;
+    if (ir > 2 * nside + 1) ir = 2 * nside + 1;
+    const int kshift = 1 - (ir & 1);
+    const int v = jp + jm - nside + kshift + 1;
+    int ip = (v >= 0) ? v / 2 : -((1 - v) / 2);
+    const int n4 = 4 * nside;
+    ip %= n4;
+    if (ip < 0) ip += n4;
+    L.ring = nside - 2 + ir;
+    L.idx = ip;
+  } else {
+    ok = ok && fabsf(t - rintf(t)) >= 1e-6f;
+    const float tp = t - floorf(t);
+    const float tmp = N * sqrtf(3.0f * (omz > 0.0f ? omz : 0.0f));
+    const float x1 = tp * tmp, x2 = (1.0f - tp) * tmp;
+    ok = ok && fabsf(x1 - rintf(x1)) >= eps && fabsf(x2 - rintf(x2)) >= eps;
+    const int jp = (int)floorf(x1), jm = (int)floorf(x2);
+    int ir = jp + jm + 1;
+    if (ir > nside) ir = nside;
+    const float x3 = t * (float)ir;
+    ok = ok && fabsf(x3 - rintf(x3)) >= eps;
+    int ip = (int)floorf(x3);
+    ip %= 4 * ir;
+    if (ip < 0) ip += 4 * ir;
+    L.ring = (z > 0.0f) ? ir - 1 : 4 * nside - ir - 1;
+    L.idx = ip;
+  }
+  return L;
+}
+
 __device__ __forceinline__ double ring_phi(const RingTable &rt, int ring, int idx) {
   return fma((double)idx, rt.dphi[ring], rt.phi0[ring]);
 }

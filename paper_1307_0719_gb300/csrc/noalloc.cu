@@ -30,7 +30,7 @@ DevState g_dev[kMaxDev];
 // host staging for the tables, sized for the largest supported plan
 double h_z[kMaxRings], h_sint[kMaxRings], h_theta[kMaxRings], h_phi0[kMaxRings], h_lsh[kMaxRings],
     h_lch[kMaxRings], h_dls[kMaxRings * kK], h_dlc[kMaxRings * kK], h_dphi[kMaxRings], h_omza[kMaxRings];
-float h_rsinf[kMaxRings];
+float h_rsinf[kMaxRings], h_ringf[8 * kMaxRings];
 int h_nphi[kMaxRings], h_inorth[kMaxRings], h_fft_order[kMaxRings];
 long long h_first[kMaxRings];
 double h_lnorm0[TL_NOALLOC_MAX_LMAX + 1];
@@ -72,7 +72,7 @@ tl_status setup(DevState &st, int nside, int lmax, int precision) {
   const long long na = tl::nalm(lmax);
 
   tl::RingHostView v{h_z,     h_sint,  h_theta, h_phi0, h_lsh,   h_lch,  h_dls,
-                     h_dlc,   h_dphi,  h_omza,  h_rsinf, h_nphi, h_inorth, h_first};
+                     h_dlc,   h_dphi,  h_omza,  h_rsinf, h_ringf, h_nphi, h_inorth, h_first};
   tl::host_ring_tables(nside, v);
   tl::host_lnorm0(lmax, h_lnorm0);
   int maxm = 0;
@@ -97,7 +97,7 @@ tl_status setup(DevState &st, int nside, int lmax, int precision) {
       {(void **)&p.ring.dls, h_dls, 8 * nr * kK}, {(void **)&p.ring.dlc, h_dlc, 8 * nr * kK},
       {(void **)&p.ring.nphi, h_nphi, 4 * nr},    {(void **)&p.ring.inorth, h_inorth, 4 * nr},
       {(void **)&p.ring.dphi, h_dphi, 8 * nr},    {(void **)&p.ring.omza, h_omza, 8 * nr},
-      {(void **)&p.ring.rsinf, h_rsinf, 4 * nr},
+      {(void **)&p.ring.rsinf, h_rsinf, 4 * nr},  {(void **)&p.ring.ringf, h_ringf, 32 * nr},
       {(void **)&p.ring.first, h_first, 8 * nr},  {(void **)&p.lnorm0, h_lnorm0, 8 * (size_t)(lmax + 1)},
       {(void **)&p.blue.offset, h_off, 8 * (size_t)(nside + 1)},
       {(void **)&p.blue.mlen, h_ml, 4 * (size_t)(nside + 1)},

@@ -42,7 +42,7 @@ extern "C" const char *tl_status_string(tl_status s) {
 
 struct HostRings {
   std::vector<double> z, sint, theta, phi0, lsh, lch, dls, dlc, dphi, omza;
-  std::vector<float> rsinf;
+  std::vector<float> rsinf, ringf;
   std::vector<int> nphi, inorth;
   std::vector<long long> first;
 };
@@ -51,10 +51,10 @@ static void build_rings(int N, HostRings &h) {
   const size_t nr = 4 * (size_t)N - 1, K = TL_MAX_NDER + 1;
   h.z.resize(nr); h.sint.resize(nr); h.theta.resize(nr); h.phi0.resize(nr);
   h.lsh.resize(nr); h.lch.resize(nr); h.dls.resize(nr * K); h.dlc.resize(nr * K);
-  h.dphi.resize(nr); h.omza.resize(nr); h.rsinf.resize(nr);
+  h.dphi.resize(nr); h.omza.resize(nr); h.rsinf.resize(nr); h.ringf.resize(8 * nr);
   h.nphi.resize(nr); h.inorth.resize(nr); h.first.resize(nr);
   RingHostView v{h.z.data(), h.sint.data(), h.theta.data(), h.phi0.data(), h.lsh.data(), h.lch.data(),
-                 h.dls.data(), h.dlc.data(), h.dphi.data(), h.omza.data(), h.rsinf.data(), h.nphi.data(), h.inorth.data(),
+                 h.dls.data(), h.dlc.data(), h.dphi.data(), h.omza.data(), h.rsinf.data(), h.ringf.data(), h.nphi.data(), h.inorth.data(),
                  h.first.data()};
   host_ring_tables(N, v);
 }
@@ -77,7 +77,7 @@ static cudaError_t dalloc(void **p, size_t b, size_t *bytes) {
 
 static void free_plan(tl_plan *p) {
   if (!p) return;
-  void *ptrs[] = {p->ring.z, p->ring.sint, p->ring.theta, p->ring.phi0, p->ring.dphi, p->ring.omza, p->ring.rsinf,
+  void *ptrs[] = {p->ring.z, p->ring.sint, p->ring.theta, p->ring.phi0, p->ring.dphi, p->ring.omza, p->ring.rsinf, p->ring.ringf,
                   p->ring.log2_sh, p->ring.log2_ch,
                   p->ring.dls, p->ring.dlc, p->ring.nphi, p->ring.inorth, p->ring.first, p->blue.spec,
                   p->blue.offset, p->blue.mlen, p->lnorm0, p->twiddle, p->tab0, p->tab2, p->rec_T, p->rec_P,
@@ -116,6 +116,7 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   TRY_CUDA(upload(&p->ring.dls, h.dls, B)); TRY_CUDA(upload(&p->ring.dlc, h.dlc, B));
   TRY_CUDA(upload(&p->ring.dphi, h.dphi, B)); TRY_CUDA(upload(&p->ring.omza, h.omza, B));
   TRY_CUDA(upload(&p->ring.rsinf, h.rsinf, B));
+  TRY_CUDA(upload(&p->ring.ringf, h.ringf, B));
   TRY_CUDA(upload(&p->ring.nphi, h.nphi, B)); TRY_CUDA(upload(&p->ring.inorth, h.inorth, B));
   TRY_CUDA(upload(&p->ring.first, h.first, B));
 

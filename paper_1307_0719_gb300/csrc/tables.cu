@@ -80,6 +80,16 @@ void host_ring_tables(int N, const RingHostView &h) {
     h.sint[r] = sqrt(omz_m * omz_p);
     h.rsinf[r] = (float)(1.0 / h.sint[r]);
     h.theta[r] = (z >= 0.0) ? 2.0 * asin(sqrt(0.5 * omz_m)) : kPiH - 2.0 * asin(sqrt(0.5 * omz_p));
+    {
+      float *f = h.ringf + 8 * (size_t)r;
+      const float th_hi = (float)h.theta[r];
+      f[0] = (float)z;
+      f[1] = (float)h.sint[r];
+      f[2] = (float)h.omza[r];
+      f[3] = th_hi;
+      f[4] = (float)(h.theta[r] - (double)th_hi);
+      f[5] = f[6] = f[7] = 0.0f;
+    }
     h.lsh[r] = 0.5 * log2(0.5 * omz_m);
     h.lch[r] = 0.5 * log2(0.5 * omz_p);
     const double w = sqrt(omz_p / omz_m), v = sqrt(omz_m / omz_p);
