@@ -55,17 +55,25 @@ __host__ __device__ __forceinline__ int faddr(int b, int i, int lg, int stride) 
 }
 __device__ __forceinline__ int brev_bits(int e, int lg) { return lg == 0 ? 0 : (int)(__brev((unsigned)e) >> (32 - lg)); }
 
-// e^{-2 pi i cc / 2^(lev+1)} (conjugated for dir > 0), cc < 2^lev, lev <= 2
+// e^{-2 pi i cc / 2^(lev+1)} (conjugated for dir > 0), cc < 2^lev, lev <= 3
 template <typename T, typename T2>
 __device__ __forceinline__ T2 unit_root(int lev, int cc, int dir) {
   const T h = (T)0.70710678118654752440;
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // cos, sin of pi/8
   T2 r;
   if (lev == 1) {
     r.x = (T)0;
     r.y = (T)-1;
-  } else {  // lev == 2
+  } else if (lev == 2) {
     r.x = (cc == 1) ? h : (cc == 2) ? (T)0 : -h;
     r.y = (cc == 2) ? (T)-1 : -h;
+  } else {  // lev == 3: cos and -sin of 2 pi cc / 16
+    const T cn = (cc == 0) ? (T)1 : (cc == 1) ? c1 : (cc == 2) ? h : (cc == 3) ? s1 : (cc == 4) ? (T)0
+               : (cc == 5) ? -s1 : (cc == 6) ? -h : -c1;
+    const T sn = (cc == 0) ? (T)0 : (cc == 1) ? s1 : (cc == 2) ? h : (cc == 3) ? c1 : (cc == 4) ? (T)1
+               : (cc == 5) ? c1 : (cc == 6) ? h : s1;
+    r.x = cn;
+    r.y = -sn;
   }
   if (dir > 0) r.y = -r.y;
   return r;
@@ -169,8 +177,10 @@ __device__ void fft_core(T2 *a, int n, int batch, int stride, int dir, const T2 
   if (n <= 1) return;
   const int lg = 31 - __clz(n);
   const int lgtw = 31 - __clz(TW);
+  // passes of four stages (16 elements per thread), then the remainder
   int sh = 0;
-  for (; sh + 3 <= lg; sh += 3) dit_pass<3, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  for (; sh + 4 <= lg; sh += 4) dit_pass<4, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  if (lg - sh == 3) dit_pass<3, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
   if (lg - sh == 2) dit_pass<2, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
   if (lg - sh == 1) dit_pass<1, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
 }
@@ -271,30 +281,36 @@ template <typename T, typename T2>
 __device__ void bluestein_batch(T2 *y, int n, int ystride, int M, int batch, T2 *work, int wstride,
                                 const T2 *__restrict__ bhr, const T2 *__restrict__ chirp,
                                 const T2 *__restrict__ tw, int TW) {
-  const int lg = 31 - __clz(M);
+  const int lg = 31 - __clz(M);  // M >= 2n >= 8 for every Bluestein length
   const int lgtw = 31 - __clz(TW);
-  // ---- forward DIF: passes of three stages from the top, then the remainder
-  const int r = lg % 3;
-  int sh = lg - 3;
-  if (sh < 0) return;  // M >= 2n >= 8 for every Bluestein length
-  if (sh == 0 && r == 0) {
-    bs_dif_pass<3, true, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+  // ---- forward DIF: passes of four stages from the top (three when M = 8), then the
+  // remainder; the first pass reads the chirped input, the last applies the spectrum
+  if (lg < 4) {
+    if (lg == 3) bs_dif_pass<3, true, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
   } else {
-    bs_dif_pass<3, true, false, T, T2>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
-    for (sh -= 3; sh >= 0; sh -= 3) {
-      if (sh == 0 && r == 0)
-        bs_dif_pass<3, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
-      else
-        bs_dif_pass<3, false, false, T, T2>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
+    const int r = lg % 4;
+    int sh = lg - 4;
+    if (sh == 0) {
+      bs_dif_pass<4, true, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+    } else {
+      bs_dif_pass<4, true, false, T, T2>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
+      for (sh -= 4; sh >= 0; sh -= 4) {
+        if (sh == 0)
+          bs_dif_pass<4, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+        else
+          bs_dif_pass<4, false, false, T, T2>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
+      }
+      if (r == 3) bs_dif_pass<3, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+      if (r == 2) bs_dif_pass<2, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+      if (r == 1) bs_dif_pass<1, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
     }
-    if (r == 2) bs_dif_pass<2, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
-    if (r == 1) bs_dif_pass<1, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
   }
-  // ---- inverse DIT, natural order out: passes of three stages from the bottom; the
-  // top pass (the remaining 1, 2 or 3 stages) writes the chirped outputs p < n to y
+  // ---- inverse DIT, natural order out: passes of four stages from the bottom; the
+  // top pass (the remaining 1 to 4 stages) writes the chirped outputs p < n to y
   int s0 = 0;
-  for (; s0 + 3 < lg; s0 += 3) dit_pass<3, true, T, T2>(work, lg, batch, wstride, s0, +1, tw, lgtw);
+  for (; s0 + 4 < lg; s0 += 4) dit_pass<4, true, T, T2>(work, lg, batch, wstride, s0, +1, tw, lgtw);
   const int R = lg - s0;
+  if (R == 4) dit_last<4, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
   if (R == 3) dit_last<3, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
   if (R == 2) dit_last<2, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
   if (R == 1) dit_last<1, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
