@@ -113,7 +113,10 @@ __device__ __forceinline__ void fold_pair(const T2 *__restrict__ FA, const T2 *_
   gb = hasb ? rot_ik(ab, kB) : ab;
 }
 
-template <typename T>
+// BLUE: the launch's rings have non-power-of-two sub-transforms (Bluestein); else
+// power-of-two ones. A launch covers one ring group, so each instance carries one
+// sub-transform path (and its own register allocation).
+template <typename T, bool BLUE>
 __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
                                                       BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
   // swizzled layout, stored in bit-reversed order (the input order of the in-place
   // FFT); other ni: plain, with SY = 4 mod 16 so that the four arrays fall on
   // different banks.
-  const bool pw2 = (ni & (ni - 1)) == 0;
+  const bool pw2 = !BLUE;  // the group is of one kind: (ni & (ni - 1)) == 0 iff !BLUE
   const int lgni = 31 - __clz(ni);
   const int SY = ring_sub_stride(ni);
   T2 *Y = (T2 *)smem_raw;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
   __syncthreads();
 
   // ---- four length-ni inverse DFTs
-  if (pw2) {
+  if (!BLUE) {
     if (yswz)
       fft_core<true, T, T2>(Y, ni, 4, SY, +1, tw, TW);
     else
@@ -633,12 +636,14 @@ static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const 
     jl.job[i].scalef = (float)jobs[i].scale;
     jl.job[i].out = jobs[i].out;
   }
-  TL_CUDA_TRY(set_group_smem(p, ringfft_kernel<T>));
+  TL_CUDA_TRY(set_group_smem(p, ringfft_kernel<T, false>));
+  TL_CUDA_TRY(set_group_smem(p, ringfft_kernel<T, true>));
   for (int gi = 0; gi < p->fft_ngroups; ++gi) {
     const FftGroup &g = p->fft_groups[gi];
     const int batch = group_batch(p, g);
     dim3 grid(g.count, (njobs + 1) / 2);
-    ringfft_kernel<T><<<grid, 512, group_smem(p, g, batch), s>>>(
+    auto kern = g.M ? ringfft_kernel<T, true> : ringfft_kernel<T, false>;
+    kern<<<grid, 512, group_smem(p, g, batch), s>>>(
         p->ring, p->nside, p->mmax, jl, p->blue,
         (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (T)(1.0 / (double)(p->lmax + 1)),
         p->fft_rings + g.first);
