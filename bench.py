@@ -50,8 +50,8 @@ FP32_LANES = 152 * 128
 # kernel sources it was taken at. The full-size workload scales them by its pixel count
 # (rings x m grows the same way); a changed source, another order or form gives null.
 TRAFFIC_NSIDE512 = {
-    "fft_total": (838.7e6, ["ringfft.cu", "fft.cuh"], "ba815d8e5303a587"),
-    "gather_total": (624.7e6, ["gather.cu", "geometry.cuh"], "0da694ee9a9fee8b"),
+    "fft_total": (838.7e6, ["ringfft.cu", "fft.cuh"], "6c26b53500746294"),
+    "gather_total": (624.6e6, ["gather.cu", "geometry.cuh"], "3d99eb1ac9a9bebc"),
     "legendre_QU": (7.520e9, ["legendre_umma.cu", "legendre.cuh"], "2bde86836b1401f0"),
     "legendre_T": (4.230e9, ["legendre_umma.cu", "legendre.cuh"], "2bde86836b1401f0"),
 }
