@@ -3,12 +3,13 @@
 One step = one full lensing pass through the C ABI (deflection synthesis, Legendre
 stage of T and Q/U with all derivative orders, ring FFTs into the derivative maps,
 gather + Taylor sum + rotation) for the step's synthetic skies, whose coefficients
-are already resident in HBM. The headline form is the 3xTF32 tensor-core
-contraction (tcgen05) with sixteen realisations per Legendre launch (--form, --batch); the plain
-FP64 GPU form is timed on the same GPU beside it.
+are already resident in HBM. The headline form is the BF16x3 tensor-core
+contraction (tcgen05; each operand split into BF16 hi + lo, FP32 accumulation) with
+sixteen realisations per Legendre launch (--form, --batch); the plain FP64 GPU form is
+timed on the same GPU beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--form fp32|tf32|tf32x3]
+                  [--workload NAME] [--form fp32|tf32|tf32x3|bf16x3]
 
 Other workloads: batched64_n4_TQU (64 uneven realisations in one batch) and
 adjoint_nside1024_lmax2048_n4_TQU (one gradient evaluation of a quadratic map loss
@@ -43,25 +44,30 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
 FP32_LANES = 152 * 128
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# `bench.py --workload nside512_lmax1024_n4_TQU --steps 1 --warmup 1` (3xTF32, 16
-# realisations per launch; profiles/traffic_nside512_lmax1024_n4_tf32x3.md): bytes per
-# realisation (ring FFTs, gather) or per Legendre launch, with the sha256 prefix of the
-# kernel sources it was taken at. The full-size workload scales them by its pixel count
-# (rings x m grows the same way); a changed source, another order or form gives null.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of
+# `bench.py --workload nside512_lmax1024_n4_TQU --steps 1 --warmup 1 --form F` (16
+# realisations per launch; profiles/traffic_nside512_lmax1024_n4_bf16x3.md): bytes per
+# realisation (ring FFTs, gather: the same in every tensor-core form) or per Legendre
+# launch of form F, with the sha256 prefix of the kernel sources it was taken at. The
+# full-size workload scales them by its pixel count (rings x m grows the same way); a
+# changed source, another order or form gives null.
 TRAFFIC_NSIDE512 = {
-    "fft_total": (838.7e6, ["ringfft.cu", "fft.cuh"], "6c26b53500746294"),
-    "gather_total": (624.6e6, ["gather.cu", "geometry.cuh"], "3d99eb1ac9a9bebc"),
-    "legendre_QU": (7.520e9, ["legendre_umma.cu", "legendre.cuh"], "2bde86836b1401f0"),
-    "legendre_T": (4.230e9, ["legendre_umma.cu", "legendre.cuh"], "2bde86836b1401f0"),
+    ("fft_total", None): (839.2e6, ["ringfft.cu", "fft.cuh"], "6c26b53500746294"),
+    ("gather_total", None): (624.6e6, ["gather.cu", "geometry.cuh"], "3d99eb1ac9a9bebc"),
+    ("legendre_QU", "bf16x3"): (7.423e9, ["legendre_umma.cu", "legendre.cuh"], "b84f954284ab2909"),
+    ("legendre_T", "bf16x3"): (4.285e9, ["legendre_umma.cu", "legendre.cuh"], "b84f954284ab2909"),
+    ("legendre_QU", "tf32x3"): (7.510e9, ["legendre_umma.cu", "legendre.cuh"], "b84f954284ab2909"),
+    ("legendre_T", "tf32x3"): (4.244e9, ["legendre_umma.cu", "legendre.cuh"], "b84f954284ab2909"),
 }
 
 
-def captured_traffic(stage, w, per_step_units):
-    """Scaled DRAM bytes of a stage for workload w, or None (see TRAFFIC_NSIDE512)."""
-    if stage not in TRAFFIC_NSIDE512 or w.order != 4:
+def captured_traffic(stage, w, per_step_units, form):
+    """Scaled DRAM bytes of a stage for workload w and contraction form, or None
+    (see TRAFFIC_NSIDE512)."""
+    key = (stage, None) if (stage, None) in TRAFFIC_NSIDE512 else (stage, form)
+    if key not in TRAFFIC_NSIDE512 or w.order != 4:
         return None
-    byt, files, sha = TRAFFIC_NSIDE512[stage]
+    byt, files, sha = TRAFFIC_NSIDE512[key]
     m = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_1307_0719_gb300", "csrc", f), "rb") as fh:
@@ -236,7 +242,7 @@ def run_ours(args):
     from paper_1307_0719_gb300 import api
 
     w = skygen.WORKLOADS[args.workload]
-    forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3}
+    forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3, "bf16x3": api.MIXED_BF16x3}
     prec = forms[args.form]
     plan = api.Plan(w.nside, w.lmax, w.order, pol=w.pol, precision=prec)
     # one Legendre launch's worth of realisations per step (16 on the tensor cores)
@@ -307,7 +313,7 @@ def run_ours(args):
         ach = fl / (stage_ms[st] / 1e3) / 1e12
         e = {"kernel": f"legendre_spin{spin}_{'umma' if tc else 'kernel'}<{w.order}>", "bound": "alu",
              "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
-             "traffic": captured_traffic(st, w, 1) if (tc and args.form == "tf32x3" and nb == 16) else None,
+             "traffic": captured_traffic(st, w, 1, args.form) if (tc and nb == 16) else None,
              "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
              "counts": "recurrence only (contraction on the tensor cores)" if tc else "recurrence + contraction"}
         if tc:
@@ -325,7 +331,7 @@ def run_ours(args):
         ach = byt / (stage_ms[st] / 1e3) / 1e9 if stage_ms.get(st) else None
         rl[st] = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                   "frac": (ach / hbm) if (ach and hbm) else None,
-                  "traffic": captured_traffic(st, w, nchunk) if (tc and args.form == "tf32x3") else None,
+                  "traffic": captured_traffic(st, w, nchunk, args.form) if tc else None,
                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)",
                   "algorithmic_bytes": byt}
     dom = max(rl, key=lambda k: stage_ms.get(k, 0.0))
@@ -417,13 +423,14 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[args.form],
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}[args.form],
             "data": "synthetic (seeded Gaussian alm, analytic spectra)",
             "config": {"workload": args.workload, "nside": w.nside, "lmax": w.lmax, "order": w.order,
                        "fields": "TQU", "form": {"fp32": "mixed FP32 (SIMT contraction)",
                                                  "tf32": "mixed, TF32 tensor-core contraction",
-                                                 "tf32x3": "mixed, 3xTF32 tensor-core contraction"}[args.form]
-                       + "; FP64 seeds and rescaling; double pixel lookup", "realisations_per_step": nb,
+                                                 "tf32x3": "mixed, 3xTF32 tensor-core contraction",
+                                                 "bf16x3": "mixed, BF16x3 tensor-core contraction"}[args.form]
+                       + "; FP64 seeds and rescaling; float pixel lookup with double fallback", "realisations_per_step": nb,
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (alm 537 MB, "
                        "derivative maps 9 GB per step)"},
             "stage_ms": stage_ms, "roofline": roof, "roofline_stages": rl, "clocks": clocks,
@@ -444,7 +451,7 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1307_0719_gb300 import api
-    forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3}
+    forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3, "bf16x3": api.MIXED_BF16x3}
     lst = skygen.batched_lmax_list(64)
     mine = [lst[i] for i in shard(len(lst), rank, world)]
     nsides = [x[1] for x in mine]
@@ -510,7 +517,7 @@ def run_adjoint(args):
     os.environ["TAYLENS_TIMING"] = "1"
     from paper_1307_0719_gb300 import api
     w = skygen.WORKLOADS["nside1024_lmax2048_n4_TQU"]
-    forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3}
+    forms = {"fp32": api.MIXED_FP32, "tf32": api.MIXED_TF32, "tf32x3": api.MIXED_TF32x3, "bf16x3": api.MIXED_BF16x3}
     form = args.form if args.form_given else "fp32"
     sky = skygen.make_sky(w.nside, w.lmax, True, w.seed_t + 1000 * rank, w.seed_e + 1000 * rank,
                           w.seed_phi + 1000 * rank, w.damp_t, w.damp_e)
@@ -612,7 +619,7 @@ def run_adjoint(args):
         line = {
             "metric": ADJ_METRIC, "value": value, "unit": "gradient evaluations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}[form],
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}[form],
             "data": "synthetic (seeded Gaussian alm, analytic spectra; targets from seeds 9000-9002)",
             "config": {"workload": ADJ_WORKLOAD, "nside": w.nside, "lmax": w.lmax, "order": w.order,
                        "fields": "TQU", "form": form + "; FP64 geometry and Jacobian",
@@ -635,7 +642,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=sorted(skygen.WORKLOADS) + ["batched64_n4_TQU", ADJ_WORKLOAD])
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--form", default=None, choices=["fp32", "tf32", "tf32x3"])
+    ap.add_argument("--form", default=None, choices=["fp32", "tf32", "tf32x3", "bf16x3"])
     ap.add_argument("--batch", type=int, default=0,
                     help="realisations per step (default: the plan's Legendre batch, 16 on tensor cores)")
     ap.add_argument("--sample-pixels", type=int, default=16)
@@ -645,7 +652,7 @@ def main():
     args = ap.parse_args()
     args.form_given = args.form is not None
     if args.form is None:
-        args.form = "tf32x3"
+        args.form = "bf16x3"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64_n4_TQU":

@@ -54,15 +54,19 @@ enum { TL_SPIN_T = 1, TL_SPIN_QU = 2 };
 /* `precision`: arithmetic of the Legendre stage, ring FFTs and Taylor sums.
  * TL_FP64          everything in double.
  * TL_MIXED_FP32    float recurrence and contraction with double seeds and
- *                  exponent rescaling; float maps; double pixel lookup.
+ *                  exponent rescaling; float maps; float pixel lookup with a
+ *                  double fallback near cell edges.
  * TL_MIXED_TF32    as TL_MIXED_FP32, but tl_lens / tl_lens_batch contract the
  *                  recurrence against the coefficients on the tensor cores
  *                  (tcgen05, accumulators in tensor memory) in TF32 (10-bit
- *                  mantissas, FP32 accumulation), up to eight realisations per
- *                  Legendre launch.
+ *                  mantissas, FP32 accumulation), up to sixteen realisations
+ *                  per Legendre launch.
  * TL_MIXED_TF32x3  the same with each operand split into TF32 hi + lo parts and
  *                  three products accumulated (errors close to FP32).
- * TL_MIXED_BF16x3  declared, not built (TL_ERR_UNSUPPORTED).
+ * TL_MIXED_BF16x3  the same with each operand split into BF16 hi + lo parts
+ *                  (8 significant bits each) and the products hi.hi, lo.hi,
+ *                  hi.lo and lo.lo accumulated by two K = 16 BF16 MMAs per
+ *                  8 values of l.
  * tl_synth_derivs and tl_deflection use the float (SIMT) stage in all mixed forms. */
 enum { TL_FP64 = 0, TL_MIXED_FP32 = 1, TL_MIXED_TF32 = 2, TL_MIXED_TF32x3 = 3, TL_MIXED_BF16x3 = 4 };
 
@@ -75,7 +79,8 @@ enum { TL_ROTATE = 1 /* apply the polarisation rotation R of Eq. 2 (default on) 
  *   lmax      1 .. 4 nside (band limit of every field, including phi)
  *   order     Taylor order n, 0 .. 6 (total degree j + k <= n; 0 = nearest-pixel lookup)
  *   spins     TL_SPIN_T, TL_SPIN_QU or both
- *   precision TL_FP64, TL_MIXED_FP32, TL_MIXED_TF32 or TL_MIXED_TF32x3
+ *   precision TL_FP64, TL_MIXED_FP32, TL_MIXED_TF32, TL_MIXED_TF32x3 or
+ *             TL_MIXED_BF16x3
  *   flags     TL_ROTATE or 0
  *   out       receives the plan; unchanged on error
  * Allocates the plan's device tables and workspace on the current device.
@@ -139,9 +144,10 @@ tl_status tl_lens(tl_plan *plan, const double *alm_T, const double *alm_E, const
  * Lens nreal realisations of this plan's geometry in one call. Arrays of nreal
  * device pointers (host arrays); entries as in tl_lens; alm_B may be NULL (all
  * B = 0); alm_phi may be NULL (none lensed), otherwise every entry must be set.
- * On tensor-core plans (TL_MIXED_TF32, TL_MIXED_TF32x3) realisations go through
- * the Legendre stage eight at a time, sharing the recurrence (the coefficient sets
- * of all eight fill the 32 columns of one tensor-core product); ring FFTs and the
+ * On tensor-core plans (TL_MIXED_TF32, TL_MIXED_TF32x3, TL_MIXED_BF16x3)
+ * realisations go through the Legendre stage tl_plan_batch at a time (16, or 8 at
+ * order 6), sharing the recurrence (the coefficient sets of all of them fill the
+ * 64 (32) columns of one tensor-core product); ring FFTs and the
  * gather then run per realisation. On other plans this equals nreal calls of
  * tl_lens.
  */
@@ -221,7 +227,7 @@ tl_status tl_deflection_noalloc(int nside, int lmax, int precision, const double
  *   tl_batch_create: nreal realisations, nside[i], lmax[i] (host arrays).
  *   tl_batch_lens modes:
  *     TL_BATCH_LOOP        one tl_lens call per realisation (the comparison point);
- *     TL_BATCH_PERSISTENT  tensor-core plans only: waves of up to eight realisations per group, each
+ *     TL_BATCH_PERSISTENT  tensor-core plans only: waves of up to tl_plan_batch realisations per group, each
  *                          wave's Legendre stage in one persistent launch whose
  *                          blocks take (plan, spin, m, ring block) items, sorted
  *                          by cost, from an atomic counter (no waits between blocks);

@@ -13,6 +13,7 @@ FP64 = _lib.TL_FP64
 MIXED_FP32 = _lib.TL_MIXED_FP32
 MIXED_TF32 = _lib.TL_MIXED_TF32
 MIXED_TF32x3 = _lib.TL_MIXED_TF32x3
+MIXED_BF16x3 = _lib.TL_MIXED_BF16x3
 
 
 def _ptr(t):

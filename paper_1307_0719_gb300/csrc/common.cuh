@@ -76,7 +76,7 @@ struct tl_plan {
   void *tab0, *tab2;    // plan-time step tables {k_l, A_{l+1}} for spin 0 and spin 2
   void *rec_T, *rec_P, *rec_QU; // coefficient records
   void *d7_T, *d7_Q, *d7_U, *d7_P; // per-ring Fourier coefficients [j][ring][m] (T2)
-  // tensor-core Legendre stage (TL_MIXED_TF32, TL_MIXED_TF32x3): blocks of 8 l per m
+  // tensor-core Legendre stage (TL_MIXED_TF32, TL_MIXED_TF32x3, TL_MIXED_BF16x3): blocks of 8 l per m
   int batch;             // realisations sharing one Legendre launch (1, or 8 on tensor cores)
   int tc_nder;           // derivative orders carried there (max(order, 1))
   long long *tc_blk0, *tc_blk2;   // [lmax+1] first block of each m (spin 0 / spin 2)

@@ -16,7 +16,11 @@
 // sets of up to NC/4 realisations that share the basis (4 reals each):
 //   spin 2: k_l (E + iB), k_l (-1)^(l+m) (E - iB);   spin 0: k_l a, k_l (-1)^(l+m) a.
 // TF32 keeps 10 mantissa bits of each operand; the 3xTF32 form splits both into
-// hi + lo and accumulates hi.hi + hi.lo + lo.hi (errors near FP32).
+// hi + lo and accumulates hi.hi + hi.lo + lo.hi (errors near FP32). The BF16x3
+// form splits both into BF16 hi + lo (8 significant bits each) and runs two
+// kind::f16 MMAs of K = 16 per order and block: the basis tile is [hi | lo] of
+// the block's 8 values of l along K, and the coefficient tiles are [hi ; hi] and
+// [lo ; lo], so the two products give hi.hi + lo.hi and hi.lo + lo.lo.
 //
 // Why 64 columns and the basis in tensor memory: measured on GB300, one CTA's
 // chain of these small MMAs advances at ~50 cycles per instruction whatever N is
@@ -55,7 +59,14 @@ constexpr uint32_t kXchBytes = 128 * 16 * 4;  // spin-2 epilogue exchange [128][
 // up to NDER = 5, 32 (8) at NDER = 6, where 64 would not fit tensor memory
 __host__ __device__ constexpr int tc_cols(int nder) { return nder <= 5 ? 64 : 32; }
 // coefficient tile of NC columns in shared memory: hi [NC x 8] then lo, TF32
+// (BF16x3: [hi ; hi] then [lo ; lo], NC x 16 BF16 each); the same bytes either way
 __host__ __device__ constexpr uint32_t btile_bytes(int nc) { return (uint32_t)nc * 64u; }
+
+// contraction forms of the tensor-core kernels (template parameter MODE)
+constexpr int kModeTf32 = 1, kModeTf32x3 = 3, kModeBf16x3 = 4;
+inline int tc_mode(int precision) {
+  return precision == TL_MIXED_TF32x3 ? kModeTf32x3 : precision == TL_MIXED_BF16x3 ? kModeBf16x3 : kModeTf32;
+}
 
 // ---------------------------------------------------------------------------
 // tcgen05 building blocks
@@ -76,10 +87,11 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D f32, A and B tf32, both K-major, M = 128, N = NC
-template <int NC> struct Idesc {
+// instruction descriptor: D f32, A and B tf32 (BF16: bf16), both K-major, M = 128, N = NC
+template <int NC, bool BF16 = false> struct Idesc {
+  static constexpr uint32_t ab = BF16 ? 1u : 2u;
   static constexpr uint32_t value =
-      (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NC >> 3) << 17) | ((128u >> 4) << 24);
+      (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(NC >> 3) << 17) | ((128u >> 4) << 24);
 };
 
 // D (tensor memory) += A (tensor memory: row i in lane i, K along 8 columns) . B (shared memory)
@@ -89,6 +101,16 @@ __device__ __forceinline__ void umma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, u
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
       "r"(tmem_a), "l"(db), "n"(Idesc<NC>::value), "r"(accumulate));
+}
+
+// the same with A and B in BF16, K = 16 (A: two values per tensor-memory column,
+// the lower k in the low half)
+template <int NC>
+__device__ __forceinline__ void umma_bf16_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t db, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(db), "n"(Idesc<NC, true>::value), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
@@ -155,14 +177,26 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 // cleared (exactly a TF32 number), lo = value - hi (exact; the tensor core reads
 // its top 19 bits), so the pair carries ~21 bits
 __device__ __forceinline__ float tf32_trunc(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+// two floats rounded to BF16 (nearest even) in one word: x0 in the low half
+__device__ __forceinline__ uint32_t bf16x2(float x0, float x1) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+  return r;
+}
+// BF16x3 split of a pair: hi = the BF16 roundings, lo = the BF16 roundings of the
+// (exact) remainders
+__device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+  hi = bf16x2(x0, x1);
+  lo = bf16x2(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xffff0000u));
+}
 
 // Tensor-memory map of a CTA: accumulators D^(j) at columns NC j (j < NJ), then
 // NB sets of basis tiles: Mu^(j) of buffer i at A0 + i ASET + AW j (hi in 8
-// columns, then lo for 3xTF32). Two buffers where they fit the 512 columns, else
+// columns, then lo for 3xTF32; BF16x3: hi pairs in 4 columns, lo pairs in 4). Two buffers where they fit the 512 columns, else
 // one. The allocation is the next power of two; `ctas` is how many CTAs of that
 // size fit the SM (at most 4).
 template <int NJ, int MODE, int NC> struct TmemMap {
-  static constexpr int AW = MODE == 3 ? 16 : 8;
+  static constexpr int AW = MODE == kModeTf32x3 ? 16 : 8;
   static constexpr int A0 = NJ * NC;
   static constexpr int ASET = NJ * AW;
   static constexpr int NB = A0 + 2 * ASET <= 512 ? 2 : 1;
@@ -246,41 +280,60 @@ __device__ __forceinline__ void steps_gated(float (&a)[NDER + 1], float (&b)[NDE
 }
 
 // the block's basis values of every order into the calling thread's lane: hi (and
-// lo for 3xTF32) of l = l0 + 8 blk + 0..7, at column a0 + AW j
+// lo for 3xTF32) of l = l0 + 8 blk + 0..7, at column a0 + AW j; BF16x3: the hi
+// pairs (l, l + 1) in 4 columns, then the lo pairs
 template <int NDER, int MODE>
 __device__ __forceinline__ void store_tiles(uint32_t a0, const float (&buf0)[NDER + 1][4],
                                             const float (&buf1)[NDER + 1][4]) {
-  constexpr int AW = MODE == 3 ? 16 : 8;
+  constexpr int AW = MODE == kModeTf32x3 ? 16 : 8;
 #pragma unroll
   for (int j = 0; j <= NDER; ++j) {
     float v[16];
+    if (MODE == kModeBf16x3) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float x0 = q < 2 ? buf0[j][2 * q] : buf1[j][2 * q - 4];
+        const float x1 = q < 2 ? buf0[j][2 * q + 1] : buf1[j][2 * q - 3];
+        uint32_t hi, lo;
+        bf16_split2(x0, x1, hi, lo);
+        v[q] = __uint_as_float(hi);
+        v[4 + q] = __uint_as_float(lo);
+      }
+      tmem_st8(a0 + (uint32_t)(AW * j), v);
+      continue;
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const float x = k < 4 ? buf0[j][k] : buf1[j][k - 4];
-      if (MODE == 3) {
+      if (MODE == kModeTf32x3) {
         v[k] = tf32_trunc(x);
         v[8 + k] = x - v[k];
       } else {
         v[k] = __uint_as_float(to_tf32(x));
       }
     }
-    if (MODE == 3)
+    if (MODE == kModeTf32x3)
       tmem_st16(a0 + (uint32_t)(AW * j), v);
     else
       tmem_st8(a0 + (uint32_t)(AW * j), v);
   }
 }
 
-// D^(j) += Mu^(j) . C for j < NJ (and the lo terms for 3xTF32), basis tiles at
-// column aset, coefficient tile at descriptor dB (its lo half btile/2 bytes on)
+// D^(j) += Mu^(j) . C for j < NJ (and the lo terms for 3xTF32 and BF16x3), basis
+// tiles at column aset, coefficient tile at descriptor dB (its lo half btile/2 bytes on)
 template <int NJ, int MODE, int NC>
 __device__ __forceinline__ void issue_block(uint32_t tmem, uint32_t aset, uint64_t dB, bool first) {
   typedef TmemMap<NJ, MODE, NC> TM;
 #pragma unroll
   for (int j = 0; j < NJ; ++j) {
     const uint32_t d = tmem + (uint32_t)(NC * j), a = tmem + aset + (uint32_t)(TM::AW * j);
+    if (MODE == kModeBf16x3) {
+      umma_bf16_ts<NC>(d, a, dB, first ? 0u : 1u);                     // [hi | lo] . [hi ; hi]
+      umma_bf16_ts<NC>(d, a, dB + ((btile_bytes(NC) / 2) >> 4), 1u);  // [hi | lo] . [lo ; lo]
+      continue;
+    }
     umma_tf32_ts<NC>(d, a, dB, first ? 0u : 1u);
-    if (MODE == 3) {
+    if (MODE == kModeTf32x3) {
       umma_tf32_ts<NC>(d, a, dB + ((btile_bytes(NC) / 2) >> 4), 1u);  // hi . lo
       umma_tf32_ts<NC>(d, a + 8u, dB, 1u);                             // lo . hi
     }
@@ -732,7 +785,9 @@ __global__ void tcstep_kernel(int lmax, int s, const long long *__restrict__ blk
 
 // Coefficient tiles per 8-l block: B[n][k] for column n = 4 rho + c (n < NC) and
 // l = l0 + 8 blk + k, as TF32 hi (first NC x 32 bytes) and lo (next), K-major
-// without swizzle.
+// without swizzle. BF16x3 (bf16 != 0): the first half holds B[n][k] for k < 16 with
+// the BF16 hi of l0 + 8 blk + (k mod 8), the second half the same with the lo parts,
+// matching the basis tile [hi | lo] along K.
 //   spin 2: c = 0,1: k_l (E + iB) re, im;  c = 2,3: k_l (-1)^(l+m) (E - iB) re, im
 //   spin 0: c = 0,1: k_l a re, im;         c = 2,3: k_l (-1)^(l+m) a re, im
 struct TcAlm {
@@ -743,7 +798,7 @@ struct TcAlm {
 // One warp per (8-l block, 32 columns) (blocks of all m numbered contiguously; the
 // block's m by binary search in blkofs); lane n owns column 32 h + n: it forms the
 // column's 8 values and writes their hi and lo parts as 16-byte vectors.
-__global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal, int nc, TcAlm alm,
+__global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal, int nc, int bf16, TcAlm alm,
                                                      const long long *__restrict__ blkofs, long long nblocks,
                                                      const float2 *__restrict__ tab, unsigned char *__restrict__ out) {
   const int groups = nc >> 5;
@@ -782,11 +837,27 @@ __global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal,
       }
     }
     const float v = (float)val;
-    hv[k] = __uint_as_float(to_tf32(v));
-    lv[k] = __uint_as_float(to_tf32(v - hv[k]));
+    if (bf16) {
+      hv[k] = v;
+    } else {
+      hv[k] = __uint_as_float(to_tf32(v));
+      lv[k] = __uint_as_float(to_tf32(v - hv[k]));
+    }
   }
   const uint32_t half = btile_bytes(nc) / 2;
   unsigned char *o = out + B * (2 * half);
+  if (bf16) {
+    uint4 h, l;
+    bf16_split2(hv[0], hv[1], h.x, l.x);
+    bf16_split2(hv[2], hv[3], h.y, l.y);
+    bf16_split2(hv[4], hv[5], h.z, l.z);
+    bf16_split2(hv[6], hv[7], h.w, l.w);
+    *(uint4 *)(o + can_off(n, 0)) = h;  // k = 0..7 (against the basis hi)
+    *(uint4 *)(o + can_off(n, 4)) = h;  // k = 8..15 (against the basis lo)
+    *(uint4 *)(o + half + can_off(n, 0)) = l;
+    *(uint4 *)(o + half + can_off(n, 4)) = l;
+    return;
+  }
   *(float4 *)(o + can_off(n, 0)) = make_float4(hv[0], hv[1], hv[2], hv[3]);
   *(float4 *)(o + can_off(n, 4)) = make_float4(hv[4], hv[5], hv[6], hv[7]);
   *(float4 *)(o + half + can_off(n, 0)) = make_float4(lv[0], lv[1], lv[2], lv[3]);
@@ -816,8 +887,10 @@ cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *cons
   const long long nblocks = (s == 2) ? p->tc_nblk2 : p->tc_nblk0;
   if (nblocks == 0) return cudaSuccess;
   const long long warps = nblocks * (nc / 32);
-  tcprep_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(p->lmax, s, nreal, nc, alm, blkofs, nblocks,
-                                                             (const float2 *)tab, (unsigned char *)out);
+  tcprep_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(p->lmax, s, nreal, nc,
+                                                             tc_mode(p->precision) == kModeBf16x3 ? 1 : 0, alm,
+                                                             blkofs, nblocks, (const float2 *)tab,
+                                                             (unsigned char *)out);
   return cudaGetLastError();
 }
 
@@ -891,7 +964,7 @@ static cudaError_t u2(const tl_plan *p, int nreal, void *dq, void *du, long long
   return cudaGetLastError();
 }
 
-template <int NDER, int MODE, int CNC>
+template <int NDER, int CNC, int MODE>
 static cudaError_t u0(const tl_plan *p, int which, int nreal, void *d7, long long rstride, cudaStream_t s) {
   typedef TmemMap<NDER + 1, MODE, CNC> TM;
   const size_t smem = umma_smem<TM::ctas, CNC>();
@@ -914,12 +987,18 @@ static cudaError_t up(const void *descs, const void *items, int nitems, int *cou
 
 #define TL_TC_ORDERS(X) X(1) X(2) X(3) X(4) X(5) X(6)
 
+// the kernel instance of contraction form `mode` (kModeTf32, kModeTf32x3, kModeBf16x3)
+#define TL_TC_BY_MODE(mode, F, ...)                                          \
+  ((mode) == kModeTf32x3   ? F<__VA_ARGS__, kModeTf32x3>                     \
+   : (mode) == kModeBf16x3 ? F<__VA_ARGS__, kModeBf16x3>                     \
+                           : F<__VA_ARGS__, kModeTf32>)
+
 cudaError_t launch_legendre_tc_persistent(int nder, int precision, const void *descs, const void *items, int nitems,
                                           int *counter, int grid, cudaStream_t s) {
-  const bool x3 = precision == TL_MIXED_TF32x3;
+  const int mode = tc_mode(precision);
   switch (nder) {
 #define CASE(n) \
-  case n: return x3 ? up<n, 3>(descs, items, nitems, counter, grid, s) : up<n, 1>(descs, items, nitems, counter, grid, s);
+  case n: return TL_TC_BY_MODE(mode, up, n)(descs, items, nitems, counter, grid, s);
     TL_TC_ORDERS(CASE)
 #undef CASE
   }
@@ -929,10 +1008,10 @@ cudaError_t launch_legendre_tc_persistent(int nder, int precision, const void *d
 cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void *dq, void *du, long long rstride,
                                      cudaStream_t s) {
   if (nder != p->tc_nder) return cudaErrorInvalidValue;
-  const bool x3 = p->precision == TL_MIXED_TF32x3;
+  const int mode = tc_mode(p->precision);
   switch (nder) {
 #define CASE(n) \
-  case n: return x3 ? u2<n, 3>(p, nreal, dq, du, rstride, s) : u2<n, 1>(p, nreal, dq, du, rstride, s);
+  case n: return TL_TC_BY_MODE(mode, u2, n)(p, nreal, dq, du, rstride, s);
     TL_TC_ORDERS(CASE)
 #undef CASE
   }
@@ -943,18 +1022,16 @@ cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void
 // NDER = 1. The columns are the plan's either way (its coefficient tiles have that width).
 cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int which, int nreal, void *d7, long long rstride,
                                      cudaStream_t s) {
-  const bool x3 = p->precision == TL_MIXED_TF32x3;
+  const int mode = tc_mode(p->precision);
   const int nc = tc_cols(p->tc_nder);
   if (which == 1) {
-    if (nc == 64) return x3 ? u0<1, 3, 64>(p, 1, nreal, d7, rstride, s) : u0<1, 1, 64>(p, 1, nreal, d7, rstride, s);
-    return x3 ? u0<1, 3, 32>(p, 1, nreal, d7, rstride, s) : u0<1, 1, 32>(p, 1, nreal, d7, rstride, s);
+    if (nc == 64) return TL_TC_BY_MODE(mode, u0, 1, 64)(p, 1, nreal, d7, rstride, s);
+    return TL_TC_BY_MODE(mode, u0, 1, 32)(p, 1, nreal, d7, rstride, s);
   }
   if (which != 0) return cudaErrorInvalidValue;
   switch (p->tc_nder) {
-#define CASE(n)                                                                         \
-  case n:                                                                               \
-    return x3 ? u0<n, 3, tc_cols(n)>(p, 0, nreal, d7, rstride, s)                      \
-              : u0<n, 1, tc_cols(n)>(p, 0, nreal, d7, rstride, s);
+#define CASE(n) \
+  case n: return TL_TC_BY_MODE(mode, u0, n, tc_cols(n))(p, 0, nreal, d7, rstride, s);
     TL_TC_ORDERS(CASE)
 #undef CASE
   }
@@ -995,10 +1072,13 @@ size_t tc_start_units(const tl_plan *p, int which) {
 
 // CTAs per SM that the persistent kernel's tensor memory allows (for the grid size).
 int tc_persistent_ctas(int nder, int precision) {
-  const bool x3 = precision == TL_MIXED_TF32x3;
+  const int mode = tc_mode(precision);
   switch (nder) {
-#define CASE(n) \
-  case n: return x3 ? Tc<n, 3>::TM::ctas : Tc<n, 1>::TM::ctas;
+#define CASE(n)                                                   \
+  case n:                                                         \
+    return mode == kModeTf32x3   ? Tc<n, kModeTf32x3>::TM::ctas   \
+           : mode == kModeBf16x3 ? Tc<n, kModeBf16x3>::TM::ctas   \
+                                 : Tc<n, kModeTf32>::TM::ctas;
     TL_TC_ORDERS(CASE)
 #undef CASE
   }

@@ -170,7 +170,7 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   const size_t t2 = e2, rec0 = 4 * (size_t)p->elem, rec2 = 8 * (size_t)p->elem;
   const size_t plane = (size_t)p->nrings * (p->mmax + 1) * t2;
   const bool pol = (spins & TL_SPIN_QU) != 0;
-  const bool tc = (precision == TL_MIXED_TF32 || precision == TL_MIXED_TF32x3);
+  const bool tc = (precision == TL_MIXED_TF32 || precision == TL_MIXED_TF32x3 || precision == TL_MIXED_BF16x3);
   p->tc_nder = order > 1 ? order : 1;
   p->batch = tc ? tc_realisations(p->tc_nder) : 1;
   const int nplanes = tc ? p->tc_nder + 1 : order + 1;  // D7 planes per field and realisation
@@ -252,7 +252,6 @@ extern "C" tl_status tl_plan_create(int nside, int lmax, int order, int spins, i
     return (spins == TL_SPIN_QU) ? TL_ERR_UNSUPPORTED : TL_ERR_ARG;
   }
   if (precision < TL_FP64 || precision > TL_MIXED_BF16x3) return TL_ERR_ARG;
-  if (precision == TL_MIXED_BF16x3) return TL_ERR_UNSUPPORTED;
   if (flags & ~TL_ROTATE) return TL_ERR_ARG;
   // the ring FFT keeps a whole ring in shared memory
   {

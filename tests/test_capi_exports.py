@@ -41,7 +41,7 @@ def test_host_argument_checks(lib):
     assert lib.tl_plan_create(4, 17, 1, 1, 0, 1, ctypes.byref(h)) == L.TL_ERR_ARG     # lmax > 4 nside
     assert lib.tl_plan_create(4, 8, 7, 1, 0, 1, ctypes.byref(h)) == L.TL_ERR_ARG      # order > 6
     assert lib.tl_plan_create(4, 8, 2, 1, 9, 1, ctypes.byref(h)) == L.TL_ERR_ARG      # precision
-    assert lib.tl_plan_create(4, 8, 2, 1, L.TL_MIXED_BF16x3, 1, ctypes.byref(h)) == L.TL_ERR_UNSUPPORTED
+    assert lib.tl_plan_create(4, 8, 2, L.TL_SPIN_QU, 0, 1, ctypes.byref(h)) == L.TL_ERR_UNSUPPORTED  # Q/U alone
     assert lib.tl_plan_create(4, 8, 2, 1, 0, 4, ctypes.byref(h)) == L.TL_ERR_ARG      # flags
     assert lib.tl_lens(None, None, None, None, None, None, None, None, None) == L.TL_ERR_ARG
     assert lib.tl_plan_destroy(None) == L.TL_OK

@@ -127,7 +127,7 @@ def test_adjoint_dot_product_fp64():
 
 
 @pytest.mark.parametrize("precision,tol_teb,tol_phi", [("MIXED_FP32", 2e-4, 1e-3), ("MIXED_TF32x3", 2e-3, 5e-3),
-                                                       ("MIXED_TF32", 2e-3, 5e-3)])
+                                                       ("MIXED_BF16x3", 2e-3, 5e-3), ("MIXED_TF32", 2e-3, 5e-3)])
 def test_adjoint_mixed(precision, tol_teb, tol_phi):
     nside, lmax, order = 32, 64, 4
     s = sky(nside, lmax, pol=True, b_scale=0.5)

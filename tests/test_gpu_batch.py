@@ -28,9 +28,9 @@ def _skies():
             for i, (ns, lm) in enumerate(zip(NSIDES, LMAXS))]
 
 
-@pytest.mark.parametrize("order", [3, 5])
-def test_batch_modes_agree_and_match_oracle(order):
-    b = api.Batch(NSIDES, LMAXS, order, pol=True, precision=api.MIXED_TF32x3)
+@pytest.mark.parametrize("order,precision", [(3, "MIXED_TF32x3"), (5, "MIXED_TF32x3"), (4, "MIXED_BF16x3")])
+def test_batch_modes_agree_and_match_oracle(order, precision):
+    b = api.Batch(NSIDES, LMAXS, order, pol=True, precision=getattr(api, precision))
     try:
         assert b.groups == 4 and b.waves == 2
         skies = _skies()

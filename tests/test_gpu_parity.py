@@ -98,12 +98,12 @@ def test_lens_mixed_fp32(nside, lmax, order):
         assert rel_rms(out[i], ref[f]) < 1e-4, (f, rel_rms(out[i], ref[f]))
 
 
-@pytest.mark.parametrize("precision,tol", [(api.MIXED_TF32x3, 1e-4), (api.MIXED_TF32, 5e-3)])
+@pytest.mark.parametrize("precision,tol", [(api.MIXED_TF32x3, 1e-4), (api.MIXED_BF16x3, 1e-4), (api.MIXED_TF32, 5e-3)])
 @pytest.mark.parametrize("nside,lmax,order", [(32, 64, 4), (64, 128, 3), (16, 40, 1), (128, 203, 2), (16, 40, 5),
                                                (8, 21, 6)])
 def test_lens_tensor_core_forms(nside, lmax, order, precision, tol):
-    """Contraction on the tensor cores: 3xTF32 meets the mixed-precision target,
-    plain TF32 is reported with its own (looser) bound."""
+    """Contraction on the tensor cores: 3xTF32 and BF16x3 meet the mixed-precision
+    target, plain TF32 is reported with its own (looser) bound."""
     s = sky(nside, lmax, pol=True, b_scale=0.4)
     ref = OL.lens(nside, lmax, order, s["T"], s["E"], s["B"], s["phi"])
     d = to_dev(s)
@@ -112,11 +112,11 @@ def test_lens_tensor_core_forms(nside, lmax, order, precision, tol):
         assert rel_rms(out[i], ref[f]) < tol, (f, rel_rms(out[i], ref[f]))
 
 
-@pytest.mark.parametrize("precision,order", [(api.MIXED_TF32x3, 4), (api.MIXED_TF32x3, 5), (api.MIXED_FP32, 4),
-                                             (api.FP64, 4)])
+@pytest.mark.parametrize("precision,order", [(api.MIXED_TF32x3, 4), (api.MIXED_TF32x3, 5), (api.MIXED_BF16x3, 4),
+                                             (api.MIXED_BF16x3, 6), (api.MIXED_FP32, 4), (api.FP64, 4)])
 def test_lens_batch_equals_single_calls(precision, order):
-    """tl_lens_batch over 20 realisations (on tensor-core plans a group of sixteen
-    that shares one basis, then a group of four) gives what twenty tl_lens calls give."""
+    """tl_lens_batch over 20 realisations (on tensor-core plans groups of tl_plan_batch
+    that share one basis, then the rest) gives what twenty tl_lens calls give."""
     nside, lmax = 32, 64
     skies = [to_dev(sky(nside, lmax, pol=True, seeds=(10 + i, 20 + i, 30 + i), b_scale=0.3)) for i in range(20)]
     plan = api.Plan(nside, lmax, order, pol=True, precision=precision)
@@ -136,7 +136,8 @@ def test_plan_batch_and_launch_count():
     """tl_plan_batch: 16 realisations per Legendre launch on the tensor-core forms up to
     order 5, 8 at order 6, 1 otherwise; tl_plan_batch_launches matches the kernels a
     tl_lens_batch call launches (counted by the CUDA profiler when it is available)."""
-    plans = {(api.MIXED_TF32x3, 4): 16, (api.MIXED_TF32x3, 6): 8, (api.MIXED_FP32, 4): 1, (api.FP64, 3): 1}
+    plans = {(api.MIXED_TF32x3, 4): 16, (api.MIXED_TF32x3, 6): 8, (api.MIXED_BF16x3, 5): 16, (api.MIXED_BF16x3, 6): 8,
+             (api.MIXED_FP32, 4): 1, (api.FP64, 3): 1}
     for (prec, order), want in plans.items():
         p = api.Plan(16, 32, order, pol=True, precision=prec)
         try:
