@@ -85,6 +85,7 @@ struct tl_plan {
   // recurrence state there
   int *tc_bs0, *tc_bsp, *tc_bs2;
   float *tc_st0, *tc_stp, *tc_st2;
+  float *tc_sm0, *tc_smp, *tc_sm2;  // the same state at each unit's midpoint block (split units)
   float *tc_step0, *tc_step2;     // [blocks][16]: A_{l+1} x 8, m s/(l(l+1)) x 8
   void *tc_b0, *tc_bp, *tc_b2;    // [blocks] 2 KB coefficient tiles (TF32 hi, lo; 32 columns x 8 l)
   int *dev_err;                   // set by a kernel whose bounded wait timed out
@@ -160,7 +161,9 @@ cudaError_t launch_legendre_spin2_tc(const tl_plan *p, int nder, int nreal, void
 cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int which, int nreal, void *d7, long long rstride,
                                      cudaStream_t s);
 // start tables of the tensor-core Legendre stage (which: 0 T, 1 potential, 2 Q/U)
-cudaError_t launch_tcstart(const tl_plan *p, int which, int *bstart, float *state, cudaStream_t s);
+cudaError_t launch_tcstart(const tl_plan *p, int which, int *bstart, float *state, float *state_mid,
+                           cudaStream_t s);
+bool tc_split(const tl_plan *p, int which);
 size_t tc_start_state_bytes(const tl_plan *p, int which);
 size_t tc_start_units(const tl_plan *p, int which);
 cudaError_t launch_bluestein_setup(tl_plan *p, cudaStream_t s);

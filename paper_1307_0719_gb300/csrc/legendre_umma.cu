@@ -190,17 +190,25 @@ __device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t &hi, ui
   lo = bf16x2(x0 - __uint_as_float(hi << 16), x1 - __uint_as_float(hi & 0xffff0000u));
 }
 
+// Halves of the l range a unit is split into (two sets of compute warps on the
+// same rings, see run_blocks): 2 where both halves' basis tiles fit the 512
+// columns double-buffered, else 1.
+__host__ __device__ constexpr int tc_halves(int nj, int mode, int nc) {
+  return nj * nc + 4 * nj * (mode == kModeTf32x3 ? 16 : 8) <= 512 ? 2 : 1;
+}
+
 // Tensor-memory map of a CTA: accumulators D^(j) at columns NC j (j < NJ), then
-// NB sets of basis tiles: Mu^(j) of buffer i at A0 + i ASET + AW j (hi in 8
-// columns, then lo for 3xTF32; BF16x3: hi pairs in 4 columns, lo pairs in 4). Two buffers where they fit the 512 columns, else
-// one. The allocation is the next power of two; `ctas` is how many CTAs of that
-// size fit the SM (at most 4).
-template <int NJ, int MODE, int NC> struct TmemMap {
+// NH x NB sets of basis tiles: Mu^(j) of half h, buffer i at A0 + (h NB + i) ASET +
+// AW j (hi in 8 columns, then lo for 3xTF32; BF16x3: hi pairs in 4 columns, lo
+// pairs in 4). Two buffers per half where they fit the 512 columns, else one. The
+// allocation is the next power of two; `ctas` is how many CTAs of that size fit the
+// SM (at most 4).
+template <int NJ, int MODE, int NC, int NH = 1> struct TmemMap {
   static constexpr int AW = MODE == kModeTf32x3 ? 16 : 8;
   static constexpr int A0 = NJ * NC;
   static constexpr int ASET = NJ * AW;
-  static constexpr int NB = A0 + 2 * ASET <= 512 ? 2 : 1;
-  static constexpr int need = A0 + NB * ASET;
+  static constexpr int NB = A0 + NH * 2 * ASET <= 512 ? 2 : 1;
+  static constexpr int need = A0 + NH * NB * ASET;
   static constexpr int cols = need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
   static constexpr int ctas = 512 / cols > 4 ? 4 : 512 / cols;
   static_assert(need <= 512, "tensor memory");
@@ -223,23 +231,34 @@ struct TcDesc {
   // state at the start of that block: [unit][2 NJ + 1][128] (a, b, scale)
   const int *bstart;
   const float *state;
+  // the same state at the first block of the unit's second half (see run_blocks),
+  // or NULL (no split)
+  const float *state_mid;
   int nrblk;
 };
 
-// Per-CTA tcgen05 state (identical in every thread). The four mbarriers are
-// adjacent 8-byte words: done[0], done[1] (MMAs of the buffer's last block
-// completed; one arrival, the commit), full[0], full[1] (the block's tiles
-// written; one arrival per compute warp). Their addresses are formed
-// arithmetically: a runtime-indexed array member would put the struct in local memory.
+// Per-CTA tcgen05 state (identical in every thread). Each half h of the compute
+// warps has four mbarriers, adjacent 8-byte words from bars + 32 h: done[0],
+// done[1] (MMAs of the buffer's last block completed; one arrival, the commit),
+// full[0], full[1] (the block's tiles written; one arrival per compute warp of the
+// half). Their addresses are formed arithmetically: a runtime-indexed array member
+// would put the struct in local memory.
 struct UmmaCta {
   uint32_t tmem;        // tensor-memory base (lane 0, first column)
-  uint32_t bars;        // shared address of done[0]
-  uint32_t count;       // blocks so far
+  uint32_t bars;        // shared address of half 0's done[0]
+  uint32_t count;       // blocks so far, first half
+  uint32_t count1;      // blocks so far, second half
   volatile int *abort;  // shared: set by a thread whose wait timed out
   bool failed;
 };
-__device__ __forceinline__ uint32_t bar_done(const UmmaCta &U, uint32_t i) { return U.bars + 8u * i; }
-__device__ __forceinline__ uint32_t bar_full(const UmmaCta &U, uint32_t i) { return U.bars + 16u + 8u * i; }
+__device__ __forceinline__ uint32_t bar_done(const UmmaCta &U, uint32_t i, uint32_t h = 0) {
+  return U.bars + 32u * h + 8u * i;
+}
+__device__ __forceinline__ uint32_t bar_full(const UmmaCta &U, uint32_t i, uint32_t h = 0) {
+  return U.bars + 32u * h + 16u + 8u * i;
+}
+// threads of a CTA with NH halves: 4 compute warps, the issuing warp, 4 more compute warps
+__host__ __device__ constexpr int umma_threads(int nh) { return nh == 2 ? 288 : 160; }
 // Block g uses buffer g % NB; it is that buffer's (g / NB)-th use, i.e. phase
 // g / NB of both of its barriers.
 template <int NB> __device__ __forceinline__ uint32_t buf_of(uint32_t g) { return NB == 2 ? (g & 1u) : 0u; }
@@ -368,17 +387,22 @@ __device__ __forceinline__ void unit_seed(const TcDesc &D, int r, int m, bool ac
 }
 
 // One (m, ring block) unit: recurrence and tiles (compute warps), MMAs (issuing
-// warp). NB: the kernel's buffer count (the same for every unit a CTA runs, so
-// that the barriers' phases follow one block count). Leaves the accumulators
-// complete in tensor memory (every MMA waited for) and returns the number of 8-l
-// blocks (0: accumulators unset).
-template <int NDER, int MODE, int NC, int NB, bool SPIN2>
+// warp). NB: the kernel's buffer count per half (the same for every unit a CTA
+// runs, so that the barriers' phases follow one block count). NH = 2 splits the
+// unit's blocks between two sets of four compute warps on the same 128 rings: the
+// first runs blocks [bs, bmid) from the start-table state, the second [bmid, nblk)
+// from the state the recurrence has at bmid (plan-time table state_mid, identical
+// arithmetic), and both feed the same accumulators; warps 0-3 form the first set,
+// warps 5-8 the second (ring 32 (warp mod 4) + lane: the tensor-memory lanes a warp
+// may access). Leaves the accumulators complete in tensor memory (every MMA waited
+// for) and returns the number of 8-l blocks run (0: accumulators unset).
+template <int NDER, int MODE, int NC, int NB, bool SPIN2, int NH>
 __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
   constexpr int NJ = NDER + 1;
-  typedef TmemMap<NJ, MODE, NC> TM;
+  typedef TmemMap<NJ, MODE, NC, NH> TM;
   static_assert(NB <= TM::NB, "buffers fit");
   constexpr uint32_t BT = btile_bytes(NC);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int l0 = unit_l0(m, SPIN2);
   const int nblk = (D.lmax >= l0) ? (D.lmax - l0 + 8) / 8 : 0;
   const long long b0 = D.blk[m];
@@ -386,37 +410,49 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
   // blocks before bs contribute nothing for any ring of the unit (start table)
   const int bs = D.bstart ? D.bstart[unit] : 0;
   const int nrun = nblk - bs;
-  const uint32_t g0 = U.count;
+  const bool split = NH == 2 && D.bstart && D.state_mid;
+  const int n0 = split ? (nrun + 1) / 2 : nrun, n1 = nrun - n0;
+  const uint32_t g00 = U.count, g01 = U.count1;
   bool bad = false;
-  if (tid >= kComputeThreads) {
-    // ---- issuing warp: one lane waits for each block's tiles and issues its MMAs
+  if (warp == kComputeThreads / 32) {
+    // ---- issuing warp: one lane waits for each block's tiles and issues its MMAs,
+    // block k of the first half, then block k of the second
     if (tid == kComputeThreads) {
       const uint64_t dB0 = umma_desc(smem_u32(sm));
-      for (int blk = 0; blk < nrun; ++blk) {
-        const uint32_t g = g0 + (uint32_t)blk, i = buf_of<NB>(g);
-        if (!mbar_wait(bar_full(U, i), phase_of<NB>(g), U.abort)) {
-          bad = true;
-          break;
+      for (int k = 0; k < n0 && !bad; ++k) {
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+          if (h == 1 && k >= n1) break;
+          const uint32_t g = (h ? g01 : g00) + (uint32_t)k, i = buf_of<NB>(g), ib = (uint32_t)h * NB + i;
+          if (!mbar_wait(bar_full(U, i, h), phase_of<NB>(g), U.abort)) {
+            bad = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          issue_block<NJ, MODE, NC>(U.tmem, (uint32_t)(TM::A0 + TM::ASET * ib), dB0 + ((ib * BT) >> 4),
+                                    h == 0 && k == 0);
+          umma_commit(bar_done(U, i, h));
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        issue_block<NJ, MODE, NC>(U.tmem, (uint32_t)(TM::A0 + TM::ASET * i), dB0 + ((i * BT) >> 4), blk == 0);
-        umma_commit(bar_done(U, i));
       }
     }
     __syncwarp();
   } else {
-    // ---- compute warps: one ring per thread (tensor-memory lane tid)
+    // ---- compute warps: one ring per thread (tensor-memory lane t)
+    const int h = (NH == 2 && warp > kComputeThreads / 32) ? 1 : 0;
+    const int t = h ? (((warp & 3) << 5) | (tid & 31)) : tid;
+    const int first = h ? bs + n0 : bs, cnt = h ? n1 : n0;
+    const uint32_t g0 = h ? g01 : g00;
     const RingTable &rt = D.rt;
     bool active;
-    const int r = unit_ring<SPIN2>(D, rblk, tid, active);
-    const uint32_t lane = U.tmem + ((uint32_t)((tid >> 5) * 32) << 16);
+    const int r = unit_ring<SPIN2>(D, rblk, t, active);
+    const uint32_t lane = U.tmem + ((uint32_t)((warp & 3) * 32) << 16);
     Leib<float, NDER> LC;
     leibniz_coefs<float, NDER>(rt.z[r], rt.sint[r], 1.0 / (double)(D.lmax + 1), LC);
     float a[NJ], b[NJ];
     int sc;
     if (D.bstart) {
-      // the state at block bs, as the recurrence from l0 leaves it
-      const float *st = D.state + unit * (2 * NJ + 1) * kComputeThreads + tid;
+      // the state at block `first`, as the recurrence from l0 leaves it
+      const float *st = (h ? D.state_mid : D.state) + unit * (2 * NJ + 1) * kComputeThreads + t;
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         a[j] = __ldg(st + j * kComputeThreads);
@@ -443,41 +479,44 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       }
       const float4 *bt = (const float4 *)(D.b + (b0 + blk) * BT);
 #pragma unroll
-      for (int q = 0; q < QV; ++q) nbq[q] = __ldg(bt + q * kComputeThreads + tid);
+      for (int q = 0; q < QV; ++q) nbq[q] = __ldg(bt + q * kComputeThreads + t);
     };
-    if (nrun > 0) prefetch(bs);
-    for (int k = 0; k < nrun; ++k) {
-      const int blk = bs + k;
-      const uint32_t g = g0 + (uint32_t)k, i = buf_of<NB>(g);
+    if (cnt > 0) prefetch(first);
+    for (int k = 0; k < cnt; ++k) {
+      const int blk = first + k;
+      const uint32_t g = g0 + (uint32_t)k, i = buf_of<NB>(g), ib = (uint32_t)h * NB + i;
       const float Av[8] = {nA0.x, nA0.y, nA0.z, nA0.w, nA1.x, nA1.y, nA1.z, nA1.w};
       const float Cv[8] = {nC0.x, nC0.y, nC0.z, nC0.w, nC1.x, nC1.y, nC1.z, nC1.w};
       float4 bq[QV];
 #pragma unroll
       for (int q = 0; q < QV; ++q) bq[q] = nbq[q];
-      if (blk + 1 < nblk) prefetch(blk + 1);
+      if (k + 1 < cnt) prefetch(blk + 1);
       float buf0[NJ][4], buf1[NJ][4];
       steps_gated<0, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf0);
       steps_gated<4, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf1);
-      // the buffer was last read by the MMAs of block g - NB
-      if (g >= (uint32_t)NB && !mbar_wait(bar_done(U, i), phase_of<NB>(g - NB), U.abort)) {
+      // the buffer was last read by the MMAs of this half's block g - NB
+      if (g >= (uint32_t)NB && !mbar_wait(bar_done(U, i, h), phase_of<NB>(g - NB), U.abort)) {
         bad = true;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int q = 0; q < QV; ++q) *(float4 *)(sm + i * BT + (q * kComputeThreads + tid) * 16) = bq[q];
-      store_tiles<NDER, MODE>(lane + (uint32_t)(TM::A0 + TM::ASET * i), buf0, buf1);
+      for (int q = 0; q < QV; ++q) *(float4 *)(sm + ib * BT + (q * kComputeThreads + t) * 16) = bq[q];
+      store_tiles<NDER, MODE>(lane + (uint32_t)(TM::A0 + TM::ASET * ib), buf0, buf1);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(bar_full(U, i));
+      if ((tid & 31) == 0) mbar_arrive(bar_full(U, i, h));
     }
   }
-  U.count = g0 + (uint32_t)nrun;
-  // the last commit covers every MMA issued before it
-  if (!bad && nrun > 0 &&
-      !mbar_wait(bar_done(U, buf_of<NB>(U.count - 1)), phase_of<NB>(U.count - 1), U.abort))
+  U.count = g00 + (uint32_t)n0;
+  U.count1 = g01 + (uint32_t)n1;
+  // the last commit of each half covers every MMA issued before it
+  if (!bad && n0 > 0 && !mbar_wait(bar_done(U, buf_of<NB>(U.count - 1), 0), phase_of<NB>(U.count - 1), U.abort))
+    bad = true;
+  if (NH == 2 && !bad && n1 > 0 &&
+      !mbar_wait(bar_done(U, buf_of<NB>(U.count1 - 1), 1), phase_of<NB>(U.count1 - 1), U.abort))
     bad = true;
   if (bad) *U.abort = 1;
   if (__syncthreads_or(bad)) {
@@ -488,17 +527,17 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
   return nrun;
 }
 
-// Dynamic shared memory of a CTA: two coefficient tile buffers, then the spin-2
-// exchange area.
-template <int NC> __host__ __device__ constexpr uint32_t xch_offset() { return 2 * btile_bytes(NC); }
+// Dynamic shared memory of a CTA: two coefficient tile buffers per half, then the
+// spin-2 exchange area.
+template <int NC, int NH> __host__ __device__ constexpr uint32_t xch_offset() { return 2 * NH * btile_bytes(NC); }
 
 // spin 2: combine each ring's S1 with its mirror's S2 into F^Q, F^U, one order and
 // one group of 8 realisations (32 columns) at a time
-template <int NDER, int MODE, int NC, int NB>
+template <int NDER, int MODE, int NC, int NB, int NH>
 __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
   constexpr int NJ = NDER + 1;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int nblk = run_blocks<NDER, MODE, NC, NB, true>(D, m, rblk, sm, U);
+  const int nblk = run_blocks<NDER, MODE, NC, NB, true, NH>(D, m, rblk, sm, U);
   if (U.failed) return;
   const bool compute = tid < kComputeThreads;
   const int rn = rblk * 64 + (tid & 63);
@@ -508,7 +547,7 @@ __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsign
   const bool writer = active && m <= D.mmax && !(mirror && rn == D.nrings - 1 - rn);  // equator: north thread
   const int partner = tid ^ 64;
   const size_t ld = (size_t)(D.mmax + 1);
-  float *xch = (float *)(sm + xch_offset<NC>());  // [128][16]: S2 (4 rho + 2, 3) of every ring
+  float *xch = (float *)(sm + xch_offset<NC, NH>());  // [128][16]: S2 (4 rho + 2, 3) of every ring
 #pragma unroll 1
   for (int j = 0; j < NJ; ++j) {
 #pragma unroll 1
@@ -544,11 +583,11 @@ __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsign
 }
 
 // spin 0: north ring r and its mirror by parity
-template <int NDER, int MODE, int NC, int NB>
+template <int NDER, int MODE, int NC, int NB, int NH>
 __device__ __forceinline__ void u0_unit(const TcDesc &D, int m, int rblk, unsigned char *sm, UmmaCta &U) {
   constexpr int NJ = NDER + 1;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int nblk = run_blocks<NDER, MODE, NC, NB, false>(D, m, rblk, sm, U);
+  const int nblk = run_blocks<NDER, MODE, NC, NB, false, NH>(D, m, rblk, sm, U);
   if (U.failed) return;
   if (tid < kComputeThreads) {
     const int rn = rblk * 128 + tid;
@@ -583,14 +622,18 @@ __device__ __forceinline__ void u0_unit(const TcDesc &D, int m, int rblk, unsign
   __syncthreads();
 }
 
-// CTA set-up and tear-down of the barriers and the tensor memory
-template <int NCOLS>
+// CTA set-up and tear-down of the barriers (4 per half, `bars` holds 8) and the
+// tensor memory
+template <int NCOLS, int NH>
 __device__ __forceinline__ void umma_open(UmmaCta &U, uint64_t *bars, uint32_t *tbase, int *abort) {
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));  // done[0]: the commit
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));  // done[1]
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars[2])));  // full[0]: 4 warps
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars[3])));  // full[1]
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[4 * h])));      // done[0]: the commit
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[4 * h + 1])));  // done[1]
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars[4 * h + 2])));  // full[0]: 4 warps
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bars[4 * h + 3])));  // full[1]
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     *abort = 0;
   }
@@ -605,18 +648,21 @@ __device__ __forceinline__ void umma_open(UmmaCta &U, uint64_t *bars, uint32_t *
   U.tmem = *tbase;
   U.bars = smem_u32(&bars[0]);
   U.count = 0;
+  U.count1 = 0;
   U.abort = abort;
   U.failed = false;
 }
 
-// NB: the buffers of the kernel's main unit type; the last block's commit covers
-// every MMA issued before it.
-template <int NCOLS, int NB>
+// NB: the buffers of the kernel's main unit type; the last block's commit of each
+// half covers every MMA issued before it.
+template <int NCOLS, int NB, int NH>
 __device__ __forceinline__ void umma_close(const TcDesc &D, UmmaCta &U) {
   if (U.failed && threadIdx.x == 0) {
     atomicExch(D.err, 1);
     // own MMAs in flight (bounded)
-    if (U.count > 0) (void)mbar_wait(bar_done(U, buf_of<NB>(U.count - 1)), phase_of<NB>(U.count - 1));
+    if (U.count > 0) (void)mbar_wait(bar_done(U, buf_of<NB>(U.count - 1), 0), phase_of<NB>(U.count - 1));
+    if (NH == 2 && U.count1 > 0)
+      (void)mbar_wait(bar_done(U, buf_of<NB>(U.count1 - 1), 1), phase_of<NB>(U.count1 - 1));
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -627,57 +673,68 @@ __device__ __forceinline__ void umma_close(const TcDesc &D, UmmaCta &U) {
 template <int NDER, int MODE>
 struct Tc {
   static constexpr int NC = tc_cols(NDER);
-  typedef TmemMap<NDER + 1, MODE, NC> TM;
+  static constexpr int NH = tc_halves(NDER + 1, MODE, NC);
+  typedef TmemMap<NDER + 1, MODE, NC, NH> TM;
 };
 
 template <int NDER, int MODE>
-__global__ void __launch_bounds__(kUmmaThreads, (Tc<NDER, MODE>::TM::ctas)) legendre_spin2_umma(TcDesc D) {
+__global__ void __launch_bounds__(umma_threads(Tc<NDER, MODE>::NH), (Tc<NDER, MODE>::TM::ctas))
+    legendre_spin2_umma(TcDesc D) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ __align__(8) uint64_t bars[8];
   __shared__ uint32_t tbase;
   __shared__ int abort_flag;
-  typedef typename Tc<NDER, MODE>::TM TM;
+  typedef Tc<NDER, MODE> C;
+  typedef typename C::TM TM;
   UmmaCta U;
-  umma_open<TM::cols>(U, bars, &tbase, &abort_flag);
-  u2_unit<NDER, MODE, Tc<NDER, MODE>::NC, TM::NB>(D, blockIdx.y, blockIdx.x, sm, U);
-  umma_close<TM::cols, TM::NB>(D, U);
+  umma_open<TM::cols, C::NH>(U, bars, &tbase, &abort_flag);
+  u2_unit<NDER, MODE, C::NC, TM::NB, C::NH>(D, blockIdx.y, blockIdx.x, sm, U);
+  umma_close<TM::cols, TM::NB, C::NH>(D, U);
 }
 
 // spin 0 at NDER with the column count CNC (the potential runs at NDER = 1 with the
 // columns of the plan's order)
 template <int NDER, int MODE, int CNC>
-__global__ void __launch_bounds__(kUmmaThreads, (TmemMap<NDER + 1, MODE, CNC>::ctas)) legendre_spin0_umma(TcDesc D) {
+struct Tc0 {
+  static constexpr int NH = tc_halves(NDER + 1, MODE, CNC);
+  typedef TmemMap<NDER + 1, MODE, CNC, NH> TM;
+};
+template <int NDER, int MODE, int CNC>
+__global__ void __launch_bounds__(umma_threads(Tc0<NDER, MODE, CNC>::NH), (Tc0<NDER, MODE, CNC>::TM::ctas))
+    legendre_spin0_umma(TcDesc D) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ __align__(8) uint64_t bars[8];
   __shared__ uint32_t tbase;
   __shared__ int abort_flag;
-  typedef TmemMap<NDER + 1, MODE, CNC> TM;
+  typedef Tc0<NDER, MODE, CNC> C;
+  typedef typename C::TM TM;
   UmmaCta U;
-  umma_open<TM::cols>(U, bars, &tbase, &abort_flag);
-  u0_unit<NDER, MODE, CNC, TM::NB>(D, blockIdx.y, blockIdx.x, sm, U);
-  umma_close<TM::cols, TM::NB>(D, U);
+  umma_open<TM::cols, C::NH>(U, bars, &tbase, &abort_flag);
+  u0_unit<NDER, MODE, CNC, TM::NB, C::NH>(D, blockIdx.y, blockIdx.x, sm, U);
+  umma_close<TM::cols, TM::NB, C::NH>(D, U);
 }
 
 // Persistent form: one launch covers the Legendre work of several plans. Items
 // (descriptor, kind, m, ring block) are pre-sorted by cost; each CTA takes them in
 // order from an atomic counter until none is left (no waits between CTAs). Kinds:
 // 0 a spin-0 field at NDER, 1 the lensing potential (spin 0, NDER = 1), 2 spin 2.
-// Every kind's tensor-memory map fits the allocation of NDER's.
+// Every kind's tensor-memory map fits the allocation of NDER's, with NDER's halves.
 template <int NDER, int MODE>
-__global__ void __launch_bounds__(kUmmaThreads, (Tc<NDER, MODE>::TM::ctas))
+__global__ void __launch_bounds__(umma_threads(Tc<NDER, MODE>::NH), (Tc<NDER, MODE>::TM::ctas))
     legendre_umma_persistent(const TcDesc *__restrict__ descs, const int4 *__restrict__ items, int nitems,
                              int *__restrict__ counter) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ __align__(8) uint64_t bars[8];
   __shared__ uint32_t tbase;
   __shared__ int abort_flag;
   __shared__ int cur;
-  constexpr int NC = Tc<NDER, MODE>::NC;
-  typedef typename Tc<NDER, MODE>::TM TM;
-  typedef TmemMap<2, MODE, NC> TM1;
-  static_assert(TM1::A0 + TM::NB * TM1::ASET <= TM::cols, "potential units fit the allocation");
+  typedef Tc<NDER, MODE> C;
+  constexpr int NC = C::NC, NH = C::NH;
+  typedef typename C::TM TM;
+  typedef TmemMap<2, MODE, NC, NH> TM1;
+  static_assert(TM1::A0 + NH * TM::NB * TM1::ASET <= TM::cols, "potential units fit the allocation");
   UmmaCta U;
-  umma_open<TM::cols>(U, bars, &tbase, &abort_flag);
+  umma_open<TM::cols, NH>(U, bars, &tbase, &abort_flag);
   TcDesc D = descs[0];
   for (;;) {
     __syncthreads();  // the previous item's readers of `cur` are done
@@ -689,25 +746,29 @@ __global__ void __launch_bounds__(kUmmaThreads, (Tc<NDER, MODE>::TM::ctas))
     D = descs[w.x & 0xffff];
     const int kind = w.x >> 16;
     if (kind == 2)
-      u2_unit<NDER, MODE, NC, TM::NB>(D, w.y, w.z, sm, U);
+      u2_unit<NDER, MODE, NC, TM::NB, NH>(D, w.y, w.z, sm, U);
     else if (kind == 1)
-      u0_unit<1, MODE, NC, TM::NB>(D, w.y, w.z, sm, U);
+      u0_unit<1, MODE, NC, TM::NB, NH>(D, w.y, w.z, sm, U);
     else
-      u0_unit<NDER, MODE, NC, TM::NB>(D, w.y, w.z, sm, U);
+      u0_unit<NDER, MODE, NC, TM::NB, NH>(D, w.y, w.z, sm, U);
     if (U.failed) break;  // uniform: set after a block-wide vote
   }
-  umma_close<TM::cols, TM::NB>(D, U);
+  umma_close<TM::cols, TM::NB, NH>(D, U);
 }
 
 // Plan-time start table (see TcDesc): one CTA of 128 threads per unit runs the
 // recurrence block by block, without the contraction, until one of its rings has
 // reached scale 0 (a basis value that is not gated off), and records every ring's
-// state at the start of that block. The launch kernels resume from it with the
-// same arithmetic, so their results are those of a run from l0. Units in which no
-// ring contributes get bstart = their block count.
+// state at the start of that block, bs. With state_mid it runs on to the first
+// block of the unit's second half, bmid = bs + (nblk - bs + 1) / 2, and records the
+// state there too. The launch kernels resume from these with the same arithmetic
+// (the same warps hold the same rings, so even the warp-uniform choices agree), so
+// their results are those of a run from l0. Units in which no ring contributes get
+// bstart = their block count.
 template <int NDER, bool SPIN2>
 __global__ void __launch_bounds__(kComputeThreads) tcstart_kernel(TcDesc D, int *__restrict__ bstart,
-                                                                   float *__restrict__ state) {
+                                                                   float *__restrict__ state,
+                                                                   float *__restrict__ state_mid) {
   constexpr int NJ = NDER + 1;
   const int rblk = blockIdx.x, m = blockIdx.y, tid = threadIdx.x;
   const int l0 = unit_l0(m, SPIN2);
@@ -722,9 +783,9 @@ __global__ void __launch_bounds__(kComputeThreads) tcstart_kernel(TcDesc D, int 
   int sc;
   unit_seed<NDER, SPIN2>(D, r, m, active, a, b, sc);
   const float X = (float)D.rt.z[r];
-  float *st = state + unit * (2 * NJ + 1) * kComputeThreads + tid;
-  int first = nblk;
-  for (int blk = 0; blk < nblk; ++blk) {
+  const size_t so = (size_t)unit * (2 * NJ + 1) * kComputeThreads + tid;
+  int first = nblk, stop = nblk;
+  for (int blk = 0; blk < stop; ++blk) {
     const float4 *stp = (const float4 *)(D.step + (b0 + blk) * 16);
     const float4 A0 = __ldg(stp), A1 = __ldg(stp + 1);
     float4 C0 = make_float4(0.f, 0.f, 0.f, 0.f), C1 = C0;
@@ -745,16 +806,28 @@ __global__ void __launch_bounds__(kComputeThreads) tcstart_kernel(TcDesc D, int 
     steps_gated<0, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf0);
     steps_gated<4, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf1);
     // a ring can have contributed in this block only if its scale is 0 at the end
-    if (__syncthreads_or(sc == 0)) {
+    if (first == nblk && __syncthreads_or(sc == 0)) {
       first = blk;
+      float *st = state + so;
 #pragma unroll
       for (int j = 0; j < NJ; ++j) {
         st[j * kComputeThreads] = sa[j];
         st[(NJ + j) * kComputeThreads] = sb[j];
       }
       st[2 * NJ * kComputeThreads] = __int_as_float(ssc);
-      break;
+      if (!state_mid) break;
+      stop = first + (nblk - first + 1) / 2;  // bmid: record the state at its start
     }
+  }
+  if (state_mid && first < nblk) {
+    // (a, b, sc) are now the state at the start of block `stop` = bmid
+    float *st = state_mid + so;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+      st[j * kComputeThreads] = a[j];
+      st[(NJ + j) * kComputeThreads] = b[j];
+    }
+    st[2 * NJ * kComputeThreads] = __int_as_float(sc);
   }
   if (tid == 0) bstart[unit] = first;
 }
@@ -905,9 +978,9 @@ int tc_ring_blocks(const tl_plan *p, int spin) {
 // Dynamic shared memory: two coefficient tiles and the spin-2 exchange area, raised
 // to the size that keeps the CTAs per SM within the tensor memory (512 columns per
 // SM): 4 CTAs (46 KB), 2 (76 KB) or 1 (114 KB).
-template <int CTAS, int NC> static size_t umma_smem() {
+template <int CTAS, int NC, int NH> static size_t umma_smem() {
   const size_t floor_b = CTAS >= 4 ? 46 * 1024 : CTAS == 2 ? 76 * 1024 : 114 * 1024;
-  const size_t need = 2 * btile_bytes(NC) + kXchBytes;
+  const size_t need = xch_offset<NC, NH>() + kXchBytes;
   return need > floor_b ? need : floor_b;
 }
 
@@ -934,7 +1007,9 @@ static TcDesc make_desc(const tl_plan *p, int which, int nreal, const void *btil
   D.nrblk = tc_ring_blocks(p, spin);
   D.bstart = which == 2 ? p->tc_bs2 : which == 1 ? p->tc_bsp : p->tc_bs0;
   D.state = which == 2 ? p->tc_st2 : which == 1 ? p->tc_stp : p->tc_st0;
+  D.state_mid = which == 2 ? p->tc_sm2 : which == 1 ? p->tc_smp : p->tc_sm0;
   if (!D.state) D.bstart = nullptr;  // no table: every unit starts at l0
+  if (!D.bstart) D.state_mid = nullptr;
   return D;
 }
 
@@ -955,33 +1030,33 @@ static cudaError_t set_smem(K kernel, size_t smem) {
 
 template <int NDER, int MODE>
 static cudaError_t u2(const tl_plan *p, int nreal, void *dq, void *du, long long rstride, cudaStream_t s) {
-  typedef typename Tc<NDER, MODE>::TM TM;
-  const size_t smem = umma_smem<TM::ctas, Tc<NDER, MODE>::NC>();
+  typedef Tc<NDER, MODE> C;
+  const size_t smem = umma_smem<C::TM::ctas, C::NC, C::NH>();
   TL_CUDA_TRY(set_smem(legendre_spin2_umma<NDER, MODE>, smem));
   dim3 grid(tc_ring_blocks(p, 2), p->mmax + 1);
   legendre_spin2_umma<NDER, MODE>
-      <<<grid, kUmmaThreads, smem, s>>>(make_desc(p, 2, nreal, p->tc_b2, dq, du, rstride));
+      <<<grid, umma_threads(C::NH), smem, s>>>(make_desc(p, 2, nreal, p->tc_b2, dq, du, rstride));
   return cudaGetLastError();
 }
 
 template <int NDER, int CNC, int MODE>
 static cudaError_t u0(const tl_plan *p, int which, int nreal, void *d7, long long rstride, cudaStream_t s) {
-  typedef TmemMap<NDER + 1, MODE, CNC> TM;
-  const size_t smem = umma_smem<TM::ctas, CNC>();
+  typedef Tc0<NDER, MODE, CNC> C;
+  const size_t smem = umma_smem<C::TM::ctas, CNC, C::NH>();
   TL_CUDA_TRY(set_smem(legendre_spin0_umma<NDER, MODE, CNC>, smem));
   dim3 grid(tc_ring_blocks(p, 0), p->mmax + 1);
-  legendre_spin0_umma<NDER, MODE, CNC><<<grid, kUmmaThreads, smem, s>>>(
+  legendre_spin0_umma<NDER, MODE, CNC><<<grid, umma_threads(C::NH), smem, s>>>(
       make_desc(p, which, nreal, which == 1 ? p->tc_bp : p->tc_b0, d7, nullptr, rstride));
   return cudaGetLastError();
 }
 
 template <int NDER, int MODE>
 static cudaError_t up(const void *descs, const void *items, int nitems, int *counter, int grid, cudaStream_t s) {
-  typedef typename Tc<NDER, MODE>::TM TM;
-  const size_t smem = umma_smem<TM::ctas, Tc<NDER, MODE>::NC>();
+  typedef Tc<NDER, MODE> C;
+  const size_t smem = umma_smem<C::TM::ctas, C::NC, C::NH>();
   TL_CUDA_TRY(set_smem(legendre_umma_persistent<NDER, MODE>, smem));
   legendre_umma_persistent<NDER, MODE>
-      <<<grid, kUmmaThreads, smem, s>>>((const TcDesc *)descs, (const int4 *)items, nitems, counter);
+      <<<grid, umma_threads(C::NH), smem, s>>>((const TcDesc *)descs, (const int4 *)items, nitems, counter);
   return cudaGetLastError();
 }
 
@@ -1039,10 +1114,12 @@ cudaError_t launch_legendre_spin0_tc(const tl_plan *p, int which, int nreal, voi
 }
 
 // Fill a start table (plan time): which as in make_desc; units of that spin.
-cudaError_t launch_tcstart(const tl_plan *p, int which, int *bstart, float *state, cudaStream_t s) {
+cudaError_t launch_tcstart(const tl_plan *p, int which, int *bstart, float *state, float *state_mid,
+                           cudaStream_t s) {
   TcDesc D = make_desc(p, which, 1, nullptr, nullptr, nullptr, 0);
   D.bstart = nullptr;
   D.state = nullptr;
+  D.state_mid = nullptr;
   const int spin = which == 2 ? 2 : 0;
   const int nder = which == 1 ? 1 : p->tc_nder;
   dim3 grid(tc_ring_blocks(p, spin), p->mmax + 1);
@@ -1050,9 +1127,9 @@ cudaError_t launch_tcstart(const tl_plan *p, int which, int *bstart, float *stat
 #define CASE(n)                                                                                      \
   case n:                                                                                            \
     if (spin == 2)                                                                                   \
-      tcstart_kernel<n, true><<<grid, kComputeThreads, 0, s>>>(D, bstart, state);                    \
+      tcstart_kernel<n, true><<<grid, kComputeThreads, 0, s>>>(D, bstart, state, state_mid);         \
     else                                                                                             \
-      tcstart_kernel<n, false><<<grid, kComputeThreads, 0, s>>>(D, bstart, state);                   \
+      tcstart_kernel<n, false><<<grid, kComputeThreads, 0, s>>>(D, bstart, state, state_mid);        \
     return cudaGetLastError();
     TL_TC_ORDERS(CASE)
 #undef CASE
@@ -1065,6 +1142,13 @@ size_t tc_start_state_bytes(const tl_plan *p, int which) {
   const int nj = (which == 1 ? 1 : p->tc_nder) + 1;
   const size_t units = (size_t)(p->mmax + 1) * tc_ring_blocks(p, which == 2 ? 2 : 0);
   return units * (2 * nj + 1) * kComputeThreads * sizeof(float);
+}
+// Whether the kernels that run a start table's units split them into two halves
+// (and so need its midpoint table): which as in make_desc.
+bool tc_split(const tl_plan *p, int which) {
+  const int mode = tc_mode(p->precision), nc = tc_cols(p->tc_nder);
+  if (which == 1) return true;  // the potential's map (2 orders) always has room
+  return tc_halves(p->tc_nder + 1, mode, nc) == 2;
 }
 size_t tc_start_units(const tl_plan *p, int which) {
   return (size_t)(p->mmax + 1) * tc_ring_blocks(p, which == 2 ? 2 : 0);

@@ -85,7 +85,8 @@ static void free_plan(tl_plan *p) {
                   p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->adj_dbar, p->adj_ga, p->stage_alm,
                   p->stage_out,
                   p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2, p->dev_err,
-                  p->tc_bs0, p->tc_bsp, p->tc_bs2, p->tc_st0, p->tc_stp, p->tc_st2,
+                  p->tc_bs0, p->tc_bsp, p->tc_bs2, p->tc_st0, p->tc_stp, p->tc_st2, p->tc_sm0, p->tc_smp,
+                  p->tc_sm2,
                   p->fft_rings};
   for (void *q : ptrs)
     if (q) cudaFree(q);
@@ -218,9 +219,11 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
     for (int which = 0; which < (pol ? 3 : 2); ++which) {
       int **bs = which == 0 ? &p->tc_bs0 : which == 1 ? &p->tc_bsp : &p->tc_bs2;
       float **st = which == 0 ? &p->tc_st0 : which == 1 ? &p->tc_stp : &p->tc_st2;
+      float **sm = which == 0 ? &p->tc_sm0 : which == 1 ? &p->tc_smp : &p->tc_sm2;
       TRY_CUDA(dalloc((void **)bs, sizeof(int) * tc_start_units(p, which), B));
       TRY_CUDA(dalloc((void **)st, tc_start_state_bytes(p, which), B));
-      TRY_CUDA(launch_tcstart(p, which, *bs, *st, 0));
+      if (tc_split(p, which)) TRY_CUDA(dalloc((void **)sm, tc_start_state_bytes(p, which), B));
+      TRY_CUDA(launch_tcstart(p, which, *bs, *st, *sm, 0));
     }
     TRY_CUDA(cudaDeviceSynchronize());
   }
