@@ -54,10 +54,10 @@ FP32_LANES = 152 * 128
 TRAFFIC_NSIDE512 = {
     ("fft_total", None): (839.2e6, ["ringfft.cu", "fft.cuh"], "6c26b53500746294"),
     ("gather_total", None): (624.6e6, ["gather.cu", "geometry.cuh"], "3d99eb1ac9a9bebc"),
-    ("legendre_QU", "bf16x3"): (7.645e9, ["legendre_umma.cu", "legendre.cuh"], "226155a5127df2c7"),
-    ("legendre_T", "bf16x3"): (4.291e9, ["legendre_umma.cu", "legendre.cuh"], "226155a5127df2c7"),
-    ("legendre_QU", "tf32x3"): (7.521e9, ["legendre_umma.cu", "legendre.cuh"], "226155a5127df2c7"),
-    ("legendre_T", "tf32x3"): (4.173e9, ["legendre_umma.cu", "legendre.cuh"], "226155a5127df2c7"),
+    ("legendre_QU", "bf16x3"): (7.645e9, ["legendre_umma.cu", "legendre.cuh"], "baebd1665fa129dd"),
+    ("legendre_T", "bf16x3"): (4.291e9, ["legendre_umma.cu", "legendre.cuh"], "baebd1665fa129dd"),
+    ("legendre_QU", "tf32x3"): (7.521e9, ["legendre_umma.cu", "legendre.cuh"], "baebd1665fa129dd"),
+    ("legendre_T", "tf32x3"): (4.173e9, ["legendre_umma.cu", "legendre.cuh"], "baebd1665fa129dd"),
 }
 
 

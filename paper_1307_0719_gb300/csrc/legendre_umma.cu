@@ -6,10 +6,11 @@
 // with FP64 seeds and exponent scaling, normalised step mu_{l+1} = A X mu_l - mu_{l-1},
 // theta-derivatives by Leibniz's rule. A CTA holds 128 rings (spin 2: 64 north
 // rings and their mirrors; spin 0: 128 north rings, south by parity) in four
-// compute warps, plus one warp that issues the tensor-core work. Every 8 values
-// of l the compute warps write the [128 rings x 8 l] tile of mu^(j) of every
-// derivative order j into tensor memory (thread t owns lane t, the tile's row t),
-// and the issuing warp runs
+// compute warps, plus one warp that issues the tensor-core work; where tensor
+// memory allows, four more compute warps run the second half of each unit's l
+// range on the same rings (see run_blocks). Every 8 values of l the compute warps
+// write the [128 rings x 8 l] tile of mu^(j) of every derivative order j into
+// tensor memory (ring slot t in lane t, the tile's row t), and the issuing warp runs
 //     D^(j)[128 x NC] += Mu^(j)[128 x 8] . C[8 x NC]       (tcgen05.mma, kind::tf32)
 // with Mu^(j) read from tensor memory and the coefficient tile C from shared
 // memory. The NC columns (64, or 32 at the highest order) hold the coefficient
@@ -26,8 +27,9 @@
 // chain of these small MMAs advances at ~50 cycles per instruction whatever N is
 // up to 128, so the MMA side of a block costs the same for 64 columns as for 32
 // and the columns per tile set the realisations served per recurrence. The
-// accumulators of 16 realisations (5 orders x 64 columns) and two sets of basis
-// tiles then fill the 512 columns of tensor memory (one CTA per SM).
+// accumulators of 16 realisations (5 orders x 64 columns) and the basis tiles
+// (2 x 80 columns for 3xTF32; 2 halves x 2 x 40 for BF16x3) then fill the 512
+// columns of tensor memory (one CTA per SM).
 //
 // Pipeline: the basis tiles (tensor memory) and the coefficient tiles (shared
 // memory) are double-buffered where the columns allow. For block g the compute
@@ -37,7 +39,9 @@
 // store the basis tiles (tcgen05.st) and the coefficient tile, and arrive on the
 // buffer's "full" barrier (one arrival per warp). The issuing warp waits for the
 // four arrivals, issues the block's MMAs and commits them to the buffer's "done",
-// so the tensor core works on one buffer while the other is being filled.
+// so the tensor core works on one buffer while the other is being filled. With two
+// halves each has its own buffers and barriers, and the issuing warp alternates
+// between them block by block.
 //
 // The coefficient tile uses the K-major shared-memory layout without swizzle:
 // 8-row x 16-byte core matrices, 128 bytes apart along K and 256 bytes apart along
@@ -51,8 +55,7 @@
 namespace tl {
 
 constexpr int kMaxReal = TL_MAX_BATCH;  // realisations per launch at most (64 columns)
-constexpr int kComputeThreads = 128;
-constexpr int kUmmaThreads = 160;  // + the issuing warp
+constexpr int kComputeThreads = 128;  // compute threads per half (umma_threads: the CTA's)
 constexpr uint32_t kXchBytes = 128 * 16 * 4;  // spin-2 epilogue exchange [128][16] floats
 
 // accumulator columns per order for NDER theta-derivatives: 64 (16 realisations)
