@@ -209,11 +209,13 @@ def deflection(nside, lmax, alm_phi, precision=FP64):
 
 class Batch:
     """Realisations of uneven geometry (tl_batch_*): grouped by (nside, lmax), each
-    group with its own plan. `lens` modes: loop, persistent, graph."""
+    group with its own plan. `lens` modes: loop, persistent, graph. Default
+    precision: the BF16x3 tensor-core contraction (MIXED_TF32x3 reaches the same
+    error level with three MMAs per block instead of two)."""
 
     MODES = {"loop": _lib.TL_BATCH_LOOP, "persistent": _lib.TL_BATCH_PERSISTENT, "graph": _lib.TL_BATCH_GRAPH}
 
-    def __init__(self, nsides, lmaxs, order, pol=True, precision=MIXED_TF32x3, rotate=True):
+    def __init__(self, nsides, lmaxs, order, pol=True, precision=MIXED_BF16x3, rotate=True):
         L = _lib.lib()
         n = len(nsides)
         self.n, self.pol, self.precision = n, pol, precision
