@@ -42,6 +42,12 @@ def test_host_argument_checks(lib):
     assert lib.tl_plan_create(4, 8, 7, 1, 0, 1, ctypes.byref(h)) == L.TL_ERR_ARG      # order > 6
     assert lib.tl_plan_create(4, 8, 2, 1, 9, 1, ctypes.byref(h)) == L.TL_ERR_ARG      # precision
     assert lib.tl_plan_create(4, 8, 2, L.TL_SPIN_QU, 0, 1, ctypes.byref(h)) == L.TL_ERR_UNSUPPORTED  # Q/U alone
+    # every precision form passes the argument checks (without a GPU the CUDA set-up then fails)
+    for prec in (L.TL_FP64, L.TL_MIXED_FP32, L.TL_MIXED_TF32, L.TL_MIXED_TF32x3, L.TL_MIXED_BF16x3):
+        rc = lib.tl_plan_create(4, 8, 2, L.TL_SPIN_T | L.TL_SPIN_QU, prec, 1, ctypes.byref(h))
+        assert rc in (L.TL_OK, L.TL_ERR_CUDA), (prec, rc)
+        if rc == L.TL_OK:
+            lib.tl_plan_destroy(h)
     assert lib.tl_plan_create(4, 8, 2, 1, 0, 4, ctypes.byref(h)) == L.TL_ERR_ARG      # flags
     assert lib.tl_lens(None, None, None, None, None, None, None, None, None) == L.TL_ERR_ARG
     assert lib.tl_plan_destroy(None) == L.TL_OK
