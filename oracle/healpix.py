@@ -151,3 +151,23 @@ def ang2pix(nside: int, z, s, phi):
 def ang2pix_theta(nside: int, theta, phi):
     theta = np.asarray(theta, dtype=np.float64)
     return ang2pix(nside, np.cos(theta), np.sin(theta), phi)
+
+
+def check_pixels(nside: int, seed: int = 11, n_random: int = 128, per_ring: int = 64, cap_rings: int = 4):
+    """Output pixels for sampled checks at full size (test infrastructure): every
+    pixel of the first and last `cap_rings` rings, `per_ring` evenly spaced pixels
+    on the last cap ring and the first belt ring of each hemisphere and on the
+    equator, and `n_random` seeded random pixels. Sorted, unique, RING indices."""
+    n = int(nside)
+    tab = ring_table(n)
+    first, nphi = tab["first"], tab["nphi"]
+    nr = 4 * n - 1
+    pix = []
+    for i in list(range(1, min(cap_rings, nr) + 1)) + list(range(max(nr - cap_rings + 1, 1), nr + 1)):
+        pix.append(first[i - 1] + np.arange(nphi[i - 1]))
+    for i in sorted({max(n - 1, 1), n, 2 * n, 3 * n, min(3 * n + 1, nr)}):
+        k = min(per_ring, int(nphi[i - 1]))
+        pix.append(first[i - 1] + (np.arange(k) * nphi[i - 1]) // k)
+    rng = np.random.default_rng(seed)
+    pix.append(rng.choice(npix(n), size=min(n_random, npix(n)), replace=False))
+    return np.unique(np.concatenate(pix).astype(np.int64))

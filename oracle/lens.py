@@ -236,10 +236,18 @@ def lens_exact(nside: int, lmax: int, alm_T, alm_E=None, alm_B=None, alm_phi=Non
     return out
 
 
+def _ring_coeffs_unique(lmax, nder, theta, nthreads=None, **alm):
+    """ring_coeffs at each point's colatitude, each distinct colatitude computed once
+    (points on one ring share it exactly)."""
+    uth, inv = np.unique(np.asarray(theta, dtype=np.float64), return_inverse=True)
+    F = sht.ring_coeffs(lmax, nder, uth, nthreads=nthreads, **alm)
+    return {f: v[inv] for f, v in F.items()}
+
+
 def deflection_at(lmax, alm_phi, theta, phi, sint, nthreads=None):
     if alm_phi is None:
         return np.zeros_like(theta), np.zeros_like(theta)
-    F = sht.ring_coeffs(lmax, 1, theta, alm_T=alm_phi, nthreads=nthreads)["T"]
+    F = _ring_coeffs_unique(lmax, 1, theta, nthreads, alm_T=alm_phi)["T"]
     a_th = sht.point_sum(F, phi, 1, 0, nthreads=nthreads)
     a_ph = sht.point_sum(F, phi, 0, 1, nthreads=nthreads) / sint
     return a_th, a_ph
@@ -271,7 +279,7 @@ def lens_at_pixels(nside: int, lmax: int, order: int, pix, alm_T, alm_E=None, al
     th_q, ph_q = hp.pix2ang(nside, q)
     dth = theta2 - th_q
     dph = wrap_pi(phi2 - ph_q)
-    F = sht.ring_coeffs(lmax, order, th_q, alm_T, alm_E, alm_B, nthreads=nthreads)
+    F = _ring_coeffs_unique(lmax, order, th_q, nthreads, alm_T=alm_T, alm_E=alm_E, alm_B=alm_B)
     out = {}
     for f in F:
         D = np.stack([sht.point_sum(F[f], ph_q, j, k, nthreads=nthreads)

@@ -86,7 +86,7 @@ struct tl_plan {
   int *tc_bs0, *tc_bsp, *tc_bs2;
   float *tc_st0, *tc_stp, *tc_st2;
   float *tc_sm0, *tc_smp, *tc_sm2;  // the same state at each unit's midpoint block (split units)
-  float *tc_step0, *tc_step2;     // [blocks][16]: A_{l+1} x 8, m s/(l(l+1)) x 8
+  float *tc_step0, *tc_step2;     // per 8-l block: A_{l+1} x 8, then A - 2 x 8 (spin 0) or Qn, Qs x 8 (spin 2)
   void *tc_b0, *tc_bp, *tc_b2;    // [blocks] 2 KB coefficient tiles (TF32 hi, lo; 32 columns x 8 l)
   int *dev_err;                   // set by a kernel whose bounded wait timed out
   long long d7_rstride, d7p_rstride;  // T2 elements between realisations' D7 planes

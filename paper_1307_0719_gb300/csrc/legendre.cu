@@ -22,7 +22,11 @@ __device__ __forceinline__ double rec_alpha(int L, int m, int s) {
   return sqrt((4.0 * L2 - 1.0) * L2 / ((L2 - (double)m * m) * (L2 - (double)s * s)));
 }
 
-// One thread per m: tab[idx(l, m)] = {k_l, A_{l+1}} for l0 <= l <= lmax (A = 0 at lmax).
+// One thread per m: tab[idx(l, m)] = {k_l, A_{l+1} - 2} for l0 <= l <= lmax (A = 0,
+// i.e. -2 stored, at lmax). k_{l0} = 1; k_{l0+1} = g is chosen so that the even
+// and odd chains k_{l+1} = beta_{l+1} k_{l-1} end at the same value: a first pass
+// runs them with g = 1 and takes g = (even chain) / (odd chain) at lmax, so the
+// normalised step factor A tends to 2 without alternating about it.
 template <typename T>
 __global__ void steptab_kernel(int lmax, int s, typename RealTraits<T>::T2 *__restrict__ tab) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,17 +38,31 @@ __global__ void steptab_kernel(int lmax, int s, typename RealTraits<T>::T2 *__re
     tm[l].x = (T)0;
     tm[l].y = (T)0;
   }
+  if (l0 > lmax) return;
+  double g = 1.0;
+  if (lmax >= l0 + 2) {
+    double k_prev = 1.0, k_cur = 1.0, a_cur = rec_alpha(l0 + 1, m, s);  // k_{l0}, k_{l0+1}, alpha_{l0+1}
+    for (int l = l0 + 1; l < lmax; ++l) {
+      const double a_next = rec_alpha(l + 1, m, s);
+      const double k_next = (a_next / a_cur) * k_prev;
+      k_prev = k_cur;
+      k_cur = k_next;
+      a_cur = a_next;
+    }
+    // k_cur = k_lmax, k_prev = k_{lmax-1}
+    g = ((lmax - l0) % 2 == 0) ? k_cur / k_prev : k_prev / k_cur;
+  }
   double k_prev = 1.0, k_cur = 1.0, a_cur = 0.0;  // k_{l-1}, k_l, alpha_l
   for (int l = l0; l <= lmax; ++l) {
-    double A = 0.0, k_next = 0.0;
+    double Am2 = -2.0, k_next = 0.0;
     if (l < lmax) {
       const double a_next = rec_alpha(l + 1, m, s);
-      k_next = (l == l0) ? 1.0 : (a_next / a_cur) * k_prev;  // beta_{l+1} k_{l-1}
-      A = a_next * k_cur / k_next;
+      k_next = (l == l0) ? g : (a_next / a_cur) * k_prev;  // beta_{l+1} k_{l-1}
+      Am2 = a_next * k_cur / k_next - 2.0;
       a_cur = a_next;
     }
     tm[l].x = (T)k_cur;
-    tm[l].y = (T)A;
+    tm[l].y = (T)Am2;
     k_prev = k_cur;
     k_cur = k_next;
   }
@@ -61,8 +79,8 @@ __global__ void prep_spin0_kernel(int lmax, const double *__restrict__ alm,
   Rec0<T> r;
   r.re = (T)(alm[2 * idx] * (double)kA.x);
   r.im = (m == 0) ? (T)0 : (T)(alm[2 * idx + 1] * (double)kA.x);
-  r.A = kA.y;
-  r.pad = (T)0;
+  r.A = (T)(2.0 + (double)kA.y);
+  r.Q = kA.y;
   rec[idx] = r;
 }
 
@@ -93,7 +111,7 @@ __global__ void prep_spin2_kernel(int lmax, const double *__restrict__ almE, con
   const int l0 = m > s ? m : s;
   Rec2<T> r;
   if (l < l0) {
-    r.c1r = r.c1i = r.c2r = r.c2i = r.A = r.cterm = r.pad0 = r.pad1 = (T)0;
+    r.c1r = r.c1i = r.c2r = r.c2i = r.A = r.cterm = r.Qn = r.Qs = (T)0;
     rec[idx] = r;
     return;
   }
@@ -108,9 +126,11 @@ __global__ void prep_spin2_kernel(int lmax, const double *__restrict__ almE, con
   r.c1i = (T)((ei + br) * k);
   r.c2r = (T)(sg * (er + bi));
   r.c2i = (T)(sg * (ei - br));
-  r.A = kA.y;
-  r.cterm = (T)((double)m * s / ((double)l * (l + 1.0)));
-  r.pad0 = r.pad1 = (T)0;
+  const double Am2 = (double)kA.y, A = 2.0 + Am2, C = (double)m * s / ((double)l * (l + 1.0));
+  r.A = (T)A;
+  r.cterm = (T)C;
+  r.Qn = (T)(Am2 + A * C);
+  r.Qs = (T)(Am2 - A * C);
   rec[idx] = r;
 }
 
@@ -137,11 +157,10 @@ __global__ void __launch_bounds__(128) legendre_spin0_kernel(RingTable rt, const
   Leib<T, NDER> LC;
   leibniz_coefs<T, NDER>(x, st, invL, LC);
 
-  T a[NDER + 1], b[NDER + 1];  // alternately mu_{l-1} and mu_l
+  T a[NDER + 1], b[NDER + 1];  // recurrence state: b = mu_l; a = d_l (float) or mu_{l-1} (double)
   int sc;
   seed_spin0<T, NDER>(rt, lnorm0, r, m, invL, b, sc);
-#pragma unroll
-  for (int j = 0; j <= NDER; ++j) a[j] = (T)0;
+  rec_init<T, NDER>(a, b);
 
   T er[NDER + 1], ei[NDER + 1], orr[NDER + 1], oi[NDER + 1];
 #pragma unroll
@@ -153,12 +172,12 @@ __global__ void __launch_bounds__(128) legendre_spin0_kernel(RingTable rt, const
   const long long base = (long long)m * (2 * lmax + 1 - m) / 2;
   const Rec0<T> *rm = rec + base;
   const T2 *pm = PHI ? recp + base : nullptr;
-  const T X = (T)x;
+  const T X = (T)x, w = (T)rt.omza[r];  // north rings: cos th >= 0
   Rec0<T> cn = rm[m];
   T2 pn;
   if (PHI) pn = pm[m];
   for (int l = m;; l += 2) {
-    // ---- even l - m: value in b
+    // ---- even l - m
     {
       const Rec0<T> c = cn;
       T2 pc;
@@ -180,10 +199,10 @@ __global__ void __launch_bounds__(128) legendre_spin0_kernel(RingTable rt, const
         }
       }
       if (l == lmax) break;
-      step_into<T, NDER>(a, b, LC, X, c.A);
-      rescale<T, NDER>(a, b, a[0], sc);
+      rec_step<T, NDER, 1>(a, b, LC, X, w, c.A, c.Q);
+      rescale<T, NDER>(a, b, b[0], sc);
     }
-    // ---- odd l - m: value in a
+    // ---- odd l - m
     {
       const Rec0<T> c = cn;
       T2 pc;
@@ -195,17 +214,17 @@ __global__ void __launch_bounds__(128) legendre_spin0_kernel(RingTable rt, const
       if (sc == 0) {
 #pragma unroll
         for (int j = 0; j <= NDER; ++j) {
-          orr[j] = fma(c.re, a[j], orr[j]);
-          oi[j] = fma(c.im, a[j], oi[j]);
+          orr[j] = fma(c.re, b[j], orr[j]);
+          oi[j] = fma(c.im, b[j], oi[j]);
         }
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-          por[j] = fma(pc.x, a[j], por[j]);
-          poi[j] = fma(pc.y, a[j], poi[j]);
+          por[j] = fma(pc.x, b[j], por[j]);
+          poi[j] = fma(pc.y, b[j], poi[j]);
         }
       }
       if (l + 1 == lmax) break;
-      step_into<T, NDER>(b, a, LC, X, c.A);
+      rec_step<T, NDER, 1>(a, b, LC, X, w, c.A, c.Q);
       rescale<T, NDER>(a, b, b[0], sc);
     }
   }
@@ -256,6 +275,24 @@ __device__ __forceinline__ void acc2(const Rec2<T> &c, const T (&v)[NDER + 1], T
   }
 }
 
+// The recurrence of one ring from l0 to lmax, contracted as it goes (SG = sign cos th).
+template <typename T, int NDER, int SG>
+__device__ __forceinline__ void spin2_sweep(const Rec2<T> *__restrict__ rm, int l0, int lmax, const Leib<T, NDER> &LC,
+                                            T X, T w, T (&a)[NDER + 1], T (&b)[NDER + 1], int &sc,
+                                            T (&s1r)[NDER + 1], T (&s1i)[NDER + 1], T (&s2r)[NDER + 1],
+                                            T (&s2i)[NDER + 1]) {
+  Rec2<T> cn = rm[l0];
+#pragma unroll 2
+  for (int l = l0;; ++l) {
+    const Rec2<T> c = cn;
+    if (l + 1 <= lmax) cn = rm[l + 1];
+    if (sc == 0) acc2<T, NDER>(c, b, s1r, s1i, s2r, s2i);
+    if (l == lmax) break;
+    rec_step<T, NDER, SG>(a, b, LC, X + c.cterm, w, c.A, SG > 0 ? c.Qn : c.Qs);
+    rescale<T, NDER>(a, b, b[0], sc);
+  }
+}
+
 template <typename T, int NDER, int RP>
 __global__ void __launch_bounds__(2 * RP) legendre_spin2_kernel(RingTable rt, const double *__restrict__ lnorm0,
                                                                 int nside, int lmax, int mmax, int nrings,
@@ -280,33 +317,18 @@ __global__ void __launch_bounds__(2 * RP) legendre_spin2_kernel(RingTable rt, co
     const double x = rt.z[r], st = rt.sint[r];
     Leib<T, NDER> LC;
     leibniz_coefs<T, NDER>(x, st, invL, LC);
-    T a[NDER + 1], b[NDER + 1];
+    T a[NDER + 1], b[NDER + 1];  // b = mu_l; a = d_l (float) or mu_{l-1} (double)
     int sc;
     const int l0 = seed_spin2<T, NDER>(rt, lnorm0, r, m, invL, b, sc);
-#pragma unroll
-    for (int j = 0; j <= NDER; ++j) a[j] = (T)0;
+    rec_init<T, NDER>(a, b);
     const Rec2<T> *rm = rec + (long long)m * (2 * lmax + 1 - m) / 2;
-    const T X = (T)x;
+    const T X = (T)x, w = (T)rt.omza[r];
     if (l0 <= lmax) {
-      Rec2<T> cn = rm[l0];
-      for (int l = l0;; l += 2) {
-        {
-          const Rec2<T> c = cn;
-          if (l + 1 <= lmax) cn = rm[l + 1];
-          if (sc == 0) acc2<T, NDER>(c, b, s1r, s1i, s2r, s2i);
-          if (l == lmax) break;
-          step_into<T, NDER>(a, b, LC, X + c.cterm, c.A);
-          rescale<T, NDER>(a, b, a[0], sc);
-        }
-        {
-          const Rec2<T> c = cn;
-          if (l + 2 <= lmax) cn = rm[l + 2];
-          if (sc == 0) acc2<T, NDER>(c, a, s1r, s1i, s2r, s2i);
-          if (l + 1 == lmax) break;
-          step_into<T, NDER>(b, a, LC, X + c.cterm, c.A);
-          rescale<T, NDER>(a, b, b[0], sc);
-        }
-      }
+      // mirror threads (cos th < 0) are whole warps: RP is a multiple of 32
+      if (mirror)
+        spin2_sweep<T, NDER, -1>(rm, l0, lmax, LC, X, w, a, b, sc, s1r, s1i, s2r, s2i);
+      else
+        spin2_sweep<T, NDER, 1>(rm, l0, lmax, LC, X, w, a, b, sc, s1r, s1i, s2r, s2i);
     }
   }
 #pragma unroll

@@ -15,6 +15,26 @@
 // which is exact and regular at every ring. Derivatives are carried divided by
 // L^j (L = lmax+1) so that all orders share one floating-point range.
 //
+// Normalisation: mu_l = lam_l / k_l with k_{l+1} = beta_{l+1} k_{l-1}, so that
+//   mu_{l+1} = A_{l+1} X mu_l - mu_{l-1},   A_{l+1} = alpha_{l+1} k_l / k_{l+1}.
+// k_{l0} = 1 and k_{l0+1} is chosen so that the even and odd chains of k meet
+// (k_{l+1}/k_l -> 1): then A_l -> 2 smoothly instead of alternating about 2, and
+// the tables hold A - 2 (computed in double) so that A X - 2 keeps its precision.
+//
+// Two forms of the step. The double kernels run it as written (plain form). The
+// float kernels run the difference form: with sg = sign(cos th), w = 1 - |cos th|
+// and the state (mu_l, d_l = mu_l - sg mu_{l-1}),
+//   c = Q - A w,  Q = (A - 2) + sg A m s/(l(l+1))        [= sg A (X + ms/(l(l+1))) - 2]
+//   d_{l+1} = sg (c mu_l + d_l) + A sum_i C(j,i) cos^(i)(th) mu^(j-i)_l,
+//   mu_{l+1} = sg mu_l + d_{l+1}.
+// Near the poles A X - 2 is a small difference of numbers near 2, and float
+// values of cos th and of A would each move it by ~1e-7, a large part of theta^2
+// on the polar rings; the plain float step also amplifies its own rounding there
+// (the two roots of the step meet at 1). The difference form uses w and A - 2,
+// each exact to float precision, and its rounding of mu moves the state along the
+// slowly varying solution (the idea of Reinsch's modification of the Goertzel
+// recurrence), which keeps float results near 1e-6 on every ring.
+//
 // Seeds lam_{l0,m}, l0 = max(m,|s|), are N sin^a(th/2) cos^b(th/2); their
 // logarithm and their theta-derivatives (via d^k/dth^k of ln sin(th/2) and
 // ln cos(th/2), tabulated per ring) are formed in double precision. Values are
@@ -45,14 +65,16 @@ template <> struct RealTraits<double> {
 };
 
 // Coefficient record of the spin-0 stage at index idx(l, m): the coefficient
-// times k_l and the factor A_{l+1} of the normalised step l -> l+1.
+// times k_l, the factor A_{l+1} of the normalised step l -> l+1 and Q = A_{l+1} - 2.
 template <typename T> struct __align__(4 * sizeof(T)) Rec0 {
-  T re, im, A, pad;
+  T re, im, A, Q;
 };
-// Spin-2 stage: k_l (E + iB), k_l (-1)^(l+m) (E - iB), A_{l+1} and m s/(l(l+1)).
+// Spin-2 stage: k_l (E + iB), k_l (-1)^(l+m) (E - iB), A_{l+1}, C = m s/(l(l+1)) and
+// the difference-form factors Qn = (A - 2) + A C (rings with cos th >= 0) and
+// Qs = (A - 2) - A C (cos th < 0).
 template <typename T> struct __align__(4 * sizeof(T)) Rec2 {
   T c1r, c1i, c2r, c2i;
-  T A, cterm, pad0, pad1;
+  T A, cterm, Qn, Qs;
 };
 
 // ---------------------------------------------------------------------------
@@ -154,7 +176,7 @@ __device__ __forceinline__ void leibniz_coefs(double x, double st, double invL, 
     for (int i = 0; i <= NDER; ++i) L.e[j][i] = (i >= 1 && i <= j) ? (T)(binom(j, i) * dc[i]) : (T)0;
 }
 
-// In-place step: old (mu_{l-1}) becomes mu_{l+1} from cur (mu_l):
+// Plain form, in place: old (mu_{l-1}) becomes mu_{l+1} from cur (mu_l):
 //   old^(j) = A (X cur^(j) + sum_{i>=1} e[j][i] cur^(j-i)) - old^(j)
 template <typename T, int NDER>
 __device__ __forceinline__ void step_into(T (&old)[NDER + 1], const T (&cur)[NDER + 1], const Leib<T, NDER> &L,
@@ -166,6 +188,54 @@ __device__ __forceinline__ void step_into(T (&old)[NDER + 1], const T (&cur)[NDE
     for (int i = 1; i <= j; ++i) acc = fma(L.e[j][i], cur[j - i], acc);
     old[j] = fma(A, acc, -old[j]);
   }
+}
+
+// Difference form (SG = sign of cos th), in place: (v, d) = (mu_l, mu_l - SG mu_{l-1})
+// become (mu_{l+1}, mu_{l+1} - SG mu_l); w = 1 - |cos th|, Q = Qn or Qs of the record.
+template <typename T, int NDER, int SG>
+__device__ __forceinline__ void step_diff(T (&v)[NDER + 1], T (&d)[NDER + 1], const Leib<T, NDER> &L, T w, T A,
+                                          T Q) {
+  const T c = fma(-A, w, Q);
+#pragma unroll
+  for (int j = NDER; j >= 0; --j) {
+    T t = fma(c, v[j], d[j]);
+    if (SG < 0) t = -t;
+    if (j >= 1) {
+      T acc = L.e[j][1] * v[j - 1];
+#pragma unroll
+      for (int i = 2; i <= j; ++i) acc = fma(L.e[j][i], v[j - i], acc);
+      t = fma(A, acc, t);
+    }
+    d[j] = t;
+    v[j] = (SG > 0) ? v[j] + t : t - v[j];
+  }
+}
+
+// One step of either form for a T-typed kernel whose current values are in v:
+// float runs the difference form (aux = d), double the plain form (aux = mu_{l-1},
+// the new value rotated into v). X = cos th + C (plain), w, A, Q (difference).
+template <typename T, int NDER, int SG>
+__device__ __forceinline__ void rec_step(T (&aux)[NDER + 1], T (&v)[NDER + 1], const Leib<T, NDER> &L, T X, T w,
+                                         T A, T Q) {
+  if constexpr (sizeof(T) == 4) {
+    step_diff<T, NDER, SG>(v, aux, L, w, A, Q);
+  } else {
+    step_into<T, NDER>(aux, v, L, X, A);
+#pragma unroll
+    for (int j = 0; j <= NDER; ++j) {
+      const T t = aux[j];
+      aux[j] = v[j];
+      v[j] = t;
+    }
+  }
+}
+
+// State at l0 from the seed values in v: the plain form's mu_{l0-1} = 0, the
+// difference form's d = mu_{l0} - SG * 0.
+template <typename T, int NDER>
+__device__ __forceinline__ void rec_init(T (&aux)[NDER + 1], const T (&v)[NDER + 1]) {
+#pragma unroll
+  for (int j = 0; j <= NDER; ++j) aux[j] = (sizeof(T) == 4) ? v[j] : (T)0;
 }
 
 // Exponent rescaling while the values are below the representable range.

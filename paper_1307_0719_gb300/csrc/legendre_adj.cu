@@ -113,18 +113,17 @@ __global__ void __launch_bounds__(128) legendre_adj0_kernel(RingTable rt, const 
   const double x = rt.z[r], st = rt.sint[r];
   Leib<T, NDER> LC;
   leibniz_coefs<T, NDER>(x, st, invL, LC);
-  T a[NDER + 1], b[NDER + 1];
+  T a[NDER + 1], b[NDER + 1];  // b = mu_l; a = d_l (float) or mu_{l-1} (double)
   int sc;
   seed_spin0<T, NDER>(rt, lnorm0, r, m, invL, b, sc);
-#pragma unroll
-  for (int j = 0; j <= NDER; ++j) a[j] = (T)0;
+  rec_init<T, NDER>(a, b);
 
   const long long base = (long long)m * (2 * lmax + 1 - m) / 2;
-  const T2 *tm = tab + base;
-  const T X = (T)x;
+  const T2 *tm = tab + base;  // {k_l, A_{l+1} - 2}
+  const T X = (T)x, w = (T)rt.omza[r];
   int lb = m;  // first l of the current window
   for (int l = m;; l += 2) {
-    // ---- even l - m: value in b
+    // ---- even l - m
     {
       const int li = l - lb;
       T cr = (T)0, ci = (T)0, pr = (T)0, pi = (T)0;
@@ -153,24 +152,25 @@ __global__ void __launch_bounds__(128) legendre_adj0_kernel(RingTable rt, const 
         lb += W;
       }
       if (l == lmax) break;
-      step_into<T, NDER>(a, b, LC, X, tm[l].y);
-      rescale<T, NDER>(a, b, a[0], sc);
+      const T Q = tm[l].y;
+      rec_step<T, NDER, 1>(a, b, LC, X, w, (T)2 + Q, Q);
+      rescale<T, NDER>(a, b, b[0], sc);
     }
-    // ---- odd l - m: value in a
+    // ---- odd l - m
     {
       const int li = l + 1 - lb;
       T cr = (T)0, ci = (T)0, pr = (T)0, pi = (T)0;
       if (sc == 0) {
 #pragma unroll
         for (int j = 0; j <= NDER; ++j) {
-          cr = fma(a[j], gmr[j], cr);
-          ci = fma(a[j], gmi[j], ci);
+          cr = fma(b[j], gmr[j], cr);
+          ci = fma(b[j], gmi[j], ci);
         }
         if (PHI) {
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
-            pr = fma(a[j], hmr[j], pr);
-            pi = fma(a[j], hmi[j], pi);
+            pr = fma(b[j], hmr[j], pr);
+            pi = fma(b[j], hmi[j], pi);
           }
         }
       }
@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(128) legendre_adj0_kernel(RingTable rt, const 
         lb += W;
       }
       if (l + 1 == lmax) break;
-      step_into<T, NDER>(b, a, LC, X, tm[l + 1].y);
+      const T Q = tm[l + 1].y;
+      rec_step<T, NDER, 1>(a, b, LC, X, w, (T)2 + Q, Q);
       rescale<T, NDER>(a, b, b[0], sc);
     }
   }
@@ -193,6 +194,53 @@ __global__ void __launch_bounds__(128) legendre_adj0_kernel(RingTable rt, const 
 
 // ---------------------------------------------------------------------------
 // spin 2: block = 64 north rings and their 64 mirrors (one thread each).
+
+// Recurrence of one ring (SG = sign cos th) with the transposed contraction into
+// the block's l windows; U1 = S1bar + S2bar (even l + m), U2 = S1bar - S2bar (odd).
+template <typename T, int NDER, int SG, int WV>
+__device__ __forceinline__ void adj2_sweep(const Rec2<T> *__restrict__ rm, int l0, int m, int lmax, long long base,
+                                           const Leib<T, NDER> &LC, T X, T w, T (&a)[NDER + 1], T (&b)[NDER + 1],
+                                           int &sc, const T (&u1r)[NDER + 1], const T (&u1i)[NDER + 1],
+                                           const T (&u2r)[NDER + 1], const T (&u2i)[NDER + 1],
+                                           T (*win)[WV + 1], double *accE, double *accB) {
+  constexpr int NT = 128, V = 4, W = WV / V;
+  const int t = threadIdx.x;
+  int lb = l0;
+  const int par0 = (l0 + m) & 1;  // parity of l + m at l0
+  for (int l = l0;; l += 2) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int ll = l + half;
+      const int li = ll - lb;
+      const bool even = ((par0 + half) & 1) == 0;
+      T er = (T)0, ei = (T)0, fr = (T)0, fi = (T)0;
+      if (sc == 0) {
+#pragma unroll
+        for (int j = 0; j <= NDER; ++j) {
+          const T p1r = even ? u1r[j] : u2r[j], p1i = even ? u1i[j] : u2i[j];
+          const T p2r = even ? u2r[j] : u1r[j], p2i = even ? u2i[j] : u1i[j];
+          er = fma(b[j], p1r, er);
+          ei = fma(b[j], p1i, ei);
+          fr = fma(b[j], p2r, fr);
+          fi = fma(b[j], p2i, fi);
+        }
+      }
+      win[t][li * V + 0] = er;
+      win[t][li * V + 1] = ei;
+      win[t][li * V + 2] = fr;
+      win[t][li * V + 3] = fi;
+      if (ll == lmax || li == W - 1) {
+        flush_window<T, NT, WV, V>(win, li + 1, base + lb, accE, accB);
+        lb += W;
+      }
+      if (ll == lmax) return;
+      const Rec2<T> c = rm[ll];
+      rec_step<T, NDER, SG>(a, b, LC, X + c.cterm, w, c.A, SG > 0 ? c.Qn : c.Qs);
+      rescale<T, NDER>(a, b, b[0], sc);
+    }
+    if (l + 1 >= lmax) return;
+  }
+}
 
 template <typename T, int NDER>
 __global__ void __launch_bounds__(128) legendre_adj2_kernel(RingTable rt, const double *__restrict__ lnorm0,
@@ -242,58 +290,21 @@ __global__ void __launch_bounds__(128) legendre_adj2_kernel(RingTable rt, const 
   const double x = rt.z[r], st = rt.sint[r];
   Leib<T, NDER> LC;
   leibniz_coefs<T, NDER>(x, st, invL, LC);
-  T a[NDER + 1], b[NDER + 1];
+  T a[NDER + 1], b[NDER + 1];  // b = mu_l; a = d_l (float) or mu_{l-1} (double)
   int sc;
   const int l0 = seed_spin2<T, NDER>(rt, lnorm0, r, m, invL, b, sc);
-#pragma unroll
-  for (int j = 0; j <= NDER; ++j) a[j] = (T)0;
+  rec_init<T, NDER>(a, b);
   if (l0 > lmax) return;  // uniform over the block
 
   const long long base = (long long)m * (2 * lmax + 1 - m) / 2;
   const Rec2<T> *rm = rec + base;
-  const T X = (T)x;
-  int lb = l0;
-  // parity of l + m at l0 (l0 = m, or 2 for m < 2)
-  const int par0 = (l0 + m) & 1;
-  for (int l = l0;; l += 2) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int ll = l + half;
-      const int li = ll - lb;
-      T(&v)[NDER + 1] = half ? a : b;
-      const bool even = ((par0 + half) & 1) == 0;
-      T er = (T)0, ei = (T)0, fr = (T)0, fi = (T)0;
-      if (sc == 0) {
-#pragma unroll
-        for (int j = 0; j <= NDER; ++j) {
-          const T p1r = even ? u1r[j] : u2r[j], p1i = even ? u1i[j] : u2i[j];
-          const T p2r = even ? u2r[j] : u1r[j], p2i = even ? u2i[j] : u1i[j];
-          er = fma(v[j], p1r, er);
-          ei = fma(v[j], p1i, ei);
-          fr = fma(v[j], p2r, fr);
-          fi = fma(v[j], p2i, fi);
-        }
-      }
-      win[t][li * V + 0] = er;
-      win[t][li * V + 1] = ei;
-      win[t][li * V + 2] = fr;
-      win[t][li * V + 3] = fi;
-      if (ll == lmax || li == W - 1) {
-        flush_window<T, NT, WV, V>(win, li + 1, base + lb, accE, accB);
-        lb += W;
-      }
-      if (ll == lmax) break;
-      const Rec2<T> c = rm[ll];
-      if (half == 0) {
-        step_into<T, NDER>(a, b, LC, X + c.cterm, c.A);
-        rescale<T, NDER>(a, b, a[0], sc);
-      } else {
-        step_into<T, NDER>(b, a, LC, X + c.cterm, c.A);
-        rescale<T, NDER>(a, b, b[0], sc);
-      }
-    }
-    if (l + 1 >= lmax) break;
-  }
+  const T X = (T)x, w = (T)rt.omza[r];
+  // mirror threads (cos th < 0) are warps 2 and 3; the window flushes inside keep
+  // every thread of the block in step, so both branches run the same l sequence
+  if (mirror)
+    adj2_sweep<T, NDER, -1, WV>(rm, l0, m, lmax, base, LC, X, w, a, b, sc, u1r, u1i, u2r, u2i, win, accE, accB);
+  else
+    adj2_sweep<T, NDER, 1, WV>(rm, l0, m, lmax, base, LC, X, w, a, b, sc, u1r, u1i, u2r, u2i, win, accE, accB);
 }
 
 // Final scaling: abar = k_l acc; B's accumulator holds f with Bbar = -i k f;

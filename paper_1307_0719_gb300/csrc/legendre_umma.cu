@@ -270,36 +270,53 @@ template <int NB> __device__ __forceinline__ uint32_t phase_of(uint32_t g) { ret
 // ---------------------------------------------------------------------------
 // recurrence steps with the basis values buffered for the tiles
 
-template <int S0, int NDER, bool GATED, bool SPIN2>
+// Four steps of the difference form (SG = sign cos th of the thread's ring), the
+// basis value of each l saved for the tiles before its step: state (b, a) =
+// (mu_l, d_l), step factors A and Q of the block's 8 values of l.
+template <int S0, int NDER, bool GATED, int SG>
 __device__ __forceinline__ void four_steps(float (&a)[NDER + 1], float (&b)[NDER + 1], int &sc,
-                                           const Leib<float, NDER> &LC, float X, const float (&Av)[8],
-                                           const float (&Cv)[8], float (&buf)[NDER + 1][4]) {
+                                           const Leib<float, NDER> &LC, float w, const float (&Av)[8],
+                                           const float (&Qv)[8], float (&buf)[NDER + 1][4]) {
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int s = S0 + q;
     const bool on = GATED ? (sc == 0) : true;
 #pragma unroll
-    for (int j = 0; j <= NDER; ++j) buf[j][q] = on ? ((s & 1) ? a[j] : b[j]) : 0.0f;
-    const float Xs = SPIN2 ? X + Cv[s] : X;
-    if (s & 1) {
-      step_into<float, NDER>(b, a, LC, Xs, Av[s]);
-      if (GATED) rescale<float, NDER>(a, b, b[0], sc);
-    } else {
-      step_into<float, NDER>(a, b, LC, Xs, Av[s]);
-      if (GATED) rescale<float, NDER>(a, b, a[0], sc);
-    }
+    for (int j = 0; j <= NDER; ++j) buf[j][q] = on ? b[j] : 0.0f;
+    step_diff<float, NDER, SG>(b, a, LC, w, Av[s], Qv[s]);
+    if (GATED) rescale<float, NDER>(a, b, b[0], sc);
   }
 }
 
-template <int S0, int NDER, bool SPIN2>
+template <int S0, int NDER, int SG>
 __device__ __forceinline__ void steps_gated(float (&a)[NDER + 1], float (&b)[NDER + 1], int &sc,
-                                            const Leib<float, NDER> &LC, float X, const float (&Av)[8],
-                                            const float (&Cv)[8], float (&buf)[NDER + 1][4]) {
+                                            const Leib<float, NDER> &LC, float w, const float (&Av)[8],
+                                            const float (&Qv)[8], float (&buf)[NDER + 1][4]) {
   if (__all_sync(0xffffffffu, sc == 0))
-    four_steps<S0, NDER, false, SPIN2>(a, b, sc, LC, X, Av, Cv, buf);
+    four_steps<S0, NDER, false, SG>(a, b, sc, LC, w, Av, Qv, buf);
   else
-    four_steps<S0, NDER, true, SPIN2>(a, b, sc, LC, X, Av, Cv, buf);
+    four_steps<S0, NDER, true, SG>(a, b, sc, LC, w, Av, Qv, buf);
 }
+
+// The 8 steps of one block; spin 2's mirror rings (cos th < 0) are whole warps
+// (threads 64-127 of a half), so the branch is warp-uniform.
+template <int NDER, bool SPIN2>
+__device__ __forceinline__ void block_steps(bool mirror, float (&a)[NDER + 1], float (&b)[NDER + 1], int &sc,
+                                            const Leib<float, NDER> &LC, float w, const float (&Av)[8],
+                                            const float (&Qv)[8], float (&buf0)[NDER + 1][4],
+                                            float (&buf1)[NDER + 1][4]) {
+  if (SPIN2 && mirror) {
+    steps_gated<0, NDER, -1>(a, b, sc, LC, w, Av, Qv, buf0);
+    steps_gated<4, NDER, -1>(a, b, sc, LC, w, Av, Qv, buf1);
+  } else {
+    steps_gated<0, NDER, 1>(a, b, sc, LC, w, Av, Qv, buf0);
+    steps_gated<4, NDER, 1>(a, b, sc, LC, w, Av, Qv, buf1);
+  }
+}
+
+// step table per 8-l block: A_{l+1} x 8, then Q x 8 (spin 0: A - 2; spin 2: Qn x 8
+// for rings with cos th >= 0, then Qs x 8 for the mirror rings)
+__host__ __device__ constexpr int step_stride(bool spin2) { return spin2 ? 24 : 16; }
 
 // the block's basis values of every order into the calling thread's lane: hi (and
 // lo for 3xTF32) of l = l0 + 8 blk + 0..7, at column a0 + AW j; BF16x3: the hi
@@ -375,7 +392,7 @@ __device__ __forceinline__ int unit_ring(const TcDesc &D, int rblk, int tid, boo
   return (SPIN2 && tid >= 64) ? D.nrings - 1 - rn : rn;
 }
 
-// recurrence state at l0: mu_{l0} in b, mu_{l0-1} = 0 in a, scale sc
+// recurrence state at l0: mu_{l0} in b, d_{l0} = mu_{l0} in a, scale sc
 template <int NDER, bool SPIN2>
 __device__ __forceinline__ void unit_seed(const TcDesc &D, int r, int m, bool active, float (&a)[NDER + 1],
                                           float (&b)[NDER + 1], int &sc) {
@@ -385,8 +402,7 @@ __device__ __forceinline__ void unit_seed(const TcDesc &D, int r, int m, bool ac
   else
     seed_spin0<float, NDER>(D.rt, D.lnorm0, r, m, invL, b, sc);
   if (!active) sc = -1000000;  // contributes nothing
-#pragma unroll
-  for (int j = 0; j <= NDER; ++j) a[j] = 0.0f;
+  rec_init<float, NDER>(a, b);  // difference form: d = mu_{l0}
 }
 
 // One (m, ring block) unit: recurrence and tiles (compute warps), MMAs (issuing
@@ -465,21 +481,21 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
     } else {
       unit_seed<NDER, SPIN2>(D, r, m, active, a, b, sc);
     }
-    const float X = (float)rt.z[r];
+    const float w = (float)rt.omza[r];
+    const bool mirror = SPIN2 && t >= 64;
     // the next block's step factors and coefficient tile (BT / 128 bytes per
     // thread), loaded one block ahead
     constexpr int QV = (int)(BT / 16 / kComputeThreads);  // float4 per thread: 1 or 2
+    const int qo = mirror ? 4 : 2;  // float4 offset of the thread's Q values
     float4 nA0 = make_float4(0.f, 0.f, 0.f, 0.f), nA1 = nA0, nC0 = nA0, nC1 = nA0, nbq[QV];
 #pragma unroll
     for (int q = 0; q < QV; ++q) nbq[q] = nA0;
     auto prefetch = [&](int blk) {
-      const float4 *stp = (const float4 *)(D.step + (b0 + blk) * 16);
+      const float4 *stp = (const float4 *)(D.step + (b0 + blk) * step_stride(SPIN2));
       nA0 = __ldg(stp);
       nA1 = __ldg(stp + 1);
-      if (SPIN2) {
-        nC0 = __ldg(stp + 2);
-        nC1 = __ldg(stp + 3);
-      }
+      nC0 = __ldg(stp + qo);
+      nC1 = __ldg(stp + qo + 1);
       const float4 *bt = (const float4 *)(D.b + (b0 + blk) * BT);
 #pragma unroll
       for (int q = 0; q < QV; ++q) nbq[q] = __ldg(bt + q * kComputeThreads + t);
@@ -495,8 +511,7 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       for (int q = 0; q < QV; ++q) bq[q] = nbq[q];
       if (k + 1 < cnt) prefetch(blk + 1);
       float buf0[NJ][4], buf1[NJ][4];
-      steps_gated<0, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf0);
-      steps_gated<4, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf1);
+      block_steps<NDER, SPIN2>(mirror, a, b, sc, LC, w, Av, Cv, buf0, buf1);
       // the buffer was last read by the MMAs of this half's block g - NB
       if (g >= (uint32_t)NB && !mbar_wait(bar_done(U, i, h), phase_of<NB>(g - NB), U.abort)) {
         bad = true;
@@ -785,17 +800,15 @@ __global__ void __launch_bounds__(kComputeThreads) tcstart_kernel(TcDesc D, int 
   float a[NJ], b[NJ];
   int sc;
   unit_seed<NDER, SPIN2>(D, r, m, active, a, b, sc);
-  const float X = (float)D.rt.z[r];
+  const float w = (float)D.rt.omza[r];
+  const bool mirror = SPIN2 && tid >= 64;
+  const int qo = mirror ? 4 : 2;
   const size_t so = (size_t)unit * (2 * NJ + 1) * kComputeThreads + tid;
   int first = nblk, stop = nblk;
   for (int blk = 0; blk < stop; ++blk) {
-    const float4 *stp = (const float4 *)(D.step + (b0 + blk) * 16);
+    const float4 *stp = (const float4 *)(D.step + (b0 + blk) * step_stride(SPIN2));
     const float4 A0 = __ldg(stp), A1 = __ldg(stp + 1);
-    float4 C0 = make_float4(0.f, 0.f, 0.f, 0.f), C1 = C0;
-    if (SPIN2) {
-      C0 = __ldg(stp + 2);
-      C1 = __ldg(stp + 3);
-    }
+    const float4 C0 = __ldg(stp + qo), C1 = __ldg(stp + qo + 1);
     const float Av[8] = {A0.x, A0.y, A0.z, A0.w, A1.x, A1.y, A1.z, A1.w};
     const float Cv[8] = {C0.x, C0.y, C0.z, C0.w, C1.x, C1.y, C1.z, C1.w};
     float sa[NJ], sb[NJ];
@@ -806,8 +819,7 @@ __global__ void __launch_bounds__(kComputeThreads) tcstart_kernel(TcDesc D, int 
     }
     const int ssc = sc;
     float buf0[NJ][4], buf1[NJ][4];
-    steps_gated<0, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf0);
-    steps_gated<4, NDER, SPIN2>(a, b, sc, LC, X, Av, Cv, buf1);
+    block_steps<NDER, SPIN2>(mirror, a, b, sc, LC, w, Av, Cv, buf0, buf1);
     // a ring can have contributed in this block only if its scale is 0 at the end
     if (first == nblk && __syncthreads_or(sc == 0)) {
       first = blk;
@@ -838,7 +850,9 @@ __global__ void __launch_bounds__(kComputeThreads) tcstart_kernel(TcDesc D, int 
 // ---------------------------------------------------------------------------
 // plan-time and per-call tables
 
-// step factors per block: A_{l+1} (8 floats) then m s/(l(l+1)) (8 floats); 0 past lmax
+// step factors per block (layout of step_stride): A_{l+1} (8 floats), then for spin 0
+// A - 2 (8 floats), for spin 2 Qn = A - 2 + A C and Qs = A - 2 - A C (8 each), with
+// C = m s/(l(l+1)), formed in double from the plan's {k_l, A_{l+1} - 2}; 0 past lmax
 __global__ void tcstep_kernel(int lmax, int s, const long long *__restrict__ blkofs,
                               const float2 *__restrict__ tab, float *__restrict__ out) {
   const int m = blockIdx.y;
@@ -849,14 +863,18 @@ __global__ void tcstep_kernel(int lmax, int s, const long long *__restrict__ blk
   if (e >= nblk * 8) return;
   const int blk = e >> 3, k = e & 7;
   const int l = l0 + 8 * blk + k;
-  float A = 0.0f, ct = 0.0f;
+  float A = 0.0f, qn = 0.0f, qs = 0.0f;
   if (l <= lmax) {
-    A = tab[(long long)m * (2 * lmax + 1 - m) / 2 + l].y;
-    ct = (float)((double)m * s / ((double)l * (l + 1.0)));
+    const double Am2 = (double)tab[(long long)m * (2 * lmax + 1 - m) / 2 + l].y, Ad = 2.0 + Am2;
+    const double C = (s == 0) ? 0.0 : (double)m * s / ((double)l * (l + 1.0));  // spin 0 has l = 0
+    A = (float)Ad;
+    qn = (float)(Am2 + Ad * C);
+    qs = (float)(Am2 - Ad * C);
   }
-  float *o = out + (blkofs[m] + blk) * 16;
+  float *o = out + (blkofs[m] + blk) * step_stride(as == 2);
   o[k] = A;
-  o[8 + k] = ct;
+  o[8 + k] = qn;
+  if (as == 2) o[16 + k] = qs;
 }
 
 // Coefficient tiles per 8-l block: B[n][k] for column n = 4 rho + c (n < NC) and

@@ -211,7 +211,7 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
     TRY_CUDA(dalloc(&p->tc_bp, bt * (size_t)n0, B));
     if (pol) {
       TRY_CUDA(upload(&p->tc_blk2, b2, B));
-      TRY_CUDA(dalloc((void **)&p->tc_step2, 64 * (size_t)(n2 > 0 ? n2 : 1), B));
+      TRY_CUDA(dalloc((void **)&p->tc_step2, 96 * (size_t)(n2 > 0 ? n2 : 1), B));
       TRY_CUDA(launch_tcstep(p, 2, p->tc_blk2, p->tab2, p->tc_step2, 0));
       TRY_CUDA(dalloc(&p->tc_b2, bt * (size_t)(n2 > 0 ? n2 : 1), B));
     }
@@ -419,12 +419,10 @@ static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s)
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
   const size_t mapb = (size_t)p->elem * p->npix;
   std::vector<MapJob> jobs;
-  // T maps pair within one coefficient plane j (the fold reads the row once for
-  // both), left-overs pair across planes; Q and U of the same (j, k) pair
-  for (const std::pair<int, int> &jk : paired_order(p->order))
-    jobs.push_back(MapJob{0, jk.first, jk.second, 0, 1.0 / (fact(jk.first) * fact(jk.second)),
-                          (char *)p->d3 + mapb * ((jk.first + jk.second) * (jk.first + jk.second + 1) / 2 +
-                                                  jk.first)});
+  // Jobs are packed two per transform in list order. Q and U of the same (j, k)
+  // pair (similar magnitudes) and come first, an even count; then the T maps, which
+  // pair within one coefficient plane j (the fold reads the row once for both),
+  // left-overs across planes, the last one alone when their count is odd.
   if (pol)
     for (int n = 0; n <= p->order; ++n)
       for (int j = 0; j <= n; ++j)
@@ -433,6 +431,10 @@ static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s)
           jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)),
                                 (char *)p->d3 + mapb * (g * p->nmaps + n * (n + 1) / 2 + j)});
         }
+  for (const std::pair<int, int> &jk : paired_order(p->order))
+    jobs.push_back(MapJob{0, jk.first, jk.second, 0, 1.0 / (fact(jk.first) * fact(jk.second)),
+                          (char *)p->d3 + mapb * ((jk.first + jk.second) * (jk.first + jk.second + 1) / 2 +
+                                                  jk.first)});
   TRY_CUDA(launch_ringfft_planes(p, planes, jobs.data(), (int)jobs.size(), s));
   return TL_OK;
 }

@@ -65,6 +65,11 @@ static int ring_sub_stride_max(const FftGroup &g) {
 //   (-1)^q [shifted rings] * w_m (i m / L)^k F_m,   w_0 = 1, w_m = 2,
 // i.e. the class's contribution without its common phase e^{i t0 phi0}.
 
+// x 2^n, exactly
+template <typename T> __device__ __forceinline__ T scale2(T x, int n);
+template <> __device__ __forceinline__ float scale2<float>(float x, int n) { return scalbnf(x, n); }
+template <> __device__ __forceinline__ double scale2<double>(double x, int n) { return scalbn(x, n); }
+
 // (i)^k g
 template <typename T2>
 __device__ __forceinline__ T2 rot_ik(T2 a, int k) {
@@ -160,9 +165,25 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
   // double operation per thread would queue on the FP64 pipe
   constexpr bool F32 = sizeof(T) == 4;
   const T inv_s = F32 ? (T)rt.rsinf[r] : (T)(1.0 / rt.sint[r]);
-  const T wa = JA.div_sint ? inv_s : (T)1;
-  const T wb = hasb ? (JB.div_sint ? inv_s : (T)1) : (T)0;
-  const T sa = F32 ? (T)JA.scalef : (T)JA.scale, sb = F32 ? (T)JB.scalef : (T)JB.scale;
+  T wa = JA.div_sint ? inv_s : (T)1;
+  T wb = hasb ? (JB.div_sint ? inv_s : (T)1) : (T)0;
+  T sa = F32 ? (T)JA.scalef : (T)JA.scale, sb = F32 ? (T)JB.scalef : (T)JB.scale;
+  // Balance of the two packed maps. A normalised phi-derivative map scales like
+  // (m/L)^k, and near the poles only m up to about L sin(theta) contribute, so there
+  // map k is ~ (L sin th)^-k times map 0 and a shared transform's rounding of the
+  // larger map would swamp the smaller one. Each job is carried times 2^(e k') in the
+  // transform (k' = k, less one for a map divided by sin theta, which that division
+  // already balances), 2^e ~ L / (1 + L sin th), and scaled back on output: powers
+  // of two, so the values are unchanged.
+  {
+    const float Lf = (float)((T)1 / invL), sf = rt.ringf[8 * (size_t)r + 1];
+    const int e = max(0, __float2int_rn(log2f(Lf / (1.0f + Lf * sf))));
+    const int ea = e * max(0, JA.k - JA.div_sint), eb = e * max(0, JB.k - JB.div_sint);
+    wa = scale2<T>(wa, ea);
+    wb = scale2<T>(wb, eb);
+    sa = scale2<T>(sa, -ea);
+    sb = scale2<T>(sb, -eb);
+  }
   const T invN = (T)1 / (T)N;
 
   // ---- fold m modulo N into the Hermitian spectrum; thread handles classes t and N - t
@@ -414,11 +435,23 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_adj_ker
       ca = (T)1 / (jfact * kfa);
       cb = hasb ? (T)1 / (jfact * kfb) : (T)0;
     }
+    // balance of the packed pair (the transpose of the forward kernel's): near the
+    // poles the gradient of map k scales like (L sin th)^k; map k is carried times
+    // 2^-(e k) in the transform and its factor c_k times 2^(e k) (exact)
+    int ea = 0, eb = 0;
+    if (!defl) {
+      const float Lf = (float)L_d, sf = rt.ringf[8 * (size_t)r + 1];
+      const int e = max(0, __float2int_rn(log2f(Lf / (1.0f + Lf * sf))));
+      ea = e * ka;
+      eb = e * kb;
+      ca = scale2<T>(ca, ea);
+      cb = scale2<T>(cb, eb);
+    }
     // conj(Z) in decimated order
     for (int p = tid; p < N; p += nth) {
       T2 z;
-      z.x = ga[first + p];
-      z.y = hasb ? -gb[first + p] : (T)0;
+      z.x = scale2<T>(ga[first + p], -ea);
+      z.y = hasb ? -scale2<T>(gb[first + p], -eb) : (T)0;
       Y[ydst(p)] = z;
     }
     __syncthreads();
