@@ -41,8 +41,18 @@ import skygen  # noqa: E402
 WORKLOAD = "nside2048_lmax4096_n4_TQU"
 METRIC = "lensed TQU maps/sec @Nside2048 lmax4096 order4 (mixed vs FP64 GPU, err vs oracle)"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
-FP32_LANES = 152 * 128
+# FP32 SIMT peak from unit counts: SMs (read from the device) x 128 FP32 lanes x
+# 2 flop/FMA x the maximum SM clock of MEASURED_PEAKS.json
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(dev, peaks):
+    """(peak TFLOP/s, description) of the FP32 SIMT pipe of device `dev`."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return (sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+            f"derived: {sms} SMs (device) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz (sm_max_mhz)")
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of
 # `bench.py --workload nside512_lmax1024_n4_TQU --steps 1 --warmup 1 --form F` (16
@@ -300,8 +310,7 @@ def run_ours(args):
         with open(PEAKS_FILE) as f:
             peaks = json.load(f)
     clocks = clk.summary()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    fp32_peak, fp32_src = fp32_peak_tflops(dev, peaks)
     hbm = peaks.get("hbm_gbs")
     # stage times are those of the step's last tl_lens_batch chunk: one Legendre launch of
     # up to 16 realisations on tensor cores, one realisation otherwise
@@ -314,7 +323,7 @@ def run_ours(args):
         e = {"kernel": f"legendre_spin{spin}_{'umma' if tc else 'kernel'}<{w.order}>", "bound": "alu",
              "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
              "traffic": captured_traffic(st, w, 1, args.form) if (tc and nb == 16) else None,
-             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
+             "peak_source": fp32_src,
              "counts": "recurrence only (contraction on the tensor cores)" if tc else "recurrence + contraction"}
         if tc:
             cf = legendre_flops_per_launch(w.nside, w.lmax, w.order, spin, part="contraction", nreal=nr_launch)
@@ -337,22 +346,16 @@ def run_ours(args):
     dom = max(rl, key=lambda k: stage_ms.get(k, 0.0))
     roof = dict(rl[dom], stage=dom)
 
-    # end to end through the public API: every step copies its coefficients in from pinned
-    # host memory, lenses them (Plan.lens_batch) and copies the maps back, inside the timed region
+    # end to end through the C ABI with host buffers (tl_lens_batch_host): every step
+    # passes the coefficients in pinned host memory; the call copies them in, lenses
+    # them and copies the maps back, all inside the timed region
     e2e = None
     if not args.no_e2e:
         hin = [{k: torch.from_numpy(v).pin_memory() for k, v in sk.items()} for sk in skies]
         hout = [torch.empty((3, plan.npix), dtype=torch.float32).pin_memory() for _ in range(nb)]
-        dbuf = [{k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in h.items()} for h in hin]
 
         def e2e_step():
-            for h, dd in zip(hin, dbuf):
-                for k in h:
-                    dd[k].copy_(h[k], non_blocking=True)
-            plan.lens_batch(dbuf, outs=outs)
-            for o, ho in zip(outs, hout):
-                ho.copy_(o, non_blocking=True)
-            torch.cuda.synchronize()
+            plan.lens_batch_host(hin, outs=hout)  # synchronises before returning
 
         e2e_step()
         k2 = max(1, min(args.steps, 3))
@@ -362,8 +365,8 @@ def run_ours(args):
         e2e_s = max_over_ranks((time.perf_counter() - t0) / k2, dev)
         e2e = {"value": world * nb / e2e_s, "unit": "maps/s", "h2d_bytes_per_step": nb * 4 * plan.nalm * 16,
                "d2h_bytes_per_step": nb * 3 * plan.npix * 4, "realisations_per_step": nb,
-               "api": "Plan.lens_batch (tl_lens_batch) with pinned host buffers"}
-        del hin, hout, dbuf
+               "api": "tl_lens_batch_host (C ABI, host buffers, copies inside the call)"}
+        del hin, hout
 
     lensed = out.cpu().numpy()
     launches_per_step = plan.batch_launches(nb)
@@ -407,15 +410,26 @@ def run_ours(args):
                          f"{nrings_total} ring syntheses) in {dt:.1f} s; full-map time "
                          "extrapolated by ring count"}
 
+        # error of both forms on a sample that includes the polar caps: every pixel of
+        # the first and last two rings, 8 pixels on each cap edge, belt edge and the
+        # equator, 16 random pixels (the oracle evaluates each pixel on its own)
+        import oracle.healpix as hp
+        import oracle.lens as OL
+        epix = hp.check_pixels(w.nside, seed=0, n_random=16, per_ring=8, cap_rings=2)
+        ref = OL.lens_at_pixels(w.nside, w.lmax, w.order, epix, sky["T"], sky.get("E"), sky.get("B"),
+                                sky["phi"], nthreads=cores)
+
         def errs(maps):
             o = {}
             for i, f in enumerate("TQU"):
                 r = ref[f]
-                dlt = maps[i][pix] - r
+                dlt = maps[i][epix] - r
                 o[f] = {"rel_rms": float(np.sqrt(np.mean(dlt ** 2) / np.mean(r ** 2))),
                         "max_rel": float(np.max(np.abs(dlt)) / np.sqrt(np.mean(r ** 2)))}
             return o
-        err = {args.form: errs(lensed), "npix": int(len(pix))}
+        err = {args.form: errs(lensed), "npix": int(len(epix)),
+               "sample": "every pixel of the first and last 2 rings; 8 on the cap edges, belt edges and "
+                         "equator; 16 random"}
         if lensed64 is not None:
             err["fp64"] = errs(lensed64)
 
@@ -437,6 +451,20 @@ def run_ours(args):
             "gpu_launches": args.steps * launches_per_step, "e2e": e2e, "fp64": fp64, "err_vs_oracle": err,
             "cpu_baseline": cpu,
         }
+        if world == 1 and not args.no_extra and args.workload == WORKLOAD:
+            # the batched (64 uneven realisations) and gradient workloads as sub-records,
+            # each with its own warm-up and timed steps, after this line's timed region
+            sub = argparse.Namespace(**vars(args))
+            sub.steps, sub.warmup, sub.no_e2e, sub.no_cpu_baseline = 3, 3, False, True
+            for key, fn in (("batched64", run_batched), ("adjoint", lambda a: run_adjoint(a, standalone=False))):
+                try:
+                    torch.cuda.empty_cache()
+                    rec = fn(sub)
+                    if rec is not None:
+                        rec.pop("metric", None)
+                    line[key] = rec
+                except Exception as exc:  # a failed extra never hides the headline
+                    line[key] = {"error": f"{type(exc).__name__}: {exc}"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -495,21 +523,20 @@ def run_batched(args):
         "graph_over_loop": ms_loop / ms, "clocks": clk.summary(),
     }
     b.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line if rank == 0 else None
 
 
 ADJ_WORKLOAD = "adjoint_nside1024_lmax2048_n4_TQU"
 ADJ_METRIC = "gradient evaluations/sec of L = sum (s' - s_target)^2 wrt alm_T,E,B,phi @Nside1024 lmax2048 order4"
 
 
-def run_adjoint(args):
+def run_adjoint(args, standalone=True):
     """One step = forward lens, loss gradient g = 2 (maps - targets), tl_lens_adjoint
     (which recomputes the derivative maps) for dL/dalm of T, E, B and phi. Targets are
     the lensed maps of an independent sky (seeds 9000..9002)."""
     import torch
     rank, world, local = dist_env()
-    if world > 1:
+    if world > 1 and standalone:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
@@ -563,7 +590,7 @@ def run_adjoint(args):
     if os.path.exists(PEAKS_FILE):
         with open(PEAKS_FILE) as f:
             peaks = json.load(f)
-    fp32_peak = FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak, fp32_src = fp32_peak_tflops(dev, peaks)
     dom = max(("gather_adj", "ringfft_adj", "legendre_T_adj", "legendre_QU_adj"), key=lambda k: stage_ms[k])
     if dom.startswith("legendre"):
         spin = 2 if dom == "legendre_QU_adj" else 0
@@ -571,7 +598,7 @@ def run_adjoint(args):
         ach = fl / (stage_ms[dom] / 1e3) / 1e12
         roof = {"kernel": f"legendre_adj{spin}_kernel<float, {w.order}>", "bound": "alu", "achieved": ach,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz",
+                "peak_source": fp32_src,
                 "counts": "recurrence + transposed contraction (same per-triple count as the forward)"}
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
@@ -628,9 +655,9 @@ def run_adjoint(args):
             "stage_ms": stage_ms, "roofline": roof, "clocks": clk.summary(),
             "gpu_launches": args.steps * 20, "e2e": e2e, "grad_norms": gnorm, "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
-    if world > 1:
+    if world > 1 and standalone:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 def main():
@@ -649,6 +676,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and gradient sub-records of the default line")
     args = ap.parse_args()
     args.form_given = args.form is not None
     if args.form is None:
@@ -656,9 +685,13 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64_n4_TQU":
-        run_batched(args)
+        line = run_batched(args)
+        if line:
+            print(json.dumps(line), flush=True)
     elif args.workload == ADJ_WORKLOAD:
-        run_adjoint(args)
+        line = run_adjoint(args)
+        if line:
+            print(json.dumps(line), flush=True)
     else:
         run_ours(args)
 

@@ -166,6 +166,20 @@ tl_status tl_lens_host(tl_plan *plan, const double *alm_T, const double *alm_E,
                        void *U_out, void *stream);
 
 /*
+ * tl_lens_batch with HOST buffers, the call a user with maps and coefficients in
+ * host memory makes: arrays (host) of nreal host pointers, layouts as in tl_lens.
+ * Each chunk of up to tl_plan_batch(plan) realisations (one Legendre launch on
+ * tensor-core plans) is copied to device staging owned by the plan (allocated on
+ * the first call and grown when a larger chunk is asked for), lensed with
+ * tl_lens_batch on `stream`, and its maps copied back; the call synchronises the
+ * stream before it returns. Host buffers should be pinned for full speed.
+ * Errors as tl_lens_batch, plus TL_ERR_CUDA if a staging allocation fails.
+ */
+tl_status tl_lens_batch_host(tl_plan *plan, int nreal, const double *const *alm_T, const double *const *alm_E,
+                             const double *const *alm_B, const double *const *alm_phi, void *const *T_out,
+                             void *const *Q_out, void *const *U_out, void *stream);
+
+/*
  * Reverse mode of tl_lens (the transpose of its linearisation): gradients of a
  * scalar loss with respect to the coefficients, given its gradients with
  * respect to the lensed maps. Naess & Louis 2013, Sec. II (Eq. 4 and the
@@ -211,11 +225,16 @@ tl_status tl_lens_adjoint(tl_plan *plan, const double *alm_T, const double *alm_
  * library (held by every GPU that loads it, until the process exits); no call
  * allocates device or host memory. The first call on a device, and any call
  * with a different (nside, lmax, precision) than the previous call on that
- * device, first lays the tables out in that array with synchronous copies and
- * kernels on the legacy default stream: make that first call before any stream
- * capture. Every call on a device shares the array and overwrites what the
- * previous call left there, so calls that overlap on the GPU (other streams,
- * other host threads) race; issue them one after another. Not thread-safe.
+ * device, first waits for all earlier work on the device (cudaDeviceSynchronize,
+ * so that kernels of earlier calls still queued on any stream have finished
+ * reading the array) and then lays the tables out in that array with
+ * synchronous copies and kernels on the legacy default stream: make that first
+ * call before any stream capture. A captured call stays valid only until a call
+ * with a different (nside, lmax, precision) is made on that device, which lays
+ * the array out again. Every call on a device shares the array and overwrites
+ * what the previous call left there, so calls that overlap on the GPU (other
+ * streams, other host threads) race; issue them one after another. Not
+ * thread-safe.
  */
 tl_status tl_deflection_noalloc(int nside, int lmax, int precision, const double *alm_phi,
                                 void *a_theta, void *a_phi, void *stream);

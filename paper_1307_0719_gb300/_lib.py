@@ -29,6 +29,7 @@ SIGNATURES = {
     "tl_lens": (ctypes.c_int, [_P] * 9),
     "tl_lens_host": (ctypes.c_int, [_P] * 9),
     "tl_lens_batch": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 8),
+    "tl_lens_batch_host": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 8),
     "tl_lens_adjoint": (ctypes.c_int, [_P] * 14),
     "tl_deflection_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "tl_batch_create": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,

@@ -150,6 +150,39 @@ class Plan:
                                       _stream(stream)), "tl_lens_host")
         return out
 
+    def lens_batch_host(self, skies, outs=None, stream=None):
+        """tl_lens_batch_host: several realisations from (pinned) host memory, maps back
+        in host memory. `skies`: list of dicts T, E, B, phi (CPU complex128 tensors);
+        returns a list of CPU [3 or 1, Npix] tensors of the plan's map dtype."""
+        n = len(skies)
+        nf = 3 if self.pol else 1
+
+        def h(t):
+            if t is None:
+                return None
+            if t.dtype == torch.complex128:
+                t = torch.view_as_real(t)
+            if t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64:
+                raise ValueError("host coefficients must be contiguous CPU complex128 tensors")
+            return t
+        if outs is None:
+            outs = [torch.empty((nf, self.npix), dtype=self.dtype, pin_memory=True) for _ in range(n)]
+        for o in outs:
+            if o.is_cuda or o.dtype != self.dtype or not o.is_contiguous():
+                raise ValueError("host outputs must be contiguous CPU tensors of the plan's dtype")
+        arr = lambda xs: (ctypes.c_void_p * n)(*[None if x is None else x.data_ptr() for x in xs])
+        keep = [{k: h(sk.get(k)) for k in ("T", "E", "B", "phi")} for sk in skies]
+        aT = arr([k["T"] for k in keep])
+        aE = arr([k["E"] for k in keep]) if self.pol else None
+        aB = arr([k["B"] for k in keep]) if self.pol else None
+        aP = arr([k["phi"] for k in keep])
+        To = arr([o[0] for o in outs])
+        Qo = arr([o[1] for o in outs]) if self.pol else None
+        Uo = arr([o[2] for o in outs]) if self.pol else None
+        check(_lib.lib().tl_lens_batch_host(self._h, n, aT, aE, aB, aP, To, Qo, Uo, _stream(stream)),
+              "tl_lens_batch_host")
+        return outs
+
     def lens_adjoint(self, alm_T, alm_E, alm_B, alm_phi, gT, gQ=None, gU=None, want=("T", "E", "B", "phi"),
                      galpha=False, stream=None):
         """tl_lens_adjoint: gradients (complex128 [nalm], dL/dRe + i dL/dIm) of the fields

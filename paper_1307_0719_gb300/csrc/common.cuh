@@ -94,8 +94,9 @@ struct tl_plan {
   void *alpha;         // [2][npix] (T)
   void *adj_dbar;      // adjoint: gradients of the derivative maps, as d3 (allocated on first use)
   void *adj_ga;        // adjoint: [2][npix] deflection gradients (allocated on first use)
-  void *stage_alm;     // host-path staging: 4 * nalm complex128
-  void *stage_out;     // host-path staging: 3 * npix (T)
+  void *stage_alm;     // host-path staging: stage_cap x 4 x nalm complex128
+  void *stage_out;     // host-path staging: stage_cap x 3 x npix (T)
+  int stage_cap;       // realisations the staging holds (0: none yet)
   size_t bytes;
   // optional stage timing
   int timing;

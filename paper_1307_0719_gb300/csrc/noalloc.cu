@@ -54,6 +54,10 @@ tl_status fail(cudaError_t e) { return e == cudaSuccess ? TL_OK : TL_ERR_CUDA; }
 
 // Lay the tables and the working memory out in the scratch array and fill them.
 tl_status setup(DevState &st, int nside, int lmax, int precision) {
+  // Earlier calls may still be running on the caller's stream, which need not
+  // synchronise with the copies below (a non-blocking stream does not): wait for
+  // the whole device before the array is laid out again. Allocates nothing.
+  if (cudaDeviceSynchronize() != cudaSuccess) return TL_ERR_CUDA;
   st.nside = 0;  // invalid until complete
   tl_plan &p = st.plan;
   memset(&p, 0, sizeof(p));

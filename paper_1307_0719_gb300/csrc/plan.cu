@@ -703,33 +703,87 @@ extern "C" tl_status tl_lens_adjoint(tl_plan *p, const double *alm_T, const doub
   return TL_OK;
 }
 
+extern "C" tl_status tl_lens_batch_host(tl_plan *p, int nreal, const double *const *alm_T,
+                                        const double *const *alm_E, const double *const *alm_B,
+                                        const double *const *alm_phi, void *const *T_out, void *const *Q_out,
+                                        void *const *U_out, void *stream) {
+  if (!p || nreal < 0 || (nreal > 0 && (!alm_T || !T_out))) return TL_ERR_ARG;
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
+  if (pol && nreal > 0 && (!alm_E || !Q_out || !U_out)) return TL_ERR_ARG;
+  for (int r = 0; r < nreal; ++r) {
+    if (!alm_T[r] || !T_out[r]) return TL_ERR_ARG;
+    if (pol && (!alm_E[r] || !Q_out[r] || !U_out[r])) return TL_ERR_ARG;
+    if ((alm_phi && alm_phi[r]) != (alm_phi && alm_phi[0])) return TL_ERR_ARG;  // all lensed, or none
+  }
+  if (nreal == 0) return TL_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long na = nalm(p->lmax);
+  const size_t ab = (size_t)na * 16, mapb = (size_t)p->elem * p->npix;
+  // device staging for one chunk of up to p->batch realisations (one Legendre launch
+  // on tensor-core plans), grown on demand and kept by the plan
+  const int cap = nreal < p->batch ? nreal : p->batch;
+  if (cap > p->stage_cap) {
+    if (p->stage_alm || p->stage_out) TRY_CUDA(cudaStreamSynchronize(s));
+    if (p->stage_alm) {
+      cudaFree(p->stage_alm);
+      p->bytes -= 4 * ab * (size_t)p->stage_cap;
+      p->stage_alm = nullptr;
+    }
+    if (p->stage_out) {
+      cudaFree(p->stage_out);
+      p->bytes -= 3 * mapb * (size_t)p->stage_cap;
+      p->stage_out = nullptr;
+    }
+    p->stage_cap = 0;
+    TRY_CUDA(dalloc(&p->stage_alm, 4 * ab * (size_t)cap, &p->bytes));
+    TRY_CUDA(dalloc(&p->stage_out, 3 * mapb * (size_t)cap, &p->bytes));
+    p->stage_cap = cap;
+  }
+  const bool phi = alm_phi && alm_phi[0];
+  for (int r0 = 0; r0 < nreal; r0 += cap) {
+    const int n = (nreal - r0) < cap ? (nreal - r0) : cap;
+    const double *dT[TL_MAX_BATCH], *dE[TL_MAX_BATCH], *dB[TL_MAX_BATCH], *dP[TL_MAX_BATCH];
+    void *oT[TL_MAX_BATCH], *oQ[TL_MAX_BATCH], *oU[TL_MAX_BATCH];
+    for (int i = 0; i < n; ++i) {
+      const int r = r0 + i;
+      char *a = (char *)p->stage_alm + 4 * ab * (size_t)i;
+      char *o = (char *)p->stage_out + 3 * mapb * (size_t)i;
+      dT[i] = (const double *)a;
+      dE[i] = pol ? (const double *)(a + ab) : nullptr;
+      dB[i] = (pol && alm_B && alm_B[r]) ? (const double *)(a + 2 * ab) : nullptr;
+      dP[i] = phi ? (const double *)(a + 3 * ab) : nullptr;
+      oT[i] = o;
+      oQ[i] = pol ? o + mapb : nullptr;
+      oU[i] = pol ? o + 2 * mapb : nullptr;
+      TRY_CUDA(cudaMemcpyAsync((void *)dT[i], alm_T[r], ab, cudaMemcpyHostToDevice, s));
+      if (dE[i]) TRY_CUDA(cudaMemcpyAsync((void *)dE[i], alm_E[r], ab, cudaMemcpyHostToDevice, s));
+      if (dB[i]) TRY_CUDA(cudaMemcpyAsync((void *)dB[i], alm_B[r], ab, cudaMemcpyHostToDevice, s));
+      if (dP[i]) TRY_CUDA(cudaMemcpyAsync((void *)dP[i], alm_phi[r], ab, cudaMemcpyHostToDevice, s));
+    }
+    tl_status st = tl_lens_batch(p, n, dT, pol ? dE : nullptr, pol ? dB : nullptr, dP, oT, pol ? oQ : nullptr,
+                                 pol ? oU : nullptr, stream);
+    if (st != TL_OK) return st;
+    for (int i = 0; i < n; ++i) {
+      const int r = r0 + i;
+      TRY_CUDA(cudaMemcpyAsync(T_out[r], oT[i], mapb, cudaMemcpyDeviceToHost, s));
+      if (pol) {
+        TRY_CUDA(cudaMemcpyAsync(Q_out[r], oQ[i], mapb, cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaMemcpyAsync(U_out[r], oU[i], mapb, cudaMemcpyDeviceToHost, s));
+      }
+    }
+  }
+  TRY_CUDA(cudaStreamSynchronize(s));
+  return TL_OK;
+}
+
 extern "C" tl_status tl_lens_host(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,
                                   const double *alm_phi, void *T_out, void *Q_out, void *U_out, void *stream) {
   if (!p || !alm_T || !T_out) return TL_ERR_ARG;
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
   if (pol && (!alm_E || !Q_out || !U_out)) return TL_ERR_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  const long long na = nalm(p->lmax);
-  const size_t ab = (size_t)na * 16, mapb = (size_t)p->elem * p->npix;
-  if (!p->stage_alm) TRY_CUDA(dalloc(&p->stage_alm, 4 * ab, &p->bytes));
-  if (!p->stage_out) TRY_CUDA(dalloc(&p->stage_out, 3 * mapb, &p->bytes));
-  char *a = (char *)p->stage_alm;
-  double *dT = (double *)a, *dE = (double *)(a + ab), *dB = (double *)(a + 2 * ab), *dP = (double *)(a + 3 * ab);
-  TRY_CUDA(cudaMemcpyAsync(dT, alm_T, ab, cudaMemcpyHostToDevice, s));
-  if (pol) TRY_CUDA(cudaMemcpyAsync(dE, alm_E, ab, cudaMemcpyHostToDevice, s));
-  if (pol && alm_B) TRY_CUDA(cudaMemcpyAsync(dB, alm_B, ab, cudaMemcpyHostToDevice, s));
-  if (alm_phi) TRY_CUDA(cudaMemcpyAsync(dP, alm_phi, ab, cudaMemcpyHostToDevice, s));
-  char *o = (char *)p->stage_out;
-  tl_status st = tl_lens(p, dT, pol ? dE : nullptr, (pol && alm_B) ? dB : nullptr, alm_phi ? dP : nullptr, o,
-                         pol ? o + mapb : nullptr, pol ? o + 2 * mapb : nullptr, stream);
-  if (st != TL_OK) return st;
-  TRY_CUDA(cudaMemcpyAsync(T_out, o, mapb, cudaMemcpyDeviceToHost, s));
-  if (pol) {
-    TRY_CUDA(cudaMemcpyAsync(Q_out, o + mapb, mapb, cudaMemcpyDeviceToHost, s));
-    TRY_CUDA(cudaMemcpyAsync(U_out, o + 2 * mapb, mapb, cudaMemcpyDeviceToHost, s));
-  }
-  TRY_CUDA(cudaStreamSynchronize(s));
-  return TL_OK;
+  const double *aT[1] = {alm_T}, *aE[1] = {alm_E}, *aB[1] = {alm_B}, *aP[1] = {alm_phi};
+  void *To[1] = {T_out}, *Qo[1] = {Q_out}, *Uo[1] = {U_out};
+  return tl_lens_batch_host(p, 1, aT, aE, aB, aP, To, Qo, Uo, stream);
 }
 
 extern "C" int tl_last_stage_ms(const tl_plan *p, float *ms, int n) {

@@ -178,3 +178,60 @@ def test_adjoint_rejects_bad_arguments():
                            None, None, None)
     assert st == _lib.TL_ERR_ARG
     plan.close()
+
+
+def test_adjoint_nside1024_central_differences():
+    """Differentiation workload (Nside 1024, lmax 2048, order 4, T+Q/U): the FP64
+    tl_lens_adjoint gradient of L = sum (s' - s_target)^2 against central differences
+    of the FP64 forward on 32 random coefficients (8 each of T, E, B, phi; real or
+    imaginary part), step 1e-6 of the entry. The loss difference is formed per pixel,
+    sum (s'+ - s'-)(s'+ + s'- - 2 s_target), so that the step is not lost in the
+    rounding of a sum of squares of order 1e11. The phi entries move the deflection,
+    and a point that crosses a pixel boundary changes its expansion pixel (the map is
+    piecewise smooth in phi; the adjoint holds q fixed): with this step a handful of
+    the 12.6 M pixels cross, each changing L by far less than the phi gradient times
+    the step, hence the 1e-3 relative tolerance for every entry."""
+    import skygen
+    w = skygen.WORKLOADS["nside1024_lmax2048_n4_TQU"]
+    s = skygen.make_sky(w.nside, w.lmax, True, w.seed_t, w.seed_e, w.seed_phi, w.damp_t, w.damp_e)
+    t = skygen.make_sky(w.nside, w.lmax, True, 9000, 9001, 9002, w.damp_t, w.damp_e)
+    d, dt = to_dev(s), to_dev(t)
+    plan = api.Plan(w.nside, w.lmax, w.order, pol=True, precision=api.FP64)
+    try:
+        target = plan.lens(dt["T"], dt["E"], dt["B"], dt["phi"]).clone()
+        out = plan.lens(d["T"], d["E"], d["B"], d["phi"]).clone()
+        g = 2.0 * (out - target)
+        gr = plan.lens_adjoint(d["T"], d["E"], d["B"], d["phi"], g[0].contiguous(), g[1].contiguous(),
+                               g[2].contiguous())
+        gr = {k: v.cpu().numpy() for k, v in gr.items()}
+        rng = np.random.default_rng(4)
+        lmax = w.lmax
+        checks = []
+        for f, lhi in (("T", 300), ("E", 300), ("B", 300), ("phi", 100)):
+            n = 0
+            while n < 8:
+                l = int(rng.integers(2, lhi))
+                m = int(rng.integers(0, l + 1))
+                idx = m * (2 * lmax + 1 - m) // 2 + l
+                # B = 0 in this workload: its step takes the scale of E at the same (l, m)
+                scale = abs(complex(s[f][idx])) if f != "B" else abs(complex(s["E"][idx]))
+                if scale == 0.0:
+                    continue
+                part = "re" if (m == 0 or rng.random() < 0.5) else "im"
+                h = 1e-6 * scale
+                pm = []
+                for sgn in (1.0, -1.0):
+                    dd = dict(d)
+                    v = dd[f].clone()
+                    v[idx] += sgn * h * (1.0 if part == "re" else 1j)
+                    dd[f] = v
+                    pm.append(plan.lens(dd["T"], dd["E"], dd["B"], dd["phi"]).clone())
+                fd = float(((pm[0] - pm[1]) * (pm[0] + pm[1] - 2.0 * target)).sum()) / (2.0 * h)
+                ana = gr[f][idx].real if part == "re" else gr[f][idx].imag
+                checks.append((f, l, m, part, fd, ana))
+                n += 1
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    for f, l, m, part, fd, ana in checks:
+        assert abs(fd - ana) <= 1e-3 * abs(ana), (f, l, m, part, fd, ana)

@@ -132,6 +132,29 @@ def test_lens_batch_equals_single_calls(precision, order):
             assert rel_rms(o[i], s1[i]) <= tol
 
 
+@pytest.mark.parametrize("precision", [api.MIXED_BF16x3, api.FP64])
+def test_lens_batch_host_equals_device_call(precision):
+    """tl_lens_batch_host (host buffers, copies inside the call) over 18 realisations,
+    i.e. a full chunk of tl_plan_batch and a partial one, gives exactly the maps of
+    tl_lens_batch on device buffers; a second, smaller call reuses the staging."""
+    nside, lmax, order = 32, 64, 4
+    host = [{k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in
+             sky(nside, lmax, pol=True, seeds=(80 + i, 90 + i, 100 + i), b_scale=0.3).items()} for i in range(18)]
+    plan = api.Plan(nside, lmax, order, pol=True, precision=precision)
+    try:
+        dev = [{k: v.cuda() for k, v in h.items()} for h in host]
+        ref = [o.cpu().numpy() for o in plan.lens_batch(dev)]
+        got = [o.numpy() for o in plan.lens_batch_host(host)]
+        got2 = [o.numpy() for o in plan.lens_batch_host(host[:3])]
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    for r, g in zip(ref, got):
+        assert np.array_equal(r, g)
+    for r, g in zip(ref[:3], got2):
+        assert np.array_equal(r, g)
+
+
 def test_plan_batch_and_launch_count():
     """tl_plan_batch: 16 realisations per Legendre launch on the tensor-core forms up to
     order 5, 8 at order 6, 1 otherwise; tl_plan_batch_launches matches the kernels a
@@ -162,3 +185,27 @@ def test_plan_batch_and_launch_count():
     finally:
         torch.cuda.synchronize()
         plan.close()
+
+
+def test_fp64_nside512_lmax1024_order4_vs_oracle_and_reruns():
+    """The plain FP64 form at Nside 512, lmax 1024, order 4, T+Q/U (Sec. II, Eq. 4,
+    R of Eq. 2): within 1e-6 of the oracle at every pixel of the cap-inclusive sample
+    (relative to the map's RMS over the sample), and bit-for-bit equal over reruns."""
+    import skygen
+    w = skygen.WORKLOADS["nside512_lmax1024_n4_TQU"]
+    s = skygen.make_sky(w.nside, w.lmax, w.pol, w.seed_t, w.seed_e, w.seed_phi, w.damp_t, w.damp_e)
+    d = to_dev(s)
+    plan = api.Plan(w.nside, w.lmax, w.order, pol=True, precision=api.FP64)
+    try:
+        runs = [plan.lens(d["T"], d["E"], d["B"], d["phi"]).cpu().numpy() for _ in range(3)]
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    for r in runs[1:]:
+        assert np.array_equal(r, runs[0])
+    pix = hp.check_pixels(w.nside)
+    ref = OL.lens_at_pixels(w.nside, w.lmax, w.order, pix, s["T"], s["E"], s["B"], s["phi"])
+    for i, f in enumerate("TQU"):
+        got = runs[0][i][pix]
+        assert rel_rms(got, ref[f]) < 1e-6 and max_rel(got, ref[f]) < 1e-6, (f, rel_rms(got, ref[f]),
+                                                                              max_rel(got, ref[f]))

@@ -224,3 +224,44 @@ def test_deflection_quantile_matches_paper():
     a_th, a_ph = L.deflection(256, 512, sky["phi"])
     q99 = np.quantile(np.hypot(a_th, a_ph), 0.99) / skygen.ARCMIN
     assert 4.8 < q99 < 5.9, q99
+
+
+def test_deflection_closed_forms_Y10_Y11():
+    """alpha = (d_theta phi, d_phi phi / sin theta) (Sec. I) for phi = Y_10 and
+    phi = 2 Re[a Y_11]: with Y_10 = sqrt(3/4pi) cos th and Y_11 = -sqrt(3/8pi) sin th
+    e^{i ph}, alpha_theta = -sqrt(3/4pi) sin th, alpha_phi = 0, and for a = ar + i ai
+    alpha_theta = -sqrt(3/2pi) cos th (ar cos ph - ai sin ph),
+    alpha_phi = sqrt(3/2pi) (ar sin ph + ai cos ph): smooth, so a dropped or doubled
+    1/sin theta shows at every ring."""
+    nside, lmax = 8, 4
+    th, ph = hp.pix2ang(nside, np.arange(hp.npix(nside)))
+    a_th, a_ph = L.deflection(nside, lmax, _single_mode(lmax, 1, 0, 1.0))
+    assert np.allclose(a_th, -np.sqrt(3 / (4 * np.pi)) * np.sin(th), atol=1e-13, rtol=0)
+    assert np.abs(a_ph).max() < 1e-13
+    ar, ai = 0.8, -0.35
+    a_th, a_ph = L.deflection(nside, lmax, _single_mode(lmax, 1, 1, ar + 1j * ai))
+    c = np.sqrt(3 / (2 * np.pi))
+    assert np.allclose(a_th, -c * np.cos(th) * (ar * np.cos(ph) - ai * np.sin(ph)), atol=1e-13, rtol=0)
+    assert np.allclose(a_ph, c * (ar * np.sin(ph) + ai * np.cos(ph)), atol=1e-13, rtol=0)
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3, 4, 5, 6])
+def test_lens_equals_sampled_evaluator(order):
+    """The whole-map oracle (derivative maps by ring FFTs, deflection maps, the
+    gather at q of every pixel) against the sampled evaluator, which takes every
+    step by direct sums at the points themselves (the deflection on the pixel's
+    ring, the derivative values at q from direct Fourier sums); the latter is pinned
+    to brute-force Y_lm sums by test_convergence_to_brute_force. phi is scaled up so
+    that the deflections move most points out of their own pixel."""
+    nside, lmax = 16, 40
+    sky = skygen.make_sky(nside, lmax, True, 0, 3, 1, b_scale=0.4)
+    phi = sky["phi"] * 200.0
+    full = L.lens(nside, lmax, order, sky["T"], sky["E"], sky["B"], phi, return_aux=True)
+    moved = np.mean(full["aux"]["q"] != np.arange(hp.npix(nside)))
+    assert moved > 0.5, moved
+    pix = np.arange(hp.npix(nside))
+    samp = L.lens_at_pixels(nside, lmax, order, pix, sky["T"], sky["E"], sky["B"], phi)
+    assert np.array_equal(samp["aux"]["q"], full["aux"]["q"])
+    for f in "TQU":
+        scale = np.sqrt(np.mean(full[f] ** 2))
+        assert np.abs(samp[f] - full[f]).max() < 1e-12 * scale, (f, np.abs(samp[f] - full[f]).max() / scale)

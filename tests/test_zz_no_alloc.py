@@ -58,3 +58,34 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     p = ctypes.c_void_p(z.data_ptr())
     assert L.tl_deflection_noalloc(256, 256, _lib.TL_FP64, p, p, p, None) == _lib.TL_ERR_ARG
     assert L.tl_deflection_noalloc(128, 300, _lib.TL_FP64, p, p, p, None) == _lib.TL_ERR_ARG
+
+
+def test_noalloc_size_change_queued_behind_earlier_call_on_nonblocking_stream():
+    """Two calls of different sizes queued on one non-blocking stream with no
+    synchronisation between them: the second call lays the array out again and
+    must first wait for the first call's kernels, which still read it."""
+    sizes = [(32, 64), (128, 256)]
+    refs, ins = [], []
+    for nside, lmax in sizes:
+        plan = api.Plan(nside, lmax, 1, pol=False, precision=_lib.TL_FP64)
+        try:
+            s = to_dev(sky(nside, lmax, pol=False, seeds=(0, 0, 21)))
+            refs.append(plan.deflection(s["phi"]).cpu().numpy())
+            ins.append(torch.view_as_real(s["phi"]))
+        finally:
+            torch.cuda.synchronize()
+            plan.close()
+    outs = [torch.empty((2, 12 * n * n), dtype=torch.float64, device="cuda") for n, _ in sizes]
+    stream = torch.cuda.Stream()  # torch's pooled streams are non-blocking
+    torch.cuda.synchronize()
+    L = _lib.lib()
+    for (nside, lmax), a, o in zip(sizes, ins, outs):
+        st = L.tl_deflection_noalloc(nside, lmax, _lib.TL_FP64, ctypes.c_void_p(a.data_ptr()),
+                                     ctypes.c_void_p(o[0].data_ptr()), ctypes.c_void_p(o[1].data_ptr()),
+                                     ctypes.c_void_p(stream.cuda_stream))
+        _lib.check(st, "tl_deflection_noalloc")
+    stream.synchronize()
+    for ref, o in zip(refs, outs):
+        got = o.cpu().numpy()
+        for i in range(2):
+            assert rel_rms(got[i], ref[i]) < 1e-12, (i, rel_rms(got[i], ref[i]))
