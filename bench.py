@@ -660,6 +660,53 @@ def run_adjoint(args, standalone=True):
     return line if rank == 0 else None
 
 
+def run_sweep(args):
+    """Error table of the full-size workload (Nside 2048, lmax 4096, T+Q/U) at orders
+    2..6 for every precision form against the FP64 oracle, on a pixel sample that
+    holds every pixel of the first and last two rings, 8 pixels on the cap and belt
+    edges and the equator and 16 random ones: per map (T, Q, U) the relative RMS
+    over the sample and the largest error relative to the sample's RMS. Prints one
+    JSON line (not a throughput record)."""
+    import torch
+    import oracle.healpix as hp
+    import oracle.lens as OL
+    from paper_1307_0719_gb300 import api
+    w = skygen.WORKLOADS[WORKLOAD]
+    dev = torch.device("cuda", 0)
+    sky = skygen.workload_sky(WORKLOAD)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in sky.items()}
+    pix = hp.check_pixels(w.nside, seed=0, n_random=16, per_ring=8, cap_rings=2)
+    forms = [("fp64", api.FP64), ("fp32", api.MIXED_FP32), ("tf32", api.MIXED_TF32), ("tf32x3", api.MIXED_TF32x3),
+             ("bf16x3", api.MIXED_BF16x3)]
+    orders = [int(x) for x in args.sweep_orders.split(",")]
+    table = {}
+    cores = os.cpu_count() or 1
+    for n in orders:
+        ref = OL.lens_at_pixels(w.nside, w.lmax, n, pix, sky["T"], sky["E"], sky["B"], sky["phi"], nthreads=cores)
+        row = {}
+        for name, prec in forms:
+            plan = api.Plan(w.nside, w.lmax, n, pol=True, precision=prec)
+            try:
+                out = plan.lens(d["T"], d["E"], d["B"], d["phi"]).double().cpu().numpy()
+            finally:
+                torch.cuda.synchronize()
+                plan.close()
+            torch.cuda.empty_cache()
+            e = {}
+            for i, f in enumerate("TQU"):
+                r = ref[f]
+                dlt = out[i][pix] - r
+                rms = np.sqrt(np.mean(r ** 2))
+                e[f] = {"rel_rms": float(np.sqrt(np.mean(dlt ** 2)) / rms), "max_rel": float(np.max(np.abs(dlt)) / rms)}
+            row[name] = e
+            print(json.dumps({"order": n, "form": name, "err": e}), file=sys.stderr, flush=True)
+        table[str(n)] = row
+    print(json.dumps({"sweep": "error vs FP64 oracle", "workload": WORKLOAD, "npix_sample": int(len(pix)),
+                      "sample": "every pixel of the first and last 2 rings; 8 on the cap edges, belt edges and "
+                                "equator; 16 random",
+                      "errors": table}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -676,13 +723,18 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-errors", action="store_true",
+                    help="print the error table of the full-size workload per order and form, then exit")
+    ap.add_argument("--sweep-orders", default="2,3,4,5,6")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and gradient sub-records of the default line")
     args = ap.parse_args()
     args.form_given = args.form is not None
     if args.form is None:
         args.form = "bf16x3"
-    if args.impl == "reference":
+    if args.sweep_errors:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64_n4_TQU":
         line = run_batched(args)

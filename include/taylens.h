@@ -70,8 +70,19 @@ enum { TL_SPIN_T = 1, TL_SPIN_QU = 2 };
  * tl_synth_derivs and tl_deflection use the float (SIMT) stage in all mixed forms. */
 enum { TL_FP64 = 0, TL_MIXED_FP32 = 1, TL_MIXED_TF32 = 2, TL_MIXED_TF32x3 = 3, TL_MIXED_BF16x3 = 4 };
 
-/* `flags` */
-enum { TL_ROTATE = 1 /* apply the polarisation rotation R of Eq. 2 (default on) */ };
+/* `flags`
+ *   TL_ROTATE          apply the polarisation rotation R of Eq. 2 (default on).
+ *   TL_NAIVE           the displaced position by naive coordinate addition,
+ *                      theta' = theta + alpha_theta, phi' = phi + alpha_phi / sin theta
+ *                      (Sec. II.A's alternative to parallel transport; a point carried
+ *                      past a pole continues on the other side), instead of the end of
+ *                      the geodesic from x along alpha. R keeps the geodesic angle.
+ *   TL_EXPAND_AT_PIXEL the Taylor series about the output pixel itself (Sec. I, Eq. 3a:
+ *                      the plain expansion about the undisplaced point, the paper's
+ *                      motivating comparison) instead of about the centre of the pixel
+ *                      containing x' (Sec. II.B).
+ * tl_lens_adjoint supports TL_ROTATE only (TL_ERR_UNSUPPORTED otherwise). */
+enum { TL_ROTATE = 1, TL_NAIVE = 2, TL_EXPAND_AT_PIXEL = 4 };
 
 /*
  * Create a plan for one (nside, lmax, order) geometry.
@@ -81,7 +92,7 @@ enum { TL_ROTATE = 1 /* apply the polarisation rotation R of Eq. 2 (default on) 
  *   spins     TL_SPIN_T, TL_SPIN_QU or both
  *   precision TL_FP64, TL_MIXED_FP32, TL_MIXED_TF32, TL_MIXED_TF32x3 or
  *             TL_MIXED_BF16x3
- *   flags     TL_ROTATE or 0
+ *   flags     any of TL_ROTATE, TL_NAIVE, TL_EXPAND_AT_PIXEL
  *   out       receives the plan; unchanged on error
  * Allocates the plan's device tables and workspace on the current device.
  * Errors: TL_ERR_ARG, TL_ERR_UNSUPPORTED, TL_ERR_NOMEM, TL_ERR_CUDA.
@@ -282,6 +293,18 @@ int tl_batch_grid(const tl_batch *batch);   /* persistent grid size in use */
  * outputs are then undefined. TL_ERR_CUDA if the device reports an error.
  */
 tl_status tl_plan_device_error(tl_plan *plan);
+
+/*
+ * Limit of the bounded waits of the tensor-core kernels (the paper has no
+ * counterpart: a control of this implementation's pipeline). Every mbarrier wait
+ * of a later launch of this plan polls at most `polls` times (0 restores the
+ * default, 2^24) before it gives up as tl_plan_device_error describes. stall = 1
+ * is a self-test of that path: the compute warps withhold their arrivals on the
+ * tile barriers, so the waits of the next launches run out (nothing faults or
+ * hangs: every wait is bounded) and their outputs are undefined; stall = 0
+ * restores normal operation. TL_ERR_ARG for polls < 0 or stall not 0 or 1.
+ */
+tl_status tl_plan_set_wait_limit(tl_plan *plan, int polls, int stall);
 
 /* Human-readable text for a status code (static storage). */
 const char *tl_status_string(tl_status status);

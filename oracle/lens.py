@@ -144,6 +144,53 @@ def wrap_pi(x):
     return np.mod(x + np.pi, 2.0 * np.pi) - np.pi
 
 
+def target_point(theta, z, s, phi, a_th, a_ph, naive=False):
+    """The displaced position x' of Sec. II.A and the geodesic pieces R uses.
+
+    Default: the end of the geodesic of length |alpha| leaving x along alpha.
+    naive=True: the paper's alternative, coordinate addition theta' = theta + a_theta,
+    phi' = phi + a_phi / sin(theta); a point carried past a pole continues on the
+    other side (theta' -> -theta' or 2 pi - theta', phi' -> phi' + pi). The
+    rotation R keeps the geodesic transport angle in both cases (beta at the geodesic
+    end point). d = 0 returns x exactly. Returns theta', phi', z', sin(theta') and the
+    pieces of R: (n, u, e_theta, d, theta_g, phi_g), (theta_g, phi_g) the geodesic end."""
+    n2, u, n, et, d = displace(z, s, phi, a_th, a_ph)
+    still = d == 0
+    theta_g = np.where(still, theta, np.arctan2(np.hypot(n2[:, 0], n2[:, 1]), n2[:, 2]))
+    phi_g = np.where(still, phi, np.mod(np.arctan2(n2[:, 1], n2[:, 0]), 2.0 * np.pi))
+    if naive:
+        theta2 = theta + a_th
+        with np.errstate(divide="ignore", invalid="ignore"):
+            phi2 = phi + np.where(s > 0, a_ph / np.where(s > 0, s, 1.0), 0.0)
+        north, south = theta2 < 0.0, theta2 > np.pi
+        theta2 = np.where(north, -theta2, np.where(south, 2.0 * np.pi - theta2, theta2))
+        phi2 = np.mod(np.where(north | south, phi2 + np.pi, phi2), 2.0 * np.pi)
+        z2, s2 = np.cos(theta2), np.sin(theta2)
+    else:
+        z2 = np.clip(n2[:, 2], -1.0, 1.0)
+        s2 = np.hypot(n2[:, 0], n2[:, 1])
+        theta2 = np.arctan2(s2, n2[:, 2])
+        phi2 = np.mod(np.arctan2(n2[:, 1], n2[:, 0]), 2.0 * np.pi)
+    theta2 = np.where(still, theta, theta2)
+    phi2 = np.where(still, phi, phi2)
+    z2 = np.where(still, z, z2)
+    s2 = np.where(still, s, s2)
+    return theta2, phi2, z2, s2, (n, u, et, d, theta_g, phi_g)
+
+
+def expansion_point(nside, pix, theta2, phi2, z2, s2, theta_p, phi_p, at_pixel=False):
+    """The expansion pixel q and the offsets (dth, dph) of Eq. 4: by default q is the
+    pixel containing x' (Sec. II.B); at_pixel=True expands about the output pixel
+    itself, q = p, the plain Taylor series about the undisplaced point of Sec. I
+    (Eq. 3a). dph is wrapped into [-pi, pi)."""
+    if at_pixel:
+        q = np.asarray(pix, dtype=np.int64)
+        return q, theta2 - theta_p, wrap_pi(phi2 - phi_p)
+    q = hp.ang2pix(nside, z2, s2, phi2)
+    th_q, ph_q = hp.pix2ang(nside, q)
+    return q, theta2 - th_q, wrap_pi(phi2 - ph_q)
+
+
 # ---------------------------------------------------------------------------
 
 def taylor_sum(D_at_q: np.ndarray, dth, dph, order: int):
@@ -158,8 +205,10 @@ def taylor_sum(D_at_q: np.ndarray, dth, dph, order: int):
 
 
 def lens(nside: int, lmax: int, order: int, alm_T, alm_E=None, alm_B=None, alm_phi=None,
-         rotate: bool = True, nthreads=None, return_aux: bool = False):
-    """Lensed T (and Q, U) maps in RING order, FP64."""
+         rotate: bool = True, nthreads=None, return_aux: bool = False, naive: bool = False,
+         at_pixel: bool = False):
+    """Lensed T (and Q, U) maps in RING order, FP64 (naive, at_pixel: see target_point
+    and expansion_point)."""
     tab = hp.ring_table(nside)
     npx = hp.npix(nside)
     pix = np.arange(npx)
@@ -173,23 +222,12 @@ def lens(nside: int, lmax: int, order: int, alm_T, alm_E=None, alm_B=None, alm_p
         a_ph = np.zeros(npx)
     else:
         a_th, a_ph = deflection(nside, lmax, alm_phi, nthreads=nthreads)
-    # 2. displaced position
-    n2, u, n, et, d = displace(z, s, phi, a_th, a_ph)
-    z2 = np.clip(n2[:, 2], -1.0, 1.0)
-    s2 = np.hypot(n2[:, 0], n2[:, 1])
-    theta2 = np.arctan2(s2, n2[:, 2])
-    phi2 = np.mod(np.arctan2(n2[:, 1], n2[:, 0]), 2.0 * np.pi)
-    # zero displacement: x' = x exactly
+    # 2. displaced position (zero displacement: x' = x exactly)
+    theta_p = tab["theta"][ring - 1]
+    theta2, phi2, z2, s2, (n, u, et, d, theta_g, phi_g) = target_point(theta_p, z, s, phi, a_th, a_ph, naive)
     still = d == 0
-    theta2 = np.where(still, tab["theta"][ring - 1], theta2)
-    phi2 = np.where(still, phi, phi2)
-    z2 = np.where(still, z, z2)
-    s2 = np.where(still, s, s2)
     # 3. expansion point
-    q = hp.ang2pix(nside, z2, s2, phi2)
-    th_q, ph_q = hp.pix2ang(nside, q)
-    dth = theta2 - th_q
-    dph = wrap_pi(phi2 - ph_q)
+    q, dth, dph = expansion_point(nside, pix, theta2, phi2, z2, s2, theta_p, phi, at_pixel)
     # 4. derivative maps
     maps = derivative_maps(nside, lmax, order, alm_T, alm_E, alm_B, nthreads=nthreads)
     # 5. Taylor sum
@@ -197,7 +235,7 @@ def lens(nside: int, lmax: int, order: int, alm_T, alm_E=None, alm_B=None, alm_p
     # 6. rotation
     beta = np.zeros(npx)
     if "Q" in out and rotate:
-        beta = np.where(still, 0.0, transport_angle(n, u, et, d, theta2, phi2))
+        beta = np.where(still, 0.0, transport_angle(n, u, et, d, theta_g, phi_g))
         P = (out["Q"] + 1j * out["U"]) * np.exp(-2j * beta)
         out["Q"], out["U"] = P.real, P.imag
     if return_aux:
@@ -254,7 +292,8 @@ def deflection_at(lmax, alm_phi, theta, phi, sint, nthreads=None):
 
 
 def lens_at_pixels(nside: int, lmax: int, order: int, pix, alm_T, alm_E=None, alm_B=None,
-                   alm_phi=None, rotate: bool = True, nthreads=None):
+                   alm_phi=None, rotate: bool = True, nthreads=None, naive: bool = False,
+                   at_pixel: bool = False):
     """The same algorithm as `lens`, evaluated only at the given output pixels:
     derivative values at each expansion pixel come from direct Fourier sums
     instead of ring FFTs (used for sampled checks at full size)."""
@@ -265,20 +304,11 @@ def lens_at_pixels(nside: int, lmax: int, order: int, pix, alm_T, alm_E=None, al
     s = tab["sint"][ring - 1]
     phi = tab["phi0"][ring - 1] + 2.0 * np.pi * jidx / tab["nphi"][ring - 1]
     a_th, a_ph = deflection_at(lmax, alm_phi, tab["theta"][ring - 1], phi, s, nthreads)
-    n2, u, n, et, d = displace(z, s, phi, a_th, a_ph)
-    z2 = np.clip(n2[:, 2], -1.0, 1.0)
-    s2 = np.hypot(n2[:, 0], n2[:, 1])
-    theta2 = np.arctan2(s2, n2[:, 2])
-    phi2 = np.mod(np.arctan2(n2[:, 1], n2[:, 0]), 2.0 * np.pi)
+    theta_p = tab["theta"][ring - 1]
+    theta2, phi2, z2, s2, (n, u, et, d, theta_g, phi_g) = target_point(theta_p, z, s, phi, a_th, a_ph, naive)
     still = d == 0
-    theta2 = np.where(still, tab["theta"][ring - 1], theta2)
-    phi2 = np.where(still, phi, phi2)
-    z2 = np.where(still, z, z2)
-    s2 = np.where(still, s, s2)
-    q = hp.ang2pix(nside, z2, s2, phi2)
+    q, dth, dph = expansion_point(nside, pix, theta2, phi2, z2, s2, theta_p, phi, at_pixel)
     th_q, ph_q = hp.pix2ang(nside, q)
-    dth = theta2 - th_q
-    dph = wrap_pi(phi2 - ph_q)
     F = _ring_coeffs_unique(lmax, order, th_q, nthreads, alm_T=alm_T, alm_E=alm_E, alm_B=alm_B)
     out = {}
     for f in F:
@@ -286,7 +316,7 @@ def lens_at_pixels(nside: int, lmax: int, order: int, pix, alm_T, alm_E=None, al
                       for (j, k) in derivative_pairs(order)])
         out[f] = taylor_sum(D, dth, dph, order)
     if "Q" in out and rotate:
-        beta = np.where(still, 0.0, transport_angle(n, u, et, d, theta2, phi2))
+        beta = np.where(still, 0.0, transport_angle(n, u, et, d, theta_g, phi_g))
         P = (out["Q"] + 1j * out["U"]) * np.exp(-2j * beta)
         out["Q"], out["U"] = P.real, P.imag
     out["aux"] = dict(q=q, dth=dth, dph=dph, a_th=a_th, a_ph=a_ph)

@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libtaylens.so")
 TL_OK, TL_ERR_ARG, TL_ERR_NOMEM, TL_ERR_CUDA, TL_ERR_TIMEOUT, TL_ERR_UNSUPPORTED = range(6)
 TL_SPIN_T, TL_SPIN_QU = 1, 2
 TL_FP64, TL_MIXED_FP32, TL_MIXED_TF32, TL_MIXED_TF32x3, TL_MIXED_BF16x3 = range(5)
-TL_ROTATE = 1
+TL_ROTATE, TL_NAIVE, TL_EXPAND_AT_PIXEL = 1, 2, 4
 TL_BATCH_LOOP, TL_BATCH_PERSISTENT, TL_BATCH_GRAPH = 0, 1, 2
 
 # every symbol include/taylens.h declares, with its ctypes signature
@@ -24,6 +24,7 @@ SIGNATURES = {
     "tl_plan_batch": (ctypes.c_int, [_P]),
     "tl_plan_batch_launches": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int]),
     "tl_plan_device_error": (ctypes.c_int, [_P]),
+    "tl_plan_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "tl_synth_derivs": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "tl_deflection": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "tl_lens": (ctypes.c_int, [_P] * 9),

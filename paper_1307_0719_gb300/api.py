@@ -41,14 +41,15 @@ class Plan:
     """A (nside, lmax, order) geometry with its device tables and workspace."""
 
     def __init__(self, nside: int, lmax: int, order: int, pol: bool = True,
-                 precision: int = FP64, rotate: bool = True):
+                 precision: int = FP64, rotate: bool = True, naive: bool = False, expand_at_pixel: bool = False):
         L = _lib.lib()
         self.nside, self.lmax, self.order, self.pol, self.precision = nside, lmax, order, pol, precision
         self.npix = 12 * nside * nside
         self.nalm = (lmax + 1) * (lmax + 2) // 2
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         spins = _lib.TL_SPIN_T | (_lib.TL_SPIN_QU if pol else 0)
-        flags = _lib.TL_ROTATE if rotate else 0
+        flags = ((_lib.TL_ROTATE if rotate else 0) | (_lib.TL_NAIVE if naive else 0) |
+                 (_lib.TL_EXPAND_AT_PIXEL if expand_at_pixel else 0))
         h = ctypes.c_void_p()
         check(L.tl_plan_create(nside, lmax, order, spins, precision, flags, ctypes.byref(h)),
               "tl_plan_create")

@@ -91,6 +91,12 @@ struct tl_plan {
   int *dev_err;                   // set by a kernel whose bounded wait timed out
   long long d7_rstride, d7p_rstride;  // T2 elements between realisations' D7 planes
   void *d3;            // derivative maps [3*nmaps][npix] (T), Taylor-ready
+  void *phase;          // ring-FFT phase table e^{i pi t / (4 ni)} per quarter length ni (T2)
+  int *gq;             // float plans: pixels the float gather defers to the double pass [npix]
+  int *gq_count;       // their number (reset before every gather)
+  int num_sms;         // multiprocessors of the plan's device
+  int wait_polls;      // polls of a tensor-core mbarrier wait (0: the default, 2^24)
+  int wait_stall;      // self-test of the timeout path (tl_plan_set_wait_limit)
   void *alpha;         // [2][npix] (T)
   void *adj_dbar;      // adjoint: gradients of the derivative maps, as d3 (allocated on first use)
   void *adj_ga;        // adjoint: [2][npix] deflection gradients (allocated on first use)
@@ -122,13 +128,25 @@ cudaError_t launch_prep_spin2(const tl_plan *p, const double *alm_E, const doubl
 cudaError_t launch_legendre_spin0(const tl_plan *p, int nder, bool phi, void *d7, void *d7p, cudaStream_t s);
 cudaError_t launch_legendre_spin2(const tl_plan *p, int nder, cudaStream_t s);
 
+// Pixel-tiled layout of the plan's derivative maps (d3): [tile][map][kD3Tile], one
+// tile holding every map's values of kD3Tile consecutive pixels, so that the gather's
+// reads of all maps at an expansion pixel fall in one 46 KB chunk (one page) instead
+// of one page per map; maps = fields x maps per field, T first.
+constexpr int kD3TileLg = 8, kD3Tile = 1 << kD3TileLg;
+__host__ __device__ __forceinline__ long long d3_tiles(long long npix) { return (npix + kD3Tile - 1) >> kD3TileLg; }
+// element of pixel p in the tile layout, relative to a map's own offset m * kD3Tile
+__host__ __device__ __forceinline__ long long d3_pix(long long p, long long tile_stride) {
+  return (p >> kD3TileLg) * tile_stride + (p & (kD3Tile - 1));
+}
+
 // One output map of the ring FFT stage.
 struct MapJob {
   int plane;       // which D7 plane set: 0 = T, 1 = Q, 2 = U, 3 = phi
   int j, k;        // derivative orders
   int div_sint;    // divide by sin(theta) of the ring
   double scale;    // multiplies d_theta^j d_phi^k (after undoing the 1/L^j, L^k normalisation)
-  void *out;       // [npix] map
+  void *out;       // plain: [npix] map; tiled: the map's first element m * kD3Tile of the tile layout
+  long long tile;  // 0: plain layout; else elements between tiles (maps x kD3Tile)
 };
 cudaError_t launch_ringfft(const tl_plan *p, const MapJob *jobs, int njobs, int nder_planes,
                            cudaStream_t s);
@@ -151,6 +169,8 @@ cudaError_t launch_legendre_adj2(const tl_plan *p, int nder, const void *FQ, con
 cudaError_t launch_adj_finish(const tl_plan *p, double *gT, double *gP, double *gE, double *gB, cudaStream_t s);
 cudaError_t launch_gather_adjoint(const tl_plan *p, const void *alpha, const void *d3, const void *gT, const void *gQ,
                                   const void *gU, void *dbar, void *ga, cudaStream_t s);
+size_t phase_table_entries(int nside);
+cudaError_t launch_phase_table(const tl_plan *p, void *out, cudaStream_t s);
 cudaError_t launch_tcstep(const tl_plan *p, int s, const long long *blkofs, const void *tab, float *out,
                           cudaStream_t st);
 cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *const *a, const double *const *b,

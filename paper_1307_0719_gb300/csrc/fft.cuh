@@ -85,9 +85,10 @@ __device__ __forceinline__ T2 unit_root(int lev, int cc, int dir) {
 // whose bit s is clear pairs with the one 2^s above it, with the twiddle
 // W_{2^(s+1)}^(index mod 2^s) = W_{2^(s+1)}^pos W_{2^(lev+1)}^cc: one table load
 // per level times a fixed root of unity.
-template <int R, bool SWZ, typename T, typename T2>
-__device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, int sh, int dir,
+template <int R, bool SWZ, typename T, typename T2, int LGC = 0>
+__device__ __forceinline__ void dit_pass(T2 *a, int lg_rt, int batch, int stride, int sh, int dir,
                                          const T2 *__restrict__ tw, int lgtw) {
+  const int lg = LGC ? LGC : lg_rt;  // a compile-time length folds the index arithmetic
   constexpr int P = 1 << R;
   const int ulg = lg - R;  // groups per array: 2^ulg
   const int total = batch << ulg;
@@ -128,10 +129,11 @@ __device__ __forceinline__ void dit_pass(T2 *a, int lg, int batch, int stride, i
 // The top DIT pass of the inverse transform in Bluestein: as dit_pass (dir +1), but
 // each output p < n is multiplied by the chirp e^{i pi p^2/n} and written to y;
 // the rest (p >= n) are not needed.
-template <int R, typename T, typename T2>
-__device__ __forceinline__ void dit_last(const T2 *a, int lg, int batch, int stride, int sh,
+template <int R, typename T, typename T2, int LGC = 0>
+__device__ __forceinline__ void dit_last(const T2 *a, int lg_rt, int batch, int stride, int sh,
                                          const T2 *__restrict__ tw, int lgtw, T2 *y, int n, int ystride,
                                          const T2 *__restrict__ chirp) {
+  const int lg = LGC ? LGC : lg_rt;
   constexpr int P = 1 << R;
   const int ulg = lg - R;
   const int total = batch << ulg;
@@ -171,18 +173,20 @@ __device__ __forceinline__ void dit_last(const T2 *a, int lg, int batch, int str
 // apart (swizzled layout when SWZ), whose input is already in bit-reversed order
 // (the writers store it so);
 // output in natural order. dir = -1: sum x e^{-2 pi i k t/n}; dir = +1: e^{+...}.
-// tw[k] = e^{-2 pi i k / TW}, k < TW/2 (TW >= n). Passes of three stages.
-template <bool SWZ, typename T, typename T2>
-__device__ void fft_core(T2 *a, int n, int batch, int stride, int dir, const T2 *__restrict__ tw, int TW) {
-  if (n <= 1) return;
-  const int lg = 31 - __clz(n);
+// tw[k] = e^{-2 pi i k / TW}, k < TW/2 (TW >= n). Passes of four stages, then the
+// remainder. LGC > 0: n = 2^LGC known at compile time (passes unrolled).
+template <bool SWZ, typename T, typename T2, int LGC = 0>
+__device__ __forceinline__ void fft_core(T2 *a, int n, int batch, int stride, int dir, const T2 *__restrict__ tw,
+                                         int TW) {
+  const int lg = LGC ? LGC : 31 - __clz(n);
+  if (lg == 0) return;
   const int lgtw = 31 - __clz(TW);
-  // passes of four stages (16 elements per thread), then the remainder
   int sh = 0;
-  for (; sh + 4 <= lg; sh += 4) dit_pass<4, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
-  if (lg - sh == 3) dit_pass<3, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
-  if (lg - sh == 2) dit_pass<2, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
-  if (lg - sh == 1) dit_pass<1, SWZ, T, T2>(a, lg, batch, stride, sh, dir, tw, lgtw);
+#pragma unroll
+  for (; sh + 4 <= lg; sh += 4) dit_pass<4, SWZ, T, T2, LGC>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  if (lg - sh == 3) dit_pass<3, SWZ, T, T2, LGC>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  if (lg - sh == 2) dit_pass<2, SWZ, T, T2, LGC>(a, lg, batch, stride, sh, dir, tw, lgtw);
+  if (lg - sh == 1) dit_pass<1, SWZ, T, T2, LGC>(a, lg, batch, stride, sh, dir, tw, lgtw);
 }
 
 // The same for contiguous, unpadded arrays in natural order (bit-reversal first).
@@ -214,10 +218,11 @@ __device__ void fft_pow2(T2 *a, int n, int batch, int dir, const T2 *__restrict_
 //          n <= 2^(lg-1), so the upper half of the first level is zero);
 //   LAST:  each output is multiplied by the tabulated spectrum (bit-reversed order)
 //          as it is stored.
-template <int R, bool FIRST, bool LAST, typename T, typename T2>
-__device__ __forceinline__ void bs_dif_pass(T2 *w, int lg, int batch, int wstride, int sh, const T2 *__restrict__ tw,
-                                            int lgtw, const T2 *y, int n, int ystride, const T2 *__restrict__ chirp,
-                                            const T2 *__restrict__ bhr) {
+template <int R, bool FIRST, bool LAST, typename T, typename T2, int LGC = 0>
+__device__ __forceinline__ void bs_dif_pass(T2 *w, int lg_rt, int batch, int wstride, int sh,
+                                            const T2 *__restrict__ tw, int lgtw, const T2 *y, int n, int ystride,
+                                            const T2 *__restrict__ chirp, const T2 *__restrict__ bhr) {
+  const int lg = LGC ? LGC : lg_rt;
   constexpr int P = 1 << R;
   const int ulg = lg - R;
   const int total = batch << ulg;
@@ -277,43 +282,50 @@ __device__ __forceinline__ void bs_dif_pass(T2 *w, int lg, int batch, int wstrid
 // pass stores), the inverse DIT transform (bit-reversed in, natural out), whose last
 // pass multiplies by the chirp and writes the n outputs back to y. No bit-reversal
 // pass, no scatter: work holds batch swizzled arrays of length M, wstride apart.
-template <typename T, typename T2>
-__device__ void bluestein_batch(T2 *y, int n, int ystride, int M, int batch, T2 *work, int wstride,
-                                const T2 *__restrict__ bhr, const T2 *__restrict__ chirp,
-                                const T2 *__restrict__ tw, int TW) {
-  const int lg = 31 - __clz(M);  // M >= 2n >= 8 for every Bluestein length
+template <typename T, typename T2, int LGC = 0>
+__device__ __forceinline__ void bluestein_batch(T2 *y, int n, int ystride, int M, int batch, T2 *work, int wstride,
+                                                const T2 *__restrict__ bhr, const T2 *__restrict__ chirp,
+                                                const T2 *__restrict__ tw, int TW) {
+  const int lg = LGC ? LGC : 31 - __clz(M);  // M >= 2n >= 8 for every Bluestein length
   const int lgtw = 31 - __clz(TW);
   // ---- forward DIF: passes of four stages from the top (three when M = 8), then the
   // remainder; the first pass reads the chirped input, the last applies the spectrum
   if (lg < 4) {
-    if (lg == 3) bs_dif_pass<3, true, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+    if (lg == 3)
+      bs_dif_pass<3, true, true, T, T2, LGC>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
   } else {
     const int r = lg % 4;
     int sh = lg - 4;
     if (sh == 0) {
-      bs_dif_pass<4, true, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+      bs_dif_pass<4, true, true, T, T2, LGC>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
     } else {
-      bs_dif_pass<4, true, false, T, T2>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
+      bs_dif_pass<4, true, false, T, T2, LGC>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
+#pragma unroll
       for (sh -= 4; sh >= 0; sh -= 4) {
         if (sh == 0)
-          bs_dif_pass<4, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+          bs_dif_pass<4, false, true, T, T2, LGC>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
         else
-          bs_dif_pass<4, false, false, T, T2>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp, bhr);
+          bs_dif_pass<4, false, false, T, T2, LGC>(work, lg, batch, wstride, sh, tw, lgtw, y, n, ystride, chirp,
+                                                   bhr);
       }
-      if (r == 3) bs_dif_pass<3, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
-      if (r == 2) bs_dif_pass<2, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
-      if (r == 1) bs_dif_pass<1, false, true, T, T2>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+      if (r == 3)
+        bs_dif_pass<3, false, true, T, T2, LGC>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+      if (r == 2)
+        bs_dif_pass<2, false, true, T, T2, LGC>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
+      if (r == 1)
+        bs_dif_pass<1, false, true, T, T2, LGC>(work, lg, batch, wstride, 0, tw, lgtw, y, n, ystride, chirp, bhr);
     }
   }
   // ---- inverse DIT, natural order out: passes of four stages from the bottom; the
   // top pass (the remaining 1 to 4 stages) writes the chirped outputs p < n to y
   int s0 = 0;
-  for (; s0 + 4 < lg; s0 += 4) dit_pass<4, true, T, T2>(work, lg, batch, wstride, s0, +1, tw, lgtw);
+#pragma unroll
+  for (; s0 + 4 < lg; s0 += 4) dit_pass<4, true, T, T2, LGC>(work, lg, batch, wstride, s0, +1, tw, lgtw);
   const int R = lg - s0;
-  if (R == 4) dit_last<4, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
-  if (R == 3) dit_last<3, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
-  if (R == 2) dit_last<2, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
-  if (R == 1) dit_last<1, T, T2>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
+  if (R == 4) dit_last<4, T, T2, LGC>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
+  if (R == 3) dit_last<3, T, T2, LGC>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
+  if (R == 2) dit_last<2, T, T2, LGC>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
+  if (R == 1) dit_last<1, T, T2, LGC>(work, lg, batch, wstride, s0, tw, lgtw, y, n, ystride, chirp);
 }
 
 }  // namespace tl

@@ -16,29 +16,33 @@
 // and  phi' - phi_p = atan2(Y, X),
 //      th' - th_p   = atan2(a_th sinc d + z w, cos d + s w),  w = Y^2 / (rho + X),  rho = |(X, Y)|,
 // which carry no cancellation, so float arithmetic gives them to ~1e-7 relative.
-// The pixel lookup then runs in double on z_p + dz and phi_p + dphi (additions,
-// floor and one square root), and the offsets to the expansion centre subtract
-// centre differences taken from the double ring table. Rings with sin(theta) < 0.1
-// (where rho + X can cancel for a point carried over the pole) and deflections
-// above 0.02 rad use the double form.
+// The pixel lookup runs in single precision with a certified error bound: every
+// floor whose argument lies within the bound of an integer marks the pixel as
+// uncertain. The offsets to the expansion centre subtract centre differences
+// taken from exact integers and hi/lo float ring colatitudes. Pixels on rings with
+// sin(theta) < 0.1 (where rho + X can cancel for a point carried over the pole),
+// pixels deflected by more than 0.02 rad and pixels whose float lookup is
+// uncertain are not computed in the float kernel: it appends them to a queue
+// (one global atomic per block) and a second kernel runs them with the double
+// geometry, so that no warp of the float kernel waits on the FP64 pipe.
 #include <math.h>
 
 #include "geometry.cuh"
 
 namespace tl {
 
-// Increment-form geometry in float (see the header comment); pixel lookup in float
-// with a double fallback near cell boundaries.
-// Returns the expansion pixel q and, in float, the scaled offsets x = L dth,
-// y = L dph and cos 2 beta, sin 2 beta (no round trip through double).
+// Increment-form geometry in float (see the header comment), pixel lookup in float.
+// Returns false when the lookup cannot certify the cell (the caller then defers the
+// pixel to the double pass); else the expansion pixel q and, in float, the scaled
+// offsets x = L dth, y = L dph and cos 2 beta, sin 2 beta.
 struct Geo32 {
   long long q;
   float x, y, c2b, s2b;
 };
 // The pixel is (ring, idx), fr its float ring record (z, sin theta, 1 - |z|, theta
-// hi, theta lo). No double arithmetic except in the rare fallback of the lookup.
-__device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, int idx, float4 fr, float th_lo,
-                                      float ath, float aph, bool rot, float Lf, Geo32 &g) {
+// hi, theta lo). No double arithmetic.
+__device__ __forceinline__ bool geo32(const RingTable &rt, int nside, long long p, int ring, int idx, float4 fr,
+                                      float th_lo, float ath, float aph, bool rot, int mode, float Lf, Geo32 &g) {
   const float d2 = ath * ath + aph * aph;
   const float d = sqrtf(d2);
   float sh, ch;
@@ -52,25 +56,54 @@ __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, 
   const float dz = -zf * omc - sf * ath * sinc;
   const float rho = sqrtf(X * X + Y * Y);
   const float w = Y * Y / (rho + X);
-  const float dthp = atan2f(ath * sinc + zf * w, (1.0f - omc) + sf * w);  // th' - th_p
-  const float dphp = atan2f(Y, X);                                        // phi' - phi_p
-  // pixel lookup: in float where every decision clears its error bound (ang2loc_f),
-  // else in double on the accurate increments; both give ang2loc's cell.
-  // Pixel centres: phi = 2 pi (idx + sh/2) / nphi, sh = 1 on half-pixel-shifted rings.
+  float dthp = atan2f(ath * sinc + zf * w, (1.0f - omc) + sf * w);  // th' - th_p
+  float dphp = atan2f(Y, X);                                        // phi' - phi_p
+  float dzx = dz;                                                   // z' - z_p
+  if (mode & kGeoNaive) {
+    // naive addition: th' - th_p = a_th, phi' - phi_p = a_ph / sin th; the rings that
+    // could carry a point past a pole (sin th < 0.1) take the double pass
+    float sa, ca;
+    sincosf(0.5f * ath, &sa, &ca);
+    dthp = ath;
+    dphp = aph * __ldg(rt.rsinf + ring);
+    dzx = -sf * (2.0f * sa * ca) - zf * (2.0f * sa * sa);  // cos(th + a) - cos th
+  }
   const int np = rt.nphi[ring];
   const int shp = __double_as_longlong(rt.phi0[ring]) != 0;  // phi0 >= 0: an integer test
+  g.c2b = 1.0f;
+  g.s2b = 0.0f;
+  if (rot) {
+    // t = (1 - a_th^2 h) e_th - a_ph a_th h e_ph - a_th sinc n, h = (1 - cos d)/d^2,
+    // in the frame turned to phi_p: e_th = (z, 0, -s), e_ph = (0, 1, 0), n = (s, 0, z);
+    // read at the geodesic end point (X, Y, Z)
+    const float h = 0.5f * hsinc * hsinc;
+    const float ct = 1.0f - ath * ath * h;
+    const float tx = ct * zf - ath * sinc * sf;
+    const float ty = -aph * ath * h;
+    const float tz = -ct * sf - ath * sinc * zf;
+    const float Z = zf + dz;
+    const float cb = Z * (tx * X + ty * Y) / rho - tz * rho;  // t . e_theta'
+    const float sb = (-tx * Y + ty * X) / rho;                // t . e_phi'
+    const float nrm = cb * cb + sb * sb;
+    g.c2b = (cb * cb - sb * sb) / nrm;
+    g.s2b = 2.0f * cb * sb / nrm;
+  }
+  if (mode & kGeoAtPixel) {  // expansion about the output pixel itself
+    g.q = p;
+    g.x = Lf * dthp;
+    float dph = dphp;
+    if (dph >= (float)kPiD) dph -= 2.0f * (float)kPiD;
+    if (dph < -(float)kPiD) dph += 2.0f * (float)kPiD;
+    g.y = Lf * dph;
+    return true;
+  }
+  // pixel lookup in float where every decision clears its error bound (ang2loc_f);
+  // else the pixel goes to the double-precision pass.
+  // Pixel centres: phi = 2 pi (idx + sh/2) / nphi, sh = 1 on half-pixel-shifted rings.
   const float tf = (float)(4 * idx + 2 * shp) / (float)np + dphp * (float)(2.0 / kPiD);  // 2 phi' / pi
   bool ok;
-  PixLoc lq = ang2loc_f(zf + dz, fr.z - (zf >= 0.0f ? dz : -dz), tf, nside, ok);
-  if (!ok) {
-    const double z = rt.z[ring], phi = ring_phi(rt, ring, idx);
-    const double z2 = z + (double)dz;
-    const double omz2 = rt.omza[ring] - (z >= 0.0 ? (double)dz : -(double)dz);
-    double phi2 = phi + (double)dphp;
-    if (phi2 >= 2.0 * kPiD) phi2 -= 2.0 * kPiD;
-    if (phi2 < 0.0) phi2 += 2.0 * kPiD;
-    lq = ang2loc(z2, omz2, phi2, nside);
-  }
+  PixLoc lq = ang2loc_f(zf + dzx, fr.z - (zf >= 0.0f ? dzx : -dzx), tf, nside, ok);
+  if (!ok) return false;
   g.q = rt.first[lq.ring] + lq.idx;
   // theta_q - theta_p from the hi/lo parts: the hi difference is exact (nearby
   // rings, Sterbenz), so this is the double difference rounded once
@@ -91,28 +124,14 @@ __device__ __forceinline__ void geo32(const RingTable &rt, int nside, int ring, 
   if (dph >= (float)kPiD) dph -= 2.0f * (float)kPiD;
   if (dph < -(float)kPiD) dph += 2.0f * (float)kPiD;
   g.y = Lf * dph;
-  g.c2b = 1.0f;
-  g.s2b = 0.0f;
-  if (rot) {
-    // t = (1 - a_th^2 h) e_th - a_ph a_th h e_ph - a_th sinc n, h = (1 - cos d)/d^2,
-    // in the frame turned to phi_p: e_th = (z, 0, -s), e_ph = (0, 1, 0), n = (s, 0, z)
-    const float h = 0.5f * hsinc * hsinc;
-    const float ct = 1.0f - ath * ath * h;
-    const float tx = ct * zf - ath * sinc * sf;
-    const float ty = -aph * ath * h;
-    const float tz = -ct * sf - ath * sinc * zf;
-    const float Z = zf + dz;
-    const float cb = Z * (tx * X + ty * Y) / rho - tz * rho;  // t . e_theta'
-    const float sb = (-tx * Y + ty * X) / rho;                // t . e_phi'
-    const float nrm = cb * cb + sb * sb;
-    g.c2b = (cb * cb - sb * sb) / nrm;
-    g.s2b = 2.0f * cb * sb / nrm;
-  }
+  return true;
 }
 
+// sum_j x^j sum_k y^k D_{j,k} at the expansion pixel, map index of (j,k) =
+// (j+k)(j+k+1)/2 + j; D: the field's first map in the tiled layout, qoff the pixel's
+// element (d3_pix)
 template <typename T, int ORDER>
-__device__ __forceinline__ T taylor_eval(const T *__restrict__ D, long long stride, long long q, T x, T y) {
-  // sum_j x^j sum_k y^k D_{j,k}, map index of (j,k) = (j+k)(j+k+1)/2 + j
+__device__ __forceinline__ T taylor_eval(const T *__restrict__ D, long long qoff, T x, T y) {
   T res = (T)0;
 #pragma unroll
   for (int j = ORDER; j >= 0; --j) {
@@ -121,57 +140,117 @@ __device__ __forceinline__ T taylor_eval(const T *__restrict__ D, long long stri
     for (int k = ORDER - j; k >= 0; --k) {
       const int N = j + k;
       const int mi = N * (N + 1) / 2 + j;
-      inner = fma(inner, y, __ldg(D + (long long)mi * stride + q));
+      inner = fma(inner, y, __ldg(D + qoff + (long long)mi * kD3Tile));
     }
     res = fma(res, x, inner);
   }
   return res;
 }
 
+// Eq. 4 at the expansion pixel q and the rotation, stored for output pixel p; d3 in
+// the pixel-tiled layout (tile: elements between tiles).
+template <typename T, int ORDER, bool POL>
+__device__ __forceinline__ void taylor_store(long long tile, long long p, long long q, T x, T y, T c2, T s2,
+                                             const T *__restrict__ d3, T *__restrict__ Tout, T *__restrict__ Qout,
+                                             T *__restrict__ Uout) {
+  constexpr int NM = (ORDER + 1) * (ORDER + 2) / 2;
+  const long long qoff = d3_pix(q, tile);
+  Tout[p] = taylor_eval<T, ORDER>(d3, qoff, x, y);
+  if (POL) {
+    const T qv = taylor_eval<T, ORDER>(d3 + NM * kD3Tile, qoff, x, y);
+    const T uv = taylor_eval<T, ORDER>(d3 + 2 * NM * kD3Tile, qoff, x, y);
+    Qout[p] = c2 * qv + s2 * uv;
+    Uout[p] = -s2 * qv + c2 * uv;
+  }
+}
+
+// One thread per output pixel. The double form computes every pixel; the float
+// form defers the pixels that need the double geometry (see the header comment)
+// to queue[0 .. *qcount), filled with one global atomic per block.
 template <typename T, int ORDER, bool POL>
 __global__ void __launch_bounds__(256) gather_kernel(RingTable rt, int nside, long long npix, double Lnorm,
                                                      const T *__restrict__ a_th, const T *__restrict__ a_ph,
                                                      const T *__restrict__ d3, T *__restrict__ Tout,
-                                                     T *__restrict__ Qout, T *__restrict__ Uout, int rotate) {
-  constexpr int NM = (ORDER + 1) * (ORDER + 2) / 2;
+                                                     T *__restrict__ Qout, T *__restrict__ Uout, int rotate,
+                                                     int *__restrict__ queue, int *__restrict__ qcount,
+                                                     long long tile, int mode) {
   constexpr bool FAST = sizeof(T) == 4;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npix) return;
-  const PixLoc loc = pix2loc(p, nside, npix);
-  const T ath = a_th[p], aph = a_ph[p];
-  const bool rot = POL && rotate;
-
-  long long q = p;
-  T x = (T)0, y = (T)0, c2 = (T)1, s2 = (T)0;
-  if (ath != (T)0 || aph != (T)0) {
-    float4 fr = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (FAST) fr = __ldg((const float4 *)(rt.ringf + 8 * (size_t)loc.ring));
-    if (FAST && fr.y >= 0.1f && (float)(ath * ath + aph * aph) < 4e-4f) {
-      Geo32 g;
-      geo32(rt, nside, loc.ring, loc.idx, fr, __ldg(rt.ringf + 8 * (size_t)loc.ring + 4), (float)ath, (float)aph, rot,
-            (float)Lnorm, g);
-      q = g.q;
-      x = (T)g.x;
-      y = (T)g.y;
-      c2 = (T)g.c2b;
-      s2 = (T)g.s2b;
-    } else {
-      Geo g;
-      const double z = rt.z[loc.ring], s = rt.sint[loc.ring];
-      geo64(rt, nside, z, s, ring_phi(rt, loc.ring, loc.idx), (double)ath, (double)aph, rot, g);
-      q = g.q;
-      x = (T)(Lnorm * g.dth);
-      y = (T)(Lnorm * g.dph);
-      c2 = (T)g.c2b;
-      s2 = (T)g.s2b;
-    }
+  __shared__ int s_cnt, s_base;
+  __shared__ int s_list[FAST ? 256 : 1];
+  if (FAST) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
   }
-  Tout[p] = taylor_eval<T, ORDER>(d3, npix, q, x, y);
-  if (POL) {
-    const T qv = taylor_eval<T, ORDER>(d3 + (long long)NM * npix, npix, q, x, y);
-    const T uv = taylor_eval<T, ORDER>(d3 + 2LL * NM * npix, npix, q, x, y);
-    Qout[p] = c2 * qv + s2 * uv;
-    Uout[p] = -s2 * qv + c2 * uv;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool rot = POL && rotate;
+  bool defer = false;
+  if (p < npix) {
+    const PixLoc loc = pix2loc(p, nside, npix);
+    const T ath = a_th[p], aph = a_ph[p];
+    long long q = p;
+    T x = (T)0, y = (T)0, c2 = (T)1, s2 = (T)0;
+    if (ath != (T)0 || aph != (T)0) {
+      if (FAST) {
+        const float4 fr = __ldg((const float4 *)(rt.ringf + 8 * (size_t)loc.ring));
+        Geo32 g;
+        defer = !(fr.y >= 0.1f && (float)(ath * ath + aph * aph) < 4e-4f) ||
+                !geo32(rt, nside, p, loc.ring, loc.idx, fr, __ldg(rt.ringf + 8 * (size_t)loc.ring + 4), (float)ath,
+                       (float)aph, rot, mode, (float)Lnorm, g);
+        if (!defer) {
+          q = g.q;
+          x = (T)g.x;
+          y = (T)g.y;
+          c2 = (T)g.c2b;
+          s2 = (T)g.s2b;
+        }
+      } else {
+        Geo g;
+        const double z = rt.z[loc.ring], s = rt.sint[loc.ring];
+        geo64(rt, nside, p, rt.theta[loc.ring], z, s, ring_phi(rt, loc.ring, loc.idx), (double)ath, (double)aph, rot,
+              mode, g);
+        q = g.q;
+        x = (T)(Lnorm * g.dth);
+        y = (T)(Lnorm * g.dph);
+        c2 = (T)g.c2b;
+        s2 = (T)g.s2b;
+      }
+    }
+    if (defer)
+      s_list[atomicAdd(&s_cnt, 1)] = (int)p;
+    else
+      taylor_store<T, ORDER, POL>(tile, p, q, x, y, c2, s2, d3, Tout, Qout, Uout);
+  }
+  if (FAST) {
+    __syncthreads();
+    const int n = s_cnt;
+    if (n == 0) return;  // uniform
+    if (threadIdx.x == 0) s_base = atomicAdd(qcount, n);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) queue[s_base + i] = s_list[i];
+  }
+}
+
+// The deferred pixels of the float kernel, with the double geometry (grid-stride
+// over the queue, whose length the device holds).
+template <int ORDER, bool POL>
+__global__ void __launch_bounds__(256) gather_fallback_kernel(RingTable rt, int nside, long long npix, double Lnorm,
+                                                              const float *__restrict__ a_th,
+                                                              const float *__restrict__ a_ph,
+                                                              const float *__restrict__ d3, float *__restrict__ Tout,
+                                                              float *__restrict__ Qout, float *__restrict__ Uout,
+                                                              int rotate, const int *__restrict__ queue,
+                                                              const int *__restrict__ qcount, long long tile,
+                                                              int mode) {
+  const int n = *qcount;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long p = queue[i];
+    const PixLoc loc = pix2loc(p, nside, npix);
+    Geo g;
+    const double z = rt.z[loc.ring], s = rt.sint[loc.ring];
+    geo64(rt, nside, p, rt.theta[loc.ring], z, s, ring_phi(rt, loc.ring, loc.idx), (double)a_th[p], (double)a_ph[p],
+          POL && rotate, mode, g);
+    taylor_store<float, ORDER, POL>(tile, p, g.q, (float)(Lnorm * g.dth), (float)(Lnorm * g.dph), (float)g.c2b,
+                                    (float)g.s2b, d3, Tout, Qout, Uout);
   }
 }
 
@@ -184,13 +263,35 @@ static cudaError_t gather_t(const tl_plan *p, const void *alpha, const void *d3,
   const T *aph = ath + p->npix;
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
   const int rot = (p->flags & TL_ROTATE) ? 1 : 0;
+  const int mode = ((p->flags & TL_NAIVE) ? kGeoNaive : 0) | ((p->flags & TL_EXPAND_AT_PIXEL) ? kGeoAtPixel : 0);
+  const double L = (double)(p->lmax + 1);
+  constexpr bool F32 = sizeof(T) == 4;
+  constexpr int NM = (ORDER + 1) * (ORDER + 2) / 2;
+  const long long tile = (long long)(pol ? 3 : 1) * NM * kD3Tile;  // d3's tile stride
+  if (F32) {
+    cudaError_t e = cudaMemsetAsync(p->gq_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   if (pol)
-    gather_kernel<T, ORDER, true><<<(unsigned)blocks, threads, 0, s>>>(
-        p->ring, p->nside, p->npix, (double)(p->lmax + 1), ath, aph, (const T *)d3, (T *)Tq, (T *)Q, (T *)U, rot);
+    gather_kernel<T, ORDER, true><<<(unsigned)blocks, threads, 0, s>>>(p->ring, p->nside, p->npix, L, ath, aph,
+                                                                       (const T *)d3, (T *)Tq, (T *)Q, (T *)U, rot,
+                                                                       p->gq, p->gq_count, tile, mode);
   else
-    gather_kernel<T, ORDER, false><<<(unsigned)blocks, threads, 0, s>>>(
-        p->ring, p->nside, p->npix, (double)(p->lmax + 1), ath, aph, (const T *)d3, (T *)Tq, nullptr, nullptr,
-        rot);
+    gather_kernel<T, ORDER, false><<<(unsigned)blocks, threads, 0, s>>>(p->ring, p->nside, p->npix, L, ath, aph,
+                                                                        (const T *)d3, (T *)Tq, nullptr, nullptr,
+                                                                        rot, p->gq, p->gq_count, tile, mode);
+  if (F32) {
+    // a fixed grid: the queue's length is known only on the device
+    const int fb = 4 * p->num_sms;
+    if (pol)
+      gather_fallback_kernel<ORDER, true><<<fb, threads, 0, s>>>(
+          p->ring, p->nside, p->npix, L, (const float *)ath, (const float *)aph, (const float *)d3, (float *)Tq,
+          (float *)Q, (float *)U, rot, p->gq, p->gq_count, tile, mode);
+    else
+      gather_fallback_kernel<ORDER, false><<<fb, threads, 0, s>>>(
+          p->ring, p->nside, p->npix, L, (const float *)ath, (const float *)aph, (const float *)d3, (float *)Tq,
+          nullptr, nullptr, rot, p->gq, p->gq_count, tile, mode);
+  }
   return cudaGetLastError();
 }
 

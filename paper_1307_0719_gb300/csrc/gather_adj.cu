@@ -127,11 +127,15 @@ __device__ __forceinline__ void geo_adj(const RingTable &rt, int nside, double z
 }
 
 // Taylor sum of one field at q, its x- and y-derivatives, and the scatter of
-// x^j y^k g into Dbar (all maps of the field, map index (j+k)(j+k+1)/2 + j).
+// x^j y^k g into Dbar (all maps of the field, map index (j+k)(j+k+1)/2 + j). D: the
+// field's first map in the pixel-tiled layout of the forward maps (tile: elements
+// between tiles); Dbar: plain maps [map][npix].
 template <typename T, int ORDER>
-__device__ __forceinline__ void taylor_adj(const T *__restrict__ D, T *__restrict__ Dbar, long long npix, long long q,
-                                           const double (&xp)[ORDER + 1], const double (&yp)[ORDER + 1], double gs,
-                                           double &val, double &dx, double &dy) {
+__device__ __forceinline__ void taylor_adj(const T *__restrict__ D, long long tile, T *__restrict__ Dbar,
+                                           long long npix, long long q, const double (&xp)[ORDER + 1],
+                                           const double (&yp)[ORDER + 1], double gs, double &val, double &dx,
+                                           double &dy) {
+  const long long qoff = d3_pix(q, tile);
   val = dx = dy = 0.0;
 #pragma unroll
   for (int n = 0; n <= ORDER; ++n)
@@ -139,7 +143,7 @@ __device__ __forceinline__ void taylor_adj(const T *__restrict__ D, T *__restric
     for (int j = 0; j <= n; ++j) {
       const int k = n - j;
       const int mi = n * (n + 1) / 2 + j;
-      const double d = (double)__ldg(D + (long long)mi * npix + q);
+      const double d = (double)__ldg(D + qoff + (long long)mi * kD3Tile);
       val += xp[j] * yp[k] * d;
       if (j > 0) dx += (double)j * xp[j - 1] * yp[k] * d;
       if (k > 0) dy += (double)k * xp[j] * yp[k - 1] * d;
@@ -173,7 +177,8 @@ __global__ void __launch_bounds__(256) gather_adj_kernel(RingTable rt, int nside
   }
   double v, dx, dy, dLdx = 0.0, dLdy = 0.0, dLdb = 0.0;
   const double gt = (double)gT[p];
-  taylor_adj<T, ORDER>(d3, dbar, npix, g.q, xp, yp, gt, v, dx, dy);
+  const long long tile = (long long)(POL ? 3 : 1) * NM * kD3Tile;  // forward maps' tile stride
+  taylor_adj<T, ORDER>(d3, tile, dbar, npix, g.q, xp, yp, gt, v, dx, dy);
   dLdx += gt * dx;
   dLdy += gt * dy;
   if (POL) {
@@ -181,8 +186,8 @@ __global__ void __launch_bounds__(256) gather_adj_kernel(RingTable rt, int nside
     const double c2 = g.c2b, s2 = g.s2b;
     const double gqt = c2 * gq - s2 * gu, gut = s2 * gq + c2 * gu;
     double qv, qx, qy, uv, ux, uy;
-    taylor_adj<T, ORDER>(d3 + (long long)NM * npix, dbar + (long long)NM * npix, npix, g.q, xp, yp, gqt, qv, qx, qy);
-    taylor_adj<T, ORDER>(d3 + 2LL * NM * npix, dbar + 2LL * NM * npix, npix, g.q, xp, yp, gut, uv, ux, uy);
+    taylor_adj<T, ORDER>(d3 + NM * kD3Tile, tile, dbar + (long long)NM * npix, npix, g.q, xp, yp, gqt, qv, qx, qy);
+    taylor_adj<T, ORDER>(d3 + 2 * NM * kD3Tile, tile, dbar + 2LL * NM * npix, npix, g.q, xp, yp, gut, uv, ux, uy);
     dLdx += gqt * qx + gut * ux;
     dLdy += gqt * qy + gut * uy;
     if (rot) {

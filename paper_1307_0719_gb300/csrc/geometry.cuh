@@ -146,9 +146,15 @@ struct Geo {
   double c2b, s2b;  // cos 2 beta, sin 2 beta
 };
 
-// Double-precision geometry (any pixel, any deflection).
-__device__ __forceinline__ void geo64(const RingTable &rt, int nside, double z, double s, double phi, double ath,
-                                      double aph, bool rot, Geo &g) {
+// Gather geometry options (plan flags): x' by naive coordinate addition instead of
+// the geodesic; expansion about the output pixel itself instead of the cell
+// containing x'. The rotation R keeps the geodesic transport angle either way.
+constexpr int kGeoNaive = 2, kGeoAtPixel = 4;
+
+// Double-precision geometry (any pixel, any deflection). p: the output pixel, at
+// (theta, phi) with z = cos theta, s = sin theta; mode: kGeoNaive | kGeoAtPixel bits.
+__device__ __forceinline__ void geo64(const RingTable &rt, int nside, long long p, double theta, double z, double s,
+                                      double phi, double ath, double aph, bool rot, int mode, Geo &g) {
   const double d = hypot(ath, aph);
   double sp, cp;
   sincos(phi, &sp, &cp);
@@ -163,11 +169,38 @@ __device__ __forceinline__ void geo64(const RingTable &rt, int nside, double z, 
   const double s2 = hypot(nx, ny);
   double phi2 = atan2(ny, nx);
   if (phi2 < 0.0) phi2 += 2.0 * kPiD;
-  const double th2 = atan2(s2, nz);
-  const PixLoc lq = ang2loc(nz, s2 * s2 / (1.0 + fabs(nz)), phi2, nside);
-  g.q = rt.first[lq.ring] + lq.idx;
-  g.dth = th2 - rt.theta[lq.ring];
-  double dph = phi2 - ring_phi(rt, lq.ring, lq.idx);
+  double th2 = atan2(s2, nz);
+  double z2 = nz, omz2 = s2 * s2 / (1.0 + fabs(nz));  // 1 - |z'| without cancellation
+  if (mode & kGeoNaive) {
+    // theta' = theta + a_theta, phi' = phi + a_phi / sin theta; past a pole the point
+    // continues on the other side (theta' -> -theta' or 2 pi - theta', phi' + pi)
+    th2 = theta + ath;
+    phi2 = phi + aph / s;
+    if (th2 < 0.0) {
+      th2 = -th2;
+      phi2 += kPiD;
+    } else if (th2 > kPiD) {
+      th2 = 2.0 * kPiD - th2;
+      phi2 += kPiD;
+    }
+    phi2 = fmod(phi2, 2.0 * kPiD);
+    if (phi2 < 0.0) phi2 += 2.0 * kPiD;
+    double sn, cn;
+    sincos(th2, &sn, &cn);
+    z2 = cn;
+    omz2 = sn * sn / (1.0 + fabs(cn));
+  }
+  double dph;
+  if (mode & kGeoAtPixel) {
+    g.q = p;
+    g.dth = th2 - theta;
+    dph = phi2 - phi;
+  } else {
+    const PixLoc lq = ang2loc(z2, omz2, phi2, nside);
+    g.q = rt.first[lq.ring] + lq.idx;
+    g.dth = th2 - rt.theta[lq.ring];
+    dph = phi2 - ring_phi(rt, lq.ring, lq.idx);
+  }
   if (dph >= kPiD) dph -= 2.0 * kPiD;
   if (dph < -kPiD) dph += 2.0 * kPiD;
   g.dph = dph;

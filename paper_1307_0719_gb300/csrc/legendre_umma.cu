@@ -120,10 +120,12 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
 }
 
-// bounded wait for the completion of the mbarrier phase with the given parity; gives
-// up early when another thread of the CTA has recorded a failure in *abort
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const volatile int *abort = nullptr) {
-  for (int it = 0; it < (1 << 24); ++it) {
+// bounded wait for the completion of the mbarrier phase with the given parity: at
+// most `polls` tries; gives up early when another thread of the CTA has recorded a
+// failure in *abort
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int polls,
+                                          const volatile int *abort = nullptr) {
+  for (int it = 0; it < polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
@@ -224,7 +226,7 @@ struct TcDesc {
   const double *lnorm0;
   int nside, lmax, mmax, nrings, nreal;
   const long long *blk;          // first 8-l block of each m
-  const float *step;             // per block: A_{l+1} x 8, m s/(l(l+1)) x 8
+  const float *step;             // per block: A_{l+1} x 8, then Q x 8 (spin 2: Qn, Qs), see step_stride
   const unsigned char *b;        // per block: coefficient tile hi [NC x 8] then lo
   float2 *d7a, *d7b;             // spin 0: the field's planes; spin 2: Q, U planes
   long long rstride;             // T2 elements between realisations' planes
@@ -238,6 +240,8 @@ struct TcDesc {
   // or NULL (no split)
   const float *state_mid;
   int nrblk;
+  int polls;  // polls of every mbarrier wait before it gives up (bounded waits)
+  int stall;  // self-test: the compute warps withhold their arrivals, so waits run out
 };
 
 // Per-CTA tcgen05 state (identical in every thread). Each half h of the compute
@@ -443,7 +447,7 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
         for (int h = 0; h < NH; ++h) {
           if (h == 1 && k >= n1) break;
           const uint32_t g = (h ? g01 : g00) + (uint32_t)k, i = buf_of<NB>(g), ib = (uint32_t)h * NB + i;
-          if (!mbar_wait(bar_full(U, i, h), phase_of<NB>(g), U.abort)) {
+          if (!mbar_wait(bar_full(U, i, h), phase_of<NB>(g), D.polls, U.abort)) {
             bad = true;
             break;
           }
@@ -513,7 +517,7 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       float buf0[NJ][4], buf1[NJ][4];
       block_steps<NDER, SPIN2>(mirror, a, b, sc, LC, w, Av, Cv, buf0, buf1);
       // the buffer was last read by the MMAs of this half's block g - NB
-      if (g >= (uint32_t)NB && !mbar_wait(bar_done(U, i, h), phase_of<NB>(g - NB), U.abort)) {
+      if (g >= (uint32_t)NB && !mbar_wait(bar_done(U, i, h), phase_of<NB>(g - NB), D.polls, U.abort)) {
         bad = true;
         break;
       }
@@ -525,16 +529,17 @@ __device__ __forceinline__ int run_blocks(const TcDesc &D, int m, int rblk, unsi
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if ((tid & 31) == 0) mbar_arrive(bar_full(U, i, h));
+      if ((tid & 31) == 0 && !D.stall) mbar_arrive(bar_full(U, i, h));
     }
   }
   U.count = g00 + (uint32_t)n0;
   U.count1 = g01 + (uint32_t)n1;
   // the last commit of each half covers every MMA issued before it
-  if (!bad && n0 > 0 && !mbar_wait(bar_done(U, buf_of<NB>(U.count - 1), 0), phase_of<NB>(U.count - 1), U.abort))
+  if (!bad && n0 > 0 &&
+      !mbar_wait(bar_done(U, buf_of<NB>(U.count - 1), 0), phase_of<NB>(U.count - 1), D.polls, U.abort))
     bad = true;
   if (NH == 2 && !bad && n1 > 0 &&
-      !mbar_wait(bar_done(U, buf_of<NB>(U.count1 - 1), 1), phase_of<NB>(U.count1 - 1), U.abort))
+      !mbar_wait(bar_done(U, buf_of<NB>(U.count1 - 1), 1), phase_of<NB>(U.count1 - 1), D.polls, U.abort))
     bad = true;
   if (bad) *U.abort = 1;
   if (__syncthreads_or(bad)) {
@@ -678,9 +683,9 @@ __device__ __forceinline__ void umma_close(const TcDesc &D, UmmaCta &U) {
   if (U.failed && threadIdx.x == 0) {
     atomicExch(D.err, 1);
     // own MMAs in flight (bounded)
-    if (U.count > 0) (void)mbar_wait(bar_done(U, buf_of<NB>(U.count - 1), 0), phase_of<NB>(U.count - 1));
+    if (U.count > 0) (void)mbar_wait(bar_done(U, buf_of<NB>(U.count - 1), 0), phase_of<NB>(U.count - 1), D.polls);
     if (NH == 2 && U.count1 > 0)
-      (void)mbar_wait(bar_done(U, buf_of<NB>(U.count1 - 1), 1), phase_of<NB>(U.count1 - 1));
+      (void)mbar_wait(bar_done(U, buf_of<NB>(U.count1 - 1), 1), phase_of<NB>(U.count1 - 1), D.polls);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -1029,6 +1034,8 @@ static TcDesc make_desc(const tl_plan *p, int which, int nreal, const void *btil
   D.bstart = which == 2 ? p->tc_bs2 : which == 1 ? p->tc_bsp : p->tc_bs0;
   D.state = which == 2 ? p->tc_st2 : which == 1 ? p->tc_stp : p->tc_st0;
   D.state_mid = which == 2 ? p->tc_sm2 : which == 1 ? p->tc_smp : p->tc_sm0;
+  D.polls = p->wait_polls > 0 ? p->wait_polls : (1 << 24);
+  D.stall = p->wait_stall;
   if (!D.state) D.bstart = nullptr;  // no table: every unit starts at l0
   if (!D.bstart) D.state_mid = nullptr;
   return D;

@@ -120,8 +120,10 @@ tl_status setup(DevState &st, int nside, int lmax, int precision) {
   p.tab0 = b.take(e2 * (size_t)na);
   p.rec_T = b.take(4 * (size_t)p.elem * (size_t)na);
   p.d7_P = b.take(e2 * 2 * nr * (size_t)(lmax + 1));
-  if (!tw64 || !p.blue.spec || !p.tab0 || !p.rec_T || !p.d7_P) return TL_ERR_ARG;
+  p.phase = b.take(e2 * tl::phase_table_entries(nside));
+  if (!tw64 || !p.blue.spec || !p.tab0 || !p.rec_T || !p.d7_P || !p.phase) return TL_ERR_ARG;
   cudaError_t e = cudaMemcpy(tw64, h_tw, 8 * (size_t)TW, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = tl::launch_phase_table(&p, p.phase, 0);
   if (e == cudaSuccess) e = tl::launch_bluestein_setup_impl(&p, tw64, 0);
   if (e == cudaSuccess) e = tl::launch_steptab(&p, 0, p.tab0, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -83,7 +83,7 @@ static void free_plan(tl_plan *p) {
                   p->blue.offset, p->blue.mlen, p->lnorm0, p->twiddle, p->tab0, p->tab2, p->rec_T, p->rec_P,
                   p->rec_QU,
                   p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->adj_dbar, p->adj_ga, p->stage_alm,
-                  p->stage_out,
+                  p->stage_out, p->gq, p->gq_count, p->phase,
                   p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2, p->dev_err,
                   p->tc_bs0, p->tc_bsp, p->tc_bs2, p->tc_st0, p->tc_stp, p->tc_st2, p->tc_sm0, p->tc_smp,
                   p->tc_sm2,
@@ -107,6 +107,7 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   p->nmaps = maps_per_field(order);
   p->elem = (precision == TL_FP64) ? 8 : 4;
   TRY_CUDA(cudaGetDevice(&p->device));
+  TRY_CUDA(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
   size_t *B = &p->bytes;
 
   HostRings h;
@@ -161,6 +162,8 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
     for (int k = 0; k < TW; ++k) tw32[k] = (float)tw64[k];
     TRY_CUDA(upload((float **)&p->twiddle, tw32, B));
   }
+  TRY_CUDA(dalloc(&p->phase, e2 * phase_table_entries(nside), B));
+  TRY_CUDA(launch_phase_table(p, p->phase, 0));
   cudaError_t e = launch_bluestein_setup_impl(p, (const double2 *)dtw64, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(dtw64);
@@ -230,8 +233,12 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   TRY_CUDA(dalloc((void **)&p->dev_err, sizeof(int), B));
   TRY_CUDA(cudaMemset(p->dev_err, 0, sizeof(int)));
   const int nfield = pol ? 3 : 1;
-  TRY_CUDA(dalloc(&p->d3, (size_t)p->elem * nfield * p->nmaps * p->npix, B));
+  TRY_CUDA(dalloc(&p->d3, (size_t)p->elem * nfield * p->nmaps * kD3Tile * d3_tiles(p->npix), B));
   TRY_CUDA(dalloc(&p->alpha, (size_t)p->elem * 2 * p->npix, B));
+  if (precision != TL_FP64) {
+    TRY_CUDA(dalloc((void **)&p->gq, sizeof(int) * (size_t)p->npix, B));
+    TRY_CUDA(dalloc((void **)&p->gq_count, sizeof(int), B));
+  }
   TRY_CUDA(cudaDeviceSynchronize());
 
   const char *fb = getenv("TAYLENS_FFT_BATCH");
@@ -255,7 +262,7 @@ extern "C" tl_status tl_plan_create(int nside, int lmax, int order, int spins, i
     return (spins == TL_SPIN_QU) ? TL_ERR_UNSUPPORTED : TL_ERR_ARG;
   }
   if (precision < TL_FP64 || precision > TL_MIXED_BF16x3) return TL_ERR_ARG;
-  if (flags & ~TL_ROTATE) return TL_ERR_ARG;
+  if (flags & ~(TL_ROTATE | TL_NAIVE | TL_EXPAND_AT_PIXEL)) return TL_ERR_ARG;
   // the ring FFT keeps a whole ring in shared memory
   {
     tl_plan probe;
@@ -305,6 +312,13 @@ extern "C" tl_status tl_plan_device_error(tl_plan *p) {
   return TL_OK;
 }
 
+extern "C" tl_status tl_plan_set_wait_limit(tl_plan *p, int polls, int stall) {
+  if (!p || polls < 0 || (stall != 0 && stall != 1)) return TL_ERR_ARG;
+  p->wait_polls = polls;
+  p->wait_stall = stall;
+  return TL_OK;
+}
+
 extern "C" int tl_plan_maps_per_field(const tl_plan *p) { return p ? p->nmaps : 0; }
 extern "C" int tl_plan_batch(const tl_plan *p) { return p ? p->batch : 0; }
 
@@ -316,8 +330,8 @@ extern "C" long long tl_plan_batch_launches(const tl_plan *p, int nreal, int wit
     // per batch: coefficient tiles and Legendre launch of T, the potential and Q/U
     const long long chunks = (nreal + p->batch - 1) / p->batch;
     const long long per_chunk = 2 + (phi ? 2 : 0) + (pol ? 2 : 0);
-    // per realisation: deflection FFT, derivative-map FFT, gather
-    return chunks * per_chunk + (long long)nreal * ((phi ? G : 0) + G + 1);
+    // per realisation: deflection FFT, derivative-map FFT, gather and its double pass
+    return chunks * per_chunk + (long long)nreal * ((phi ? G : 0) + G + 2);
   }
   const bool fuse = phi && p->order >= 1;
   long long per = 0;
@@ -325,7 +339,7 @@ extern "C" long long tl_plan_batch_launches(const tl_plan *p, int nreal, int wit
   per += 2 + (fuse ? 1 : 0);       // spin-0 prep (T, and phi when fused), Legendre
   if (fuse) per += G;              // deflection FFT
   if (pol) per += 2;               // spin-2 prep, Legendre
-  per += G + 1;                    // derivative-map FFT, gather
+  per += G + (p->precision == TL_FP64 ? 1 : 2);  // derivative-map FFT, gather (float: and its double pass)
   return (long long)nreal * per;
 }
 
@@ -417,24 +431,24 @@ extern "C" tl_status tl_synth_derivs(tl_plan *p, const double *alm, int spin, vo
 // ring FFTs into Taylor-ready maps d_th^j d_ph^k s / (j! k! L^(j+k)) for one realisation
 static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s) {
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
-  const size_t mapb = (size_t)p->elem * p->npix;
   std::vector<MapJob> jobs;
   // Jobs are packed two per transform in list order. Q and U of the same (j, k)
   // pair (similar magnitudes) and come first, an even count; then the T maps, which
   // pair within one coefficient plane j (the fold reads the row once for both),
   // left-overs across planes, the last one alone when their count is odd.
+  // outputs in the pixel-tiled layout of d3 (map g * nmaps + index of (j, k))
+  const long long tile = (long long)(pol ? 3 : 1) * p->nmaps * kD3Tile;
+  auto out = [&](int map) { return (void *)((char *)p->d3 + (size_t)p->elem * map * kD3Tile); };
   if (pol)
     for (int n = 0; n <= p->order; ++n)
       for (int j = 0; j <= n; ++j)
         for (int g = 1; g < 3; ++g) {
           int k = n - j;
-          jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)),
-                                (char *)p->d3 + mapb * (g * p->nmaps + n * (n + 1) / 2 + j)});
+          jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)), out(g * p->nmaps + n * (n + 1) / 2 + j), tile});
         }
   for (const std::pair<int, int> &jk : paired_order(p->order))
     jobs.push_back(MapJob{0, jk.first, jk.second, 0, 1.0 / (fact(jk.first) * fact(jk.second)),
-                          (char *)p->d3 + mapb * ((jk.first + jk.second) * (jk.first + jk.second + 1) / 2 +
-                                                  jk.first)});
+                          out((jk.first + jk.second) * (jk.first + jk.second + 1) / 2 + jk.first), tile});
   TRY_CUDA(launch_ringfft_planes(p, planes, jobs.data(), (int)jobs.size(), s));
   return TL_OK;
 }
@@ -637,6 +651,7 @@ extern "C" tl_status tl_lens_adjoint(tl_plan *p, const double *alm_T, const doub
                                      double *galm_T, double *galm_E, double *galm_B, double *galm_phi, void *galpha,
                                      void *stream) {
   if (!p || !alm_T || !gT) return TL_ERR_ARG;
+  if (p->flags & ~TL_ROTATE) return TL_ERR_UNSUPPORTED;  // the transpose of the default geometry only
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
   if (pol && (!alm_E || !gQ || !gU)) return TL_ERR_ARG;
   if (!pol && (galm_E || galm_B)) return TL_ERR_ARG;

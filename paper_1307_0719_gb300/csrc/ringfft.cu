@@ -26,6 +26,7 @@ struct JobDev {
   double scale;
   float scalef;
   int k, div_sint;
+  long long tile;  // output layout: 0 plain, else the tile stride (see d3_pix)
 };
 #define TL_MAX_JOBS 96
 struct JobList {
@@ -120,19 +121,24 @@ __device__ __forceinline__ void fold_pair(const T2 *__restrict__ FA, const T2 *_
 
 // BLUE: the launch's rings have non-power-of-two sub-transforms (Bluestein); else
 // power-of-two ones. A launch covers one ring group, so each instance carries one
-// sub-transform path (and its own register allocation).
-template <typename T, bool BLUE>
+// sub-transform path (and its own register allocation). LG > 0: the group's
+// transform length is known at compile time, 2^LG (power-of-two rings: the
+// sub-transform length ni; Bluestein: the convolution length M), so the FFT's index
+// and address arithmetic folds into constants; LG = 0 takes it from the ring.
+template <typename T, bool BLUE, int LG = 0>
 __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
                                                       BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
-                                                      int bbatch, T invL, const int *__restrict__ rings) {
+                                                      int bbatch, T invL, const int *__restrict__ rings,
+                                                      const typename RealTraits<T>::T2 *__restrict__ phase) {
   typedef typename RealTraits<T>::T2 T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = rings[blockIdx.x];
   const int pair = blockIdx.y;
   const int ja = 2 * pair, jb = 2 * pair + 1;
   const bool hasb = jb < jobs.n;
-  const int N = rt.nphi[r];
+  constexpr bool LGP = LG > 0 && !BLUE;  // power-of-two rings of one known length
+  const int N = LGP ? (4 << LG) : rt.nphi[r];
   const int ni = N >> 2;
   const int half = N >> 1;
   const long long first = rt.first[r];
@@ -142,8 +148,8 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
   // FFT); other ni: plain, with SY = 4 mod 16 so that the four arrays fall on
   // different banks.
   const bool pw2 = !BLUE;  // the group is of one kind: (ni & (ni - 1)) == 0 iff !BLUE
-  const int lgni = 31 - __clz(ni);
-  const int SY = ring_sub_stride(ni);
+  const int lgni = LGP ? LG : 31 - __clz(ni);
+  const int SY = LGP ? (1 << LG) : ring_sub_stride(ni);
   T2 *Y = (T2 *)smem_raw;
   T2 *W = Y + 4 * SY;  // work area
   const bool yswz = pw2 && ni >= 16;  // the XOR layout needs whole 16-element blocks
@@ -185,6 +191,8 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
     sb = scale2<T>(sb, -eb);
   }
   const T invN = (T)1 / (T)N;
+  // e^{i pi t / N}, t = 0 .. N/2, of this ring's length (plan-time table, see phase_table_kernel)
+  const T2 *__restrict__ eph = phase + ((size_t)ni * ni - 1);
 
   // ---- fold m modulo N into the Hermitian spectrum; thread handles classes t and N - t
   // (t = 0 .. N/2): C_t = (B_t + conj(B_{-t}))/2, C_{-t} = conj(C_t), Z = C^a + i C^b.
@@ -202,15 +210,12 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
     }
     if (shifted) {
       // class phases e^{i t phi0} and e^{i (N-t) phi0} = -conj(e^{i t phi0}) (t > 0)
-      T s, co;
-      sincos_pi<T>((T)tt * invN, &s, &co);
-      T2 e, em;
-      e.x = co;
-      e.y = s;
+      const T2 e = eph[tt];
+      T2 em;
       if (tt == 0) em = e;
       else {
-        em.x = -co;
-        em.y = s;
+        em.x = -e.x;
+        em.y = e.y;
       }
       Ba = cmul(Ba, e);
       Bb = cmul(Bb, e);
@@ -317,31 +322,33 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
   // ---- four length-ni inverse DFTs
   if (!BLUE) {
     if (yswz)
-      fft_core<true, T, T2>(Y, ni, 4, SY, +1, tw, TW);
+      fft_core<true, T, T2, LGP ? LG : 0>(Y, ni, 4, SY, +1, tw, TW);
     else
-      fft_core<false, T, T2>(Y, ni, 4, SY, +1, tw, TW);
+      fft_core<false, T, T2, LGP ? LG : 0>(Y, ni, 4, SY, +1, tw, TW);
   } else {
     const long long off = bt.offset[ni];
-    const int M = bt.mlen[ni];
+    const int M = LG ? (1 << LG) : bt.mlen[ni];
     const T2 *bh = (const T2 *)bt.spec + off;
     const T2 *ch = bh + M;  // the length's chirp follows its spectrum
     const int SW = M;
     if (bbatch >= 4) {
-      bluestein_batch<T, T2>(Y, ni, SY, M, 4, W, SW, bh, ch, tw, TW);
+      bluestein_batch<T, T2, LG>(Y, ni, SY, M, 4, W, SW, bh, ch, tw, TW);
     } else {
-      for (int t2 = 0; t2 < 4; ++t2) bluestein_batch<T, T2>(Y + t2 * SY, ni, SY, M, 1, W, SW, bh, ch, tw, TW);
+      for (int t2 = 0; t2 < 4; ++t2)
+        bluestein_batch<T, T2, LG>(Y + t2 * SY, ni, SY, M, 1, W, SW, bh, ch, tw, TW);
     }
   }
 
   // ---- radix-4 pass: X_{p1 + ni p2} = sum_t2 i^{t2 p2} e^{2 pi i t2 p1 / N} Y_t2(p1)
-  T *outA = (T *)JA.out + first;
-  T *outB = hasb ? (T *)JB.out + first : nullptr;
+  T *outA = (T *)JA.out;
+  T *outB = hasb ? (T *)JB.out : nullptr;
+  // output index of ring pixel p (plain, or the pixel-tiled layout of the plan's maps)
+  auto oidx = [&](long long tile, int p) -> long long {
+    const long long g = first + p;
+    return tile ? d3_pix(g, tile) : g;
+  };
   for (int p1 = tid; p1 < ni; p1 += nth) {
-    T s, c;
-    sincos_pi<T>((T)(2 * p1) * invN, &s, &c);
-    T2 w1;
-    w1.x = c;
-    w1.y = s;
+    const T2 w1 = eph[2 * p1];  // e^{2 pi i p1 / N}
     const T2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
     T2 y[4];
     y[0] = Y[yaddr(0, p1)];
@@ -355,15 +362,15 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
     ib1.y = b1.x;
     const T2 X0 = cadd(a0, b0), X2 = csub(a0, b0);
     const T2 X1 = cadd(a1, ib1), X3 = csub(a1, ib1);
-    outA[p1] = sa * X0.x;
-    outA[p1 + ni] = sa * X1.x;
-    outA[p1 + 2 * ni] = sa * X2.x;
-    outA[p1 + 3 * ni] = sa * X3.x;
+    outA[oidx(JA.tile, p1)] = sa * X0.x;
+    outA[oidx(JA.tile, p1 + ni)] = sa * X1.x;
+    outA[oidx(JA.tile, p1 + 2 * ni)] = sa * X2.x;
+    outA[oidx(JA.tile, p1 + 3 * ni)] = sa * X3.x;
     if (hasb) {
-      outB[p1] = sb * X0.y;
-      outB[p1 + ni] = sb * X1.y;
-      outB[p1 + 2 * ni] = sb * X2.y;
-      outB[p1 + 3 * ni] = sb * X3.y;
+      outB[oidx(JB.tile, p1)] = sb * X0.y;
+      outB[oidx(JB.tile, p1 + ni)] = sb * X1.y;
+      outB[oidx(JB.tile, p1 + 2 * ni)] = sb * X2.y;
+      outB[oidx(JB.tile, p1 + 3 * ni)] = sb * X3.y;
     }
   }
 }
@@ -385,7 +392,8 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_adj_ker
                                                           AdjJobList jobs,
                                                           BluesteinTable bt,
                                                           const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
-                                                          int bbatch, double L_d, const int *__restrict__ rings) {
+                                                          int bbatch, double L_d, const int *__restrict__ rings,
+                                                          const typename RealTraits<T>::T2 *__restrict__ phase) {
   typedef typename RealTraits<T>::T2 T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = rings[blockIdx.x];
@@ -402,6 +410,7 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_adj_ker
   const bool yswz = pw2 && ni >= 16;  // the XOR layout needs whole 16-element blocks
   auto yaddr = [&](int b, int i) { return yswz ? faddr(b, i, lgni, SY) : b * SY + i; };
   auto ydst = [&](int t) { return yaddr(t & 3, pw2 ? brev_bits(t >> 2, lgni) : (t >> 2)); };
+  const T2 *__restrict__ eph = phase + ((size_t)ni * ni - 1);  // e^{i pi t / N}, t <= N/2
   const bool shifted = __double_as_longlong(rt.phi0[r]) != 0;  // phi0 = pi / N
   const T invL = (T)(1.0 / L_d);
   const T inv_s = (T)1 / (T)rt.sint[r];
@@ -474,11 +483,7 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_adj_ker
     }
     // radix-4 pass in place (slots p1 + ni t2 are read and written by one thread), then conj
     for (int p1 = tid; p1 < ni; p1 += nth) {
-      T s, c;
-      sincos_pi<T>((T)(2 * p1) / (T)N, &s, &c);
-      T2 w1;
-      w1.x = c;
-      w1.y = s;
+      const T2 w1 = eph[2 * p1];  // e^{2 pi i p1 / N}
       const T2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
       T2 y[4];
       y[0] = Y[yaddr(0, p1)];
@@ -543,12 +548,12 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_adj_ker
       // w_m e^{-i m phi0}
       T wm = (m > 0) ? (T)2 : (T)1;
       if (shifted) {
-        const int m2 = m % (2 * N);
-        T s, c;
-        sincos_pi<T>((T)m2 / (T)N, &s, &c);
+        // e^{-i pi m2 / N}, m2 = m mod 2N = q (N/2) + r: conj(e^{i pi r / N} i^q)
+        const int m2 = m % (2 * N), q = m2 / (N >> 1), rr = m2 - q * (N >> 1);
+        const T2 er = rot_ik(eph[rr], q);
         T2 e;
-        e.x = wm * c;
-        e.y = -wm * s;
+        e.x = wm * er.x;
+        e.y = -wm * er.y;
         v = cmul(v, e);
       } else {
         v.x *= wm;
@@ -615,6 +620,33 @@ __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const l
   }
 }
 
+// Per-ring phase table: for every quarter length ni = 1 .. nside (cap rings of
+// nphi = 4 ni, and the belt, ni = nside) the factors e^{i pi t / (4 ni)}, t = 0 .. 2 ni,
+// at offset ni^2 - 1 (the tables of ni' < ni take sum (2 ni' + 1) = ni^2 - 1
+// entries). They give the class phases of half-pixel-shifted rings and the
+// radix-4 twiddles e^{2 pi i p / nphi}; formed in double.
+template <typename T>
+__global__ void phase_table_kernel(int nside, typename RealTraits<T>::T2 *__restrict__ out) {
+  const int ni = blockIdx.x + 1;
+  typename RealTraits<T>::T2 *o = out + ((size_t)ni * ni - 1);
+  for (int t = threadIdx.x; t <= 2 * ni; t += blockDim.x) {
+    double sn, cs;
+    sincospi((double)t / (4.0 * ni), &sn, &cs);
+    o[t].x = (T)cs;
+    o[t].y = (T)sn;
+  }
+}
+
+size_t phase_table_entries(int nside) { return (size_t)(nside + 1) * (nside + 1) - 1; }
+
+cudaError_t launch_phase_table(const tl_plan *p, void *out, cudaStream_t s) {
+  if (p->precision == TL_FP64)
+    phase_table_kernel<double><<<p->nside, 256, 0, s>>>(p->nside, (double2 *)out);
+  else
+    phase_table_kernel<float><<<p->nside, 256, 0, s>>>(p->nside, (float2 *)out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 
 // Shared memory of a ring-FFT launch: the ring (4 ni entries) plus a work area for
@@ -654,6 +686,65 @@ static cudaError_t set_group_smem(const tl_plan *p, K kernel) {
 }
 
 template <typename T>
+using RingKernel = void (*)(RingTable, int, int, JobList, BluesteinTable, const typename RealTraits<T>::T2 *, int,
+                            int, T, const int *, const typename RealTraits<T>::T2 *);
+
+// The kernel instance of a ring group: single precision has compile-time lengths for
+// the belt (sub-transforms of 2^8 .. 2^11, Nside 256 .. 2048) and the larger Bluestein
+// groups (M = 2^9 .. 2^12); every other group, and double precision, the generic one.
+template <typename T>
+static RingKernel<T> pick_ring_kernel(const FftGroup &g) {
+  if constexpr (sizeof(T) == 4) {
+    const int lgM = g.M ? 31 - __builtin_clz((unsigned)g.M) : 0;
+    const int lgn = (g.ni_min == g.ni_max && g.ni_min > 0) ? 31 - __builtin_clz((unsigned)g.ni_min) : 0;
+    if (g.M) {
+      switch (lgM) {
+        case 9: return ringfft_kernel<T, true, 9>;
+        case 10: return ringfft_kernel<T, true, 10>;
+        case 11: return ringfft_kernel<T, true, 11>;
+        case 12: return ringfft_kernel<T, true, 12>;
+        default: break;
+      }
+    } else if (lgn && (1 << lgn) == g.ni_min) {
+      switch (lgn) {
+        case 8: return ringfft_kernel<T, false, 8>;
+        case 9: return ringfft_kernel<T, false, 9>;
+        case 10: return ringfft_kernel<T, false, 10>;
+        case 11: return ringfft_kernel<T, false, 11>;
+        default: break;
+      }
+    }
+  }
+  return g.M ? ringfft_kernel<T, true, 0> : ringfft_kernel<T, false, 0>;
+}
+
+// Raise a kernel's dynamic shared-memory limit on the current device to what a launch
+// needs, once (kept per kernel and device; host-side, not thread-safe, as the rest
+// of a plan's launches).
+static cudaError_t raise_smem(const void *fn, size_t bytes) {
+  constexpr int kMax = 128;
+  static const void *keys[kMax];
+  static int devs[kMax];
+  static size_t vals[kMax];
+  static int nk = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int i = 0;
+  while (i < nk && (keys[i] != fn || devs[i] != dev)) ++i;
+  if (i < nk && vals[i] >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  if (i == nk && nk < kMax) {
+    keys[nk] = fn;
+    devs[nk] = dev;
+    ++nk;
+  }
+  if (i < kMax) vals[i] = bytes;
+  return cudaSuccess;
+}
+
+template <typename T>
 static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const MapJob *jobs, int njobs,
                              cudaStream_t s) {
   JobList jl;
@@ -668,18 +759,18 @@ static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const 
     jl.job[i].scale = jobs[i].scale;
     jl.job[i].scalef = (float)jobs[i].scale;
     jl.job[i].out = jobs[i].out;
+    jl.job[i].tile = jobs[i].tile;
   }
-  TL_CUDA_TRY(set_group_smem(p, ringfft_kernel<T, false>));
-  TL_CUDA_TRY(set_group_smem(p, ringfft_kernel<T, true>));
   for (int gi = 0; gi < p->fft_ngroups; ++gi) {
     const FftGroup &g = p->fft_groups[gi];
     const int batch = group_batch(p, g);
     dim3 grid(g.count, (njobs + 1) / 2);
-    auto kern = g.M ? ringfft_kernel<T, true> : ringfft_kernel<T, false>;
+    const RingKernel<T> kern = pick_ring_kernel<T>(g);
+    TL_CUDA_TRY(raise_smem((const void *)kern, group_smem(p, g, batch)));
     kern<<<grid, 512, group_smem(p, g, batch), s>>>(
         p->ring, p->nside, p->mmax, jl, p->blue,
         (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (T)(1.0 / (double)(p->lmax + 1)),
-        p->fft_rings + g.first);
+        p->fft_rings + g.first, (const typename RealTraits<T>::T2 *)p->phase);
   }
   return cudaGetLastError();
 }
@@ -720,7 +811,7 @@ static cudaError_t ringfft_adj_t(const tl_plan *p, void *const *planes, const Ad
     ringfft_adj_kernel<T><<<grid, 512, group_smem(p, g, batch), s>>>(
         p->ring, p->mmax, p->npix, p->nmaps, jl, p->blue,
         (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (double)(p->lmax + 1),
-        p->fft_rings + g.first);
+        p->fft_rings + g.first, (const typename RealTraits<T>::T2 *)p->phase);
   }
   return cudaGetLastError();
 }

@@ -51,6 +51,8 @@ def test_host_argument_checks(lib):
     assert lib.tl_plan_create(4, 8, 2, 1, 0, 4, ctypes.byref(h)) == L.TL_ERR_ARG      # flags
     assert lib.tl_lens(None, None, None, None, None, None, None, None, None) == L.TL_ERR_ARG
     assert lib.tl_plan_destroy(None) == L.TL_OK
+    assert lib.tl_plan_set_wait_limit(None, 0, 0) == L.TL_ERR_ARG
+    assert lib.tl_lens_batch_host(None, 1, None, None, None, None, None, None, None, None) == L.TL_ERR_ARG
     assert lib.tl_plan_workspace_bytes(None) == 0
     assert lib.tl_status_string(L.TL_ERR_ARG) == b"invalid argument"
     # allocation-free entry point: sizes beyond its fixed array are refused up front

@@ -209,3 +209,43 @@ def test_fp64_nside512_lmax1024_order4_vs_oracle_and_reruns():
         got = runs[0][i][pix]
         assert rel_rms(got, ref[f]) < 1e-6 and max_rel(got, ref[f]) < 1e-6, (f, rel_rms(got, ref[f]),
                                                                               max_rel(got, ref[f]))
+
+
+@pytest.mark.parametrize("naive,at_pixel", [(True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("precision,tol", [("FP64", 1e-10), ("MIXED_FP32", 1e-4), ("MIXED_BF16x3", 1e-4)])
+def test_lens_geometry_options_vs_oracle(naive, at_pixel, precision, tol):
+    """Plan flags TL_NAIVE (x' by coordinate addition, Sec. II.A) and
+    TL_EXPAND_AT_PIXEL (the plain Taylor series about the output pixel itself, Sec. I
+    Eq. 3a) against the oracle with the same options. The deflections are scaled up
+    (about 75 arcmin RMS at Nside 32) so that expansion pixels move, the float path
+    defers many pixels to its double pass, and naive addition carries points across
+    the poles."""
+    nside, lmax, order = 32, 64, 4
+    s = sky(nside, lmax, pol=True, b_scale=0.4)
+    phi = s["phi"] * 30.0
+    ref = OL.lens(nside, lmax, order, s["T"], s["E"], s["B"], phi, naive=naive, at_pixel=at_pixel)
+    d = to_dev(s)
+    plan = api.Plan(nside, lmax, order, pol=True, precision=getattr(api, precision), naive=naive,
+                    expand_at_pixel=at_pixel)
+    try:
+        out = plan.lens(d["T"], d["E"], d["B"], torch.from_numpy(phi).to("cuda:0")).cpu().numpy()
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    for i, f in enumerate("TQU"):
+        assert rel_rms(out[i], ref[f]) < tol, (f, rel_rms(out[i], ref[f]))
+
+
+def test_adjoint_refuses_geometry_options():
+    from paper_1307_0719_gb300 import _lib
+    nside, lmax = 8, 16
+    s = to_dev(sky(nside, lmax, pol=True, b_scale=0.3))
+    plan = api.Plan(nside, lmax, 2, pol=True, precision=api.FP64, naive=True)
+    try:
+        g = torch.zeros(12 * nside * nside, dtype=torch.float64, device="cuda:0")
+        with pytest.raises(_lib.TaylensError) as e:
+            plan.lens_adjoint(s["T"], s["E"], s["B"], s["phi"], g, g, g)
+        assert e.value.status == _lib.TL_ERR_UNSUPPORTED
+    finally:
+        torch.cuda.synchronize()
+        plan.close()

@@ -265,3 +265,62 @@ def test_lens_equals_sampled_evaluator(order):
     for f in "TQU":
         scale = np.sqrt(np.mean(full[f] ** 2))
         assert np.abs(samp[f] - full[f]).max() < 1e-12 * scale, (f, np.abs(samp[f] - full[f]).max() / scale)
+
+
+def test_naive_displacement_meridian_equals_geodesic_across_pole():
+    """Naive coordinate addition (Sec. II.A's alternative) for a deflection along
+    e_theta only: the geodesic is then the meridian, so both give the same x',
+    including points carried past a pole (theta' = -theta, phi' = phi + pi)."""
+    rng = np.random.default_rng(7)
+    K = 2000
+    th = rng.uniform(1e-3, np.pi - 1e-3, K)
+    phi = rng.uniform(0, 2 * np.pi, K)
+    a_th = rng.uniform(-0.5, 0.5, K)
+    a_th[:200] = -th[:200] - rng.uniform(1e-3, 0.2, 200)        # past the north pole
+    a_th[200:400] = np.pi - th[200:400] + rng.uniform(1e-3, 0.2, 200)  # past the south pole
+    z, s = np.cos(th), np.sin(th)
+    zero = np.zeros(K)
+    tn, pn, zn, sn, _ = L.target_point(th, z, s, phi, a_th, zero, naive=True)
+    tg, pg, zg, sg, _ = L.target_point(th, z, s, phi, a_th, zero, naive=False)
+    assert np.allclose(tn, tg, atol=1e-12)
+    assert np.allclose(np.abs(L.wrap_pi(pn - pg)) * sg, 0.0, atol=1e-12)
+
+
+def test_naive_displacement_second_order_agreement():
+    """For small deflections naive addition and the geodesic end point differ at
+    second order in |alpha| (transverse to the meridian), so the lensed maps do too."""
+    nside, lmax, n = 16, 32, 4
+    sky = skygen.make_sky(nside, lmax, True, 0, 3, 1, b_scale=0.4)
+    diffs = []
+    for scale in (10.0, 20.0):
+        phi = sky["phi"] * scale
+        g = L.lens(nside, lmax, n, sky["T"], sky["E"], sky["B"], phi, return_aux=True)
+        nv = L.lens(nside, lmax, n, sky["T"], sky["E"], sky["B"], phi, naive=True)
+        diffs.append(max(np.sqrt(np.mean((nv[f] - g[f]) ** 2) / np.mean(g[f] ** 2)) for f in "TQU"))
+    # doubling the deflection multiplies the difference by about four (second order)
+    assert 2.5 < diffs[1] / diffs[0] < 6.0, diffs
+
+
+def test_expansion_about_the_pixel_itself():
+    """The plain Taylor series about the undisplaced point (Sec. I, Eq. 3a; q = p):
+    zero deflection returns the order-0 map exactly; with deflections the error
+    against brute-force Y_lm sums falls with the order; and at a fixed low order it is
+    larger than the pixel-relative expansion about the cell containing x' (the
+    paper's motivation, Fig. 1), for deflections of several pixels."""
+    nside, lmax = 32, 32
+    sky = skygen.make_sky(nside, lmax, True, 0, 3, 1, b_scale=0.5)
+    zero = np.zeros_like(sky["phi"])
+    o = L.lens(nside, lmax, 4, sky["T"], sky["E"], sky["B"], zero, at_pixel=True)
+    base = L.derivative_maps(nside, lmax, 0, sky["T"], sky["E"], sky["B"])
+    for f in "TQU":
+        assert np.array_equal(o[f], base[f][0])
+    phi = sky["phi"] * 30.0
+    pix = np.random.default_rng(3).choice(hp.npix(nside), 400, replace=False)
+    ex = L.lens_exact(nside, lmax, sky["T"], sky["E"], sky["B"], phi, pix=pix)
+
+    def err(n, at_pixel):
+        r = L.lens_at_pixels(nside, lmax, n, pix, sky["T"], sky["E"], sky["B"], phi, at_pixel=at_pixel)
+        return max(np.sqrt(np.mean((r[f] - ex[f]) ** 2) / np.mean(ex[f] ** 2)) for f in "TQU")
+    e_px = [err(n, True) for n in (1, 3, 5, 8, 12)]
+    assert np.all(np.diff(e_px) < 0) and e_px[-1] < 1e-6, e_px
+    assert err(2, True) > 2.0 * err(2, False)
