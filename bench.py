@@ -707,6 +707,141 @@ def run_sweep(args):
                       "errors": table}), flush=True)
 
 
+def _ring_latitude_deg(nside):
+    """Latitude (degrees) of each HEALPix ring 1 .. 4 Nside - 1 and its pixel count,
+    for binning the output maps by latitude."""
+    i = np.arange(1, 4 * nside, dtype=np.float64)
+    ii = np.minimum(i, 4 * nside - i)
+    z = np.where(ii < nside, 1.0 - ii * ii / (3.0 * nside * nside), 4.0 / 3.0 - 2.0 * ii / (3.0 * nside))
+    z = np.where(i > 2 * nside, -z, z)
+    n = np.where(ii < nside, 4 * ii, 4 * nside).astype(np.int64)
+    return np.degrees(np.arcsin(z)), n
+
+
+def _lensed_spectra(plan, lmax, maps):
+    """TT, EE, BB, TE, TB, EB of lensed maps through tl_map2alm and tl_anafast."""
+    from paper_1307_0719_gb300 import api
+    a = plan.map2alm(maps[0].contiguous(), maps[1].contiguous(), maps[2].contiguous())
+    return api.anafast(lmax, a["T"], a["E"], a["B"]).cpu().numpy()
+
+
+def run_experiment(args):
+    """The paper's accuracy experiments (Sec. III.A) on synthetic skies, one JSON line
+    each. No CAMB spectra exist here, so the convergence study measures each order
+    against the highest one on the same realisations (self-convergence).
+      convergence (Fig. 3 analogue): for each Nside of 512, 1024, 2048 (lmax = 2 Nside,
+        the workloads' spectra) the lensed TT, EE, BB spectra (tl_map2alm + tl_anafast
+        of the lensed maps, two realisations summed) at orders 0 .. 5 against order 6.
+        Per Delta l = 50 bin the deviation is (sum_bin C_l(n)) / (sum_bin C_l(6)) - 1;
+        l_star is the centre of the last bin before the first one whose |deviation|
+        reaches 0.5% (the paper's definition of the highest accurate multipole).
+      rotation (Fig. 7 analogue): Nside 2048, lmax 4096, order 4, one realisation. The
+        maps with the geodesic displacement and the rotation R against (a) the same
+        without R and (b) the naive displacement (coordinates added) without R: per
+        latitude bin the error's standard deviation over the signal's, for T and for
+        P = Q + iU, and the error's TT, EE, BB spectra over the signal's per Delta l =
+        50 bin (maximum over l <= 2 Nside)."""
+    import torch
+    from paper_1307_0719_gb300 import api
+    dev = torch.device("cuda", 0)
+    prec = api.MIXED_FP32
+    if args.experiment == "convergence":
+        out = {"experiment": "self-convergence of the lensed spectra against order 6 (Fig. 3 analogue)",
+               "form": "mixed FP32", "realisations": 2, "bins": "Delta l = 50 from l = 2",
+               "criterion": "|sum_bin C_l(n) / sum_bin C_l(6) - 1| < 0.5%", "nside": {}}
+        for name in ("nside512_lmax1024_n4_TQU", "nside1024_lmax2048_n4_TQU", "nside2048_lmax4096_n4_TQU"):
+            w = skygen.WORKLOADS[name]
+            skies = [skygen.make_sky(w.nside, w.lmax, True, w.seed_t + 100 * i, w.seed_e + 100 * i,
+                                     w.seed_phi + 100 * i, w.damp_t, w.damp_e) for i in range(2)]
+            cls = {}
+            for n in range(0, 7):
+                plan = api.Plan(w.nside, w.lmax, n, pol=True, precision=prec)
+                try:
+                    acc = 0.0
+                    for sk in skies:
+                        d = {k: torch.from_numpy(v).to(dev) for k, v in sk.items()}
+                        acc = acc + _lensed_spectra(plan, w.lmax, plan.lens(d["T"], d["E"], d["B"], d["phi"]))
+                        del d
+                    cls[n] = acc
+                finally:
+                    torch.cuda.synchronize()
+                    plan.close()
+            bins = [(lo, min(lo + 50, w.lmax + 1)) for lo in range(2, w.lmax + 1, 50)]
+            row = {}
+            for n in range(0, 6):
+                per = {}
+                for q, spec in ((0, "TT"), (1, "EE"), (2, "BB")):
+                    devs = [float(cls[n][q][lo:hi].sum() / cls[6][q][lo:hi].sum() - 1.0) for lo, hi in bins]
+                    ls = None
+                    for (lo, hi), e in zip(bins, devs):
+                        if abs(e) >= 5e-3:
+                            break
+                        ls = 0.5 * (lo + hi - 1)
+                    lim = lambda lm: float(max(abs(e) for (lo, hi), e in zip(bins, devs) if hi - 1 <= lm))
+                    per[spec] = {"l_star": ls, "l_star_over_nside": None if ls is None else ls / w.nside,
+                                 "max_dev_l_le_nside": lim(w.nside), "max_dev_l_le_1p5nside": lim(1.5 * w.nside)}
+                row[str(n)] = per
+            out["nside"][str(w.nside)] = {"lmax": w.lmax, "orders": row}
+            print(json.dumps({"progress": name, "orders": row}), file=sys.stderr, flush=True)
+        print(json.dumps(out), flush=True)
+        return
+    # rotation
+    w = skygen.WORKLOADS["nside2048_lmax4096_n4_TQU"]
+    sky = skygen.workload_sky(w.name)
+    d = {k: torch.from_numpy(v).to(dev) for k, v in sky.items()}
+    variants = {"full": dict(rotate=True), "no_R": dict(rotate=False), "naive": dict(rotate=False, naive=True)}
+    maps = {}
+    for key, kw in variants.items():
+        plan = api.Plan(w.nside, w.lmax, w.order, pol=True, precision=prec, **kw)
+        try:
+            maps[key] = plan.lens(d["T"], d["E"], d["B"], d["phi"])
+        finally:
+            torch.cuda.synchronize()
+            plan.close()
+    lat, nring = _ring_latitude_deg(w.nside)
+    edges = np.array([0, 10, 20, 30, 40, 50, 60, 70, 80, 85, 88, 89, 90.0])
+    rbin = np.clip(np.searchsorted(edges, np.abs(lat), side="right") - 1, 0, len(edges) - 2)
+    pbin = torch.from_numpy(np.repeat(rbin, nring)).to(dev)
+    nb = len(edges) - 1
+
+    def per_bin(x):  # mean of x per latitude bin
+        x = x.double()
+        s = torch.zeros(nb, dtype=torch.float64, device=dev).index_add_(0, pbin, x)
+        c = torch.zeros(nb, dtype=torch.float64, device=dev).index_add_(0, pbin, torch.ones_like(x))
+        return (s / c).cpu().numpy()
+
+    def std_bin(x):
+        x = x.double()
+        m = per_bin(x)
+        return np.sqrt(np.maximum(per_bin(x * x) - m * m, 0.0))
+
+    F = maps["full"]
+    sT, sP = std_bin(F[0]), np.sqrt(std_bin(F[1]) ** 2 + std_bin(F[2]) ** 2)
+    plan = api.Plan(w.nside, w.lmax, 0, pol=True, precision=prec)
+    try:
+        c_sig = _lensed_spectra(plan, w.lmax, F)
+        res = {}
+        for key in ("no_R", "naive"):
+            E = maps[key] - F  # rounded relative to the difference itself
+            eT, eP = std_bin(E[0]), np.sqrt(std_bin(E[1]) ** 2 + std_bin(E[2]) ** 2)
+            c_err = _lensed_spectra(plan, w.lmax, E)
+            spec = {}
+            for q, nm in ((0, "TT"), (1, "EE"), (2, "BB")):
+                r = [float(c_err[q][lo:lo + 50].sum() / c_sig[q][lo:lo + 50].sum())
+                     for lo in range(2, 2 * w.nside + 1, 50)]
+                spec[nm] = {"max_err_over_signal_l_le_2nside": max(r)}
+            res[key] = {"by_latitude": [{"abs_lat_deg": [float(edges[b]), float(edges[b + 1])],
+                                         "T": float(eT[b] / sT[b]), "P": float(eP[b] / sP[b])} for b in range(nb)],
+                        "spectra": spec}
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    print(json.dumps({"experiment": "error of leaving out R, and of the naive displacement (Fig. 7 analogue)",
+                      "workload": w.name, "form": "mixed FP32, order 4",
+                      "measure": "std of error / std of signal per |latitude| bin; error C_l / signal C_l",
+                      "variants": res}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -726,6 +861,8 @@ def main():
     ap.add_argument("--sweep-errors", action="store_true",
                     help="print the error table of the full-size workload per order and form, then exit")
     ap.add_argument("--sweep-orders", default="2,3,4,5,6")
+    ap.add_argument("--experiment", default=None, choices=["convergence", "rotation"],
+                    help="print one of the paper's accuracy experiments on synthetic skies, then exit")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and gradient sub-records of the default line")
     args = ap.parse_args()
@@ -734,6 +871,8 @@ def main():
         args.form = "bf16x3"
     if args.sweep_errors:
         run_sweep(args)
+    elif args.experiment:
+        run_experiment(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched64_n4_TQU":

@@ -222,6 +222,37 @@ tl_status tl_lens_adjoint(tl_plan *plan, const double *alm_T, const double *alm_
                           double *galm_E, double *galm_B, double *galm_phi, void *galpha, void *stream);
 
 /*
+ * Spherical-harmonic analysis of maps on the plan's geometry (Sec. III: the paper
+ * measures the lensed maps through their power spectra, from healpy's map2alm with
+ * uniform weights and no iteration, and anafast):
+ *   a_lm = (4 pi / Npix) sum_p s(p) conj(sY_lm(p)),
+ * s = T (spin 0) and, for Q/U plans, Q +- iU (spin 2) into E and B in the HEALPix
+ * convention of tl_synth_derivs (Q + iU = -sum (E + iB) 2Y_lm). This is the
+ * transpose of the ring synthesis with those weights (it runs the adjoint kernels
+ * of tl_lens_adjoint at order 0), exact for band-limited maps only up to the
+ * quadrature error of the HEALPix grid.
+ *   T, Q, U        device maps, RING order, the plan's map type (double for TL_FP64,
+ *                  float for the mixed forms); Q and U NULL for temperature only
+ *   alm_T, E, B    device outputs, complex128 interleaved, healpy order, lmax of the
+ *                  plan (E, B NULL when Q, U are)
+ * Uses the plan's coefficient planes as workspace (overwrites the last tl_lens's).
+ * Errors: TL_ERR_ARG (NULL T or alm_T, unaligned pointers, Q/U on a T-only plan),
+ * TL_ERR_CUDA.
+ */
+tl_status tl_map2alm(tl_plan *plan, const void *T, const void *Q, const void *U, double *alm_T, double *alm_E,
+                     double *alm_B, void *stream);
+
+/*
+ * Angular power spectra of coefficient sets (Sec. III, Figs. 2, 3, 5, 6):
+ *   C_l^XY = (1 / (2l + 1)) sum_{m=-l..l} Re(x_lm conj(y_lm)),   l = 0 .. lmax,
+ * real fields (x_l,-m = (-1)^m conj x_lm). cl: device double [6][lmax + 1], rows TT,
+ * EE, BB, TE, TB, EB; rows whose fields are NULL are left 0. alm as in tl_map2alm.
+ * Errors: TL_ERR_ARG (lmax < 0, NULL cl, no field, unaligned pointers), TL_ERR_CUDA.
+ */
+tl_status tl_anafast(int lmax, const double *alm_T, const double *alm_E, const double *alm_B, double *cl,
+                     void *stream);
+
+/*
  * tl_deflection without any allocation, for callers that cannot allocate device
  * memory while they run (code inside a memory pool or allocator of its own,
  * or a process whose device memory is fixed up front).

@@ -321,3 +321,54 @@ def lens_at_pixels(nside: int, lmax: int, order: int, pix, alm_T, alm_E=None, al
         out["Q"], out["U"] = P.real, P.imag
     out["aux"] = dict(q=q, dth=dth, dph=dph, a_th=a_th, a_ph=a_ph)
     return out
+
+
+# ---------------------------------------------------------------------------
+# analysis side (Sec. III: the lensed maps are measured through power spectra)
+
+def map2alm(nside: int, lmax: int, T, Q=None, U=None):
+    """a_lm = (4 pi / Npix) sum_p s(p) conj(sY_lm(p)) with uniform weights (healpy's
+    map2alm without iterations), written out as direct sums: per ring the weighted
+    Fourier sums over its pixels, then the spin-weighted lambda_lm of the ring.
+    Spin 2 in the HEALPix convention Q +- iU = -sum (E +- iB) +-2Y_lm:
+    E = -(X+ + X-)/2, B = i (X+ - X-)/2 with X+- = sum w (Q +- iU) conj(+-2Y)."""
+    tab = hp.ring_table(nside)
+    w = 4.0 * np.pi / hp.npix(nside)
+    na = (lmax + 1) * (lmax + 2) // 2
+    out = {"T": np.zeros(na, complex)}
+    pol = Q is not None
+    if pol:
+        out["E"] = np.zeros(na, complex)
+        out["B"] = np.zeros(na, complex)
+    ms = np.arange(lmax + 1)
+    for r in range(len(tab["nphi"])):
+        n, f0 = int(tab["nphi"][r]), int(tab["first"][r])
+        ph = tab["phi0"][r] + 2.0 * np.pi * np.arange(n) / n
+        e = np.exp(-1j * np.outer(ms, ph))  # [m, p]
+        th = tab["theta"][r]
+        ft = w * (e @ np.asarray(T[f0:f0 + n], float))
+        if pol:
+            p = np.asarray(Q[f0:f0 + n], float) + 1j * np.asarray(U[f0:f0 + n], float)
+            fp, fm = w * (e @ p), w * (e @ np.conj(p))
+        for m in range(lmax + 1):
+            blk = slice(m * (2 * lmax + 1 - m) // 2 + m, m * (2 * lmax + 1 - m) // 2 + lmax + 1)  # l = m..lmax
+            out["T"][blk] += ft[m] * sht.spin_lambda(lmax, m, 0, th)[m:]
+            if pol:
+                xp = fp[m] * sht.spin_lambda(lmax, m, 2, th)[m:]
+                xm = fm[m] * sht.spin_lambda(lmax, m, -2, th)[m:]
+                out["E"][blk] += -0.5 * (xp + xm)
+                out["B"][blk] += 0.5j * (xp - xm)
+    for f in out:  # m = 0 coefficients of a real field are real
+        out[f][:lmax + 1] = out[f][:lmax + 1].real
+    return out
+
+
+def anafast(lmax: int, alm_x, alm_y=None):
+    """C_l = (1/(2l+1)) sum_{m=-l..l} Re(x_lm conj(y_lm)) for real fields."""
+    y = alm_x if alm_y is None else alm_y
+    cl = np.zeros(lmax + 1)
+    for m in range(lmax + 1):
+        blk = slice(m * (2 * lmax + 1 - m) // 2 + m, m * (2 * lmax + 1 - m) // 2 + lmax + 1)  # l = m..lmax
+        v = (alm_x[blk] * np.conj(y[blk])).real
+        cl[m:] += v if m == 0 else 2.0 * v
+    return cl / (2.0 * np.arange(lmax + 1) + 1.0)

@@ -33,6 +33,8 @@ SIGNATURES = {
     "tl_lens_batch_host": (ctypes.c_int, [_P, ctypes.c_int] + [_P] * 8),
     "tl_lens_adjoint": (ctypes.c_int, [_P] * 14),
     "tl_deflection_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "tl_map2alm": (ctypes.c_int, [_P] * 8),
+    "tl_anafast": (ctypes.c_int, [ctypes.c_int] + [_P] * 5),
     "tl_batch_create": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "tl_batch_destroy": (ctypes.c_int, [_P]),

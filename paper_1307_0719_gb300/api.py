@@ -207,10 +207,36 @@ class Plan:
             out["alpha"] = ga
         return out
 
+    def map2alm(self, T, Q=None, U=None, stream=None):
+        """tl_map2alm: coefficients (complex128 [nalm]) of maps on this plan's geometry
+        (the plan's map dtype, CUDA); returns dict T (and E, B when Q, U are given)."""
+        for name, m in (("T", T), ("Q", Q), ("U", U)):
+            if m is not None and (m.dtype != self.dtype or not m.is_cuda or not m.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous CUDA tensor of {self.dtype}")
+        dev = T.device
+        out = {"T": torch.empty(self.nalm, dtype=torch.complex128, device=dev)}
+        if Q is not None:
+            out["E"] = torch.empty(self.nalm, dtype=torch.complex128, device=dev)
+            out["B"] = torch.empty(self.nalm, dtype=torch.complex128, device=dev)
+        o = lambda f: _ptr(torch.view_as_real(out[f])) if f in out else None
+        check(_lib.lib().tl_map2alm(self._h, _ptr(T), _ptr(Q), _ptr(U), o("T"), o("E"), o("B"), _stream(stream)),
+              "tl_map2alm")
+        return out
+
     def last_stage_ms(self):
         buf = (ctypes.c_float * 16)()
         n = _lib.lib().tl_last_stage_ms(self._h, buf, 16)
         return list(buf[:n])
+
+
+def anafast(lmax, alm_T=None, alm_E=None, alm_B=None, stream=None):
+    """tl_anafast: [6, lmax+1] float64 CUDA tensor of C_l for TT, EE, BB, TE, TB, EB."""
+    a = {k: _alm(v, k) for k, v in (("T", alm_T), ("E", alm_E), ("B", alm_B))}
+    dev = next(v for v in a.values() if v is not None).device
+    cl = torch.zeros((6, lmax + 1), dtype=torch.float64, device=dev)
+    check(_lib.lib().tl_anafast(int(lmax), _ptr(a["T"]), _ptr(a["E"]), _ptr(a["B"]), _ptr(cl), _stream(stream)),
+          "tl_anafast")
+    return cl
 
 
 def lens(nside, lmax, order, alm_T, alm_E=None, alm_B=None, alm_phi=None, precision=FP64,

@@ -48,7 +48,7 @@ def test_host_argument_checks(lib):
         assert rc in (L.TL_OK, L.TL_ERR_CUDA), (prec, rc)
         if rc == L.TL_OK:
             lib.tl_plan_destroy(h)
-    assert lib.tl_plan_create(4, 8, 2, 1, 0, 4, ctypes.byref(h)) == L.TL_ERR_ARG      # flags
+    assert lib.tl_plan_create(4, 8, 2, 1, 0, 8, ctypes.byref(h)) == L.TL_ERR_ARG      # unknown flag
     assert lib.tl_lens(None, None, None, None, None, None, None, None, None) == L.TL_ERR_ARG
     assert lib.tl_plan_destroy(None) == L.TL_OK
     assert lib.tl_plan_set_wait_limit(None, 0, 0) == L.TL_ERR_ARG
@@ -57,3 +57,10 @@ def test_host_argument_checks(lib):
     assert lib.tl_status_string(L.TL_ERR_ARG) == b"invalid argument"
     # allocation-free entry point: sizes beyond its fixed array are refused up front
     assert lib.tl_deflection_noalloc(256, 256, 0, None, None, None, None) == L.TL_ERR_ARG
+
+
+def test_analysis_argument_checks(lib):
+    from paper_1307_0719_gb300 import _lib as L
+    assert lib.tl_map2alm(None, None, None, None, None, None, None, None) == L.TL_ERR_ARG
+    assert lib.tl_anafast(-1, None, None, None, None, None) == L.TL_ERR_ARG
+    assert lib.tl_anafast(8, None, None, None, None, None) == L.TL_ERR_ARG
