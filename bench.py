@@ -54,13 +54,14 @@ def fp32_peak_tflops(dev, peaks):
     return (sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
             f"derived: {sms} SMs (device) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz (sm_max_mhz)")
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of
-# `bench.py --workload nside512_lmax1024_n4_TQU --steps 1 --warmup 1 --form F` (16
-# realisations per launch; profiles/traffic_nside512_lmax1024_n4_bf16x3.md): bytes per
-# realisation (ring FFTs, gather: the same in every tensor-core form) or per Legendre
-# launch of form F, with the sha256 prefix of the kernel sources it was taken at. The
-# full-size workload scales them by its pixel count (rings x m grows the same way); a
-# changed source, another order or form gives null.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) from one-kernel ncu
+# captures of `bench.py --workload nside512_lmax1024_n4_TQU --steps 1 --warmup 1
+# --form F` (16 realisations per launch; the command and counters are kept with the
+# profile summaries): bytes per realisation (ring FFTs, gather: the same in every
+# tensor-core form) or per Legendre launch of form F, with the sha256 prefix of the
+# kernel sources it was taken at. The full-size workload scales them by its pixel
+# count (rings x m grows the same way); a changed source, another order or form
+# gives null.
 TRAFFIC_NSIDE512 = {
     ("fft_total", None): (839.2e6, ["ringfft.cu", "fft.cuh"], "6c26b53500746294"),
     ("gather_total", None): (624.6e6, ["gather.cu", "geometry.cuh"], "3d99eb1ac9a9bebc"),

@@ -1,8 +1,9 @@
 // Batched lensing of many realisations of uneven size (tl_batch_*).
 //
 // Realisations are grouped by geometry (nside, lmax); each group owns a plan.
-// On tensor-core plans the work goes in waves: a wave takes the next (up to) eight
-// realisations from every group that still has some, prepares their coefficient
+// On tensor-core plans the work goes in waves: a wave takes the next realisations,
+// up to the plan's batch (16 at orders up to 5, 8 above), from every group that
+// still has some, prepares their coefficient
 // fragments, and runs the Legendre stage of all of them in ONE persistent
 // launch whose blocks pull (plan, spin, m, ring block) items, pre-sorted by cost,
 // from an atomic counter; ring FFTs and the gather then follow per realisation.

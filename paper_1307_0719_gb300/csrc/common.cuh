@@ -68,7 +68,10 @@ struct tl_plan {
   void *twiddle;        // [TW/2] e^{-2 pi i k / TW} in T2 (device)
   int tw_len;
   int blue_maxm;        // largest Bluestein FFT length (0 if none)
+  int blue_reg_lg;      // Bluestein lengths M >= 2^blue_reg_lg (up to 2^12) run the register passes and keep
+                        // their spectra in natural order (0: none; bit-reversed order for the others)
   int fft_batch;        // Bluestein sub-transforms run together in the ring FFT (1 or 4; 0 = choose)
+  int ring_reg;         // single precision: register-pass ring FFT where a group allows it (1, default) or not (0)
   int *fft_rings;       // ring indices grouped by FFT launch (device)
   int fft_ngroups;
   tl::FftGroup fft_groups[TL_MAX_FFT_GROUPS];

@@ -164,6 +164,9 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   }
   TRY_CUDA(dalloc(&p->phase, e2 * phase_table_entries(nside), B));
   TRY_CUDA(launch_phase_table(p, p->phase, 0));
+  const char *rr = getenv("TAYLENS_RING_FFT");  // "shared": the shared-memory kernel for every group
+  p->ring_reg = (rr && strcmp(rr, "shared") == 0) ? 0 : 1;
+  p->blue_reg_lg = (precision != TL_FP64 && p->ring_reg) ? 11 : 0;
   cudaError_t e = launch_bluestein_setup_impl(p, (const double2 *)dtw64, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   cudaFree(dtw64);

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "fft.cuh"
+#include "regfft.cuh"
 
 namespace tl {
 
@@ -119,14 +120,56 @@ __device__ __forceinline__ void fold_pair(const T2 *__restrict__ FA, const T2 *_
   gb = hasb ? rot_ik(ab, kB) : ab;
 }
 
+// Bluestein on the four sub-sequences Y + t2 SY (t2 < 4) of length ni, in place,
+//   y_p <- sum_{t < ni} y_t e^{+2 pi i t p / ni}   (what bluestein_batch computes),
+// with register passes, for M = 2^LG: the 512 threads of the block form 512 / (M/16)
+// groups; each takes one sub-sequence at a time with its own padded exchange array
+// of M elements in W. The chirped input (zero from ni on; ni <= M / 2) goes through a
+// forward transform, the product with the length's spectrum (stored in natural
+// order, 1/M included, followed by the chirp e^{i pi t^2 / ni}) and an unnormalised
+// inverse transform; the chirped outputs p < ni go back to the sub-sequence.
+template <int LG>
+__device__ __forceinline__ void reg_bluestein(float2 *Y, int SY, int ni, float2 *W, const float2 *__restrict__ spec,
+                                              const float2 *__restrict__ tw, int lgtw) {
+  static_assert(LG >= 8 && LG <= 12, "M = 2^8 .. 2^12");
+  typedef RegFft<LG, -1> Ff;
+  typedef RegFft<LG, +1> Fi;
+  constexpr int M = 1 << LG, TGB = M / 16, K = 512 / TGB, KK = K < 4 ? K : 4;
+  static_assert(K == 2 || K == 4, "two or four groups of the 512 threads");
+  const int tid = threadIdx.x;
+  const int grp = tid / TGB, hh = tid - grp * TGB;
+  const float2 *__restrict__ chirp = spec + M;
+  float2 *xb = W + (size_t)grp * Ff::SMEM;
+  for (int round = 0; round < 4 / KK; ++round) {
+    float2 *yq = Y + (size_t)(round * KK + grp) * SY;
+    float2 x[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int t = hh + TGB * c;
+      x[c] = (c < 8 && t < ni) ? cmul(yq[t], __ldg(chirp + t)) : f2(0.0f, 0.0f);
+    }
+    Ff::run(x, xb, hh, tw, lgtw);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) x[c] = cmul(x[c], __ldg(spec + hh + TGB * c));
+    Fi::run(x, xb, hh, tw, lgtw);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int pp = hh + TGB * c;
+      if (pp < ni) yq[pp] = cmul(x[c], __ldg(chirp + pp));
+    }
+  }
+  __syncthreads();
+}
+
 // BLUE: the launch's rings have non-power-of-two sub-transforms (Bluestein); else
-// power-of-two ones. A launch covers one ring group, so each instance carries one
+// power-of-two ones. REG: Bluestein by register passes (reg_bluestein; M = 2^12
+// takes one CTA per SM through its shared memory, so it keeps the full register file). A launch covers one ring group, so each instance carries one
 // sub-transform path (and its own register allocation). LG > 0: the group's
 // transform length is known at compile time, 2^LG (power-of-two rings: the
 // sub-transform length ni; Bluestein: the convolution length M), so the FFT's index
 // and address arithmetic folds into constants; LG = 0 takes it from the ring.
-template <typename T, bool BLUE, int LG = 0>
-__global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
+template <typename T, bool BLUE, int LG = 0, bool REG = false>
+__global__ void __launch_bounds__(512, (sizeof(T) == 4 && !(REG && LG >= 12)) ? 2 : 1) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
                                                       BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
                                                       int bbatch, T invL, const int *__restrict__ rings,
@@ -325,6 +368,9 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
       fft_core<true, T, T2, LGP ? LG : 0>(Y, ni, 4, SY, +1, tw, TW);
     else
       fft_core<false, T, T2, LGP ? LG : 0>(Y, ni, 4, SY, +1, tw, TW);
+  } else if constexpr (REG) {
+    reg_bluestein<LG>((float2 *)Y, SY, ni, (float2 *)W, (const float2 *)bt.spec + bt.offset[ni],
+                      (const float2 *)tw, 31 - __clz(TW));
   } else {
     const long long off = bt.offset[ni];
     const int M = LG ? (1 << LG) : bt.mlen[ni];
@@ -376,6 +422,159 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// Rings of N = 2^LG pixels without aliasing (N > mmax), single precision: one CTA of
+// N / 16 threads per (ring, pair of output maps). The fold is formed straight in the
+// registers of the first FFT pass (thread h, slot c: Z_t with t = h + (N/16) c), the
+// register passes of RegFft run the inverse DFT, and each thread stores its sixteen
+// outputs. Per output class t, with class t holding m1 = t and class N - t holding
+// m2 = N - t (m2 = 0 for t = 0), each present when m <= mmax:
+//   Z_t = e_t [ u_a p_a(m1) F^a_m1 + u_b p_b(m1) F^b_m1
+//               + sigma conj(u_a p_a(m2) F^a_m2 - u_b p_b(m2) F^b_m2) ],
+// u_a = w_a i^k_a / 2, u_b = i w_b i^k_b / 2 (w: the job's 1/sin(theta) weight and
+// balance), p(m) = w_m (m / L)^k, e_t = e^{i pi t / N} and sigma = -1 on
+// half-pixel-shifted rings (t > 0), e_t = sigma = 1 otherwise: the class sums and
+// the Hermitian split of the shared-memory kernel above, written per class.
+template <int LG>
+__global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
+    ringfft_reg_kernel(RingTable rt, int mmax, JobList jobs, const float2 *__restrict__ tw, int lgtw, float invL,
+                       const int *__restrict__ rings, const float2 *__restrict__ phase) {
+  typedef RegFft<LG, +1> F;
+  constexpr int N = F::N, TG = F::TG, HALF = N / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *sm = (float2 *)smem_raw;
+  const int r = rings[blockIdx.x];
+  const int pair = blockIdx.y, ja = 2 * pair, jb = 2 * pair + 1;
+  const bool hasb = jb < jobs.n;
+  const int h = threadIdx.x;
+  const long long first = rt.first[r];
+  const bool shifted = __double_as_longlong(rt.phi0[r]) != 0;
+  const JobDev JA = jobs.job[ja];
+  const JobDev JB = hasb ? jobs.job[jb] : jobs.job[ja];
+  const float2 *FA = (const float2 *)JA.in + (size_t)r * (mmax + 1);
+  const float2 *FB = (const float2 *)JB.in + (size_t)r * (mmax + 1);
+  const bool same = JA.in == JB.in;
+  const float inv_s = rt.rsinf[r];
+  float wa = JA.div_sint ? inv_s : 1.0f;
+  float wb = hasb ? (JB.div_sint ? inv_s : 1.0f) : 0.0f;
+  float sa = JA.scalef, sb = JB.scalef;
+  {  // magnitude balance of the packed maps, as in ringfft_kernel
+    const float Lf = 1.0f / invL, sf = rt.ringf[8 * (size_t)r + 1];
+    const int e = max(0, __float2int_rn(log2f(Lf / (1.0f + Lf * sf))));
+    const int ea = e * max(0, JA.k - JA.div_sint), eb = e * max(0, JB.k - JB.div_sint);
+    wa = scalbnf(wa, ea);
+    wb = scalbnf(wb, eb);
+    sa = scalbnf(sa, -ea);
+    sb = scalbnf(sb, -eb);
+  }
+  const int kA = JA.k, kB = hasb ? JB.k : 0;
+  const int klo = min(kA, kB), khi = max(kA, kB);
+  const float2 ua = rot_ik(f2(0.5f * wa, 0.0f), kA);
+  const float2 ub = rot_ik(f2(0.5f * wb, 0.0f), kB + 1);
+  const float2 *__restrict__ eph = phase + ((size_t)(N / 4) * (N / 4) - 1);  // e^{i pi t / N}, t <= N/2
+
+  // w_m (m / L)^k for the two jobs: binary powers (k <= 7), no loops
+  auto powers = [&](int m, float &pa, float &pb) {
+    const float m1 = (float)m * invL, m2 = m1 * m1, m4 = m2 * m2;
+    const float w = (m > 0) ? 2.0f : 1.0f;
+    pa = w;
+    pb = w;
+    if (kA & 1) pa *= m1;
+    if (kA & 2) pa *= m2;
+    if (kA & 4) pa *= m4;
+    if (kB & 1) pb *= m1;
+    if (kB & 2) pb *= m2;
+    if (kB & 4) pb *= m4;
+  };
+  // u_a p_a(m) F^a_m + s u_b p_b(m) F^b_m (s = +1: the class's own term; -1 inside
+  // the conjugate of the partner class's term)
+  auto comb = [&](int m, float2 fa, float2 fb, float s) -> float2 {
+    float pa, pb;
+    powers(m, pa, pb);
+    const float2 ta = cmul(ua, f2(pa * fa.x, pa * fa.y));
+    const float2 tb = cmul(ub, f2(pb * fb.x, pb * fb.y));
+    return f2(fmaf(s, tb.x, ta.x), fmaf(s, tb.y, ta.y));
+  };
+  const float sg = shifted ? -1.0f : 1.0f;  // sigma of the classes t > 0
+  const float2 zero = f2(0.0f, 0.0f);
+  float2 x[16];
+  if (mmax <= HALF) {
+    // Slot c < 8 (t < N/2) holds class t's own term only, slot c >= 8 (t >= N/2) the
+    // conjugate of class N - t's only: one coefficient per map and slot, all loads
+    // issued before the arithmetic. Classes 0 and N/2 get their other term below.
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float2 va[8], vb[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = h + TG * (8 * half + u);
+        const int m = half ? N - t : t;
+        const bool ok = m <= mmax;
+        va[u] = ok ? __ldg(FA + m) : zero;
+        vb[u] = (ok && !same) ? __ldg(FB + m) : va[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = h + TG * (8 * half + u);
+        if (half == 0) {
+          x[u] = comb(t, va[u], vb[u], 1.0f);
+        } else {
+          const float2 d = comb(N - t, va[u], vb[u], -1.0f);
+          x[8 + u] = f2(sg * d.x, -sg * d.y);
+        }
+      }
+    }
+    if (h == 0) {
+      // t = 0: the partner class is class 0 itself (sigma = +1)
+      const float2 d0 = comb(0, __ldg(FA), same ? __ldg(FA) : __ldg(FB), -1.0f);
+      x[0] = f2(x[0].x + d0.x, x[0].y - d0.y);
+      // t = N/2: class N/2's own term m = N/2
+      if (HALF <= mmax) {
+        const float2 fa = __ldg(FA + HALF);
+        x[8] = cadd(x[8], comb(HALF, fa, same ? fa : __ldg(FB + HALF), 1.0f));
+      }
+    }
+  } else {
+    // band limit above N/2: both terms wherever m <= mmax
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int t = h + TG * c;
+      const int m2 = t ? N - t : 0;
+      float2 z = zero;
+      if (t <= mmax) {
+        const float2 fa = __ldg(FA + t);
+        z = comb(t, fa, same ? fa : __ldg(FB + t), 1.0f);
+      }
+      if (m2 <= mmax) {
+        const float2 fa = __ldg(FA + m2);
+        const float2 d = comb(m2, fa, same ? fa : __ldg(FB + m2), -1.0f);
+        const float s2 = t ? sg : 1.0f;
+        z.x = fmaf(s2, d.x, z.x);
+        z.y = fmaf(-s2, d.y, z.y);
+      }
+      x[c] = z;
+    }
+  }
+  if (shifted) {
+    // e_t = e^{i pi t / N} = e_h e^{i pi c / 16} (t = h + (N/16) c)
+    // cos, sin of pi c / 16
+    constexpr float kc[16] = {1.00000000000000000000f, 0.98078528040323043058f, 0.92387953251128673848f, 0.83146961230254523567f, 0.70710678118654757274f, 0.55557023301960228867f, 0.38268343236508983729f, 0.19509032201612833135f, 0.00000000000000006123f, -0.19509032201612819257f, -0.38268343236508972627f, -0.55557023301960195560f, -0.70710678118654746172f, -0.83146961230254534669f, -0.92387953251128673848f, -0.98078528040323043058f};
+    constexpr float ks[16] = {0.00000000000000000000f, 0.19509032201612824808f, 0.38268343236508978178f, 0.55557023301960217765f, 0.70710678118654746172f, 0.83146961230254523567f, 0.92387953251128673848f, 0.98078528040323043058f, 1.00000000000000000000f, 0.98078528040323043058f, 0.92387953251128673848f, 0.83146961230254545772f, 0.70710678118654757274f, 0.55557023301960217765f, 0.38268343236508989280f, 0.19509032201612860891f};
+    const float2 eh = __ldg(eph + h);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) x[c] = cmul(x[c], cmul(eh, f2(kc[c], ks[c])));
+  }
+  F::run(x, sm, h, tw, lgtw);
+  float *outA = (float *)JA.out;
+  float *outB = hasb ? (float *)JB.out : nullptr;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const long long g = first + h + TG * c;
+    outA[JA.tile ? d3_pix(g, JA.tile) : g] = sa * x[c].x;
+    if (hasb) outB[JB.tile ? d3_pix(g, JB.tile) : g] = sb * x[c].y;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint of the ring synthesis. For an output plane (field, j) fed by the real
 // maps g_k (k = derivative order in phi, scale c_k, optional 1/sin(theta)), the
 // gradient with respect to the plane's coefficients is
@@ -393,7 +592,8 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_adj_ker
                                                           BluesteinTable bt,
                                                           const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
                                                           int bbatch, double L_d, const int *__restrict__ rings,
-                                                          const typename RealTraits<T>::T2 *__restrict__ phase) {
+                                                          const typename RealTraits<T>::T2 *__restrict__ phase,
+                                                          int reg_lg) {
   typedef typename RealTraits<T>::T2 T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int r = rings[blockIdx.x];
@@ -475,7 +675,20 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 ? 2 : 1)) ringfft_adj_ker
       const T2 *bh = (const T2 *)bt.spec + off;
       const T2 *ch = bh + M;
       const int SW = M;
-      if (bbatch >= 4) {
+      const int lgM = 31 - __clz(M);
+      bool done = false;
+      if constexpr (sizeof(T) == 4) {
+        // the lengths whose spectra are stored for the register passes
+        if (reg_lg > 0 && lgM >= reg_lg && lgM <= 12) {
+          if (lgM == 12)
+            reg_bluestein<12>((float2 *)Y, SY, ni, (float2 *)W, (const float2 *)bh, (const float2 *)tw, 31 - __clz(TW));
+          else
+            reg_bluestein<11>((float2 *)Y, SY, ni, (float2 *)W, (const float2 *)bh, (const float2 *)tw, 31 - __clz(TW));
+          done = true;
+        }
+      }
+      if (done) {
+      } else if (bbatch >= 4) {
         bluestein_batch<T, T2>(Y, ni, SY, M, 4, W, SW, bh, ch, tw, TW);
       } else {
         for (int t2 = 0; t2 < 4; ++t2) bluestein_batch<T, T2>(Y + t2 * SY, ni, SY, M, 1, W, SW, bh, ch, tw, TW);
@@ -574,7 +787,7 @@ template <typename T>
 __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const long long *__restrict__ offset,
                                                               const int *__restrict__ mlen,
                                                               typename RealTraits<T>::T2 *__restrict__ spec,
-                                                              const double2 *__restrict__ tw, int TW) {
+                                                              const double2 *__restrict__ tw, int TW, int nat_lg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2 *w = (double2 *)smem_raw;
   const int n = blockIdx.x;
@@ -599,10 +812,12 @@ __global__ void __launch_bounds__(512) bluestein_setup_kernel(int nside, const l
   __syncthreads();
   fft_pow2<double, double2>(w, M, 1, -1, tw, TW);
   typedef typename RealTraits<T>::T2 T2;
-  // stored in bit-reversed order, the order in which the DIF transform leaves its output
+  // stored in bit-reversed order, the order in which the shared-memory DIF transform
+  // leaves its output, or in natural order for the lengths of the register passes
   const int lgM = 31 - __clz(M);
+  const bool nat = nat_lg > 0 && lgM >= nat_lg && lgM <= 12;
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
-    const int kr = brev_bits(k, lgM);
+    const int kr = nat ? k : brev_bits(k, lgM);
     T2 v;
     v.x = (T)(w[kr].x / M);
     v.y = (T)(w[kr].y / M);
@@ -652,9 +867,21 @@ cudaError_t launch_phase_table(const tl_plan *p, void *out, cudaStream_t s) {
 // Shared memory of a ring-FFT launch: the ring (4 ni entries) plus a work area for
 // the folding partial sums (2 x 512, only when a ring has fewer than 512 classes)
 // and, for Bluestein lengths, `batch` sub-transforms of length M.
+// Bluestein groups of the register passes: single precision, M from 2^blue_reg_lg up to 2^12
+static bool group_reg_blue(const tl_plan *p, const FftGroup &g) {
+  if (p->precision == TL_FP64 || p->blue_reg_lg == 0 || g.M == 0) return false;
+  const int lgM = 31 - __builtin_clz((unsigned)g.M);
+  return lgM >= p->blue_reg_lg && lgM <= 12;
+}
 static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch) {
   const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
   const size_t fold = (2 * g.ni_min + 1 < 512) ? 1024 : 0;
+  if (group_reg_blue(p, g)) {  // Y, then one padded exchange array per concurrent sub-transform
+    const size_t k = 512 / ((size_t)g.M / 16);
+    size_t wl = (k < 4 ? k : 4) * ((size_t)g.M + (size_t)g.M / 16);
+    if (wl < fold) wl = fold;
+    return e2 * ((size_t)4 * ring_sub_stride_max(g) + wl);
+  }
   size_t wl = g.M ? (size_t)batch * (size_t)g.M : 0;
   if (wl < fold) wl = fold;
   return e2 * ((size_t)4 * ring_sub_stride_max(g) + wl);
@@ -662,7 +889,7 @@ static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch) {
 // Four sub-transforms at once when two CTAs still fit on an SM (or when asked to and
 // one fits); one at a time otherwise.
 static int group_batch(const tl_plan *p, const FftGroup &g) {
-  if (g.M == 0 || p->fft_batch == 1) return 1;
+  if (g.M == 0 || p->fft_batch == 1 || group_reg_blue(p, g)) return 1;
   const size_t s4 = group_smem(p, g, 4);
   if (p->fft_batch == 4) return s4 <= 227 * 1024 ? 4 : 1;
   return s4 <= 113 * 1024 ? 4 : 1;
@@ -693,10 +920,17 @@ using RingKernel = void (*)(RingTable, int, int, JobList, BluesteinTable, const 
 // the belt (sub-transforms of 2^8 .. 2^11, Nside 256 .. 2048) and the larger Bluestein
 // groups (M = 2^9 .. 2^12); every other group, and double precision, the generic one.
 template <typename T>
-static RingKernel<T> pick_ring_kernel(const FftGroup &g) {
+static RingKernel<T> pick_ring_kernel(const tl_plan *p, const FftGroup &g) {
   if constexpr (sizeof(T) == 4) {
     const int lgM = g.M ? 31 - __builtin_clz((unsigned)g.M) : 0;
     const int lgn = (g.ni_min == g.ni_max && g.ni_min > 0) ? 31 - __builtin_clz((unsigned)g.ni_min) : 0;
+    if (g.M && group_reg_blue(p, g)) {
+      switch (lgM) {
+        case 11: return ringfft_kernel<T, true, 11, true>;
+        case 12: return ringfft_kernel<T, true, 12, true>;
+        default: break;
+      }
+    }
     if (g.M) {
       switch (lgM) {
         case 9: return ringfft_kernel<T, true, 9>;
@@ -744,6 +978,24 @@ static cudaError_t raise_smem(const void *fn, size_t bytes) {
   return cudaSuccess;
 }
 
+// The register-pass kernel of a ring group, or nullptr: single precision, rings of
+// one power-of-two length N = 4 ni = 2^LG (LG 10 .. 13) without aliasing (N > mmax),
+// and a twiddle table that reaches W_N.
+typedef void (*RegRingKernel)(RingTable, int, JobList, const float2 *, int, float, const int *, const float2 *);
+static RegRingKernel pick_reg_kernel(const tl_plan *p, const FftGroup &g, int *lg) {
+  if (p->precision == TL_FP64 || !p->ring_reg || g.M != 0 || g.ni_min != g.ni_max) return nullptr;
+  const int N = 4 * g.ni_min;
+  if ((N & (N - 1)) != 0 || N <= p->mmax || N > p->tw_len) return nullptr;
+  *lg = 31 - __builtin_clz((unsigned)N);
+  switch (*lg) {
+    case 10: return ringfft_reg_kernel<10>;
+    case 11: return ringfft_reg_kernel<11>;
+    case 12: return ringfft_reg_kernel<12>;
+    case 13: return ringfft_reg_kernel<13>;
+    default: return nullptr;
+  }
+}
+
 template <typename T>
 static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const MapJob *jobs, int njobs,
                              cudaStream_t s) {
@@ -761,11 +1013,22 @@ static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const 
     jl.job[i].out = jobs[i].out;
     jl.job[i].tile = jobs[i].tile;
   }
+  const int lgtw = 31 - __builtin_clz((unsigned)p->tw_len);
   for (int gi = 0; gi < p->fft_ngroups; ++gi) {
     const FftGroup &g = p->fft_groups[gi];
-    const int batch = group_batch(p, g);
     dim3 grid(g.count, (njobs + 1) / 2);
-    const RingKernel<T> kern = pick_ring_kernel<T>(g);
+    int lg = 0;
+    const RegRingKernel rk = (sizeof(T) == 4) ? pick_reg_kernel(p, g, &lg) : nullptr;
+    if (rk) {
+      const size_t smem = sizeof(float2) * (size_t)((1 << lg) + (1 << (lg - 4)));
+      TL_CUDA_TRY(raise_smem((const void *)rk, smem));
+      rk<<<grid, 1 << (lg - 4), smem, s>>>(p->ring, p->mmax, jl, (const float2 *)p->twiddle, lgtw,
+                                           (float)(1.0 / (double)(p->lmax + 1)), p->fft_rings + g.first,
+                                           (const float2 *)p->phase);
+      continue;
+    }
+    const int batch = group_batch(p, g);
+    const RingKernel<T> kern = pick_ring_kernel<T>(p, g);
     TL_CUDA_TRY(raise_smem((const void *)kern, group_smem(p, g, batch)));
     kern<<<grid, 512, group_smem(p, g, batch), s>>>(
         p->ring, p->nside, p->mmax, jl, p->blue,
@@ -811,7 +1074,7 @@ static cudaError_t ringfft_adj_t(const tl_plan *p, void *const *planes, const Ad
     ringfft_adj_kernel<T><<<grid, 512, group_smem(p, g, batch), s>>>(
         p->ring, p->mmax, p->npix, p->nmaps, jl, p->blue,
         (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (double)(p->lmax + 1),
-        p->fft_rings + g.first, (const typename RealTraits<T>::T2 *)p->phase);
+        p->fft_rings + g.first, (const typename RealTraits<T>::T2 *)p->phase, p->blue_reg_lg);
   }
   return cudaGetLastError();
 }
@@ -830,12 +1093,14 @@ cudaError_t launch_bluestein_setup_impl(tl_plan *p, const double2 *tw64, cudaStr
     TL_CUDA_TRY(cudaFuncSetAttribute(bluestein_setup_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     bluestein_setup_kernel<double><<<p->nside + 1, 512, smem, s>>>(p->nside, p->blue.offset, p->blue.mlen,
-                                                                   (double2 *)p->blue.spec, tw64, p->tw_len);
+                                                                   (double2 *)p->blue.spec, tw64, p->tw_len,
+                                                                   p->blue_reg_lg);
   } else {
     TL_CUDA_TRY(cudaFuncSetAttribute(bluestein_setup_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     bluestein_setup_kernel<float><<<p->nside + 1, 512, smem, s>>>(p->nside, p->blue.offset, p->blue.mlen,
-                                                                  (float2 *)p->blue.spec, tw64, p->tw_len);
+                                                                  (float2 *)p->blue.spec, tw64, p->tw_len,
+                                                                  p->blue_reg_lg);
   }
   return cudaGetLastError();
 }

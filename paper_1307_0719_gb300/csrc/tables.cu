@@ -166,9 +166,11 @@ int host_fft_groups(int nside, int nrings, const int *nphi, const int *ml, FftGr
   return n == nrings ? ng : -1;
 }
 
+// long enough for every Bluestein length and for a whole belt ring (4 nside), whose
+// register FFT takes its first pass's twiddles W_N^j from this table
 int host_twiddle_len(int nside, int maxm) {
   int TW = 2;
-  while (TW < maxm || TW < nside) TW <<= 1;
+  while (TW < maxm || TW < 4 * nside) TW <<= 1;
   return TW;
 }
 
