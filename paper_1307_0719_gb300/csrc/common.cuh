@@ -83,6 +83,7 @@ struct tl_plan {
   int batch;             // realisations sharing one Legendre launch (1, or 8 on tensor cores)
   int tc_nder;           // derivative orders carried there (max(order, 1))
   long long *tc_blk0, *tc_blk2;   // [lmax+1] first block of each m (spin 0 / spin 2)
+  int *tc_bm0, *tc_bm2;           // [blocks] the m of each block (spin 0 / spin 2)
   long long tc_nblk0, tc_nblk2;   // blocks in all
   // start tables (T, potential, Q/U): first contributing block per unit and the
   // recurrence state there

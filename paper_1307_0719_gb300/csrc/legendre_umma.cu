@@ -895,23 +895,18 @@ struct TcAlm {
 };
 
 // One warp per (8-l block, 32 columns) (blocks of all m numbered contiguously; the
-// block's m by binary search in blkofs); lane n owns column 32 h + n: it forms the
+// block's m from the plan's block table); lane n owns column 32 h + n: it forms the
 // column's 8 values and writes their hi and lo parts as 16-byte vectors.
 __global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal, int nc, int bf16, TcAlm alm,
-                                                     const long long *__restrict__ blkofs, long long nblocks,
+                                                     const long long *__restrict__ blkofs,
+                                                     const int *__restrict__ blkm, long long nblocks,
                                                      const float2 *__restrict__ tab, unsigned char *__restrict__ out) {
   const int groups = nc >> 5;
   const long long W = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
   const long long B = W / groups;
   if (B >= nblocks) return;
   const int n = (int)(W - B * groups) * 32 + (threadIdx.x & 31);
-  int lo_m = 0, hi_m = lmax;  // largest m with blkofs[m] <= B
-  while (lo_m < hi_m) {
-    const int mid = (lo_m + hi_m + 1) >> 1;
-    if (blkofs[mid] <= B) lo_m = mid;
-    else hi_m = mid - 1;
-  }
-  const int m = lo_m;
+  const int m = __ldg(blkm + B);
   const int blk = (int)(B - blkofs[m]);
   const int as = s < 0 ? -s : s;
   const int l0 = m > as ? m : as;
@@ -988,7 +983,8 @@ cudaError_t launch_tcprep(const tl_plan *p, int s, int nreal, const double *cons
   const long long warps = nblocks * (nc / 32);
   tcprep_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(p->lmax, s, nreal, nc,
                                                              tc_mode(p->precision) == kModeBf16x3 ? 1 : 0, alm,
-                                                             blkofs, nblocks, (const float2 *)tab,
+                                                             blkofs, (s == 2) ? p->tc_bm2 : p->tc_bm0, nblocks,
+                                                             (const float2 *)tab,
                                                              (unsigned char *)out);
   return cudaGetLastError();
 }

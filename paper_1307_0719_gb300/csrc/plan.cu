@@ -84,7 +84,7 @@ static void free_plan(tl_plan *p) {
                   p->rec_QU,
                   p->d7_T, p->d7_Q, p->d7_U, p->d7_P, p->d3, p->alpha, p->adj_dbar, p->adj_ga, p->stage_alm,
                   p->stage_out, p->gq, p->gq_count, p->phase,
-                  p->tc_blk0, p->tc_blk2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2, p->dev_err,
+                  p->tc_blk0, p->tc_blk2, p->tc_bm0, p->tc_bm2, p->tc_step0, p->tc_step2, p->tc_b0, p->tc_bp, p->tc_b2, p->dev_err,
                   p->tc_bs0, p->tc_bsp, p->tc_bs2, p->tc_st0, p->tc_stp, p->tc_st2, p->tc_sm0, p->tc_smp,
                   p->tc_sm2,
                   p->fft_rings};
@@ -209,6 +209,15 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
     }
     p->tc_nblk0 = n0;
     p->tc_nblk2 = n2;
+    {  // and the m of every block, so that a warp of the tile preparation finds it in one load
+      std::vector<int> m0((size_t)n0), m2((size_t)(n2 > 0 ? n2 : 1), 0);
+      for (int m = 0; m <= lmax; ++m) {
+        for (long long k = b0[m]; k < (m < lmax ? b0[m + 1] : n0); ++k) m0[(size_t)k] = m;
+        for (long long k = b2[m]; k < (m < lmax ? b2[m + 1] : n2); ++k) m2[(size_t)k] = m;
+      }
+      TRY_CUDA(upload(&p->tc_bm0, m0, B));
+      if (pol) TRY_CUDA(upload(&p->tc_bm2, m2, B));
+    }
     TRY_CUDA(upload(&p->tc_blk0, b0, B));
     TRY_CUDA(dalloc((void **)&p->tc_step0, 64 * (size_t)n0, B));
     TRY_CUDA(launch_tcstep(p, 0, p->tc_blk0, p->tab0, p->tc_step0, 0));

@@ -148,14 +148,36 @@ __device__ __forceinline__ void reg_bluestein(float2 *Y, int SY, int ni, float2 
       const int t = hh + TGB * c;
       x[c] = (c < 8 && t < ni) ? cmul(yq[t], __ldg(chirp + t)) : f2(0.0f, 0.0f);
     }
-    Ff::run(x, xb, hh, tw, lgtw);
+    if constexpr (LG >= 12) {
+      // one CTA per SM with the full register file: the table loads of each product
+      // are issued before the transform that precedes it, so they overlap its passes
+      float2 bq[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) x[c] = cmul(x[c], __ldg(spec + hh + TGB * c));
-    Fi::run(x, xb, hh, tw, lgtw);
+      for (int c = 0; c < 16; ++c) bq[c] = __ldg(spec + hh + TGB * c);
+      Ff::run(x, xb, hh, tw, lgtw);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int pp = hh + TGB * c;
-      if (pp < ni) yq[pp] = cmul(x[c], __ldg(chirp + pp));
+      for (int c = 0; c < 16; ++c) x[c] = cmul(x[c], bq[c]);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int pp = hh + TGB * c;
+        bq[c] = pp < ni ? __ldg(chirp + pp) : f2(0.0f, 0.0f);
+      }
+      Fi::run(x, xb, hh, tw, lgtw);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int pp = hh + TGB * c;
+        if (pp < ni) yq[pp] = cmul(x[c], bq[c]);
+      }
+    } else {
+      Ff::run(x, xb, hh, tw, lgtw);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) x[c] = cmul(x[c], __ldg(spec + hh + TGB * c));
+      Fi::run(x, xb, hh, tw, lgtw);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int pp = hh + TGB * c;
+        if (pp < ni) yq[pp] = cmul(x[c], __ldg(chirp + pp));
+      }
     }
   }
   __syncthreads();
@@ -497,10 +519,38 @@ __global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
   const float sg = shifted ? -1.0f : 1.0f;  // sigma of the classes t > 0
   const float2 zero = f2(0.0f, 0.0f);
   float2 x[16];
-  if (mmax <= HALF) {
+  if (mmax <= HALF && same) {
     // Slot c < 8 (t < N/2) holds class t's own term only, slot c >= 8 (t >= N/2) the
-    // conjugate of class N - t's only: one coefficient per map and slot, all loads
-    // issued before the arithmetic. Classes 0 and N/2 get their other term below.
+    // conjugate of class N - t's only: one coefficient per slot (both maps read one
+    // plane), all sixteen loads in flight before the arithmetic, which then runs in
+    // place. Classes 0 and N/2 get their other term below.
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int t = h + TG * c;
+      const int m = c < 8 ? t : N - t;
+      x[c] = m <= mmax ? __ldg(FA + m) : zero;
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const int t = h + TG * c;
+      if (c < 8) {
+        x[c] = comb(t, x[c], x[c], 1.0f);
+      } else {
+        const float2 d = comb(N - t, x[c], x[c], -1.0f);
+        x[c] = f2(sg * d.x, -sg * d.y);
+      }
+    }
+    if (h == 0) {
+      const float2 f0 = __ldg(FA);
+      const float2 d0 = comb(0, f0, f0, -1.0f);
+      x[0] = f2(x[0].x + d0.x, x[0].y - d0.y);
+      if (HALF <= mmax) {
+        const float2 fa = __ldg(FA + HALF);
+        x[8] = cadd(x[8], comb(HALF, fa, fa, 1.0f));
+      }
+    }
+  } else if (mmax <= HALF) {
+    // as above with two coefficient rows: two batches of eight slots
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       float2 va[8], vb[8];
@@ -566,11 +616,25 @@ __global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
   F::run(x, sm, h, tw, lgtw);
   float *outA = (float *)JA.out;
   float *outB = hasb ? (float *)JB.out : nullptr;
+  const long long tile = JA.tile;  // one layout for every job of a launch
+  // The ring starts a tile (the host launches this kernel only for such rings), so
+  // pixel h + TG c sits in tile first / 256 + (h + TG c) / 256 at (h + TG c) mod 256.
+  // For TG >= 256 that is tile (h / 256) + (TG / 256) c at h mod 256; for TG < 256,
+  // h + TG (c mod 256/TG) < 256, so it is tile (TG c) / 256 at h + TG (c mod 256/TG).
+  // Plain maps: first + h + TG c.
+  constexpr int PER = TG >= kD3Tile ? 1 : kD3Tile / TG;
+  const long long base =
+      tile ? ((first >> kD3TileLg) + (TG >= kD3Tile ? (h >> kD3TileLg) : 0)) * tile +
+                 (TG >= kD3Tile ? (h & (kD3Tile - 1)) : h)
+           : first + h;
+  float *oa = outA + base;
+  float *ob = hasb ? outB + base : nullptr;
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
-    const long long g = first + h + TG * c;
-    outA[JA.tile ? d3_pix(g, JA.tile) : g] = sa * x[c].x;
-    if (hasb) outB[JB.tile ? d3_pix(g, JB.tile) : g] = sb * x[c].y;
+    const long long off =
+        tile ? (long long)((TG * c) >> kD3TileLg) * tile + (TG >= kD3Tile ? 0 : TG * (c % PER)) : (long long)TG * c;
+    oa[off] = sa * x[c].x;
+    if (hasb) ob[off] = sb * x[c].y;
   }
 }
 
@@ -986,6 +1050,13 @@ static RegRingKernel pick_reg_kernel(const tl_plan *p, const FftGroup &g, int *l
   if (p->precision == TL_FP64 || !p->ring_reg || g.M != 0 || g.ni_min != g.ni_max) return nullptr;
   const int N = 4 * g.ni_min;
   if ((N & (N - 1)) != 0 || N <= p->mmax || N > p->tw_len) return nullptr;
+  // every ring of the group starts a 256-pixel tile of the derivative maps: north cap
+  // rings at 2 i (i - 1), south ones at Npix - 2 i (i + 1), belt rings at
+  // 2 N (N - 1) + k 4 N (N = nside)
+  const long long i = g.ni_min, ns = p->nside, T = kD3Tile;
+  const bool aligned = (i == ns) ? ((2 * ns * (ns - 1)) % T == 0 && (4 * ns) % T == 0)
+                                 : ((2 * i * (i - 1)) % T == 0 && (p->npix - 2 * i * (i + 1)) % T == 0);
+  if (!aligned) return nullptr;
   *lg = 31 - __builtin_clz((unsigned)N);
   switch (*lg) {
     case 10: return ringfft_reg_kernel<10>;
