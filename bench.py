@@ -318,7 +318,10 @@ def run_ours(args):
     launches = 1
     nchunk = min(nb, plan.batch) if tc else 1
     rl = {}
+    nf = 3 if w.pol else 1  # fields: T, Q, U (or T alone)
     for st, spin in (("legendre_QU", 2), ("legendre_T", 0)):
+        if not stage_ms.get(st):
+            continue  # a temperature-only workload has no spin-2 stage
         fl = legendre_flops_per_launch(w.nside, w.lmax, w.order, spin, part=part) * launches
         ach = fl / (stage_ms[st] / 1e3) / 1e12
         e = {"kernel": f"legendre_spin{spin}_{'umma' if tc else 'kernel'}<{w.order}>", "bound": "alu",
@@ -330,12 +333,12 @@ def run_ours(args):
             cf = legendre_flops_per_launch(w.nside, w.lmax, w.order, spin, part="contraction", nreal=nr_launch)
             e["tensor_tflops_contraction"] = cf / (stage_ms[st] / 1e3) / 1e12
         rl[st] = e
-    nplanes = 3 * (w.order + 1) + 2  # D7 planes read once: T, Q, U (j <= n) and phi (j <= 1)
-    nmaps = 3 * (w.order + 1) * (w.order + 2) // 2 + 2  # derivative maps and the deflection
+    nplanes = nf * (w.order + 1) + 2  # D7 planes read once: T, Q, U (j <= n) and phi (j <= 1)
+    nmaps = nf * (w.order + 1) * (w.order + 2) // 2 + 2  # derivative maps and the deflection
     nrings = 4 * w.nside - 1
     npix = 12 * w.nside * w.nside
     fft_bytes = nchunk * (nplanes * nrings * (w.lmax + 1) * 8 + nmaps * npix * 4)
-    gat_bytes = nchunk * npix * (3 * (w.order + 1) * (w.order + 2) // 2 * 4 + 2 * 4 + 3 * 4)
+    gat_bytes = nchunk * npix * (nf * (w.order + 1) * (w.order + 2) // 2 * 4 + 2 * 4 + nf * 4)
     for st, byt, kname in (("fft_total", fft_bytes, "ringfft_kernel<float> (all ring groups)"),
                            ("gather_total", gat_bytes, f"gather_kernel<float, {w.order}, 1>")):
         ach = byt / (stage_ms[st] / 1e3) / 1e9 if stage_ms.get(st) else None

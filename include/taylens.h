@@ -87,7 +87,8 @@ enum { TL_ROTATE = 1, TL_NAIVE = 2, TL_EXPAND_AT_PIXEL = 4 };
 /*
  * Create a plan for one (nside, lmax, order) geometry.
  *   nside     power of two, 1 .. 8192
- *   lmax      1 .. 4 nside (band limit of every field, including phi)
+ *   lmax      1 .. 8 nside (band limit of every field, and of phi unless
+ *             tl_plan_set_lmax_phi gives it its own)
  *   order     Taylor order n, 0 .. 6 (total degree j + k <= n; 0 = nearest-pixel lookup)
  *   spins     TL_SPIN_T, TL_SPIN_QU or both
  *   precision TL_FP64, TL_MIXED_FP32, TL_MIXED_TF32, TL_MIXED_TF32x3 or
@@ -336,6 +337,24 @@ tl_status tl_plan_device_error(tl_plan *plan);
  * restores normal operation. TL_ERR_ARG for polls < 0 or stall not 0 or 1.
  */
 tl_status tl_plan_set_wait_limit(tl_plan *plan, int polls, int stall);
+
+/* Band limit of the lensing potential (Sec. II.A: the paper takes the gradient map
+ * to min(8 Nside, 10000), above the fields' lmax, since the gradient is sensitive
+ * to small scales). Default: the plan's lmax.
+ *   lmax_phi  1 .. 8 nside. Any other value than the plan's lmax attaches a deflection plan
+ *             at (nside, lmax_phi, order 1, temperature only; the single-precision
+ *             SIMT form for every mixed form, FP64 for FP64), which then computes
+ *             alpha for every tl_lens, tl_lens_batch, tl_lens_host,
+ *             tl_lens_batch_host and tl_deflection call; lmax_phi = lmax removes it.
+ * After it, every alm_phi argument holds (lmax_phi+1)(lmax_phi+2)/2 coefficients
+ * (healpy order for lmax_phi); the other fields keep the plan's lmax.
+ * tl_lens_adjoint returns TL_ERR_UNSUPPORTED while a separate lmax_phi is set.
+ * The call waits for the device (work queued on any stream may still use the
+ * previous deflection plan) and frees the host-call staging, which the next host
+ * call allocates again. Errors: TL_ERR_ARG for a NULL plan or lmax_phi < 1; the
+ * errors of tl_plan_create (the plan keeps lmax_phi = lmax then).
+ */
+tl_status tl_plan_set_lmax_phi(tl_plan *plan, int lmax_phi);
 
 /* Human-readable text for a status code (static storage). */
 const char *tl_status_string(tl_status status);

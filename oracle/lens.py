@@ -206,9 +206,10 @@ def taylor_sum(D_at_q: np.ndarray, dth, dph, order: int):
 
 def lens(nside: int, lmax: int, order: int, alm_T, alm_E=None, alm_B=None, alm_phi=None,
          rotate: bool = True, nthreads=None, return_aux: bool = False, naive: bool = False,
-         at_pixel: bool = False):
+         at_pixel: bool = False, lmax_phi=None):
     """Lensed T (and Q, U) maps in RING order, FP64 (naive, at_pixel: see target_point
-    and expansion_point)."""
+    and expansion_point). lmax_phi: the potential's own band limit (Sec. II.A: the
+    gradient map is taken to min(8 Nside, 10000)); alm_phi is then in that layout."""
     tab = hp.ring_table(nside)
     npx = hp.npix(nside)
     pix = np.arange(npx)
@@ -221,7 +222,7 @@ def lens(nside: int, lmax: int, order: int, alm_T, alm_E=None, alm_B=None, alm_p
         a_th = np.zeros(npx)
         a_ph = np.zeros(npx)
     else:
-        a_th, a_ph = deflection(nside, lmax, alm_phi, nthreads=nthreads)
+        a_th, a_ph = deflection(nside, lmax if lmax_phi is None else lmax_phi, alm_phi, nthreads=nthreads)
     # 2. displaced position (zero displacement: x' = x exactly)
     theta_p = tab["theta"][ring - 1]
     theta2, phi2, z2, s2, (n, u, et, d, theta_g, phi_g) = target_point(theta_p, z, s, phi, a_th, a_ph, naive)
@@ -252,9 +253,9 @@ def exact_at(lmax: int, theta, phi, alm_T=None, alm_E=None, alm_B=None, nthreads
 
 
 def lens_exact(nside: int, lmax: int, alm_T, alm_E=None, alm_B=None, alm_phi=None, pix=None,
-               nthreads=None):
+               nthreads=None, lmax_phi=None):
     """Exact Born remap (Eqs. 1-2) at the given pixels by direct spherical-harmonic
-    sums at the displaced positions, with the same rotation R."""
+    sums at the displaced positions, with the same rotation R (lmax_phi as in lens)."""
     tab = hp.ring_table(nside)
     npx = hp.npix(nside)
     pix = np.arange(npx) if pix is None else np.asarray(pix)
@@ -262,7 +263,8 @@ def lens_exact(nside: int, lmax: int, alm_T, alm_E=None, alm_B=None, alm_phi=Non
     z = tab["z"][ring - 1]
     s = tab["sint"][ring - 1]
     phi = tab["phi0"][ring - 1] + 2.0 * np.pi * jidx / tab["nphi"][ring - 1]
-    a_th, a_ph = deflection_at(lmax, alm_phi, tab["theta"][ring - 1], phi, s, nthreads)
+    a_th, a_ph = deflection_at(lmax if lmax_phi is None else lmax_phi, alm_phi, tab["theta"][ring - 1], phi, s,
+                               nthreads)
     n2, u, n, et, d = displace(z, s, phi, a_th, a_ph)
     theta2 = np.arctan2(np.hypot(n2[:, 0], n2[:, 1]), n2[:, 2])
     phi2 = np.mod(np.arctan2(n2[:, 1], n2[:, 0]), 2.0 * np.pi)
@@ -293,7 +295,7 @@ def deflection_at(lmax, alm_phi, theta, phi, sint, nthreads=None):
 
 def lens_at_pixels(nside: int, lmax: int, order: int, pix, alm_T, alm_E=None, alm_B=None,
                    alm_phi=None, rotate: bool = True, nthreads=None, naive: bool = False,
-                   at_pixel: bool = False):
+                   at_pixel: bool = False, lmax_phi=None):
     """The same algorithm as `lens`, evaluated only at the given output pixels:
     derivative values at each expansion pixel come from direct Fourier sums
     instead of ring FFTs (used for sampled checks at full size)."""
@@ -303,7 +305,8 @@ def lens_at_pixels(nside: int, lmax: int, order: int, pix, alm_T, alm_E=None, al
     z = tab["z"][ring - 1]
     s = tab["sint"][ring - 1]
     phi = tab["phi0"][ring - 1] + 2.0 * np.pi * jidx / tab["nphi"][ring - 1]
-    a_th, a_ph = deflection_at(lmax, alm_phi, tab["theta"][ring - 1], phi, s, nthreads)
+    a_th, a_ph = deflection_at(lmax if lmax_phi is None else lmax_phi, alm_phi, tab["theta"][ring - 1], phi, s,
+                               nthreads)
     theta_p = tab["theta"][ring - 1]
     theta2, phi2, z2, s2, (n, u, et, d, theta_g, phi_g) = target_point(theta_p, z, s, phi, a_th, a_ph, naive)
     still = d == 0

@@ -25,6 +25,7 @@ SIGNATURES = {
     "tl_plan_batch_launches": (ctypes.c_longlong, [_P, ctypes.c_int, ctypes.c_int]),
     "tl_plan_device_error": (ctypes.c_int, [_P]),
     "tl_plan_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "tl_plan_set_lmax_phi": (ctypes.c_int, [_P, ctypes.c_int]),
     "tl_synth_derivs": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P]),
     "tl_deflection": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "tl_lens": (ctypes.c_int, [_P] * 9),

@@ -41,7 +41,8 @@ class Plan:
     """A (nside, lmax, order) geometry with its device tables and workspace."""
 
     def __init__(self, nside: int, lmax: int, order: int, pol: bool = True,
-                 precision: int = FP64, rotate: bool = True, naive: bool = False, expand_at_pixel: bool = False):
+                 precision: int = FP64, rotate: bool = True, naive: bool = False, expand_at_pixel: bool = False,
+                 lmax_phi: int | None = None):
         L = _lib.lib()
         self.nside, self.lmax, self.order, self.pol, self.precision = nside, lmax, order, pol, precision
         self.npix = 12 * nside * nside
@@ -56,6 +57,15 @@ class Plan:
         self._h = h
         self.nmaps = L.tl_plan_maps_per_field(h)
         self.batch = L.tl_plan_batch(h)  # realisations per Legendre launch in lens_batch
+        self.lmax_phi = lmax
+        if lmax_phi is not None and lmax_phi != lmax:
+            self.set_lmax_phi(lmax_phi)
+
+    def set_lmax_phi(self, lmax_phi: int):
+        """tl_plan_set_lmax_phi: the potential's own band limit (its coefficients then
+        come in that layout)."""
+        check(_lib.lib().tl_plan_set_lmax_phi(self._h, lmax_phi), "tl_plan_set_lmax_phi")
+        self.lmax_phi = lmax_phi
 
     def batch_launches(self, nreal, with_phi=True):
         """Kernel launches lens_batch makes for nreal realisations."""

@@ -30,7 +30,8 @@ size_t tc_desc_bytes();
 cudaError_t launch_legendre_tc_persistent(int nder, int precision, const void *descs, const void *items, int nitems,
                                           int *counter, int grid, cudaStream_t s);
 tl_status lens_stage_after_legendre(tl_plan *p, int nreal, bool phi, void *const *To, void *const *Qo,
-                                    void *const *Uo, cudaStream_t s);
+                                    void *const *Uo, cudaStream_t s,
+                                    const double *const *aP);
 }  // namespace tl
 
 using namespace tl;
@@ -316,7 +317,7 @@ static tl_status batch_pass(tl_batch *b, int mode, const double *const *aT, cons
         Q2[r] = pol ? Qo[i] : nullptr;
         U2[r] = pol ? Uo[i] : nullptr;
       }
-      tl_status st = lens_stage_after_legendre(b->plans[g], cnt, phi, T2, Q2, U2, s);
+      tl_status st = lens_stage_after_legendre(b->plans[g], cnt, phi, T2, Q2, U2, s, nullptr);
       if (st != TL_OK) return st;
     }
   }

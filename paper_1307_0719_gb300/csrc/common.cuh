@@ -57,6 +57,8 @@ struct FftGroup {
 
 struct tl_plan {
   int nside, lmax, mmax, order, spins, precision, flags;
+  int lmax_phi;          // band limit of the lensing potential (lmax unless set)
+  tl_plan *phi_plan;     // its deflection plan when lmax_phi != lmax (else nullptr)
   int nrings;
   long long npix;
   int nmaps;      // maps per field
@@ -143,6 +145,16 @@ __host__ __device__ __forceinline__ long long d3_pix(long long p, long long tile
   return (p >> kD3TileLg) * tile_stride + (p & (kD3Tile - 1));
 }
 
+// Coefficient planes written by the tensor-core Legendre stage interleave four rings
+// per 32-byte sector, element (ring r, order m) at ((r / 4) (mmax + 1) + m) 4 + r mod 4,
+// so that a warp of consecutive rings stores whole sectors (a plain [ring][m] row
+// would take one partial sector per ring); such a plane has a multiple of 4 rows.
+// The SIMT stages and the adjoint keep plain [ring][m] rows.
+__host__ __device__ __forceinline__ int d7_rows_il(int nrings) { return (nrings + 3) & ~3; }
+__host__ __device__ __forceinline__ size_t d7_il(int r, int m, size_t ld) {
+  return ((size_t)(r >> 2) * ld + (size_t)m) * 4 + (size_t)(r & 3);
+}
+
 // One output map of the ring FFT stage.
 struct MapJob {
   int plane;       // which D7 plane set: 0 = T, 1 = Q, 2 = U, 3 = phi
@@ -151,6 +163,7 @@ struct MapJob {
   double scale;    // multiplies d_theta^j d_phi^k (after undoing the 1/L^j, L^k normalisation)
   void *out;       // plain: [npix] map; tiled: the map's first element m * kD3Tile of the tile layout
   long long tile;  // 0: plain layout; else elements between tiles (maps x kD3Tile)
+  int il;          // the plane's rows are four-ring interleaved (tensor-core stage output)
 };
 cudaError_t launch_ringfft(const tl_plan *p, const MapJob *jobs, int njobs, int nder_planes,
                            cudaStream_t s);

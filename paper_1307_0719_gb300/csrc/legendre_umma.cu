@@ -230,6 +230,7 @@ struct TcDesc {
   const unsigned char *b;        // per block: coefficient tile hi [NC x 8] then lo
   float2 *d7a, *d7b;             // spin 0: the field's planes; spin 2: Q, U planes
   long long rstride;             // T2 elements between realisations' planes
+  int prows;                     // rows of a plane (the rings rounded up to 4: interleaved layout)
   int *err;                      // set to 1 when a wait times out
   // start table (plan-time, tcstart_kernel): per unit m * nrblk + rblk the first
   // 8-l block in which one of its rings contributes, and every ring's recurrence
@@ -594,7 +595,7 @@ __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsign
           const float s2r = xch[partner * 16 + 2 * rho], s2i = xch[partner * 16 + 2 * rho + 1];
           const float ar = s1r + sg * s2r, ai = s1i + sg * s2i;
           const float br = s1r - sg * s2r, bi = s1i - sg * s2i;
-          const size_t o = (size_t)(8 * h + rho) * D.rstride + ((size_t)j * D.nrings + r) * ld + m;
+          const size_t o = (size_t)(8 * h + rho) * D.rstride + (size_t)j * D.prows * ld + d7_il(r, m, ld);
           D.d7a[o] = make_float2(-0.5f * ar, -0.5f * ai);
           D.d7b[o] = make_float2(-0.5f * bi, 0.5f * br);
         }
@@ -634,9 +635,9 @@ __device__ __forceinline__ void u0_unit(const TcDesc &D, int m, int rblk, unsign
 #pragma unroll
         for (int rho = 0; rho < 8; ++rho) {
           if (8 * h + rho >= D.nreal) break;
-          const size_t o = (size_t)(8 * h + rho) * D.rstride + (size_t)j * D.nrings * ld + m;
-          D.d7a[o + (size_t)r * ld] = make_float2(v[4 * rho], v[4 * rho + 1]);
-          if (rs != r) D.d7a[o + (size_t)rs * ld] = make_float2(sg * v[4 * rho + 2], sg * v[4 * rho + 3]);
+          const size_t o = (size_t)(8 * h + rho) * D.rstride + (size_t)j * D.prows * ld;
+          D.d7a[o + d7_il(r, m, ld)] = make_float2(v[4 * rho], v[4 * rho + 1]);
+          if (rs != r) D.d7a[o + d7_il(rs, m, ld)] = make_float2(sg * v[4 * rho + 2], sg * v[4 * rho + 3]);
         }
       }
     }
@@ -1025,6 +1026,7 @@ static TcDesc make_desc(const tl_plan *p, int which, int nreal, const void *btil
   D.d7a = (float2 *)d7a;
   D.d7b = (float2 *)d7b;
   D.rstride = rstride;
+  D.prows = d7_rows_il(p->nrings);
   D.err = p->dev_err;
   D.nrblk = tc_ring_blocks(p, spin);
   D.bstart = which == 2 ? p->tc_bs2 : which == 1 ? p->tc_bsp : p->tc_bs0;

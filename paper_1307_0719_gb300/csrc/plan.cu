@@ -77,6 +77,10 @@ static cudaError_t dalloc(void **p, size_t b, size_t *bytes) {
 
 static void free_plan(tl_plan *p) {
   if (!p) return;
+  if (p->phi_plan) {
+    free_plan(p->phi_plan);
+    p->phi_plan = nullptr;
+  }
   void *ptrs[] = {p->ring.z, p->ring.sint, p->ring.theta, p->ring.phi0, p->ring.dphi, p->ring.omza, p->ring.rsinf, p->ring.ringf,
                   p->ring.log2_sh, p->ring.log2_ch,
                   p->ring.dls, p->ring.dlc, p->ring.nphi, p->ring.inorth, p->ring.first, p->blue.spec,
@@ -101,6 +105,7 @@ static void free_plan(tl_plan *p) {
 
 static tl_status create_impl(int nside, int lmax, int order, int spins, int precision, int flags, tl_plan *p) {
   p->nside = nside; p->lmax = lmax; p->mmax = lmax; p->order = order; p->spins = spins;
+  p->lmax_phi = lmax;
   p->precision = precision; p->flags = flags;
   p->nrings = 4 * nside - 1;
   p->npix = 12LL * nside * nside;
@@ -175,14 +180,17 @@ static tl_status create_impl(int nside, int lmax, int order, int spins, int prec
   // workspace
   const long long na = nalm(lmax);
   const size_t t2 = e2, rec0 = 4 * (size_t)p->elem, rec2 = 8 * (size_t)p->elem;
-  const size_t plane = (size_t)p->nrings * (p->mmax + 1) * t2;
   const bool pol = (spins & TL_SPIN_QU) != 0;
   const bool tc = (precision == TL_MIXED_TF32 || precision == TL_MIXED_TF32x3 || precision == TL_MIXED_BF16x3);
+  // tensor-core plans: the planes' rows rounded up to 4 (the stage writes them four-ring
+  // interleaved; the SIMT stages and the adjoint use the first nrings rows plainly)
+  const int prows = tc ? d7_rows_il(p->nrings) : p->nrings;
+  const size_t plane = (size_t)prows * (p->mmax + 1) * t2;
   p->tc_nder = order > 1 ? order : 1;
   p->batch = tc ? tc_realisations(p->tc_nder) : 1;
   const int nplanes = tc ? p->tc_nder + 1 : order + 1;  // D7 planes per field and realisation
-  p->d7_rstride = (long long)nplanes * p->nrings * (p->mmax + 1);
-  p->d7p_rstride = 2LL * p->nrings * (p->mmax + 1);
+  p->d7_rstride = (long long)nplanes * prows * (p->mmax + 1);
+  p->d7p_rstride = 2LL * prows * (p->mmax + 1);
   TRY_CUDA(dalloc(&p->tab0, t2 * na, B));
   TRY_CUDA(launch_steptab(p, 0, p->tab0, 0));
   TRY_CUDA(dalloc(&p->rec_T, rec0 * na, B));
@@ -268,7 +276,7 @@ extern "C" tl_status tl_plan_create(int nside, int lmax, int order, int spins, i
                                     tl_plan **out) {
   if (!out) return TL_ERR_ARG;
   if (nside < 1 || nside > 8192 || (nside & (nside - 1)) != 0) return TL_ERR_ARG;
-  if (lmax < 1 || lmax > 4 * nside) return TL_ERR_ARG;
+  if (lmax < 1 || lmax > 8 * nside) return TL_ERR_ARG;  // 8 nside: the paper's gradient band limit
   if (order < 0 || order > TL_MAX_ORDER) return TL_ERR_ARG;
   if (spins != TL_SPIN_T && spins != (TL_SPIN_T | TL_SPIN_QU)) {
     return (spins == TL_SPIN_QU) ? TL_ERR_UNSUPPORTED : TL_ERR_ARG;
@@ -310,7 +318,9 @@ extern "C" tl_status tl_plan_destroy(tl_plan *p) {
   return TL_OK;
 }
 
-extern "C" size_t tl_plan_workspace_bytes(const tl_plan *p) { return p ? p->bytes : 0; }
+extern "C" size_t tl_plan_workspace_bytes(const tl_plan *p) {
+  return p ? p->bytes + (p->phi_plan ? p->phi_plan->bytes : 0) : 0;
+}
 
 extern "C" tl_status tl_plan_device_error(tl_plan *p) {
   if (!p) return TL_ERR_ARG;
@@ -336,14 +346,17 @@ extern "C" int tl_plan_batch(const tl_plan *p) { return p ? p->batch : 0; }
 
 extern "C" long long tl_plan_batch_launches(const tl_plan *p, int nreal, int with_phi) {
   if (!p || nreal < 0) return -1;
-  const bool pol = (p->spins & TL_SPIN_QU) != 0, phi = with_phi != 0;
+  const bool pol = (p->spins & TL_SPIN_QU) != 0;
   const long long G = p->fft_ngroups;  // one ring-FFT launch per ring group
+  // a potential with its own band limit: prep, Legendre and FFT on its plan per realisation
+  const long long sub = (with_phi && p->phi_plan) ? 2 + p->phi_plan->fft_ngroups : 0;
+  const bool phi = with_phi != 0 && !p->phi_plan;
   if (p->batch > 1) {
     // per batch: coefficient tiles and Legendre launch of T, the potential and Q/U
     const long long chunks = (nreal + p->batch - 1) / p->batch;
     const long long per_chunk = 2 + (phi ? 2 : 0) + (pol ? 2 : 0);
     // per realisation: deflection FFT, derivative-map FFT, gather and its double pass
-    return chunks * per_chunk + (long long)nreal * ((phi ? G : 0) + G + 2);
+    return chunks * per_chunk + (long long)nreal * ((phi ? G : 0) + G + 2 + sub);
   }
   const bool fuse = phi && p->order >= 1;
   long long per = 0;
@@ -352,7 +365,7 @@ extern "C" long long tl_plan_batch_launches(const tl_plan *p, int nreal, int wit
   if (fuse) per += G;              // deflection FFT
   if (pol) per += 2;               // spin-2 prep, Legendre
   per += G + (p->precision == TL_FP64 ? 1 : 2);  // derivative-map FFT, gather (float: and its double pass)
-  return (long long)nreal * per;
+  return (long long)nreal * (per + sub);
 }
 
 // ---------------------------------------------------------------------------
@@ -363,9 +376,10 @@ static void mark(tl_plan *p, int i, cudaStream_t s) {
 }
 
 // alpha from the phi planes (j = 0, 1) already in d7_P
-static tl_status deflection_fft(tl_plan *p, void *ath, void *aph, cudaStream_t s) {
+// il: the phi planes come from the tensor-core stage (four-ring interleaved rows)
+static tl_status deflection_fft(tl_plan *p, void *ath, void *aph, cudaStream_t s, int il = 0) {
   const double L = deriv_norm(p);
-  MapJob jobs[2] = {{3, 1, 0, 0, L, ath}, {3, 0, 1, 1, L, aph}};
+  MapJob jobs[2] = {{3, 1, 0, 0, L, ath, 0, il}, {3, 0, 1, 1, L, aph, 0, il}};
   TRY_CUDA(launch_ringfft(p, jobs, 2, 2, s));
   return TL_OK;
 }
@@ -377,10 +391,51 @@ static tl_status deflection_impl(tl_plan *p, const double *alm_phi, void *ath, v
   return deflection_fft(p, ath, aph, s);
 }
 
+// the plan's deflection: on its own plan at lmax_phi when one is set
+static tl_status plan_deflection(tl_plan *p, const double *alm_phi, void *ath, void *aph, cudaStream_t s) {
+  return deflection_impl(p->phi_plan ? p->phi_plan : p, alm_phi, ath, aph, s);
+}
+
 extern "C" tl_status tl_deflection(tl_plan *p, const double *alm_phi, void *ath, void *aph, void *stream) {
   if (!p || !alm_phi || !ath || !aph) return TL_ERR_ARG;
   if (!aligned16(alm_phi) || !aligned16(ath) || !aligned16(aph)) return TL_ERR_ARG;
-  return deflection_impl(p, alm_phi, ath, aph, (cudaStream_t)stream);
+  return plan_deflection(p, alm_phi, ath, aph, (cudaStream_t)stream);
+}
+
+// Sec. II.A: the gradient of the potential is taken to its own band limit
+// (min(8 Nside, 10000) in the paper). A separate deflection plan at lmax_phi (order
+// 1, temperature only; single-precision SIMT form for the mixed forms, FP64 for FP64)
+// then supplies alpha; lmax_phi = lmax removes it.
+extern "C" tl_status tl_plan_set_lmax_phi(tl_plan *p, int lmax_phi) {
+  if (!p || lmax_phi < 1) return TL_ERR_ARG;
+  if (lmax_phi == p->lmax_phi) return TL_OK;
+  TRY_CUDA(cudaDeviceSynchronize());  // queued work may still read the old plan or the staging
+  if (p->phi_plan) {
+    free_plan(p->phi_plan);
+    p->phi_plan = nullptr;
+  }
+  // host-call staging is laid out for the potential's coefficient count
+  const size_t slot_old = 3 * (size_t)nalm(p->lmax) * 16 + (size_t)nalm(p->lmax_phi) * 16;
+  if (p->stage_alm) {
+    cudaFree(p->stage_alm);
+    p->bytes -= slot_old * (size_t)p->stage_cap;
+    p->stage_alm = nullptr;
+  }
+  if (p->stage_out) {
+    cudaFree(p->stage_out);
+    p->bytes -= 3 * (size_t)p->elem * (size_t)p->npix * (size_t)p->stage_cap;
+    p->stage_out = nullptr;
+  }
+  p->stage_cap = 0;
+  p->lmax_phi = p->lmax;
+  if (lmax_phi == p->lmax) return TL_OK;
+  tl_plan *q = nullptr;
+  const int prec = p->precision == TL_FP64 ? TL_FP64 : TL_MIXED_FP32;
+  tl_status st = tl_plan_create(p->nside, lmax_phi, 1, TL_SPIN_T, prec, 0, &q);
+  if (st != TL_OK) return st;
+  p->phi_plan = q;
+  p->lmax_phi = lmax_phi;
+  return TL_OK;
 }
 
 static double fact(int n) {
@@ -441,7 +496,7 @@ extern "C" tl_status tl_synth_derivs(tl_plan *p, const double *alm, int spin, vo
 }
 
 // ring FFTs into Taylor-ready maps d_th^j d_ph^k s / (j! k! L^(j+k)) for one realisation
-static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s) {
+static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s, int il) {
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
   std::vector<MapJob> jobs;
   // Jobs are packed two per transform in list order. Q and U of the same (j, k)
@@ -456,11 +511,12 @@ static tl_status lens_fft(tl_plan *p, const void *const *planes, cudaStream_t s)
       for (int j = 0; j <= n; ++j)
         for (int g = 1; g < 3; ++g) {
           int k = n - j;
-          jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)), out(g * p->nmaps + n * (n + 1) / 2 + j), tile});
+          jobs.push_back(MapJob{g, j, k, 0, 1.0 / (fact(j) * fact(k)), out(g * p->nmaps + n * (n + 1) / 2 + j), tile,
+                                il});
         }
   for (const std::pair<int, int> &jk : paired_order(p->order))
     jobs.push_back(MapJob{0, jk.first, jk.second, 0, 1.0 / (fact(jk.first) * fact(jk.second)),
-                          out((jk.first + jk.second) * (jk.first + jk.second + 1) / 2 + jk.first), tile});
+                          out((jk.first + jk.second) * (jk.first + jk.second + 1) / 2 + jk.first), tile, il});
   TRY_CUDA(launch_ringfft_planes(p, planes, jobs.data(), (int)jobs.size(), s));
   return TL_OK;
 }
@@ -469,7 +525,7 @@ namespace tl {
 // After the tensor-core Legendre stage of nreal realisations: per realisation the
 // deflection's and the fields' ring FFTs, then the gather into the outputs.
 tl_status lens_stage_after_legendre(tl_plan *p, int nreal, bool phi, void *const *To, void *const *Qo,
-                                    void *const *Uo, cudaStream_t s) {
+                                    void *const *Uo, cudaStream_t s, const double *const *aP) {
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
   const size_t mapb = (size_t)p->elem * p->npix;
   const size_t t2 = 2 * (size_t)p->elem;
@@ -483,12 +539,15 @@ tl_status lens_stage_after_legendre(tl_plan *p, int nreal, bool phi, void *const
                                pol ? (char *)p->d7_U + off : nullptr, (char *)p->d7_P + offp};
       if (phi) {
         const double L = deriv_norm(p);
-        MapJob jobs[2] = {{3, 1, 0, 0, L, ath}, {3, 0, 1, 1, L, aph}};
+        MapJob jobs[2] = {{3, 1, 0, 0, L, ath, 0, 1}, {3, 0, 1, 1, L, aph, 0, 1}};
         TRY_CUDA(launch_ringfft_planes(p, planes, jobs, 2, s));
+      } else if (aP && aP[r] && p->phi_plan) {
+        tl_status st = plan_deflection(p, aP[r], ath, aph, s);
+        if (st != TL_OK) return st;
       } else {
         TRY_CUDA(cudaMemsetAsync(p->alpha, 0, 2 * mapb, s));
       }
-      tl_status st = lens_fft(p, planes, s);
+      tl_status st = lens_fft(p, planes, s, 1);
       if (st != TL_OK) return st;
       if (tm) cudaEventRecord(p->evr[3 * r + 1], s);
       TRY_CUDA(launch_gather(p, p->alpha, p->d3, To[r], pol ? Qo[r] : nullptr, pol ? Uo[r] : nullptr, s));
@@ -509,7 +568,9 @@ static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, cons
   const size_t mapb = (size_t)p->elem * p->npix;
   const size_t t2 = 2 * (size_t)p->elem;
   void *ath = p->alpha, *aph = (char *)p->alpha + mapb;
-  const bool phi = aP[0] != nullptr;
+  // the potential runs through the plan's own Legendre stage unless it has its own
+  // band limit (then its deflection plan supplies alpha per realisation)
+  const bool phi = aP[0] != nullptr && !p->phi_plan;
   p->nstage = 0;
   mark(p, 0, s);
   if (p->batch > 1) {
@@ -527,7 +588,7 @@ static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, cons
     if (pol) TRY_CUDA(launch_legendre_spin2_tc(p, p->tc_nder, nreal, p->d7_Q, p->d7_U, p->d7_rstride, s));
     mark(p, 5, s);
     {
-      tl_status st = lens_stage_after_legendre(p, nreal, phi, To, Qo, Uo, s);
+      tl_status st = lens_stage_after_legendre(p, nreal, phi, To, Qo, Uo, s, aP);
       if (st != TL_OK) return st;
     }
     mark(p, 6, s);
@@ -540,9 +601,9 @@ static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, cons
   const double *alm_phi = aP[0];
   // 1. spin-0 Legendre stage: T with all derivative orders; the lensing potential
   //    shares its basis for j <= 1 (needs order >= 1, else it runs on its own)
-  const bool fuse = alm_phi && p->order >= 1;
+  const bool fuse = alm_phi && p->order >= 1 && !p->phi_plan;
   if (alm_phi && !fuse) {
-    tl_status st = deflection_impl(p, alm_phi, ath, aph, s);
+    tl_status st = plan_deflection(p, alm_phi, ath, aph, s);
     if (st != TL_OK) return st;
   }
   TRY_CUDA(launch_prep_spin0(p, alm_T, fuse ? alm_phi : nullptr, s));
@@ -564,7 +625,7 @@ static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, cons
   mark(p, 5, s);
   // 4. ring FFTs
   const void *planes[4] = {p->d7_T, p->d7_Q, p->d7_U, p->d7_P};
-  tl_status st = lens_fft(p, planes, s);
+  tl_status st = lens_fft(p, planes, s, 0);
   if (st != TL_OK) return st;
   mark(p, 6, s);
   // 5. gather + Taylor + rotate
@@ -648,20 +709,23 @@ static tl_status forward_derivs(tl_plan *p, const double *alm_T, const double *a
       TRY_CUDA(launch_legendre_spin2(p, p->order, s));
     }
   }
+  // the tensor-core stage leaves its planes four-ring interleaved
+  const int il = p->batch > 1 ? 1 : 0;
   if (alm_phi && !defl_done) {
-    tl_status st = deflection_fft(p, ath, aph, s);
+    tl_status st = deflection_fft(p, ath, aph, s, il);
     if (st != TL_OK) return st;
   } else if (!alm_phi) {
     TRY_CUDA(cudaMemsetAsync(p->alpha, 0, 2 * mapb, s));
   }
   const void *planes[4] = {p->d7_T, p->d7_Q, p->d7_U, p->d7_P};
-  return lens_fft(p, planes, s);
+  return lens_fft(p, planes, s, il);
 }
 
 extern "C" tl_status tl_lens_adjoint(tl_plan *p, const double *alm_T, const double *alm_E, const double *alm_B,
                                      const double *alm_phi, const void *gT, const void *gQ, const void *gU,
                                      double *galm_T, double *galm_E, double *galm_B, double *galm_phi, void *galpha,
                                      void *stream) {
+  if (p && p->phi_plan) return TL_ERR_UNSUPPORTED;  // the potential's own band limit: forward only
   if (!p || !alm_T || !gT) return TL_ERR_ARG;
   if (p->flags & ~TL_ROTATE) return TL_ERR_UNSUPPORTED;  // the transpose of the default geometry only
   const bool pol = (p->spins & TL_SPIN_QU) != 0;
@@ -746,6 +810,8 @@ extern "C" tl_status tl_lens_batch_host(tl_plan *p, int nreal, const double *con
   cudaStream_t s = (cudaStream_t)stream;
   const long long na = nalm(p->lmax);
   const size_t ab = (size_t)na * 16, mapb = (size_t)p->elem * p->npix;
+  const size_t abp = (size_t)nalm(p->lmax_phi) * 16;  // the potential's coefficients
+  const size_t slot = 3 * ab + abp;                    // staging per realisation
   // device staging for one chunk of up to p->batch realisations (one Legendre launch
   // on tensor-core plans), grown on demand and kept by the plan
   const int cap = nreal < p->batch ? nreal : p->batch;
@@ -753,7 +819,7 @@ extern "C" tl_status tl_lens_batch_host(tl_plan *p, int nreal, const double *con
     if (p->stage_alm || p->stage_out) TRY_CUDA(cudaStreamSynchronize(s));
     if (p->stage_alm) {
       cudaFree(p->stage_alm);
-      p->bytes -= 4 * ab * (size_t)p->stage_cap;
+      p->bytes -= slot * (size_t)p->stage_cap;
       p->stage_alm = nullptr;
     }
     if (p->stage_out) {
@@ -762,7 +828,7 @@ extern "C" tl_status tl_lens_batch_host(tl_plan *p, int nreal, const double *con
       p->stage_out = nullptr;
     }
     p->stage_cap = 0;
-    TRY_CUDA(dalloc(&p->stage_alm, 4 * ab * (size_t)cap, &p->bytes));
+    TRY_CUDA(dalloc(&p->stage_alm, slot * (size_t)cap, &p->bytes));
     TRY_CUDA(dalloc(&p->stage_out, 3 * mapb * (size_t)cap, &p->bytes));
     p->stage_cap = cap;
   }
@@ -773,7 +839,7 @@ extern "C" tl_status tl_lens_batch_host(tl_plan *p, int nreal, const double *con
     void *oT[TL_MAX_BATCH], *oQ[TL_MAX_BATCH], *oU[TL_MAX_BATCH];
     for (int i = 0; i < n; ++i) {
       const int r = r0 + i;
-      char *a = (char *)p->stage_alm + 4 * ab * (size_t)i;
+      char *a = (char *)p->stage_alm + slot * (size_t)i;
       char *o = (char *)p->stage_out + 3 * mapb * (size_t)i;
       dT[i] = (const double *)a;
       dE[i] = pol ? (const double *)(a + ab) : nullptr;
@@ -785,7 +851,7 @@ extern "C" tl_status tl_lens_batch_host(tl_plan *p, int nreal, const double *con
       TRY_CUDA(cudaMemcpyAsync((void *)dT[i], alm_T[r], ab, cudaMemcpyHostToDevice, s));
       if (dE[i]) TRY_CUDA(cudaMemcpyAsync((void *)dE[i], alm_E[r], ab, cudaMemcpyHostToDevice, s));
       if (dB[i]) TRY_CUDA(cudaMemcpyAsync((void *)dB[i], alm_B[r], ab, cudaMemcpyHostToDevice, s));
-      if (dP[i]) TRY_CUDA(cudaMemcpyAsync((void *)dP[i], alm_phi[r], ab, cudaMemcpyHostToDevice, s));
+      if (dP[i]) TRY_CUDA(cudaMemcpyAsync((void *)dP[i], alm_phi[r], abp, cudaMemcpyHostToDevice, s));
     }
     tl_status st = tl_lens_batch(p, n, dT, pol ? dE : nullptr, pol ? dB : nullptr, dP, oT, pol ? oQ : nullptr,
                                  pol ? oU : nullptr, stream);

@@ -28,7 +28,16 @@ struct JobDev {
   float scalef;
   int k, div_sint;
   long long tile;  // output layout: 0 plain, else the tile stride (see d3_pix)
+  int il;          // input rows four-ring interleaved (element m at row[4 m])
 };
+
+// The ring's coefficient row in a plane and the element stride along m
+template <typename T2>
+__device__ __forceinline__ const T2 *job_row(const JobDev &J, int r, int mmax, int &fs) {
+  fs = J.il ? 4 : 1;
+  return J.il ? (const T2 *)J.in + (size_t)(r >> 2) * (size_t)(mmax + 1) * 4 + (r & 3)
+              : (const T2 *)J.in + (size_t)r * (mmax + 1);
+}
 #define TL_MAX_JOBS 96
 struct JobList {
   int n;
@@ -93,15 +102,15 @@ __device__ __forceinline__ T2 rot_ik(T2 a, int k) {
 template <typename T, typename T2>
 __device__ __forceinline__ void fold_pair(const T2 *__restrict__ FA, const T2 *__restrict__ FB, bool same,
                                           bool hasb, int t0, int mstep, int mmax, int kA, int kB, T invL,
-                                          bool shifted, int qstep_odd, T2 &ga, T2 &gb) {
+                                          bool shifted, int qstep_odd, T2 &ga, T2 &gb, int fs) {
   T2 aa, ab;
   aa.x = aa.y = ab.x = ab.y = (T)0;
   const int kmax = (hasb && kB > kA) ? kB : kA;
   int q = 0;
   for (int m = t0; m <= mmax; m += mstep, q += 1) {
-    const T2 fa = FA[m];
+    const T2 fa = FA[(size_t)m * fs];
     T2 fb = fa;
-    if (hasb && !same) fb = FB[m];
+    if (hasb && !same) fb = FB[(size_t)m * fs];
     const T mm = (T)m * invL;
     T w = (m > 0) ? (T)2 : (T)1;
     if (shifted && ((q * qstep_odd) & 1)) w = -w;
@@ -226,8 +235,9 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && !(REG && LG >= 12)) ? 
 
   const JobDev JA = jobs.job[ja];
   const JobDev JB = hasb ? jobs.job[jb] : jobs.job[ja];
-  const T2 *FA = (const T2 *)JA.in + (size_t)r * (mmax + 1);
-  const T2 *FB = (const T2 *)JB.in + (size_t)r * (mmax + 1);
+  int fs;
+  const T2 *FA = job_row<T2>(JA, r, mmax, fs);
+  const T2 *FB = job_row<T2>(JB, r, mmax, fs);
   const bool same = JA.in == JB.in;  // both maps from one coefficient plane (different k)
   // both packed maps are transformed in the normalised units of the Legendre stage
   // (similar magnitudes, so the shared transform's rounding does not leak from a
@@ -337,10 +347,10 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && !(REG && LG >= 12)) ? 
         const int tt = t0 + u * nth;
         const int tm = tt ? N - tt : 0;
         const bool lo = tt < ncls && tt <= mmax, hi = tt < ncls && tm <= mmax;
-        fa[u] = lo ? FA[tt] : zero;
-        fam[u] = hi ? FA[tm] : zero;
-        fb[u] = (hasb && !same && lo) ? FB[tt] : fa[u];
-        fbm[u] = (hasb && !same && hi) ? FB[tm] : fam[u];
+        fa[u] = lo ? FA[(size_t)tt * fs] : zero;
+        fam[u] = hi ? FA[(size_t)tm * fs] : zero;
+        fb[u] = (hasb && !same && lo) ? FB[(size_t)tt * fs] : fa[u];
+        fbm[u] = (hasb && !same && hi) ? FB[(size_t)tm * fs] : fam[u];
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -358,8 +368,8 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && !(REG && LG >= 12)) ? 
       const int tm = tt ? N - tt : 0;
       const int m0 = tt + c * N, m1 = tm + c * N, step = C * N;
       T2 Ba, Bb, Bam, Bbm;
-      fold_pair<T, T2>(FA, FB, same, hasb, m0, step, mmax, JA.k, JB.k, invL, shifted, C, Ba, Bb);
-      fold_pair<T, T2>(FA, FB, same, hasb, m1, step, mmax, JA.k, JB.k, invL, shifted, C, Bam, Bbm);
+      fold_pair<T, T2>(FA, FB, same, hasb, m0, step, mmax, JA.k, JB.k, invL, shifted, C, Ba, Bb, fs);
+      fold_pair<T, T2>(FA, FB, same, hasb, m1, step, mmax, JA.k, JB.k, invL, shifted, C, Bam, Bbm, fs);
       if (!hasb) Bb.x = Bb.y = Bbm.x = Bbm.y = (T)0;
       finish(tt, c, Ba, Bam, Bb, Bbm);
     }
@@ -472,8 +482,9 @@ __global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
   const bool shifted = __double_as_longlong(rt.phi0[r]) != 0;
   const JobDev JA = jobs.job[ja];
   const JobDev JB = hasb ? jobs.job[jb] : jobs.job[ja];
-  const float2 *FA = (const float2 *)JA.in + (size_t)r * (mmax + 1);
-  const float2 *FB = (const float2 *)JB.in + (size_t)r * (mmax + 1);
+  int fs;
+  const float2 *FA = job_row<float2>(JA, r, mmax, fs);
+  const float2 *FB = job_row<float2>(JB, r, mmax, fs);
   const bool same = JA.in == JB.in;
   const float inv_s = rt.rsinf[r];
   float wa = JA.div_sint ? inv_s : 1.0f;
@@ -528,7 +539,7 @@ __global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
     for (int c = 0; c < 16; ++c) {
       const int t = h + TG * c;
       const int m = c < 8 ? t : N - t;
-      x[c] = m <= mmax ? __ldg(FA + m) : zero;
+      x[c] = m <= mmax ? __ldg(FA + (size_t)m * fs) : zero;
     }
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
@@ -545,7 +556,7 @@ __global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
       const float2 d0 = comb(0, f0, f0, -1.0f);
       x[0] = f2(x[0].x + d0.x, x[0].y - d0.y);
       if (HALF <= mmax) {
-        const float2 fa = __ldg(FA + HALF);
+        const float2 fa = __ldg(FA + (size_t)HALF * fs);
         x[8] = cadd(x[8], comb(HALF, fa, fa, 1.0f));
       }
     }
@@ -559,8 +570,8 @@ __global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
         const int t = h + TG * (8 * half + u);
         const int m = half ? N - t : t;
         const bool ok = m <= mmax;
-        va[u] = ok ? __ldg(FA + m) : zero;
-        vb[u] = (ok && !same) ? __ldg(FB + m) : va[u];
+        va[u] = ok ? __ldg(FA + (size_t)m * fs) : zero;
+        vb[u] = (ok && !same) ? __ldg(FB + (size_t)m * fs) : va[u];
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -579,8 +590,8 @@ __global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
       x[0] = f2(x[0].x + d0.x, x[0].y - d0.y);
       // t = N/2: class N/2's own term m = N/2
       if (HALF <= mmax) {
-        const float2 fa = __ldg(FA + HALF);
-        x[8] = cadd(x[8], comb(HALF, fa, same ? fa : __ldg(FB + HALF), 1.0f));
+        const float2 fa = __ldg(FA + (size_t)HALF * fs);
+        x[8] = cadd(x[8], comb(HALF, fa, same ? fa : __ldg(FB + (size_t)HALF * fs), 1.0f));
       }
     }
   } else {
@@ -591,12 +602,12 @@ __global__ void __launch_bounds__(1 << (LG - 4), 1024 >> (LG - 4))
       const int m2 = t ? N - t : 0;
       float2 z = zero;
       if (t <= mmax) {
-        const float2 fa = __ldg(FA + t);
-        z = comb(t, fa, same ? fa : __ldg(FB + t), 1.0f);
+        const float2 fa = __ldg(FA + (size_t)t * fs);
+        z = comb(t, fa, same ? fa : __ldg(FB + (size_t)t * fs), 1.0f);
       }
       if (m2 <= mmax) {
-        const float2 fa = __ldg(FA + m2);
-        const float2 d = comb(m2, fa, same ? fa : __ldg(FB + m2), -1.0f);
+        const float2 fa = __ldg(FA + (size_t)m2 * fs);
+        const float2 d = comb(m2, fa, same ? fa : __ldg(FB + (size_t)m2 * fs), -1.0f);
         const float s2 = t ? sg : 1.0f;
         z.x = fmaf(s2, d.x, z.x);
         z.y = fmaf(-s2, d.y, z.y);
@@ -1073,10 +1084,11 @@ static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const 
   JobList jl;
   if (njobs > TL_MAX_JOBS) return cudaErrorInvalidValue;
   jl.n = njobs;
-  const size_t plane_len = (size_t)p->nrings * (p->mmax + 1);
   for (int i = 0; i < njobs; ++i) {
     if (jobs[i].plane < 0 || jobs[i].plane > 3) return cudaErrorInvalidValue;
+    const size_t plane_len = (size_t)(jobs[i].il ? d7_rows_il(p->nrings) : p->nrings) * (p->mmax + 1);
     jl.job[i].in = (const typename RealTraits<T>::T2 *)planes[jobs[i].plane] + (size_t)jobs[i].j * plane_len;
+    jl.job[i].il = jobs[i].il;
     jl.job[i].k = jobs[i].k;
     jl.job[i].div_sint = jobs[i].div_sint;
     jl.job[i].scale = jobs[i].scale;

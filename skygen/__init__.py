@@ -141,6 +141,9 @@ WORKLOADS = {
     "nside512_lmax1024_n4_TQU": Workload("nside512_lmax1024_n4_TQU", 512, 1024, 4, True, 100.0, 800.0, 2, 3, 4),
     # Nside 2048, lmax 4096, order 4 (2..6 swept), T+Q/U, damping scales x4
     "nside2048_lmax4096_n4_TQU": Workload("nside2048_lmax4096_n4_TQU", 2048, 4096, 4, True, 400.0, 3200.0, 2, 3, 4),
+    # Nside 2048, lmax 4096, order 4, temperature only: the full-size ring FFT and gather
+    # kernels in a few GB (profiling)
+    "nside2048_lmax4096_n4_T": Workload("nside2048_lmax4096_n4_T", 2048, 4096, 4, False, 400.0, 3200.0, 2, 3, 4),
     # Nside 1024, lmax 2048, order 4: differentiation workload (targets from seed 9000)
     "nside1024_lmax2048_n4_TQU": Workload("nside1024_lmax2048_n4_TQU", 1024, 2048, 4, True, 400.0, 3200.0, 2, 3, 4),
 }

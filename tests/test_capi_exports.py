@@ -38,7 +38,7 @@ def test_host_argument_checks(lib):
     from paper_1307_0719_gb300 import _lib as L
     h = ctypes.c_void_p()
     assert lib.tl_plan_create(3, 4, 1, 1, 0, 1, ctypes.byref(h)) == L.TL_ERR_ARG      # nside not 2^k
-    assert lib.tl_plan_create(4, 17, 1, 1, 0, 1, ctypes.byref(h)) == L.TL_ERR_ARG     # lmax > 4 nside
+    assert lib.tl_plan_create(4, 33, 1, 1, 0, 1, ctypes.byref(h)) == L.TL_ERR_ARG     # lmax > 8 nside
     assert lib.tl_plan_create(4, 8, 7, 1, 0, 1, ctypes.byref(h)) == L.TL_ERR_ARG      # order > 6
     assert lib.tl_plan_create(4, 8, 2, 1, 9, 1, ctypes.byref(h)) == L.TL_ERR_ARG      # precision
     assert lib.tl_plan_create(4, 8, 2, L.TL_SPIN_QU, 0, 1, ctypes.byref(h)) == L.TL_ERR_UNSUPPORTED  # Q/U alone
@@ -52,6 +52,7 @@ def test_host_argument_checks(lib):
     assert lib.tl_lens(None, None, None, None, None, None, None, None, None) == L.TL_ERR_ARG
     assert lib.tl_plan_destroy(None) == L.TL_OK
     assert lib.tl_plan_set_wait_limit(None, 0, 0) == L.TL_ERR_ARG
+    assert lib.tl_plan_set_lmax_phi(None, 100) == L.TL_ERR_ARG
     assert lib.tl_lens_batch_host(None, 1, None, None, None, None, None, None, None, None) == L.TL_ERR_ARG
     assert lib.tl_plan_workspace_bytes(None) == 0
     assert lib.tl_status_string(L.TL_ERR_ARG) == b"invalid argument"

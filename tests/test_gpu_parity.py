@@ -249,3 +249,63 @@ def test_adjoint_refuses_geometry_options():
     finally:
         torch.cuda.synchronize()
         plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("FP64", 1e-10), ("MIXED_FP32", 1e-4), ("MIXED_BF16x3", 1e-4)])
+def test_lens_with_own_lmax_phi_vs_oracle(precision, tol):
+    """The potential at its own band limit, the paper's min(8 Nside, 10000) (Sec. II.A):
+    single calls, a batch (on the tensor-core forms: the realisations' Legendre launch
+    without the potential, alpha from the deflection plan per realisation) and the
+    deflection alone, against the oracle at the same lmax_phi; lmax_phi = lmax again
+    restores the plain plan."""
+    import skygen
+    nside, lmax, order = 16, 32, 3
+    lp = 8 * nside
+    s = sky(nside, lmax, pol=True, b_scale=0.4)
+    phi = skygen.make_sky(nside, lp, False, 0, 0, 5)["phi"] * 3.0
+    ref = OL.lens(nside, lmax, order, s["T"], s["E"], s["B"], phi, lmax_phi=lp)
+    a_th, a_ph = OL.deflection(nside, lp, phi)
+    d = to_dev(s)
+    dphi = torch.from_numpy(phi).cuda()
+    plan = api.Plan(nside, lmax, order, pol=True, precision=getattr(api, precision), lmax_phi=lp)
+    try:
+        one = plan.lens(d["T"], d["E"], d["B"], dphi).cpu().numpy()
+        two = plan.lens_batch([dict(T=d["T"], E=d["E"], B=d["B"], phi=dphi)] * 2)
+        al = plan.deflection(dphi).cpu().numpy()
+        plan.set_lmax_phi(lmax)
+        back = plan.lens(d["T"], d["E"], d["B"], d["phi"]).cpu().numpy()
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    for i, f in enumerate("TQU"):
+        assert rel_rms(one[i], ref[f]) < tol, (f, rel_rms(one[i], ref[f]))
+        for o in two:
+            assert rel_rms(o[i].cpu().numpy(), ref[f]) < tol, (f, "batch")
+    assert rel_rms(al[0], a_th) < tol and rel_rms(al[1], a_ph) < tol
+    plain = OL.lens(nside, lmax, order, s["T"], s["E"], s["B"], s["phi"])
+    for i, f in enumerate("TQU"):
+        assert rel_rms(back[i], plain[f]) < tol, (f, "lmax_phi reset")
+
+
+def test_lmax_phi_host_call_and_adjoint_refusal():
+    """The host-buffer batch call stages the potential at its own coefficient count;
+    the adjoint is refused while a separate lmax_phi is set."""
+    import skygen
+    nside, lmax, lp = 16, 32, 80
+    s = sky(nside, lmax, pol=True, b_scale=0.4)
+    phi = skygen.make_sky(nside, lp, False, 0, 0, 6)["phi"] * 3.0
+    plan = api.Plan(nside, lmax, 2, pol=True, precision=api.MIXED_FP32, lmax_phi=lp)
+    try:
+        d = to_dev(s)
+        dphi = torch.from_numpy(phi).cuda()
+        dev = plan.lens(d["T"], d["E"], d["B"], dphi).cpu().numpy()
+        host = plan.lens_batch_host([{k: torch.from_numpy(v) for k, v in
+                                      dict(T=s["T"], E=s["E"], B=s["B"], phi=phi).items()}])[0].numpy()
+        assert np.array_equal(dev, host)
+        g = torch.ones(plan.npix, device="cuda", dtype=plan.dtype)
+        with pytest.raises(api._lib.TaylensError) as ei:
+            plan.lens_adjoint(d["T"], d["E"], d["B"], dphi, g, g, g)
+        assert ei.value.status == api._lib.TL_ERR_UNSUPPORTED
+    finally:
+        torch.cuda.synchronize()
+        plan.close()

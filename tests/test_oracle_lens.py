@@ -370,3 +370,35 @@ def test_anafast_single_modes():
     y = _single_mode(lmax, 6, 3, 2.0j)
     assert np.allclose(L.anafast(lmax, x), np.where(np.arange(lmax + 1) == 6, 2 * 1.0 / 13, 0.0))
     assert np.allclose(L.anafast(lmax, x, y), np.where(np.arange(lmax + 1) == 6, 2 * (-1.6) / 13, 0.0))
+
+
+def test_lmax_phi_default_is_the_plan_lmax_and_matches_brute_force():
+    """The potential's own band limit (Sec. II.A: the gradient map is taken to
+    min(8 Nside, 10000)): lmax_phi = lmax is the default exactly, and with a larger
+    lmax_phi the lensed maps converge with order to the brute-force remap whose
+    deflection comes from direct sums at the same lmax_phi (an independent route:
+    point sums instead of ring FFTs)."""
+    nside, lmax = 16, 24
+    sky = skygen.make_sky(nside, lmax, True, 0, 3, 1, b_scale=0.4)
+    a = L.lens(nside, lmax, 3, sky["T"], sky["E"], sky["B"], sky["phi"])
+    b = L.lens(nside, lmax, 3, sky["T"], sky["E"], sky["B"], sky["phi"], lmax_phi=lmax)
+    for f in "TQU":
+        assert np.array_equal(a[f], b[f])
+    lp = 8 * nside
+    phi = skygen.make_sky(nside, lp, False, 0, 0, 5)["phi"] * 5.0
+    pix = np.random.default_rng(2).choice(hp.npix(nside), 300, replace=False)
+    ex = L.lens_exact(nside, lmax, sky["T"], sky["E"], sky["B"], phi, pix=pix, lmax_phi=lp)
+    errs = []
+    for n in (1, 3, 6):
+        r = L.lens_at_pixels(nside, lmax, n, pix, sky["T"], sky["E"], sky["B"], phi, lmax_phi=lp)
+        errs.append(max(np.sqrt(np.mean((r[f] - ex[f]) ** 2) / np.mean(ex[f] ** 2)) for f in "TQU"))
+    assert np.all(np.diff(errs) < 0) and errs[-1] < 1e-6, errs
+    # the modes above lmax move the maps: truncating the potential to lmax changes them
+    t = L.lens_at_pixels(nside, lmax, 6, pix, sky["T"], sky["E"], sky["B"], phi[:skygen.alm_size(lmax)] * 0.0,
+                         lmax_phi=lmax)
+    high = phi.copy()
+    high[:] = 0.0
+    ells = np.concatenate([np.arange(m, lp + 1) for m in range(lp + 1)])
+    high[ells > lmax] = phi[ells > lmax]
+    h = L.lens_at_pixels(nside, lmax, 6, pix, sky["T"], sky["E"], sky["B"], high, lmax_phi=lp)
+    assert max(np.sqrt(np.mean((h[f] - t[f]) ** 2) / np.mean(t[f] ** 2)) for f in "TQU") > 1e-4
