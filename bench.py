@@ -63,12 +63,10 @@ def fp32_peak_tflops(dev, peaks):
 # count (rings x m grows the same way); a changed source, another order or form
 # gives null.
 TRAFFIC_NSIDE512 = {
-    ("fft_total", None): (839.2e6, ["ringfft.cu", "fft.cuh"], "6c26b53500746294"),
-    ("gather_total", None): (624.6e6, ["gather.cu", "geometry.cuh"], "3d99eb1ac9a9bebc"),
-    ("legendre_QU", "bf16x3"): (7.645e9, ["legendre_umma.cu", "legendre.cuh"], "baebd1665fa129dd"),
-    ("legendre_T", "bf16x3"): (4.291e9, ["legendre_umma.cu", "legendre.cuh"], "baebd1665fa129dd"),
-    ("legendre_QU", "tf32x3"): (7.521e9, ["legendre_umma.cu", "legendre.cuh"], "baebd1665fa129dd"),
-    ("legendre_T", "tf32x3"): (4.173e9, ["legendre_umma.cu", "legendre.cuh"], "baebd1665fa129dd"),
+    ("fft_total", None): (858.6e6, ['ringfft.cu', 'fft.cuh', 'regfft.cuh', 'common.cuh'], "f3e52036d679edb2"),
+    ("gather_total", None): (670.9e6, ['gather.cu', 'geometry.cuh'], "404b9cada9d1bcb7"),
+    ("legendre_QU", "bf16x3"): (3.1034e9, ['legendre_umma.cu', 'legendre.cuh', 'common.cuh'], "abf8e50b1b86ba39"),
+    ("legendre_T", "bf16x3"): (2.4596e9, ['legendre_umma.cu', 'legendre.cuh', 'common.cuh'], "abf8e50b1b86ba39"),
 }
 
 
