@@ -56,7 +56,10 @@ namespace tl {
 
 constexpr int kMaxReal = TL_MAX_BATCH;  // realisations per launch at most (64 columns)
 constexpr int kComputeThreads = 128;  // compute threads per half (umma_threads: the CTA's)
-constexpr uint32_t kXchBytes = 128 * 16 * 4;  // spin-2 epilogue exchange [128][16] floats
+// spin-2 epilogue exchange: [128 rings][9] float2 (8 used; the odd row length puts the
+// 32 rows a warp writes or reads at once on distinct bank pairs)
+constexpr int kXchRow = 9;
+constexpr uint32_t kXchBytes = 128 * kXchRow * 8;
 
 // accumulator columns per order for NDER theta-derivatives: 64 (16 realisations)
 // up to NDER = 5, 32 (8) at NDER = 6, where 64 would not fit tensor memory
@@ -571,7 +574,7 @@ __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsign
   const bool writer = active && m <= D.mmax && !(mirror && rn == D.nrings - 1 - rn);  // equator: north thread
   const int partner = tid ^ 64;
   const size_t ld = (size_t)(D.mmax + 1);
-  float *xch = (float *)(sm + xch_offset<NC, NH>());  // [128][16]: S2 (4 rho + 2, 3) of every ring
+  float2 *xch = (float2 *)(sm + xch_offset<NC, NH>());  // [128][kXchRow]: S2 (4 rho + 2, 3) of every ring
 #pragma unroll 1
   for (int j = 0; j < NJ; ++j) {
 #pragma unroll 1
@@ -581,8 +584,7 @@ __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsign
         tmem_ld32(U.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(NC * j + 32 * h), v);
 #pragma unroll
         for (int rho = 0; rho < 8; ++rho) {
-          xch[tid * 16 + 2 * rho] = nblk ? v[4 * rho + 2] : 0.f;
-          xch[tid * 16 + 2 * rho + 1] = nblk ? v[4 * rho + 3] : 0.f;
+          xch[tid * kXchRow + rho] = nblk ? make_float2(v[4 * rho + 2], v[4 * rho + 3]) : make_float2(0.f, 0.f);
         }
       }
       __syncthreads();
@@ -592,7 +594,8 @@ __device__ __forceinline__ void u2_unit(const TcDesc &D, int m, int rblk, unsign
         for (int rho = 0; rho < 8; ++rho) {
           if (8 * h + rho >= D.nreal) break;
           const float s1r = nblk ? v[4 * rho] : 0.f, s1i = nblk ? v[4 * rho + 1] : 0.f;
-          const float s2r = xch[partner * 16 + 2 * rho], s2i = xch[partner * 16 + 2 * rho + 1];
+          const float2 s2 = xch[partner * kXchRow + rho];
+          const float s2r = s2.x, s2i = s2.y;
           const float ar = s1r + sg * s2r, ai = s1i + sg * s2i;
           const float br = s1r - sg * s2r, bi = s1i - sg * s2i;
           const size_t o = (size_t)(8 * h + rho) * D.rstride + (size_t)j * D.prows * ld + d7_il(r, m, ld);
