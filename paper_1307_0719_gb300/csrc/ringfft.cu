@@ -131,20 +131,20 @@ __device__ __forceinline__ void fold_pair(const T2 *__restrict__ FA, const T2 *_
 
 // Bluestein on the four sub-sequences Y + t2 SY (t2 < 4) of length ni, in place,
 //   y_p <- sum_{t < ni} y_t e^{+2 pi i t p / ni}   (what bluestein_batch computes),
-// with register passes, for M = 2^LG: the 512 threads of the block form 512 / (M/16)
+// with register passes, for M = 2^LG: the NT threads of the block form NT / (M/16)
 // groups; each takes one sub-sequence at a time with its own padded exchange array
 // of M elements in W. The chirped input (zero from ni on; ni <= M / 2) goes through a
 // forward transform, the product with the length's spectrum (stored in natural
 // order, 1/M included, followed by the chirp e^{i pi t^2 / ni}) and an unnormalised
 // inverse transform; the chirped outputs p < ni go back to the sub-sequence.
-template <int LG>
+template <int LG, int NT = 512>
 __device__ __forceinline__ void reg_bluestein(float2 *Y, int SY, int ni, float2 *W, const float2 *__restrict__ spec,
                                               const float2 *__restrict__ tw, int lgtw) {
   static_assert(LG >= 8 && LG <= 12, "M = 2^8 .. 2^12");
   typedef RegFft<LG, -1> Ff;
   typedef RegFft<LG, +1> Fi;
-  constexpr int M = 1 << LG, TGB = M / 16, K = 512 / TGB, KK = K < 4 ? K : 4;
-  static_assert(K == 2 || K == 4, "two or four groups of the 512 threads");
+  constexpr int M = 1 << LG, TGB = M / 16, K = NT / TGB, KK = K < 4 ? K : 4;
+  static_assert(K == 1 || K == 2 || K == 4, "one, two or four groups of the block's threads");
   const int tid = threadIdx.x;
   const int grp = tid / TGB, hh = tid - grp * TGB;
   const float2 *__restrict__ chirp = spec + M;
@@ -193,14 +193,18 @@ __device__ __forceinline__ void reg_bluestein(float2 *Y, int SY, int ni, float2 
 }
 
 // BLUE: the launch's rings have non-power-of-two sub-transforms (Bluestein); else
-// power-of-two ones. REG: Bluestein by register passes (reg_bluestein; M = 2^12
-// takes one CTA per SM through its shared memory, so it keeps the full register file). A launch covers one ring group, so each instance carries one
+// power-of-two ones. REG: Bluestein by register passes (reg_bluestein; see ring_threads). A launch covers one ring group, so each instance carries one
 // sub-transform path (and its own register allocation). LG > 0: the group's
 // transform length is known at compile time, 2^LG (power-of-two rings: the
 // sub-transform length ni; Bluestein: the convolution length M), so the FFT's index
 // and address arithmetic folds into constants; LG = 0 takes it from the ring.
+// threads of a ring-FFT CTA: 256 for the register Bluestein of M = 2^12 (one
+// sub-transform at a time, 100 KB of shared memory: two CTAs per SM whose phases
+// interleave, at 128 registers), else 512
+template <bool REG, int LG> constexpr int ring_threads() { return (REG && LG >= 12) ? 256 : 512; }
+
 template <typename T, bool BLUE, int LG = 0, bool REG = false>
-__global__ void __launch_bounds__(512, (sizeof(T) == 4 && !(REG && LG >= 12)) ? 2 : 1) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
+__global__ void __launch_bounds__(ring_threads<REG, LG>(), (sizeof(T) == 4) ? 2 : 1) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
                                                       BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
                                                       int bbatch, T invL, const int *__restrict__ rings,
@@ -401,8 +405,9 @@ __global__ void __launch_bounds__(512, (sizeof(T) == 4 && !(REG && LG >= 12)) ? 
     else
       fft_core<false, T, T2, LGP ? LG : 0>(Y, ni, 4, SY, +1, tw, TW);
   } else if constexpr (REG) {
-    reg_bluestein<LG>((float2 *)Y, SY, ni, (float2 *)W, (const float2 *)bt.spec + bt.offset[ni],
-                      (const float2 *)tw, 31 - __clz(TW));
+    reg_bluestein<LG, ring_threads<REG, LG>()>((float2 *)Y, SY, ni, (float2 *)W,
+                                               (const float2 *)bt.spec + bt.offset[ni], (const float2 *)tw,
+                                               31 - __clz(TW));
   } else {
     const long long off = bt.offset[ni];
     const int M = LG ? (1 << LG) : bt.mlen[ni];
@@ -948,11 +953,15 @@ static bool group_reg_blue(const tl_plan *p, const FftGroup &g) {
   const int lgM = 31 - __builtin_clz((unsigned)g.M);
   return lgM >= p->blue_reg_lg && lgM <= 12;
 }
+// threads of a group's CTA (ring_threads of its kernel instance)
+static int group_threads(const tl_plan *p, const FftGroup &g) {
+  return (group_reg_blue(p, g) && g.M >= 4096) ? 256 : 512;
+}
 static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch) {
   const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
   const size_t fold = (2 * g.ni_min + 1 < 512) ? 1024 : 0;
   if (group_reg_blue(p, g)) {  // Y, then one padded exchange array per concurrent sub-transform
-    const size_t k = 512 / ((size_t)g.M / 16);
+    const size_t k = (size_t)group_threads(p, g) / ((size_t)g.M / 16);
     size_t wl = (k < 4 ? k : 4) * ((size_t)g.M + (size_t)g.M / 16);
     if (wl < fold) wl = fold;
     return e2 * ((size_t)4 * ring_sub_stride_max(g) + wl);
@@ -1113,7 +1122,7 @@ static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const 
     const int batch = group_batch(p, g);
     const RingKernel<T> kern = pick_ring_kernel<T>(p, g);
     TL_CUDA_TRY(raise_smem((const void *)kern, group_smem(p, g, batch)));
-    kern<<<grid, 512, group_smem(p, g, batch), s>>>(
+    kern<<<grid, group_threads(p, g), group_smem(p, g, batch), s>>>(
         p->ring, p->nside, p->mmax, jl, p->blue,
         (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (T)(1.0 / (double)(p->lmax + 1)),
         p->fft_rings + g.first, (const typename RealTraits<T>::T2 *)p->phase);
