@@ -916,25 +916,26 @@ __global__ void __launch_bounds__(256) tcprep_kernel(int lmax, int s, int nreal,
   const int l0 = m > as ? m : as;
   const int rho = n >> 2, c = n & 3;
   float hv[8], lv[8];
+  // the coefficients are taken to float once and scaled in float: the tiles hold
+  // float (split) values, and double arithmetic would queue on the slow FP64 pipe
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int l = l0 + 8 * blk + k;
-    double val = 0.0;
+    float v = 0.0f;
     if (l <= lmax && rho < nreal) {
       const long long idx = (long long)m * (2 * lmax + 1 - m) / 2 + l;
-      const double kl = (double)tab[idx].x;
-      const double sg = ((l + m) & 1) ? -1.0 : 1.0;
+      const float kl = tab[idx].x;
+      const float sg = ((l + m) & 1) ? -1.0f : 1.0f;
       const double *A = alm.a[rho], *Bm = alm.b[rho];
-      const double ar = A[2 * idx], ai = (m > 0) ? A[2 * idx + 1] : 0.0;
+      const float ar = (float)A[2 * idx], ai = (m > 0) ? (float)A[2 * idx + 1] : 0.0f;
       if (s == 0) {
-        const double re = ar * kl, im = ai * kl;
-        val = (c == 0) ? re : (c == 1) ? im : (c == 2) ? sg * re : sg * im;
+        const float re = ar * kl, im = ai * kl;
+        v = (c == 0) ? re : (c == 1) ? im : (c == 2) ? sg * re : sg * im;
       } else {
-        const double br = Bm ? Bm[2 * idx] : 0.0, bi = (Bm && m > 0) ? Bm[2 * idx + 1] : 0.0;
-        val = (c == 0) ? (ar - bi) * kl : (c == 1) ? (ai + br) * kl : (c == 2) ? sg * kl * (ar + bi) : sg * kl * (ai - br);
+        const float br = Bm ? (float)Bm[2 * idx] : 0.0f, bi = (Bm && m > 0) ? (float)Bm[2 * idx + 1] : 0.0f;
+        v = (c == 0) ? (ar - bi) * kl : (c == 1) ? (ai + br) * kl : (c == 2) ? sg * kl * (ar + bi) : sg * kl * (ai - br);
       }
     }
-    const float v = (float)val;
     if (bf16) {
       hv[k] = v;
     } else {
