@@ -198,13 +198,19 @@ __device__ __forceinline__ void reg_bluestein(float2 *Y, int SY, int ni, float2 
 // transform length is known at compile time, 2^LG (power-of-two rings: the
 // sub-transform length ni; Bluestein: the convolution length M), so the FFT's index
 // and address arithmetic folds into constants; LG = 0 takes it from the ring.
-// threads of a ring-FFT CTA: 256 for the register Bluestein of M = 2^12 (one
-// sub-transform at a time, 100 KB of shared memory: two CTAs per SM whose phases
-// interleave, at 128 registers), else 512
-template <bool REG, int LG> constexpr int ring_threads() { return (REG && LG >= 12) ? 256 : 512; }
+// threads of a ring-FFT CTA: 256 for the register Bluestein (M = 2^12: one
+// sub-transform at a time, 100 KB of shared memory, two CTAs per SM at 128 registers;
+// M = 2^11: two at a time, 68 KB, three CTAs per SM), so that the CTAs' phases
+// (fold from HBM, transforms, output pass) interleave; else 512
+template <bool REG, int LG> constexpr int ring_threads() { return (REG && LG >= 11) ? 256 : 512; }
+// CTAs per SM the register allocation is held to: M = 2^11 fits three (68 KB of shared
+// memory each), M = 2^12 two
+template <typename T, bool REG, int LG> constexpr int ring_min_ctas() {
+  return sizeof(T) != 4 ? 1 : (REG && LG == 11) ? 3 : 2;
+}
 
 template <typename T, bool BLUE, int LG = 0, bool REG = false>
-__global__ void __launch_bounds__(ring_threads<REG, LG>(), (sizeof(T) == 4) ? 2 : 1) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
+__global__ void __launch_bounds__(ring_threads<REG, LG>(), ring_min_ctas<T, REG, LG>()) ringfft_kernel(RingTable rt, int nside, int mmax, JobList jobs,
                                                       BluesteinTable bt,
                                                       const typename RealTraits<T>::T2 *__restrict__ tw, int TW,
                                                       int bbatch, T invL, const int *__restrict__ rings,
@@ -955,7 +961,7 @@ static bool group_reg_blue(const tl_plan *p, const FftGroup &g) {
 }
 // threads of a group's CTA (ring_threads of its kernel instance)
 static int group_threads(const tl_plan *p, const FftGroup &g) {
-  return (group_reg_blue(p, g) && g.M >= 4096) ? 256 : 512;
+  return (group_reg_blue(p, g) && g.M >= 2048) ? 256 : 512;
 }
 static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch) {
   const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
