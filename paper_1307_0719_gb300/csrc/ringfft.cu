@@ -963,11 +963,14 @@ static bool group_reg_blue(const tl_plan *p, const FftGroup &g) {
 static int group_threads(const tl_plan *p, const FftGroup &g) {
   return (group_reg_blue(p, g) && g.M >= 2048) ? 256 : 512;
 }
-static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch) {
+// threads: the CTA size of the kernel that runs the group (group_threads for the
+// forward kernels; 512 for the adjoint), which sets how many register Bluestein
+// sub-transforms run at once, each with its own exchange array
+static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch, int threads) {
   const size_t e2 = (p->precision == TL_FP64) ? 16 : 8;
   const size_t fold = (2 * g.ni_min + 1 < 512) ? 1024 : 0;
   if (group_reg_blue(p, g)) {  // Y, then one padded exchange array per concurrent sub-transform
-    const size_t k = (size_t)group_threads(p, g) / ((size_t)g.M / 16);
+    const size_t k = (size_t)threads / ((size_t)g.M / 16);
     size_t wl = (k < 4 ? k : 4) * ((size_t)g.M + (size_t)g.M / 16);
     if (wl < fold) wl = fold;
     return e2 * ((size_t)4 * ring_sub_stride_max(g) + wl);
@@ -980,7 +983,7 @@ static size_t group_smem(const tl_plan *p, const FftGroup &g, int batch) {
 // one fits); one at a time otherwise.
 static int group_batch(const tl_plan *p, const FftGroup &g) {
   if (g.M == 0 || p->fft_batch == 1 || group_reg_blue(p, g)) return 1;
-  const size_t s4 = group_smem(p, g, 4);
+  const size_t s4 = group_smem(p, g, 4, 512);
   if (p->fft_batch == 4) return s4 <= 227 * 1024 ? 4 : 1;
   return s4 <= 113 * 1024 ? 4 : 1;
 }
@@ -996,7 +999,7 @@ template <typename K>
 static cudaError_t set_group_smem(const tl_plan *p, K kernel) {
   size_t mx = 0;
   for (int i = 0; i < p->fft_ngroups; ++i) {
-    const size_t sm = group_smem(p, p->fft_groups[i], group_batch(p, p->fft_groups[i]));
+    const size_t sm = group_smem(p, p->fft_groups[i], group_batch(p, p->fft_groups[i]), 512);
     if (sm > mx) mx = sm;
   }
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
@@ -1127,8 +1130,9 @@ static cudaError_t ringfft_t(const tl_plan *p, const void *const *planes, const 
     }
     const int batch = group_batch(p, g);
     const RingKernel<T> kern = pick_ring_kernel<T>(p, g);
-    TL_CUDA_TRY(raise_smem((const void *)kern, group_smem(p, g, batch)));
-    kern<<<grid, group_threads(p, g), group_smem(p, g, batch), s>>>(
+    const int nt = group_threads(p, g);
+    TL_CUDA_TRY(raise_smem((const void *)kern, group_smem(p, g, batch, nt)));
+    kern<<<grid, nt, group_smem(p, g, batch, nt), s>>>(
         p->ring, p->nside, p->mmax, jl, p->blue,
         (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (T)(1.0 / (double)(p->lmax + 1)),
         p->fft_rings + g.first, (const typename RealTraits<T>::T2 *)p->phase);
@@ -1169,7 +1173,7 @@ static cudaError_t ringfft_adj_t(const tl_plan *p, void *const *planes, const Ad
     const FftGroup &g = p->fft_groups[gi];
     const int batch = group_batch(p, g);
     dim3 grid(g.count, njobs);
-    ringfft_adj_kernel<T><<<grid, 512, group_smem(p, g, batch), s>>>(
+    ringfft_adj_kernel<T><<<grid, 512, group_smem(p, g, batch, 512), s>>>(
         p->ring, p->mmax, p->npix, p->nmaps, jl, p->blue,
         (const typename RealTraits<T>::T2 *)p->twiddle, p->tw_len, batch, (double)(p->lmax + 1),
         p->fft_rings + g.first, (const typename RealTraits<T>::T2 *)p->phase, p->blue_reg_lg);

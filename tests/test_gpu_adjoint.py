@@ -237,3 +237,25 @@ def test_adjoint_nside1024_central_differences():
         plan.close()
     for f, l, m, part, fd, ana in checks:
         assert abs(fd - ana) <= 1e-3 * abs(ana), (f, l, m, part, fd, ana)
+
+
+@pytest.mark.parametrize("nside,lmax,precision", [(1024, 2048, "MIXED_FP32"), (2048, 4096, "MIXED_BF16x3")])
+def test_adjoint_dot_product_mixed_full_size(nside, lmax, precision):
+    """The transpose identity <y, lens(x)> = Re <lens^T y, x> for (T, E, B) at fixed phi
+    at the sizes where the adjoint ring FFT runs its register Bluestein sub-transforms
+    (cap rings with 513 <= i <= 2047), in single precision (float sums over 12.6M and
+    50M pixels: 1e-4)."""
+    s = sky(nside, lmax, pol=True, b_scale=0.5)
+    rng = np.random.default_rng(5)
+    g, gd = _grads(rng, nside, torch.float32, True)
+    plan = api.Plan(nside, lmax, 4, pol=True, precision=getattr(api, precision))
+    try:
+        d = to_dev(s)
+        maps = plan.lens(d["T"], d["E"], d["B"], d["phi"]).double()
+        lhs = sum(float(torch.dot(maps[i], gd[f].double())) for i, f in enumerate("TQU"))
+        gr = plan.lens_adjoint(d["T"], d["E"], d["B"], d["phi"], gd["T"], gd["Q"], gd["U"], want=("T", "E", "B"))
+        rhs = sum(float((gr[f].conj() * d[f]).real.sum()) for f in "TEB")
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    assert abs(lhs - rhs) < 1e-4 * abs(lhs), (lhs, rhs)

@@ -58,3 +58,32 @@ def test_anafast_vs_oracle():
         assert np.allclose(cl[row], ref, rtol=1e-12, atol=1e-15 * np.abs(ref).max()), (x, y)
     cl_t = api.anafast(lmax, d["T"]).cpu().numpy()
     assert np.allclose(cl_t[0], cl[0], rtol=1e-14) and not cl_t[1:].any()
+
+
+@pytest.mark.parametrize("nside,lmax", [(1024, 2048), (2048, 4096)])
+def test_map2alm_transpose_identity_full_size(nside, lmax):
+    """tl_map2alm is the transpose of the synthesis with weight 4 pi / Npix:
+    sum c_m Re(a conj(map2alm(m))) = (4 pi / Npix) sum_p m(p) synth(a)(p), c_0 = 1,
+    c_m>0 = 2, for T and (E, B) <-> (Q, U), at the sizes where the adjoint ring FFT runs
+    its register Bluestein sub-transforms; single precision sums: 1e-4."""
+    s = sky(nside, lmax, pol=True, b_scale=0.5)
+    d = {k: torch.from_numpy(v).cuda() for k, v in s.items()}
+    rng = np.random.default_rng(8)
+    m = {f: torch.from_numpy(rng.normal(size=hp.npix(nside))).cuda().float() for f in "TQU"}
+    plan = api.Plan(nside, lmax, 0, pol=True, precision=api.MIXED_FP32)
+    try:
+        syn_t = plan.synth_derivs(d["T"], 0)[0].double()
+        syn_p = plan.synth_derivs(torch.cat([d["E"], d["B"]]), 2).double()
+        b = plan.map2alm(m["T"], m["Q"], m["U"])
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    w = 4 * np.pi / hp.npix(nside)
+    c = torch.full((plan.nalm,), 2.0, dtype=torch.float64, device="cuda")
+    c[:lmax + 1] = 1.0
+    lhs_t = float((c * (d["T"] * b["T"].conj()).real).sum())
+    rhs_t = w * float(torch.dot(m["T"].double(), syn_t))
+    assert abs(lhs_t - rhs_t) < 1e-4 * abs(rhs_t), (lhs_t, rhs_t)
+    lhs_p = float((c * ((d["E"] * b["E"].conj()).real + (d["B"] * b["B"].conj()).real)).sum())
+    rhs_p = w * float(torch.dot(m["Q"].double(), syn_p[0]) + torch.dot(m["U"].double(), syn_p[1]))
+    assert abs(lhs_p - rhs_p) < 1e-4 * abs(rhs_p), (lhs_p, rhs_p)
