@@ -109,6 +109,10 @@ struct tl_plan {
   void *stage_alm;     // host-path staging: stage_cap x 4 x nalm complex128
   void *stage_out;     // host-path staging: stage_cap x 3 x npix (T)
   int stage_cap;       // realisations the staging holds (0: none yet)
+  cudaStream_t copy_stream;                 // host-path copies of finished maps (created on first use)
+  cudaEvent_t done_ev[TL_MAX_BATCH];        // a realisation's maps are final (recorded after its gather)
+  cudaEvent_t copied_ev;                    // the copy stream's last copy of a call
+  int done_rec;                             // lens_stage_after_legendre records done_ev[r] while set
   size_t bytes;
   // optional stage timing
   int timing;

@@ -77,6 +77,14 @@ static cudaError_t dalloc(void **p, size_t b, size_t *bytes) {
 
 static void free_plan(tl_plan *p) {
   if (!p) return;
+  if (p->copy_stream) {
+    cudaStreamSynchronize(p->copy_stream);
+    for (int i = 0; i < TL_MAX_BATCH; ++i)
+      if (p->done_ev[i]) cudaEventDestroy(p->done_ev[i]);
+    if (p->copied_ev) cudaEventDestroy(p->copied_ev);
+    cudaStreamDestroy(p->copy_stream);
+    p->copy_stream = nullptr;
+  }
   if (p->phi_plan) {
     free_plan(p->phi_plan);
     p->phi_plan = nullptr;
@@ -551,6 +559,7 @@ tl_status lens_stage_after_legendre(tl_plan *p, int nreal, bool phi, void *const
       if (st != TL_OK) return st;
       if (tm) cudaEventRecord(p->evr[3 * r + 1], s);
       TRY_CUDA(launch_gather(p, p->alpha, p->d3, To[r], pol ? Qo[r] : nullptr, pol ? Uo[r] : nullptr, s));
+      if (p->done_rec && r < TL_MAX_BATCH) TRY_CUDA(cudaEventRecord(p->done_ev[r], s));
       if (tm) {
         cudaEventRecord(p->evr[3 * r + 2], s);
         p->nevr = r + 1;
@@ -853,19 +862,38 @@ extern "C" tl_status tl_lens_batch_host(tl_plan *p, int nreal, const double *con
       if (dB[i]) TRY_CUDA(cudaMemcpyAsync((void *)dB[i], alm_B[r], ab, cudaMemcpyHostToDevice, s));
       if (dP[i]) TRY_CUDA(cudaMemcpyAsync((void *)dP[i], alm_phi[r], abp, cudaMemcpyHostToDevice, s));
     }
+    // On tensor-core plans a chunk's realisations run their ring FFTs and gathers one
+    // after another, so each one's maps are copied back on a second stream as soon as its
+    // gather has run, while the later ones are still being computed.
+    const bool overlap = p->batch > 1 && n > 1;
+    if (overlap && !p->copy_stream) {
+      TRY_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+      for (int i = 0; i < TL_MAX_BATCH; ++i) TRY_CUDA(cudaEventCreateWithFlags(&p->done_ev[i], cudaEventDisableTiming));
+      TRY_CUDA(cudaEventCreateWithFlags(&p->copied_ev, cudaEventDisableTiming));
+    }
+    if (overlap) {
+      // the previous chunk's copies read the staging this chunk overwrites
+      TRY_CUDA(cudaStreamWaitEvent(s, p->copied_ev, 0));
+    }
+    p->done_rec = overlap ? 1 : 0;
     tl_status st = tl_lens_batch(p, n, dT, pol ? dE : nullptr, pol ? dB : nullptr, dP, oT, pol ? oQ : nullptr,
                                  pol ? oU : nullptr, stream);
+    p->done_rec = 0;
     if (st != TL_OK) return st;
+    cudaStream_t cs = overlap ? p->copy_stream : s;
     for (int i = 0; i < n; ++i) {
       const int r = r0 + i;
-      TRY_CUDA(cudaMemcpyAsync(T_out[r], oT[i], mapb, cudaMemcpyDeviceToHost, s));
+      if (overlap) TRY_CUDA(cudaStreamWaitEvent(cs, p->done_ev[i], 0));
+      TRY_CUDA(cudaMemcpyAsync(T_out[r], oT[i], mapb, cudaMemcpyDeviceToHost, cs));
       if (pol) {
-        TRY_CUDA(cudaMemcpyAsync(Q_out[r], oQ[i], mapb, cudaMemcpyDeviceToHost, s));
-        TRY_CUDA(cudaMemcpyAsync(U_out[r], oU[i], mapb, cudaMemcpyDeviceToHost, s));
+        TRY_CUDA(cudaMemcpyAsync(Q_out[r], oQ[i], mapb, cudaMemcpyDeviceToHost, cs));
+        TRY_CUDA(cudaMemcpyAsync(U_out[r], oU[i], mapb, cudaMemcpyDeviceToHost, cs));
       }
     }
+    if (overlap) TRY_CUDA(cudaEventRecord(p->copied_ev, cs));
   }
   TRY_CUDA(cudaStreamSynchronize(s));
+  if (p->copy_stream) TRY_CUDA(cudaStreamSynchronize(p->copy_stream));
   return TL_OK;
 }
 
