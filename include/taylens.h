@@ -367,7 +367,8 @@ const char *tl_status_string(tl_status status);
  * T/Q/U maps), gather, then two totals: all ring FFTs and all gathers of the call
  * (on tensor-core plans the ringfft stage spans every realisation's ring FFTs and
  * gathers, and the deflection_fft and gather stages are empty; the totals
- * separate them). tl_lens_adjoint: forward (recomputed derivative maps and
+ * separate them; prep_T holds the temperature's coefficient tiles only, and the
+ * potential's tiles are prepared inside legendre_T, after the temperature's launch). tl_lens_adjoint: forward (recomputed derivative maps and
  * deflection), gather (transposed), ringfft (transposed), legendre_T (transposed,
  * with phi), legendre_QU (transposed), finish. Synchronises on the last event.
  * Returns the number of stages written (<= n). */

@@ -113,6 +113,8 @@ struct tl_plan {
   cudaEvent_t done_ev[TL_MAX_BATCH];        // a realisation's maps are final (recorded after its gather)
   cudaEvent_t copied_ev;                    // the copy stream's last copy of a call
   int done_rec;                             // lens_stage_after_legendre records done_ev[r] while set
+  cudaEvent_t in_ev[3];                     // host path: T staged (compute stream), phi staged, E/B staged
+  int in_wait;                              // the tensor-core chunk waits for in_ev[1], in_ev[2] while set
   size_t bytes;
   // optional stage timing
   int timing;

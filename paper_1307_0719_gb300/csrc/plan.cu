@@ -82,6 +82,8 @@ static void free_plan(tl_plan *p) {
     for (int i = 0; i < TL_MAX_BATCH; ++i)
       if (p->done_ev[i]) cudaEventDestroy(p->done_ev[i]);
     if (p->copied_ev) cudaEventDestroy(p->copied_ev);
+    for (int i = 0; i < 3; ++i)
+      if (p->in_ev[i]) cudaEventDestroy(p->in_ev[i]);
     cudaStreamDestroy(p->copy_stream);
     p->copy_stream = nullptr;
   }
@@ -584,14 +586,22 @@ static tl_status lens_chunk(tl_plan *p, int nreal, const double *const *aT, cons
   mark(p, 0, s);
   if (p->batch > 1) {
     // ---- tensor-core Legendre stage for all realisations of the chunk
-    // the temperature at all orders, the lensing potential at j <= 1 (its own launch)
+    // the temperature at all orders, then the lensing potential at j <= 1 (its own
+    // launch), then Q/U; on the host path the potential's and E/B's coefficients may
+    // still be arriving on the copy stream while the temperature's launch runs
     TRY_CUDA(launch_tcprep(p, 0, nreal, aT, nullptr, p->tc_blk0, p->tab0, p->tc_b0, s));
-    if (phi) TRY_CUDA(launch_tcprep(p, 0, nreal, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
     mark(p, 1, s);
     TRY_CUDA(launch_legendre_spin0_tc(p, 0, nreal, p->d7_T, p->d7_rstride, s));
-    if (phi) TRY_CUDA(launch_legendre_spin0_tc(p, 1, nreal, p->d7_P, p->d7p_rstride, s));
+    // (the potential's coefficients are also read later, by its own deflection plan
+    // when it has one)
+    if (p->in_wait && aP[0] != nullptr) TRY_CUDA(cudaStreamWaitEvent(s, p->in_ev[1], 0));
+    if (phi) {
+      TRY_CUDA(launch_tcprep(p, 0, nreal, aP, nullptr, p->tc_blk0, p->tab0, p->tc_bp, s));
+      TRY_CUDA(launch_legendre_spin0_tc(p, 1, nreal, p->d7_P, p->d7p_rstride, s));
+    }
     mark(p, 2, s);
     mark(p, 3, s);
+    if (pol && p->in_wait) TRY_CUDA(cudaStreamWaitEvent(s, p->in_ev[2], 0));
     if (pol) TRY_CUDA(launch_tcprep(p, 2, nreal, aE, aB, p->tc_blk2, p->tab2, p->tc_b2, s));
     mark(p, 4, s);
     if (pol) TRY_CUDA(launch_legendre_spin2_tc(p, p->tc_nder, nreal, p->d7_Q, p->d7_U, p->d7_rstride, s));
@@ -857,28 +867,45 @@ extern "C" tl_status tl_lens_batch_host(tl_plan *p, int nreal, const double *con
       oT[i] = o;
       oQ[i] = pol ? o + mapb : nullptr;
       oU[i] = pol ? o + 2 * mapb : nullptr;
-      TRY_CUDA(cudaMemcpyAsync((void *)dT[i], alm_T[r], ab, cudaMemcpyHostToDevice, s));
-      if (dE[i]) TRY_CUDA(cudaMemcpyAsync((void *)dE[i], alm_E[r], ab, cudaMemcpyHostToDevice, s));
-      if (dB[i]) TRY_CUDA(cudaMemcpyAsync((void *)dB[i], alm_B[r], ab, cudaMemcpyHostToDevice, s));
-      if (dP[i]) TRY_CUDA(cudaMemcpyAsync((void *)dP[i], alm_phi[r], abp, cudaMemcpyHostToDevice, s));
     }
     // On tensor-core plans a chunk's realisations run their ring FFTs and gathers one
     // after another, so each one's maps are copied back on a second stream as soon as its
-    // gather has run, while the later ones are still being computed.
+    // gather has run, while the later ones are still being computed; and only the
+    // temperature's coefficients are needed before the first Legendre launch, so the
+    // potential's and E/B's arrive on that stream meanwhile.
     const bool overlap = p->batch > 1 && n > 1;
     if (overlap && !p->copy_stream) {
       TRY_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
       for (int i = 0; i < TL_MAX_BATCH; ++i) TRY_CUDA(cudaEventCreateWithFlags(&p->done_ev[i], cudaEventDisableTiming));
       TRY_CUDA(cudaEventCreateWithFlags(&p->copied_ev, cudaEventDisableTiming));
+      for (int i = 0; i < 3; ++i) TRY_CUDA(cudaEventCreateWithFlags(&p->in_ev[i], cudaEventDisableTiming));
     }
+    cudaStream_t ins = overlap ? p->copy_stream : s;
+    for (int i = 0; i < n; ++i)
+      TRY_CUDA(cudaMemcpyAsync((void *)dT[i], alm_T[(size_t)r0 + i], ab, cudaMemcpyHostToDevice, s));
+    if (overlap) {
+      // the staging is free once the compute stream has passed the previous chunk
+      TRY_CUDA(cudaEventRecord(p->in_ev[0], s));
+      TRY_CUDA(cudaStreamWaitEvent(ins, p->in_ev[0], 0));
+    }
+    for (int i = 0; i < n; ++i)
+      if (dP[i]) TRY_CUDA(cudaMemcpyAsync((void *)dP[i], alm_phi[(size_t)r0 + i], abp, cudaMemcpyHostToDevice, ins));
+    if (overlap) TRY_CUDA(cudaEventRecord(p->in_ev[1], ins));
+    for (int i = 0; i < n; ++i) {
+      if (dE[i]) TRY_CUDA(cudaMemcpyAsync((void *)dE[i], alm_E[(size_t)r0 + i], ab, cudaMemcpyHostToDevice, ins));
+      if (dB[i]) TRY_CUDA(cudaMemcpyAsync((void *)dB[i], alm_B[(size_t)r0 + i], ab, cudaMemcpyHostToDevice, ins));
+    }
+    if (overlap) TRY_CUDA(cudaEventRecord(p->in_ev[2], ins));
     if (overlap) {
       // the previous chunk's copies read the staging this chunk overwrites
       TRY_CUDA(cudaStreamWaitEvent(s, p->copied_ev, 0));
     }
     p->done_rec = overlap ? 1 : 0;
+    p->in_wait = overlap ? 1 : 0;
     tl_status st = tl_lens_batch(p, n, dT, pol ? dE : nullptr, pol ? dB : nullptr, dP, oT, pol ? oQ : nullptr,
                                  pol ? oU : nullptr, stream);
     p->done_rec = 0;
+    p->in_wait = 0;
     if (st != TL_OK) return st;
     cudaStream_t cs = overlap ? p->copy_stream : s;
     for (int i = 0; i < n; ++i) {

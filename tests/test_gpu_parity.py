@@ -309,3 +309,30 @@ def test_lmax_phi_host_call_and_adjoint_refusal():
     finally:
         torch.cuda.synchronize()
         plan.close()
+
+
+@pytest.mark.parametrize("lmax_phi", [None, 80])
+def test_batch_host_overlapped_copies_equal_device_call(lmax_phi):
+    """The host-buffer batch call on a tensor-core plan (several realisations: the
+    potential's and E/B's coefficients arrive on the copy stream while the temperature's
+    Legendre launch runs, and each realisation's maps go back as soon as its gather has
+    run) gives the device call's maps bit for bit, also with the potential's own band
+    limit (its deflection plan reads the coefficients that arrive last)."""
+    import skygen
+    nside, lmax = 16, 32
+    lp = lmax if lmax_phi is None else lmax_phi
+    skies = []
+    for i in range(3):
+        s = sky(nside, lmax, pol=True, seeds=(30 + i, 40 + i, 1), b_scale=0.4)
+        s["phi"] = skygen.make_sky(nside, lp, False, 0, 0, 50 + i)["phi"] * 3.0
+        skies.append(s)
+    plan = api.Plan(nside, lmax, 3, pol=True, precision=api.MIXED_BF16x3, lmax_phi=lmax_phi)
+    try:
+        dev = plan.lens_batch([to_dev(s) for s in skies])
+        dev = [o.cpu().numpy() for o in dev]
+        host = plan.lens_batch_host([{k: torch.from_numpy(v) for k, v in s.items()} for s in skies])
+    finally:
+        torch.cuda.synchronize()
+        plan.close()
+    for a, b in zip(dev, host):
+        assert np.array_equal(a, b.numpy())
