@@ -18,13 +18,17 @@
 // which carry no cancellation, so float arithmetic gives them to ~1e-7 relative.
 // The pixel lookup runs in single precision with a certified error bound: every
 // floor whose argument lies within the bound of an integer marks the pixel as
-// uncertain. The offsets to the expansion centre subtract centre differences
-// taken from exact integers and hi/lo float ring colatitudes. Pixels on rings with
-// sin(theta) < 0.1 (where rho + X can cancel for a point carried over the pole),
-// pixels deflected by more than 0.02 rad and pixels whose float lookup is
-// uncertain are not computed in the float kernel: it appends them to a queue
-// (one global atomic per block) and a second kernel runs them with the double
-// geometry, so that no warp of the float kernel waits on the FP64 pipe.
+// uncertain. It works in increments from the output pixel, whose centre sits at
+// half-integer cell coordinates, so the bound scales with the displacement rather
+// than with the position (ang2loc_inc); only a point that crosses between belt and
+// cap takes the whole-coordinate lookup (ang2loc_f, bound N * 2.5e-6 cells). The
+// offsets to the expansion centre subtract centre differences taken from exact
+// integers and hi/lo float ring colatitudes. Pixels deflected by more than
+// sin(theta)/4 (near a pole, where rho + X could cancel for a point carried over
+// it) or by more than 0.02 rad, and pixels whose float lookup is uncertain, are
+// not computed in the float kernel: it appends them to a queue (one global atomic
+// per block) and a second kernel runs them with the double geometry, so that no
+// warp of the float kernel waits on the FP64 pipe.
 #include <math.h>
 
 #include "geometry.cuh"
@@ -59,14 +63,16 @@ __device__ __forceinline__ bool geo32(const RingTable &rt, int nside, long long 
   float dthp = atan2f(ath * sinc + zf * w, (1.0f - omc) + sf * w);  // th' - th_p
   float dphp = atan2f(Y, X);                                        // phi' - phi_p
   float dzx = dz;                                                   // z' - z_p
+  float dzmag = fabsf(zf * omc) + fabsf(sf * ath * sinc);           // its terms' sizes
   if (mode & kGeoNaive) {
-    // naive addition: th' - th_p = a_th, phi' - phi_p = a_ph / sin th; the rings that
-    // could carry a point past a pole (sin th < 0.1) take the double pass
+    // naive addition: th' - th_p = a_th, phi' - phi_p = a_ph / sin th; points that
+    // could be carried past a pole (|alpha| > sin th / 4) take the double pass
     float sa, ca;
     sincosf(0.5f * ath, &sa, &ca);
     dthp = ath;
     dphp = aph * __ldg(rt.rsinf + ring);
     dzx = -sf * (2.0f * sa * ca) - zf * (2.0f * sa * sa);  // cos(th + a) - cos th
+    dzmag = fabsf(sf * (2.0f * sa * ca)) + fabsf(zf * (2.0f * sa * sa));
   }
   const int np = rt.nphi[ring];
   const int shp = __double_as_longlong(rt.phi0[ring]) != 0;  // phi0 >= 0: an integer test
@@ -97,13 +103,20 @@ __device__ __forceinline__ bool geo32(const RingTable &rt, int nside, long long 
     g.y = Lf * dph;
     return true;
   }
-  // pixel lookup in float where every decision clears its error bound (ang2loc_f);
-  // else the pixel goes to the double-precision pass.
+  // pixel lookup in float where every decision clears its error bound: in
+  // increments from p (ang2loc_inc), or, for x' in the other region (belt / cap),
+  // from the whole coordinates (ang2loc_f); else the pixel goes to the double pass.
   // Pixel centres: phi = 2 pi (idx + sh/2) / nphi, sh = 1 on half-pixel-shifted rings.
-  const float tf = (float)(4 * idx + 2 * shp) / (float)np + dphp * (float)(2.0 / kPiD);  // 2 phi' / pi
-  bool ok;
-  PixLoc lq = ang2loc_f(zf + dzx, fr.z - (zf >= 0.0f ? dzx : -dzx), tf, nside, ok);
-  if (!ok) return false;
+  const float dt = dphp * (float)(2.0 / kPiD);  // t' - t_p, t = 2 phi / pi
+  PixLoc lq;
+  const int how = ang2loc_inc(nside, ring, idx, shp, dzx, dzmag, dt, lq);
+  if (how == 0) return false;
+  if (how == 2) {
+    const float tf = (float)(4 * idx + 2 * shp) / (float)np + dt;
+    bool ok;
+    lq = ang2loc_f(zf + dzx, fr.z - (zf >= 0.0f ? dzx : -dzx), tf, nside, ok);
+    if (!ok) return false;
+  }
   g.q = rt.first[lq.ring] + lq.idx;
   // theta_q - theta_p from the hi/lo parts: the hi difference is exact (nearby
   // rings, Sterbenz), so this is the double difference rounded once
@@ -193,7 +206,8 @@ __global__ void __launch_bounds__(256) gather_kernel(RingTable rt, int nside, lo
       if (FAST) {
         const float4 fr = __ldg((const float4 *)(rt.ringf + 8 * (size_t)loc.ring));
         Geo32 g;
-        defer = !(fr.y >= 0.1f && (float)(ath * ath + aph * aph) < 4e-4f) ||
+        const float d2 = (float)(ath * ath + aph * aph);
+        defer = !(d2 < 4e-4f && d2 < 0.0625f * fr.y * fr.y) ||
                 !geo32(rt, nside, p, loc.ring, loc.idx, fr, __ldg(rt.ringf + 8 * (size_t)loc.ring + 4), (float)ath,
                        (float)aph, rot, mode, (float)Lnorm, g);
         if (!defer) {

@@ -136,6 +136,91 @@ __device__ __forceinline__ PixLoc ang2loc_f(float z, float omz, float t, int nsi
   return L;
 }
 
+// Pixel lookup of x' in increments from the output pixel p = (ring, idx), for the
+// float gather. In HEALPix's cell coordinates every pixel centre sits at
+// half-integers: in the belt x1 = N(t + 1/2) - (3/4) N z = idx + (sh + i - N)/2 and
+// x2 = N(t + 1/2) + (3/4) N z = idx + (3N + sh - i)/2 (i = ring + 1, sh the ring's
+// half-pixel shift); in a cap, with i the ring's distance from its pole,
+// tmp = N sqrt(3 (1 - |z|)) = i and t = f + (k + 1/2)/i (face f, k = idx - f i), so
+// x1 = tp tmp = k + 1/2 and x2 = (1 - tp) tmp = i - k - 1/2. The displaced
+// coordinates are then an exact integer plus 1/2 plus a term e formed from
+// dz = z' - z and dt = t' - t alone, whose rounding error is relative to the
+// displacement terms rather than to the absolute position. dz and dt carry
+// errors under a few units in the last place relative to dzmag (the sum of the
+// magnitudes of the terms dz was formed from) and |dt|; every floor below is
+// certified against kIncRel times the magnitude of its terms plus 1e-6.
+// Returns 1 with the cell in L, 0 when a decision is within its bound (the caller
+// defers the pixel to the double pass), 2 when x' certainly lies in another
+// region (belt / cap) than p (the caller then takes ang2loc_f).
+constexpr float kIncRel = 4e-6f;
+__device__ __forceinline__ int ang2loc_inc(int nside, int ring, int idx, int sh, float dz, float dzmag, float dt,
+                                           PixLoc &L) {
+  const int N = nside, i = ring + 1;
+  const float Nf = (float)N;
+  if (i >= N && i <= 3 * N) {  // belt pixel
+    const float a = Nf * dt, b = 0.75f * Nf * dz, bm = 0.75f * Nf * dzmag;
+    // |z'| <= 2/3  <=>  (i - 3N)/2 <= b <= (i - N)/2, both bounds exact
+    const float lo = 0.5f * (float)(i - 3 * N), hi = 0.5f * (float)(i - N);
+    const float eb = 1e-6f + kIncRel * bm;
+    if (fabsf(b - lo) < eb || fabsf(b - hi) < eb) return 0;
+    if (b < lo || b > hi) return 2;
+    const float e = 1e-6f + kIncRel * (fabsf(a) + bm);
+    const float f1 = 0.5f + (a - b), f2 = 0.5f + (a + b);
+    if (fabsf(f1 - rintf(f1)) < e || fabsf(f2 - rintf(f2)) < e) return 0;
+    const int jp = idx + ((sh + i - N - 1) >> 1) + (int)floorf(f1);
+    const int jm = idx + ((3 * N + sh - i - 1) >> 1) + (int)floorf(f2);
+    int ir = N + 1 + jp - jm;  // 1 .. 2N+1 by the region test
+    if (ir < 1) ir = 1;
+    if (ir > 2 * N + 1) ir = 2 * N + 1;
+    const int v = jp + jm - N + (1 - (ir & 1)) + 1;
+    int ip = (v >= 0) ? v / 2 : -((1 - v) / 2);
+    ip %= 4 * N;
+    if (ip < 0) ip += 4 * N;
+    L.ring = N - 2 + ir;
+    L.idx = ip;
+    return 1;
+  }
+  const bool north = i < N;
+  const int ir = north ? i : 4 * N - i;  // p's ring counted from its pole
+  const float irf = (float)ir;
+  // tmp'^2 - ir^2 = 3 N^2 ((1 - |z'|) - (1 - |z|))
+  const float c = 3.0f * Nf * Nf * (north ? -dz : dz), cm = 3.0f * Nf * Nf * dzmag;
+  const float s2 = irf * irf + c;
+  if (!(s2 > 0.0f)) return 0;
+  const float den = sqrtf(s2) + irf;
+  const float del = c / den, delm = cm / den;  // tmp' - ir, no cancellation
+  // x' in the same cap  <=>  tmp' < N
+  const float gap = (float)(N - ir);
+  if (fabsf(del - gap) < 1e-6f + kIncRel * delm) return 0;
+  if (del > gap) return 2;
+  const int f = idx / ir, k = idx - f * ir;
+  const float v = ((float)k + 0.5f) / irf + dt;  // t' - f
+  if (fabsf(v - rintf(v)) < 1e-6f + kIncRel * fabsf(dt)) return 0;
+  const int fl = (int)floorf(v);
+  const float tp = v - (float)fl;  // frac(t')
+  const float a = dt * irf;
+  const float g1 = 0.5f + (a + tp * del), g2 = 0.5f + ((1.0f - tp) * del - a);
+  const float e = 1e-6f + kIncRel * (fabsf(a) + delm);
+  if (fabsf(g1 - rintf(g1)) < e || fabsf(g2 - rintf(g2)) < e) return 0;
+  const int K1 = k - fl * ir;
+  const int jp = K1 + (int)floorf(g1);
+  const int jm = ir - 1 - K1 + (int)floorf(g2);
+  int ir2 = jp + jm + 1;  // 1 .. N by the region test
+  if (ir2 < 1) ir2 = 1;
+  if (ir2 > N) ir2 = N;
+  // ip = floor(t' ir2) with t' ir2 = f ir2 + (2k + 1) ir2 / (2 ir) + dt ir2
+  const int num = (2 * k + 1) * ir2, twoir = 2 * ir;
+  const int qq = num / twoir;
+  const float g3 = (float)(num - qq * twoir) / (float)twoir + dt * (float)ir2;
+  if (fabsf(g3 - rintf(g3)) < 1e-6f + kIncRel * fabsf(dt) * (float)ir2) return 0;
+  int ip = f * ir2 + qq + (int)floorf(g3);
+  ip %= 4 * ir2;
+  if (ip < 0) ip += 4 * ir2;
+  L.ring = north ? ir2 - 1 : 4 * N - ir2 - 1;
+  L.idx = ip;
+  return 1;
+}
+
 __device__ __forceinline__ double ring_phi(const RingTable &rt, int ring, int idx) {
   return fma((double)idx, rt.dphi[ring], rt.phi0[ring]);
 }
