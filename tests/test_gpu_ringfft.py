@@ -1,8 +1,9 @@
-"""Ring synthesis of the single-precision forms where the register-pass kernel runs
-(rings of 2^10 .. 2^13 pixels without aliasing: the belt at Nside 256 .. 2048): the
-derivative maps d_theta^j d_phi^k of Eq. 4 against the oracle's per-ring library FFT
-(Sec. II.B), over the whole sphere and over the belt alone, for band limits below,
-at and above half the belt ring length, spin 0 and spin 2.
+"""Ring synthesis of the single-precision forms where the register-pass kernels run
+(rings of 2^10 .. 2^13 pixels without aliasing: the belt at Nside 256 .. 2048; Bluestein
+lengths 2048 and 4096 on the cap rings) and the shared-memory Bluestein of length 1024
+beside them: the derivative maps d_theta^j d_phi^k of Eq. 4 against the oracle's
+per-ring library FFT (Sec. II.B), over the whole sphere and over the belt alone, for band
+limits below, at and above half the belt ring length, spin 0 and spin 2.
 
 Tolerance: 5e-5 relative RMS per map and ring. The single-precision Legendre data
 set the level: both ring-FFT kernels (register passes and shared memory) measure
@@ -109,3 +110,12 @@ def test_cap_rings_bluestein_4096_nside2048():
     nside = 2048
     rings = [700, 1025, 1536, 2039, 2047, 4095, 4 * nside - 1 - 1300]
     _rings_vs_oracle(nside, 2 * nside, 4, [r - 1 for r in rings], 0, api.MIXED_FP32, TOL)
+
+
+@pytest.mark.parametrize("spin", [0, 2])
+def test_cap_rings_bluestein_1024_nside512(spin):
+    """Cap rings with i in 257 .. 511 (Bluestein length 1024, shared-memory passes), the
+    power-of-two ring i = 256 and the last cap ring, north and south, and a belt ring."""
+    nside = 512
+    rings = [256, 257, 300, 444, 511, 1024, 4 * nside - 1 - 300]
+    _rings_vs_oracle(nside, 2 * nside, 4, [r - 1 for r in rings], spin, api.MIXED_FP32, TOL)
