@@ -64,7 +64,7 @@ def fp32_peak_tflops(dev, peaks):
 # gives null.
 TRAFFIC_NSIDE512 = {
     ("fft_total", None): (858.2e6, ['ringfft.cu', 'fft.cuh', 'regfft.cuh', 'common.cuh'], "331f595a91f2531e"),
-    ("gather_total", None): (670.6e6, ['gather.cu', 'geometry.cuh'], "404b9cada9d1bcb7"),
+    ("gather_total", None): (627.4e6, ['gather.cu', 'geometry.cuh'], "bcdaeea7440cc516"),
     ("legendre_QU", "bf16x3"): (3.1023e9, ['legendre_umma.cu', 'legendre.cuh', 'common.cuh'], "1b171c4fa0306540"),
     ("legendre_T", "bf16x3"): (2.4593e9, ['legendre_umma.cu', 'legendre.cuh', 'common.cuh'], "1b171c4fa0306540"),
 }
