@@ -73,3 +73,45 @@ def test_batch_autotune_keeps_results():
     finally:
         torch.cuda.synchronize()
         b.close()
+
+
+def test_batch_uneven_nside256_to_2048_vs_oracle():
+    """Uneven realisations at the sizes of a production mix (Nside 256 to 2048, lmax from
+    2 to 2 Nside, order 4, the default BF16x3 form): the persistent launch and its graph
+    replay against the per-realisation loop on every map, and realisations of each size
+    against the FP64 oracle on sampled pixels (the first and last ring, the cap and belt
+    edges and the equator, random pixels), to the mixed forms' 1e-4."""
+    import os
+    import skygen
+    import oracle.healpix as hp
+    nsides = [2048, 256, 512, 1024, 256, 512, 256]
+    lmaxs = [4096, 512, 1024, 2048, 512, 768, 600]
+    order = 4
+    skies = [skygen.make_sky(ns, lm, True, 600 + i, 700 + i, 800 + i, 100.0, 800.0, b_scale=0.3)
+             for i, (ns, lm) in enumerate(zip(nsides, lmaxs))]
+    dev = [to_dev(s) for s in skies]
+    b = api.Batch(nsides, lmaxs, order, pol=True, precision=api.MIXED_BF16x3)
+    try:
+        res = {}
+        for mode in ("loop", "graph", "graph"):
+            outs = b.outputs()
+            b.lens(dev, outs, mode)
+            torch.cuda.synchronize()
+            res.setdefault(mode, []).append([o.cpu().numpy() for o in outs])
+            del outs
+    finally:
+        torch.cuda.synchronize()
+        b.close()
+    for run in res["graph"]:
+        for i in range(len(nsides)):
+            for f in range(3):
+                assert rel_rms(run[i][f], res["loop"][0][i][f]) < 1e-6, (i, f)
+    for i in (0, 1, 2, 3):
+        ns = nsides[i]
+        pix = hp.check_pixels(ns, n_random=16, per_ring=8, cap_rings=1)
+        sk = skies[i]
+        ref = OL.lens_at_pixels(ns, lmaxs[i], order, pix, sk["T"], sk["E"], sk["B"], sk["phi"],
+                                nthreads=os.cpu_count())
+        for f, name in enumerate("TQU"):
+            got = res["graph"][1][i][f][pix]
+            assert rel_rms(got, ref[name]) < 1e-4, (ns, name, rel_rms(got, ref[name]))
