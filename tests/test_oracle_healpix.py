@@ -84,3 +84,34 @@ def test_containing_pixel_is_close(nside):
     d = np.arccos(np.clip(cosd, -1, 1))
     # max pixel radius is below ~ 1.4 x the mean cell size
     assert d.max() < 1.4 * np.sqrt(4 * np.pi / hp.npix(nside))
+
+
+@pytest.mark.parametrize("nside", [1, 2, 8, 64, 1024])
+def test_pixel_centres_at_half_integer_cell_coordinates(nside):
+    """Every pixel centre sits at half-integers of the cell coordinates that bound the
+    cells (Gorski et al. 2005): in the belt x1 = N(t + 1/2) - (3/4) N z = idx + (sh + i - N)/2
+    and x2 = N(t + 1/2) + (3/4) N z = idx + (3N + sh - i)/2 (ring i, half-pixel shift sh);
+    in a cap, with i the ring's distance from its pole, N sqrt(3 (1 - |z|)) = i and
+    frac(t) = (k + 1/2)/i with k = idx mod i. The float gather's pixel lookup works in
+    increments from these exact values."""
+    n = nside
+    tab = hp.ring_table(n)
+    p = np.arange(hp.npix(n))
+    ring, idx = hp.pix2ring(n, p)
+    th, ph = hp.pix2ang(n, p)
+    z = np.cos(th)
+    t = ph * (2.0 / np.pi)
+    sh = (tab["phi0"][ring - 1] != 0).astype(np.int64)
+    belt = (ring >= n) & (ring <= 3 * n)
+    x1 = n * (0.5 + t) - 0.75 * n * z
+    x2 = n * (0.5 + t) + 0.75 * n * z
+    tol = 1e-9 * 4 * n
+    assert np.all(((sh + ring - n) % 2 == 1)[belt])
+    assert np.allclose(x1[belt], (idx + (sh + ring - n) / 2.0)[belt], rtol=0, atol=tol)
+    assert np.allclose(x2[belt], (idx + (3 * n + sh - ring) / 2.0)[belt], rtol=0, atol=tol)
+    cap = ~belt
+    i = np.where(ring < n, ring, 4 * n - ring)[cap]
+    omz = tab["omz"][ring - 1][cap]
+    assert np.allclose(n * np.sqrt(3.0 * omz), i, rtol=0, atol=tol)
+    k = idx[cap] % i
+    assert np.allclose(t[cap] - np.floor(t[cap]), (k + 0.5) / i, rtol=0, atol=1e-12)
